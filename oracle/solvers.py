@@ -1,0 +1,171 @@
+"""Proximal solvers for the constrained analysis problem (oracle, FP64).  Test infrastructure only.
+
+Problem (Sec. 3.1, analysis form; Sec. 5):
+    min_x ||Psi^dagger x||_1  s.t.  ||y - Phi x||_2 <= eps,  x >= 0.
+
+* ``power_iteration``: the power method for the largest eigenvalue of
+  Phi^dagger Phi, used to normalise the operator (Sec. 6.3.1).
+* ``primal_dual``: Algorithm 7 (Appendix A.4) with L = [Psi^dagger; Phi],
+  f(a, b) = gamma ||a||_1 + iota_{B(y, eps)}(b) and g = iota_{R_+^N}.  By the
+  Moreau decomposition prox_{sigma f*}(z) = z - sigma prox_{f/sigma}(z/sigma)
+  (Appendix A.4), the dual step splits into (reading R8):
+      z1 <- clip(z1 + sigma1 Psi^dagger xhat, [-gamma, gamma])
+      t  <- z2 + sigma2 Phi xhat
+      z2 <- t - sigma2 P_B(y,eps)(t / sigma2)
+      x+ <- max(x - tau (Psi z1 + Re Phi^dagger z2), 0)
+      xhat <- x+ + theta (x+ - x)
+* ``admm``: Dual Forward-Backward ADMM, Algorithm 1 (Sec. 5), with the DualFB
+  inner loop reading its argument z (reading R9) and the dual d warm-started
+  across outer iterations.
+
+Convergence (Sec. 6.6): relative iterate change ||x+ - x|| / ||x+|| < delta.
+Every norm is FP64.
+"""
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import prox
+
+
+def splitmix64(n, seed):
+    """Raw 64-bit outputs of SplitMix64 (Steele, Lea & Flood 2014) at counters seed + k*golden, k = 1..n."""
+    mask = (1 << 64) - 1
+    out = []
+    for i in range(n):
+        z = (seed + (i + 1) * 0x9E3779B97F4A7C15) & mask
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def splitmix64_uniform(n, seed):
+    """n uniforms in [0, 1): the top 53 bits of ``splitmix64`` times 2^-53.
+
+    This is the counter-based generator both sides implement for the power method's start vector.
+    """
+    return np.array([(z >> 11) * (1.0 / (1 << 53)) for z in splitmix64(n, seed)], dtype=np.float64)
+
+
+def power_iteration(phi, phi_adj, shape, seed=0, max_iter=200, tol=1e-8, b0=None):
+    """Largest eigenvalue of Phi^dagger Phi (= ||Phi||^2) by the power method (Sec. 6.3.1).
+
+    Start vector: 0.5 + U[0,1) from ``splitmix64_uniform`` unless ``b0`` is given.
+    Returns (op_norm_sq, iterations).
+    """
+    n = int(np.prod(shape))
+    b = (0.5 + splitmix64_uniform(n, seed)).reshape(shape) if b0 is None else np.array(b0, dtype=np.float64)
+    b = b / np.sqrt(np.sum(b * b))
+    prev = 0.0
+    val = 0.0
+    it = 0
+    for it in range(1, max_iter + 1):
+        c = phi_adj(phi(b))
+        val = float(np.sqrt(np.sum(np.abs(c) ** 2)))
+        b = c / val
+        if it > 1 and abs(val - prev) <= tol * val:
+            break
+        prev = val
+    return val, it
+
+
+@dataclass
+class PDParams:
+    """Primal-dual parameters (reading R8): sigma1 = 1, sigma2 = 1/||Phi||^2, tau = 0.49, theta = 1."""
+    gamma: float
+    op_norm_sq: float
+    eps: float
+    max_iter: int = 200
+    rel_tol: float = 0.0
+    tau: float = 0.49
+    sigma1: float = 1.0
+    sigma2: float = 0.0  # <= 0 means 1 / op_norm_sq
+    theta: float = 1.0
+
+
+def primal_dual(y, phi, phi_adj, psi, psi_adj, p, x0=None):
+    """Algorithm 7 instantiated for the constrained analysis problem (reading R8).
+
+    Returns (x, info) with info = {'iters', 'rel_change', 'residual_norm', 'history'}.
+    """
+    sigma2 = p.sigma2 if p.sigma2 > 0 else 1.0 / p.op_norm_sq
+    x = np.zeros_like(np.real(phi_adj(y))) if x0 is None else np.array(x0, dtype=np.float64)
+    xhat = x.copy()
+    z1 = np.zeros_like(psi_adj(x))
+    z2 = np.zeros_like(np.asarray(y, dtype=np.complex128))
+    rel = np.inf
+    hist = []
+    it = 0
+    for it in range(1, p.max_iter + 1):
+        z1 = prox.clip_linf(z1 + p.sigma1 * psi_adj(xhat), p.gamma)
+        t = z2 + sigma2 * phi(xhat)
+        proj, _ = prox.proj_l2ball(t / sigma2, y, p.eps)
+        z2 = t - sigma2 * proj
+        x_new = prox.proj_positive(x - p.tau * (psi(z1) + np.real(phi_adj(z2))))
+        xhat = x_new + p.theta * (x_new - x)
+        dn = float(np.sqrt(np.sum((x_new - x) ** 2)))
+        xn = float(np.sqrt(np.sum(x_new ** 2)))
+        rel = dn / xn if xn > 0 else (0.0 if dn == 0 else np.inf)
+        hist.append(rel)
+        x = x_new
+        if p.rel_tol > 0 and rel < p.rel_tol:
+            break
+    res = float(np.sqrt(np.sum(np.abs(y - phi(x)) ** 2)))
+    return x, {"iters": it, "rel_change": rel, "residual_norm": res, "history": hist}
+
+
+@dataclass
+class ADMMParams:
+    """Dual Forward-Backward ADMM parameters (Algorithm 1; reading R9)."""
+    gamma: float
+    eps: float
+    rho: float
+    varrho: float = 1.0
+    eta: float = 1.0
+    dualfb_iters: int = 1
+    max_iter: int = 200
+    rel_tol: float = 0.0
+
+
+def admm(y, phi, phi_adj, psi, psi_adj, p, x0=None):
+    """Algorithm 1: v = Phi x; r = P_B(v + s); s += varrho (v - r); xt = x - rho Phi^dagger(v - r + s);
+    x = DualFB(xt, gamma) with DualFB: zbar = P_C(z); repeat { d = (1/eta)(I - soft_gamma)(eta d + Psi^dagger zbar);
+    zbar = P_C(z - Psi d) }."""
+    y = np.asarray(y, dtype=np.complex128)
+    x = np.zeros_like(np.real(phi_adj(y))) if x0 is None else np.array(x0, dtype=np.float64)
+    s = np.zeros_like(y)
+    d = np.zeros_like(psi_adj(x))
+    rel = np.inf
+    hist = []
+    it = 0
+    for it in range(1, p.max_iter + 1):
+        v = phi(x)
+        r, _ = prox.proj_l2ball(v + s, y, p.eps)
+        s = s + p.varrho * (v - r)
+        xt = x - p.rho * np.real(phi_adj(v - r + s))
+        zbar = prox.proj_positive(xt)
+        for _ in range(p.dualfb_iters):
+            d = (1.0 / p.eta) * prox.clip_linf(p.eta * d + psi_adj(zbar), p.gamma)
+            zbar = prox.proj_positive(xt - psi(d))
+        dn = float(np.sqrt(np.sum((zbar - x) ** 2)))
+        xn = float(np.sqrt(np.sum(zbar ** 2)))
+        rel = dn / xn if xn > 0 else (0.0 if dn == 0 else np.inf)
+        hist.append(rel)
+        x = zbar
+        if p.rel_tol > 0 and rel < p.rel_tol:
+            break
+    res = float(np.sqrt(np.sum(np.abs(y - phi(x)) ** 2)))
+    return x, {"iters": it, "rel_change": rel, "residual_norm": res, "history": hist}
+
+
+def default_gamma(y, phi_adj, psi_adj, op_norm_sq, factor=1e-3):
+    """gamma = factor * max|Psi^dagger Phi^dagger y| / ||Phi||^2 (proposed; gamma does not move the
+    constrained minimiser, only the speed of convergence)."""
+    return factor * float(np.max(np.abs(psi_adj(np.real(phi_adj(y)))))) / op_norm_sq
+
+
+def epsilon_from_sigma(sigma, M):
+    """eps = sigma sqrt(M + 2 sqrt(M)): mean plus two standard deviations of ||W n||^2 / sigma^2."""
+    return float(sigma * np.sqrt(M + 2.0 * np.sqrt(M)))

@@ -1,0 +1,134 @@
+"""Pins for the oracle's solvers: closed-form special case, an independent constrained solver,
+the dense operator norm, and the counter-based generator."""
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+import synth
+from oracle import measurement as me, solvers as so, wavelets as wv
+
+
+def test_splitmix64_published_sequence():
+    # first outputs of SplitMix64 from state 0 (reference sequence of the published generator)
+    assert so.splitmix64(4, 0) == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F,
+                                   0xF88BB8A8724C81EC]
+    u = so.splitmix64_uniform(1000, 5)
+    assert np.all((u >= 0) & (u < 1)) and abs(u.mean() - 0.5) < 0.05
+
+
+def _closed_form(y, eps):
+    """min ||x||_1 s.t. ||y - x|| <= eps, x >= 0  ->  x = max(y - lam, 0), lam by bisection."""
+    lo, hi = 0.0, float(np.abs(y).max())
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.linalg.norm(y - np.maximum(y - mid, 0)) < eps:
+            lo = mid
+        else:
+            hi = mid
+    return np.maximum(y - lo, 0)
+
+
+def test_identity_operator_special_case_pd_and_admm():
+    y = synth.normal(200, seed=1) + 0.5
+    eps = 0.5 * np.linalg.norm(np.maximum(y, 0))
+    xs = _closed_form(y, eps)
+    ident = lambda x: x.astype(complex)
+    ident_t = lambda z: np.real(z)
+    dirac = lambda a: a[0]
+    dirac_t = lambda x: x[None]
+    for gamma in (0.05, 1.0):
+        x, _ = so.primal_dual(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                              so.PDParams(gamma=gamma, op_norm_sq=1.0, eps=eps, max_iter=20000, rel_tol=1e-14))
+        assert np.max(np.abs(x - xs)) < 1e-8
+        x, _ = so.admm(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                       so.ADMMParams(gamma=gamma, eps=eps, rho=1.0, max_iter=20000, rel_tol=1e-14))
+        assert np.max(np.abs(x - xs)) < 1e-8
+
+
+def _tiny_problem():
+    n, M = 8, 40
+    x_true = np.zeros((n, n))
+    x_true[3, 4], x_true[5, 2], x_true[2, 2] = 1.0, 0.5, 0.3
+    uvw = synth.uv_coverage(M, seed=1, weights="uniform")
+    geo = me.Geometry(uvw, n, 2, 4, 4096)
+    orders, L = (0, 1, 2), 2
+    ops = (lambda x: me.phi(np.reshape(x, (n, n)), geo), lambda y: me.phi_adjoint(y, geo),
+           lambda a: wv.psi(a, orders, L), lambda x: wv.psi_adjoint(x, orders, L))
+    y0 = ops[0](x_true)
+    sigma = 0.05 * np.linalg.norm(y0) / np.sqrt(M)
+    y = y0 + sigma * synth.complex_normal(M, seed=2)
+    return n, M, ops, y, so.epsilon_from_sigma(sigma, M)
+
+
+def test_power_iteration_matches_dense_norm():
+    n, M, (phi, phit, _, _), _, _ = _tiny_problem()
+    A = np.stack([phi(e.reshape(n, n)) for e in np.eye(n * n)], 1)
+    Ar = np.vstack([A.real, A.imag])       # Phi acts on real images
+    val, _ = so.power_iteration(phi, phit, (n, n), seed=0)
+    assert val == pytest.approx(np.linalg.norm(Ar, 2) ** 2, rel=1e-6)
+
+
+def test_primal_dual_matches_independent_constrained_solver():
+    """SLSQP on the LP-with-one-quadratic-constraint form of the analysis problem."""
+    n, M, (phi, phit, psi, psit), y, eps = _tiny_problem()
+    N = n * n
+    A = np.stack([phi(e.reshape(n, n)) for e in np.eye(N)], 1)
+    P = np.stack([psit(e.reshape(n, n)).ravel() for e in np.eye(N)], 1)
+    Ar, yr = np.vstack([A.real, A.imag]), np.concatenate([y.real, y.imag])
+    K = P.shape[0]
+    G = np.block([[P, -np.eye(K)], [-P, -np.eye(K)]])        # |Psi^dagger x| <= t
+
+    def qc(z):
+        r = Ar @ z[:N] - yr
+        return np.array([eps ** 2 - r @ r])
+
+    def qcj(z):
+        g = np.zeros((1, N + K))
+        g[0, :N] = -2 * Ar.T @ (Ar @ z[:N] - yr)
+        return g
+
+    res = minimize(lambda z: z[N:].sum(), np.zeros(N + K), jac=lambda z: np.r_[np.zeros(N), np.ones(K)],
+                   method="SLSQP", bounds=[(0, None)] * (N + K),
+                   constraints=[{"type": "ineq", "fun": lambda z: -(G @ z), "jac": lambda z: -G},
+                                {"type": "ineq", "fun": qc, "jac": qcj}],
+                   options={"maxiter": 2000, "ftol": 1e-14})
+    opn, _ = so.power_iteration(phi, phit, (n, n))
+    gamma = so.default_gamma(y, phit, psit, opn)
+    x, info = so.primal_dual(y, phi, phit, psi, psit,
+                             so.PDParams(gamma=gamma, op_norm_sq=opn, eps=eps, max_iter=30000, rel_tol=1e-13))
+    assert np.max(np.abs(x.ravel() - res.x[:N])) < 1e-6
+    assert np.abs(psit(x)).sum() == pytest.approx(res.fun, rel=1e-7)
+    assert info["residual_norm"] <= eps * (1 + 1e-6)
+    assert np.all(x >= 0)
+
+
+def test_pd_and_admm_reach_the_same_constrained_solution():
+    n, M = 16, 400
+    x_true = synth.sky(n, 3, 1, seed=3)
+    uvw = synth.uv_coverage(M, seed=4, weights="uniform")
+    geo = me.Geometry(uvw, n, 2, 4, 4096)
+    orders, L = (0, 1, 2), 2
+    phi = lambda x: me.phi(x, geo)
+    phit = lambda y: me.phi_adjoint(y, geo)
+    psi = lambda a: wv.psi(a, orders, L)
+    psit = lambda x: wv.psi_adjoint(x, orders, L)
+    y0 = phi(x_true)
+    sigma = 10 ** (-30 / 20) * np.linalg.norm(y0) / np.sqrt(M)
+    y = y0 + sigma * synth.complex_normal(M, seed=5)
+    eps = so.epsilon_from_sigma(sigma, M)
+    opn, _ = so.power_iteration(phi, phit, (n, n))
+    gamma = so.default_gamma(y, phit, psit, opn, factor=1e-2)
+    xp, ip = so.primal_dual(y, phi, phit, psi, psit,
+                            so.PDParams(gamma=gamma, op_norm_sq=opn, eps=eps, max_iter=20000, rel_tol=1e-10))
+    # Algorithm 1's DualFB is an inexact inner prox; with enough inner iterations its fixed point is the
+    # constrained minimiser that the primal-dual iteration reaches.
+    xa, ia = so.admm(y, phi, phit, psi, psit,
+                     so.ADMMParams(gamma=gamma, eps=eps, rho=1.0 / opn, max_iter=20000, rel_tol=1e-10,
+                                   dualfb_iters=20))
+    assert np.linalg.norm(xp - xa) / np.linalg.norm(xp) < 5e-4
+    for info, x in ((ip, xp), (ia, xa)):
+        assert info["residual_norm"] <= eps * (1 + 1e-3)
+        assert np.all(x >= 0)
+    # the primal-dual objective is the smaller one (both are feasible)
+    assert np.abs(psit(xp)).sum() <= np.abs(psit(xa)).sum() * (1 + 1e-9)
