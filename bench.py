@@ -1,0 +1,338 @@
+"""Benchmark: primal-dual iterations of the sparse imaging hot path on one GB300 (or N replicas).
+
+Workload (FP32 bulk, FP64 norms): 1024^2 sky (50 points + 20 blobs), 2048^2 grid,
+Kaiser-Bessel J = 4 with a 2^12-per-cell table, M = 1e7 visibilities (Gaussian core
+plus 20 % uniform-disk outliers, weights U[0.5, 1], 30 dB noise), SARA Dirac +
+db1..db8 over 4 levels.  One step = one primal-dual iteration: Psi^dagger with the
+l1-dual update, Phi (pad/correct, FFT, degrid with the l2-ball dual update), the
+FP64 ball scalar, Phi^dagger (grid, inverse FFT), Psi, and the primal update with
+the FP64 convergence norms.  Metric: visibilities per second through Phi and
+Phi^dagger (M per iteration) and ms per iteration.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbri|reference]
+Under torchrun each rank solves its own problem (seed + rank): replicas, weak scaling.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gbri", choices=["gbri", "reference"])
+    ap.add_argument("--config", default="large", choices=["large", "small"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(cfg_name, rank=0):
+    cfg = dict(synth.CONFIGS[cfg_name])
+    seed = cfg["seed"] + rank
+    x_true = synth.sky(cfg["n_side"], cfg["n_points"], cfg["n_blobs"], seed=seed)
+    uvw = synth.uv_coverage(cfg["M"], seed=seed + 1, outlier_frac=cfg["outlier_frac"], weights=cfg["weights"])
+    return cfg, seed, x_true, uvw
+
+
+def describe(cfg):
+    return ("%d^2 sky, %d^2 grid, J=%d, S=%d, M=%.0e, SARA %s over %d levels, primal-dual iteration"
+            % (cfg["n_side"], cfg["n_side"] * cfg["oversample"], cfg["J"], cfg["S"], cfg["M"],
+               "Dirac+db1-%d" % max(cfg["db_orders"]), cfg["levels"]))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(cfg, x_true, uvw, sample, iters=2):
+    """The oracle as it stands: primal-dual iterations on a bounded sample of the visibilities
+    (full image and dictionary), on this host's cores."""
+    from oracle import measurement as me, solvers as so, wavelets as wv
+    idx = np.random.default_rng(0).choice(len(uvw), min(sample, len(uvw)), replace=False)
+    sub = uvw[np.sort(idx)]
+    n, orders, L = cfg["n_side"], cfg["db_orders"], cfg["levels"]
+    geo = me.Geometry(sub, n, cfg["oversample"], cfg["J"], cfg["S"])
+    ops = (lambda v: me.phi(v, geo), lambda v: me.phi_adjoint(v, geo),
+           lambda a: wv.psi(a, orders, L), lambda v: wv.psi_adjoint(v, orders, L))
+    y = ops[0](x_true)
+    wv.psi_adjoint(x_true, orders, L)  # build the cached analysis matrices outside the timing
+    p = so.PDParams(gamma=1e-3, op_norm_sq=float(len(sub)), eps=1e-3 * np.linalg.norm(y), max_iter=iters)
+    t0 = time.perf_counter()
+    so.primal_dual(y, *ops, p)
+    dt = (time.perf_counter() - t0) / iters
+    cores = len(os.sched_getaffinity(0))
+    return {"value": len(sub) / dt, "unit": "vis/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of the M visibilities (uniform subsample), full %d^2 image and dictionary, "
+                      "%d primal-dual iterations, FP64; %.2f s per iteration" % (len(sub), n, iters, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cfg, seed, x_true, uvw = workload(args.config, 0)
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    # each step: one oracle primal-dual iteration on the bounded sample; keep the run to minutes
+    steps = min(steps, 3)
+    warm = min(warm, 1)
+    from oracle import measurement as me, solvers as so, wavelets as wv
+    idx = np.random.default_rng(0).choice(len(uvw), min(args.cpu_sample, len(uvw)), replace=False)
+    sub = uvw[np.sort(idx)]
+    n, orders, L = cfg["n_side"], cfg["db_orders"], cfg["levels"]
+    geo = me.Geometry(sub, n, cfg["oversample"], cfg["J"], cfg["S"])
+    ops = (lambda v: me.phi(v, geo), lambda v: me.phi_adjoint(v, geo),
+           lambda a: wv.psi(a, orders, L), lambda v: wv.psi_adjoint(v, orders, L))
+    y = ops[0](x_true)
+    p = so.PDParams(gamma=1e-3, op_norm_sq=float(len(sub)), eps=1e-3 * np.linalg.norm(y), max_iter=1)
+    for _ in range(warm):
+        so.primal_dual(y, *ops, p)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        so.primal_dual(y, *ops, p)
+    dt = (time.perf_counter() - t0) / steps
+    v = len(sub) / dt
+    cores = len(os.sched_getaffinity(0))
+    line = {"metric": "Phi+Phi-dagger visibilities/s per primal-dual iteration", "value": v, "unit": "vis/s",
+            "n_gpus": args.gpus, "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": describe(cfg) + " (oracle on a %d-visibility sample)" % len(sub)},
+            "cpu_baseline": {"value": v, "unit": "vis/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d visibilities of the workload, one oracle primal-dual iteration per step"
+                                       % len(sub)},
+            "e2e": {"value": v, "unit": "vis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gbri(args):
+    import torch
+    import paper_1903_04502_gb300 as g
+    from paper_1903_04502_gb300 import _lib
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cfg, seed, x_true, uvw = workload(args.config, rank)
+    n, M = cfg["n_side"], cfg["M"]
+    stream = torch.cuda.current_stream()
+
+    t_plan = time.perf_counter()
+    plan = g.Plan(torch.from_numpy(uvw).to(dev), n, oversample=cfg["oversample"], J=cfg["J"], S=cfg["S"])
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t_plan
+    wav = g.Wavelet(n, cfg["levels"], cfg["db_orders"])
+    xt = torch.from_numpy(x_true.astype(np.float32)).to(dev)
+    y0 = g.phi(plan, xt)
+    sigma = 10 ** (-cfg["snr_db"] / 20) * float(torch.linalg.vector_norm(y0.to(torch.complex128))) / np.sqrt(M)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed + 3)
+    noise = torch.randn(M, dtype=torch.complex64, device=dev, generator=gen)
+    y = y0 + sigma * noise
+    eps = sigma * np.sqrt(M + 2 * np.sqrt(M))
+    opn, _ = g.op_norm(plan, 100, 1e-6, seed=seed)
+    solver = g.Solver(plan, wav, y, eps=eps, op_norm_sq=opn)
+    gamma = solver.report()["gamma"]
+
+    # warm-up
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+    # timed region: K iterations, kernels timed with events on the launching stream
+    g.profile_enable(args.steps + 8)
+    clocks = Clocks(dev.index if dev.index is not None else 0)
+    if rank == 0:
+        clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    n0 = g.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = g.launch_count() - n0
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.stop() if rank == 0 else None
+    kern = {}
+    for k, name in enumerate(_lib.K_NAMES):
+        tot, cnt = g.profile_read(k)
+        if cnt:
+            kern[name] = {"ms_total": tot, "launches": cnt, "ms_avg": tot / cnt}
+    g.profile_enable(0)
+    ms_per = ms / args.steps
+    value = ws * M * args.steps / (ms / 1e3)
+
+    # roofline of the dominant visibility kernel (algorithmic bytes per launch)
+    K = plan.K
+    alg = {"degrid": 32 * M + 8 * K * K,  # meta 8 + u 8 + y 8 read, u 8 written; grid read once
+           "grid": 16 * M + 8 * K * K}    # meta 8 + u 8 read; grid written once
+    dom = max(("degrid", "grid"), key=lambda k: kern.get(k, {}).get("ms_total", 0.0))
+    peak, peak_kind = measured_peak()
+    achieved = alg[dom] / (kern[dom]["ms_avg"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": dom, "algorithmic_bytes": alg[dom],
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+            else "fallback 6.8 TB/s"}
+    other = "grid" if dom == "degrid" else "degrid"
+    if other in kern:
+        a2 = alg[other] / (kern[other]["ms_avg"] * 1e-3) / 1e9
+        roof["other"] = {"kernel": other, "achieved": a2, "frac": a2 / peak}
+
+    # end to end through the public API with host buffers: pinned y in, full solve, x out
+    y_host = y.cpu().pin_memory()
+    x_host = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    iters_e2e = cfg["iters"]
+    y_dev = torch.empty_like(y)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, args.e2e_steps)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        y_dev.copy_(y_host, non_blocking=True)
+        x_dev, rep = g.solve(plan, wav, y_dev, eps=eps, op_norm_sq=opn, gamma=gamma, max_iter=iters_e2e)
+        x_host.copy_(x_dev, non_blocking=True)
+        torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": ws * M * iters_e2e / dt, "unit": "vis/s", "h2d_bytes_per_step": M * 8,
+           "d2h_bytes_per_step": n * n * 4, "iterations_per_step": iters_e2e, "ms_per_step": dt * 1e3}
+
+    # operator-level throughput (context): Phi and Phi^dagger alone, caller order, events
+    xd = xt
+    yd = torch.empty(M, dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        g.phi(plan, xd, yd)
+        g.phi_adjoint(plan, yd, xd.clone())
+    reps = 20
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    xo = torch.empty_like(xd)
+    a.record(stream)
+    for _ in range(reps):
+        g.phi(plan, xd, yd, plan_order=True)
+    b.record(stream)
+    for _ in range(reps):
+        g.phi_adjoint(plan, yd, xo, plan_order=True)
+    c.record(stream)
+    torch.cuda.synchronize()
+    ops = {"phi_vis_per_s": M * reps / (a.elapsed_time(b) * 1e-3),
+           "phi_adjoint_vis_per_s": M * reps / (b.elapsed_time(c) * 1e-3)}
+
+    if ws > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(cfg, x_true, uvw, args.cpu_sample)
+    ws_bytes = plan.device_bytes + 2 * M * 8 + cfg["n_side"] ** 2 * 4 * (len(cfg["db_orders"]) + 8)
+    line = {
+        "metric": "Phi+Phi-dagger visibilities/s per primal-dual iteration", "value": value, "unit": "vis/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": describe(cfg), "n_side": n, "M": M, "J": cfg["J"], "grid": K,
+                   "bases": len(cfg["db_orders"]), "levels": cfg["levels"], "parallelism": "replicas" if ws > 1
+                   else "single", "l2": "inputs larger than L2: per-iteration working set %.2f GB > 129 MB"
+                   % (ws_bytes / 1e9), "plan_s": t_plan, "op_norm_sq": opn, "gamma": gamma},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk, "kernels": kern, "operators": ops, "impl": "gbri",
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gbri(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,227 @@
+/*
+ * gbri.h -- C ABI of the GB300-native sparse radio-interferometric imaging library.
+ *
+ * The library implements, for one GPU (sm_103a), the measurement operator of
+ * Sec. 2 / Eq. 2 of the paper (Phi = W G F Z S: Kaiser-Bessel correction S,
+ * zero padding Z, oversampled FFT F, degridding G with a pre-sampled kernel
+ * table (Sec. 8.1), noise weights W), its adjoint Phi^dagger = S^T Z^T F^H G^T W^T,
+ * the SARA wavelet dictionary Psi / Psi^dagger (Sec. 3.1, Sec. 6.4), the proximal
+ * operators of Sec. 4 (soft thresholding, l2-ball projection), the power method
+ * for ||Phi||^2 (Sec. 6.3.1) and the solvers of the constrained analysis problem
+ * min ||Psi^dagger x||_1 s.t. ||y - Phi x||_2 <= eps, x >= 0: primal-dual
+ * (Appendix A.4, Algorithm 7) and Dual Forward-Backward ADMM (Sec. 5,
+ * Algorithm 1).
+ *
+ * Conventions (every call):
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device, owned by
+ *     the caller; the library never frees them and never keeps them after the
+ *     call returns (except where a create call documents a copy).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; nothing synchronises unless the call says so.
+ *   - Precision: GBRI_F32 (float / interleaved complex64) for the bulk, with FP64
+ *     global norms.  Images are row-major [n_side][n_side] float; visibilities
+ *     are interleaved complex {re, im} float pairs.
+ *   - Return value: GBRI_OK (0) or a negative gbri_status.  On error nothing has
+ *     been enqueued unless the status is GBRI_ECUDA / GBRI_ECUFFT, in which case
+ *     the stream may hold partial work.  gbri_last_error() gives a message
+ *     (thread-local, valid until the next call on the same thread).
+ *   - Objects (plan, wavelet, solver) are not thread-safe: one object may be used
+ *     by one stream at a time.  Different objects are independent.
+ */
+#ifndef GBRI_H
+#define GBRI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define GBRI_OK 0
+#define GBRI_EINVAL (-1)      /* bad argument (null pointer, size, unsupported shape) */
+#define GBRI_ENOMEM (-2)      /* device or host allocation failed */
+#define GBRI_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
+#define GBRI_ECUFFT (-4)      /* a cuFFT call failed */
+#define GBRI_ETIMEOUT (-5)    /* a bounded device wait gave up */
+#define GBRI_ENONFINITE (-6)  /* non-finite input rejected */
+#define GBRI_ENOTCONV 1       /* warning: solver stopped at max_iter before rel_tol */
+
+#define GBRI_F32 0
+#define GBRI_F64 1
+
+/* flags for phi / phi_adjoint / solver_create */
+#define GBRI_PLAN_ORDER 1u   /* visibility buffers are in the plan's sorted order (no permutation) */
+
+typedef struct gbri_plan gbri_plan;
+typedef struct gbri_wavelet gbri_wavelet;
+typedef struct gbri_solver gbri_solver;
+
+/* ---- measurement operator plan (Sec. 2, Eq. 2; Sec. 8.1) ------------------ */
+typedef struct {
+  int32_t n_side;            /* image side N_side (image is N_side x N_side); even, >= 16 */
+  int32_t oversample;        /* grid oversampling alpha per axis; K = alpha * N_side (only 2 is tested) */
+  int32_t J;                 /* kernel support in grid cells: 4 or 6 */
+  int32_t samples_per_unit;  /* table samples per grid cell S: power of two, 16 <= S <= 4096 */
+  double kb_beta;            /* Kaiser-Bessel shape; <= 0 selects 2.34 * J */
+  int64_t M;                 /* number of visibilities, >= 0 */
+  int32_t precision;         /* GBRI_F32 */
+  int32_t reserved;          /* must be 0 */
+} gbri_plan_desc;
+
+/* Build a plan: quantises every (u, v) once in FP64 to the fixed-point grid
+ * coordinate k~ = round_half_away(u * K * S / (2 pi)) (Sec. 8.1 zeroth-order
+ * pre-sampling), sorts the visibilities by grid tile and cell, packs per-visibility
+ * metadata, builds the kernel table and the correction 1/ghat, and creates the
+ * cuFFT plan.  d_uvw_weight: [M][4] float rows {u, v, w, weight}, u and v in
+ * radians per pixel, normally |u|, |v| <= pi; values outside wrap around the
+ * grid, as the DFT is 2 pi periodic (w is ignored: coplanar array).  The plan
+ * copies what it needs; d_uvw_weight may be freed after the call returns.
+ * Synchronises `stream`.  Errors: EINVAL (shape; |u| or |v| > 16 pi), ENOMEM,
+ * ENONFINITE (non-finite u, v or weight), ECUDA, ECUFFT. */
+int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* desc, const float* d_uvw_weight,
+                         void* stream);
+int32_t gbri_plan_destroy(gbri_plan* plan);
+
+/* Plan facts: K, M, number of work chunks, device bytes held. Any pointer may be NULL. */
+int32_t gbri_plan_info(const gbri_plan* plan, int64_t* K, int64_t* M, int64_t* n_chunks,
+                       int64_t* device_bytes);
+
+/* Copy the plan's permutation (plan position -> caller's visibility index) to d_perm [M] int32. */
+int32_t gbri_plan_permutation(const gbri_plan* plan, int32_t* d_perm, void* stream);
+
+/* Reorder a complex visibility vector [M] between the caller's order and plan order.
+ * to_plan = 1: d_out[pos] = d_in[perm[pos]]; to_plan = 0: d_out[perm[pos]] = d_in[pos].
+ * d_in and d_out must not overlap. */
+int32_t gbri_vis_reorder(const gbri_plan* plan, const float* d_in, float* d_out, int32_t to_plan,
+                         void* stream);
+
+/* y = Phi x = W G F Z S x (Sec. 2, Eq. 2).  d_x: [n_side][n_side] float image.
+ * d_y: [M] complex, written (caller's order unless flags has GBRI_PLAN_ORDER). */
+int32_t gbri_phi(gbri_plan* plan, const float* d_x, float* d_y, uint32_t flags, void* stream);
+
+/* x = Phi^dagger y = Re(S^T Z^T F^H G^T W^T y) (Sec. 2; real part because the sky
+ * is real).  d_y: [M] complex (caller's order unless GBRI_PLAN_ORDER); d_x:
+ * [n_side][n_side] float, overwritten. */
+int32_t gbri_phi_adjoint(gbri_plan* plan, const float* d_y, float* d_x, uint32_t flags, void* stream);
+
+/* ||Phi||^2 by the power method on Phi^dagger Phi (Sec. 6.3.1), FP64 norms.
+ * Start vector 0.5 + U[0,1) with U from SplitMix64 at counters seed + k * 0x9E3779B97F4A7C15
+ * (k = 1..N, top 53 bits).  Stops when the relative change of the estimate is
+ * <= tol or after max_iter iterations.  Synchronises `stream` each iteration.
+ * Writes the estimate to *op_norm_sq and the iteration count to *iters (host,
+ * iters may be NULL). */
+int32_t gbri_op_norm(gbri_plan* plan, int32_t max_iter, double tol, uint64_t seed, double* op_norm_sq,
+                     int32_t* iters, void* stream);
+
+/* ---- SARA wavelet dictionary (Sec. 3.1, Sec. 6.4, Sec. 7.5) --------------- */
+/* db_orders[n_w] (host): 0 = Dirac basis, N in 1..16 = Daubechies dbN (2N taps,
+ * minimum phase, derived in the library by spectral factorisation).  Periodic
+ * boundaries, rows then columns per level, Mallat layout, `levels` levels; the
+ * stack is scaled by 1/sqrt(n_w) so that Psi Psi^dagger = I.  n_side must be
+ * divisible by 2^levels and n_side >> levels >= 2. */
+int32_t gbri_wavelet_create(gbri_wavelet** out, int32_t n_side, int32_t levels, const int32_t* db_orders,
+                            int32_t n_w, int32_t precision);
+int32_t gbri_wavelet_destroy(gbri_wavelet* wav);
+
+/* x = Psi alpha = sum_b IDWT_b(alpha_b) / sqrt(n_w).  d_alpha: [n_w][n_side][n_side]; d_x: image. */
+int32_t gbri_psi(gbri_wavelet* wav, const float* d_alpha, float* d_x, void* stream);
+
+/* alpha = Psi^dagger x: alpha_b = DWT_b(x) / sqrt(n_w). */
+int32_t gbri_psi_adjoint(gbri_wavelet* wav, const float* d_x, float* d_alpha, void* stream);
+
+/* ---- proximal operators (Sec. 4) ------------------------------------------ */
+/* Soft thresholding (Sec. 4.3): out_i = 0 if |in_i| <= lambda, else in_i (|in_i| - lambda) / |in_i|.
+ * n elements of float (is_complex = 0) or complex (is_complex = 1).  d_in == d_out allowed. */
+int32_t gbri_prox_l1(const float* d_in, float* d_out, int64_t n, double lambda, int32_t is_complex,
+                     int32_t precision, void* stream);
+
+/* Projection onto the l2 ball of radius eps centred at d_center (Sec. 4.2 and the
+ * global constraint of Sec. 6.8): out = z if ||z - c|| <= eps, else c + eps (z - c) / ||z - c||.
+ * Complex vectors of length M; the norm is accumulated in FP64 (per-thread partial
+ * sums in FP32, compensated).  d_norm_out (device double, may be NULL) receives
+ * ||z - c||.  d_out may alias d_z.  Uses a temporary device buffer from the
+ * stream-ordered allocator. */
+int32_t gbri_proj_l2ball(const float* d_z, const float* d_center, float* d_out, int64_t M, double eps,
+                         double* d_norm_out, int32_t precision, void* stream);
+
+/* ---- solvers (Appendix A.4 Algorithm 7; Sec. 5 Algorithm 1) --------------- */
+#define GBRI_ALGO_PD 0
+#define GBRI_ALGO_ADMM 1
+
+typedef struct {
+  int32_t algo;          /* GBRI_ALGO_PD or GBRI_ALGO_ADMM */
+  int32_t max_iter;      /* iterations run by gbri_solve */
+  double rel_tol;        /* stop when ||x+ - x|| / ||x+|| < rel_tol (Sec. 6.6); 0 = never */
+  double eps;            /* l2-ball radius epsilon (> 0) */
+  double gamma;          /* l1 weight; <= 0 selects 1e-3 max|Psi^dagger Phi^dagger y| / ||Phi||^2 */
+  double op_norm_sq;     /* ||Phi||^2; <= 0 runs the power method (200 iterations, tol 1e-8, seed) */
+  double tau;            /* PD primal step; <= 0 selects 0.49 */
+  double sigma1;         /* PD step of the l1 dual; <= 0 selects 1 */
+  double sigma2;         /* PD step of the l2-ball dual; <= 0 selects 1 / ||Phi||^2 */
+  double theta;          /* PD extrapolation in [0, 1]; < 0 selects 1 */
+  double rho;            /* ADMM gradient step; <= 0 selects 1 / ||Phi||^2 */
+  double varrho;         /* ADMM multiplier step; <= 0 selects 1 */
+  double eta;            /* DualFB step; <= 0 selects 1 */
+  int32_t dualfb_iters;  /* DualFB inner iterations (>= 1; 0 selects 1) */
+  int32_t check_every;   /* host reads the convergence test every k iterations (0 selects 10) */
+  uint64_t seed;         /* power-method start vector seed */
+} gbri_solve_params;
+
+typedef struct {
+  int32_t iters;             /* iterations run */
+  int32_t status;            /* GBRI_OK or GBRI_ENOTCONV */
+  double rel_change;         /* last ||x+ - x|| / ||x+|| (FP64) */
+  double residual_norm;      /* ||y - Phi x|| at exit (FP64) */
+  double op_norm_sq;         /* ||Phi||^2 used */
+  double gamma;              /* gamma used */
+  double ms_total;           /* wall time of the solve on the device, ms */
+} gbri_solve_report;
+
+/* Stateful solver: keeps the iterate and dual variables resident on the device.
+ * d_y: [M] complex data (caller's order unless GBRI_PLAN_ORDER); it is copied.
+ * Synchronises `stream` (power method / gamma when requested). */
+int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav, const float* d_y,
+                           const gbri_solve_params* params, uint32_t flags, void* stream);
+int32_t gbri_solver_destroy(gbri_solver* s);
+/* Run n_iter iterations without any host synchronisation. */
+int32_t gbri_solver_step(gbri_solver* s, int32_t n_iter, void* stream);
+/* Copy the current iterate x to d_x (image). */
+int32_t gbri_solver_get_x(gbri_solver* s, float* d_x, void* stream);
+/* Fill *report (host) with the iteration count, last relative change and residual. Synchronises. */
+int32_t gbri_solver_report(gbri_solver* s, gbri_solve_report* report, void* stream);
+
+/* One-shot solve: create, iterate up to max_iter (checking rel_tol every check_every
+ * iterations on the host), write x to d_x_out, fill *report (host, may be NULL), destroy.
+ * Returns GBRI_OK, GBRI_ENOTCONV (max_iter reached with rel_tol > 0) or an error. */
+int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const float* d_y, const gbri_solve_params* params,
+                   float* d_x_out, gbri_solve_report* report, uint32_t flags, void* stream);
+
+/* ---- diagnostics ------------------------------------------------------------ */
+/* Kernel timing with CUDA events recorded around each library kernel launch on its
+ * own stream.  capacity = events per kind to keep (0 disables).  Kinds: */
+#define GBRI_K_PAD 0
+#define GBRI_K_FFT_FWD 1
+#define GBRI_K_DEGRID 2
+#define GBRI_K_GRID 3
+#define GBRI_K_FFT_INV 4
+#define GBRI_K_CROP 5
+#define GBRI_K_PSI_ADJ 6
+#define GBRI_K_PSI 7
+#define GBRI_K_UPDATE 8
+#define GBRI_K_OTHER 9
+#define GBRI_K_COUNT 10
+int32_t gbri_profile_enable(int32_t capacity);
+/* Sum of recorded durations (ms) and number of launches of one kind. Synchronises the device. */
+int32_t gbri_profile_read(int32_t kind, double* total_ms, int64_t* launches);
+/* Total number of library kernel launches since the last gbri_profile_enable / reset. */
+int64_t gbri_launch_count(void);
+void gbri_launch_count_reset(void);
+
+const char* gbri_last_error(void);
+const char* gbri_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBRI_H */

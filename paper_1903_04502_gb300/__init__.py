@@ -1,0 +1,283 @@
+"""GB300-native sparse radio-interferometric imaging (the hot path of arXiv:1903.04502).
+
+A thin Python binding over the C ABI of ``include/gbri.h``: the functions here
+only marshal torch tensors (device memory, streams) into the C calls; every
+step of the computation runs in the library's CUDA kernels.  The binding
+refuses to work when the library is missing: there is no CPU fallback.
+
+Calls (same names as the C entry points without the ``gbri_`` prefix):
+``Plan`` (gbri_plan_create), ``phi``, ``phi_adjoint``, ``op_norm``, ``Wavelet``
+(gbri_wavelet_create), ``psi``, ``psi_adjoint``, ``prox_l1``, ``proj_l2ball``,
+``Solver`` (gbri_solver_*), ``solve``.
+"""
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import (ALGO_ADMM, ALGO_PD, F32, PLAN_ORDER, GbriError, SolveParams, SolveReport,  # noqa: F401
+                   K_NAMES)
+
+__all__ = ["Plan", "Wavelet", "Solver", "phi", "phi_adjoint", "op_norm", "psi", "psi_adjoint", "prox_l1",
+           "proj_l2ball", "solve", "vis_reorder", "profile_enable", "profile_read", "launch_count",
+           "GbriError", "library"]
+
+
+def library():
+    return _lib.load()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+def _need(t, dtype, shape=None, name="tensor"):
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+
+
+class Plan:
+    """Measurement-operator plan for one problem (gbri_plan_create).
+
+    uvw: float32 CUDA tensor [M, 4] of {u, v, w, weight}.
+    """
+
+    def __init__(self, uvw, n_side, oversample=2, J=4, S=4096, beta=0.0, stream=None):
+        lib = _lib.load()
+        _need(uvw, torch.float32, name="uvw")
+        if uvw.dim() != 2 or uvw.shape[1] != 4:
+            raise ValueError("uvw must be [M, 4]")
+        self.n_side, self.J, self.S = int(n_side), int(J), int(S)
+        self.M = int(uvw.shape[0])
+        self.device = uvw.device
+        d = _lib.PlanDesc(self.n_side, int(oversample), self.J, self.S, float(beta), self.M, F32, 0)
+        h = C.c_void_p()
+        _lib.check(lib.gbri_plan_create(C.byref(h), C.byref(d), _ptr(uvw), _stream(stream)))
+        self._h = h
+        K, M, nc, nb = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _lib.check(lib.gbri_plan_info(h, C.byref(K), C.byref(M), C.byref(nc), C.byref(nb)))
+        self.K, self.n_chunks, self.device_bytes = K.value, nc.value, nb.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def permutation(self, stream=None):
+        out = torch.empty(self.M, dtype=torch.int32, device=self.device)
+        _lib.check(_lib.load().gbri_plan_permutation(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().gbri_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def phi(plan, x, y=None, plan_order=False, stream=None):
+    """y = Phi x (gbri_phi).  x: float32 [n_side, n_side]; returns complex64 [M]."""
+    _need(x, torch.float32, (plan.n_side, plan.n_side), "x")
+    if y is None:
+        y = torch.empty(plan.M, dtype=torch.complex64, device=x.device)
+    _need(y, torch.complex64, (plan.M,), "y")
+    _lib.check(_lib.load().gbri_phi(plan.handle, _ptr(x), _ptr(y), PLAN_ORDER if plan_order else 0, _stream(stream)))
+    return y
+
+
+def phi_adjoint(plan, y, x=None, plan_order=False, stream=None):
+    """x = Phi^dagger y (gbri_phi_adjoint).  y: complex64 [M]; returns float32 [n_side, n_side]."""
+    _need(y, torch.complex64, (plan.M,), "y")
+    if x is None:
+        x = torch.empty((plan.n_side, plan.n_side), dtype=torch.float32, device=y.device)
+    _need(x, torch.float32, (plan.n_side, plan.n_side), "x")
+    _lib.check(_lib.load().gbri_phi_adjoint(plan.handle, _ptr(y), _ptr(x), PLAN_ORDER if plan_order else 0,
+                                            _stream(stream)))
+    return x
+
+
+def vis_reorder(plan, vis, to_plan=True, out=None, stream=None):
+    """Reorder a complex64 [M] vector between caller order and plan order (gbri_vis_reorder)."""
+    _need(vis, torch.complex64, (plan.M,), "vis")
+    if out is None:
+        out = torch.empty_like(vis)
+    _lib.check(_lib.load().gbri_vis_reorder(plan.handle, _ptr(vis), _ptr(out), 1 if to_plan else 0, _stream(stream)))
+    return out
+
+
+def op_norm(plan, max_iter=200, tol=1e-8, seed=0, stream=None):
+    """||Phi||^2 by the power method (gbri_op_norm); returns (value, iterations)."""
+    v, it = C.c_double(), C.c_int32()
+    _lib.check(_lib.load().gbri_op_norm(plan.handle, int(max_iter), float(tol), int(seed), C.byref(v), C.byref(it),
+                                        _stream(stream)))
+    return v.value, it.value
+
+
+class Wavelet:
+    """SARA dictionary (gbri_wavelet_create): db_orders with 0 = Dirac, N = dbN."""
+
+    def __init__(self, n_side, levels, db_orders):
+        lib = _lib.load()
+        self.n_side, self.levels = int(n_side), int(levels)
+        self.db_orders = tuple(int(o) for o in db_orders)
+        self.n_w = len(self.db_orders)
+        arr = (C.c_int32 * self.n_w)(*self.db_orders)
+        h = C.c_void_p()
+        _lib.check(lib.gbri_wavelet_create(C.byref(h), self.n_side, self.levels, arr, self.n_w, F32))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().gbri_wavelet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def psi(wav, alpha, x=None, stream=None):
+    """x = Psi alpha (gbri_psi).  alpha: float32 [n_w, n, n]."""
+    _need(alpha, torch.float32, (wav.n_w, wav.n_side, wav.n_side), "alpha")
+    if x is None:
+        x = torch.empty((wav.n_side, wav.n_side), dtype=torch.float32, device=alpha.device)
+    _need(x, torch.float32, (wav.n_side, wav.n_side), "x")
+    _lib.check(_lib.load().gbri_psi(wav.handle, _ptr(alpha), _ptr(x), _stream(stream)))
+    return x
+
+
+def psi_adjoint(wav, x, alpha=None, stream=None):
+    """alpha = Psi^dagger x (gbri_psi_adjoint)."""
+    _need(x, torch.float32, (wav.n_side, wav.n_side), "x")
+    if alpha is None:
+        alpha = torch.empty((wav.n_w, wav.n_side, wav.n_side), dtype=torch.float32, device=x.device)
+    _need(alpha, torch.float32, (wav.n_w, wav.n_side, wav.n_side), "alpha")
+    _lib.check(_lib.load().gbri_psi_adjoint(wav.handle, _ptr(x), _ptr(alpha), _stream(stream)))
+    return alpha
+
+
+def prox_l1(x, lam, out=None, stream=None):
+    """Soft thresholding (gbri_prox_l1) of a float32 or complex64 CUDA tensor."""
+    if x.dtype not in (torch.float32, torch.complex64):
+        raise ValueError("prox_l1 takes float32 or complex64")
+    _need(x, x.dtype, name="x")
+    if out is None:
+        out = torch.empty_like(x)
+    _need(out, x.dtype, tuple(x.shape), "out")
+    _lib.check(_lib.load().gbri_prox_l1(_ptr(x), _ptr(out), x.numel(), float(lam),
+                                        1 if x.dtype == torch.complex64 else 0, F32, _stream(stream)))
+    return out
+
+
+def proj_l2ball(z, center, eps, out=None, norm_out=None, stream=None):
+    """Projection of complex64 z onto the l2 ball of radius eps around center (gbri_proj_l2ball).
+    norm_out: optional float64 CUDA tensor of one element receiving ||z - center||."""
+    _need(z, torch.complex64, name="z")
+    _need(center, torch.complex64, tuple(z.shape), "center")
+    if out is None:
+        out = torch.empty_like(z)
+    _need(out, torch.complex64, tuple(z.shape), "out")
+    if norm_out is not None:
+        _need(norm_out, torch.float64, (1,), "norm_out")
+    _lib.check(_lib.load().gbri_proj_l2ball(_ptr(z), _ptr(center), _ptr(out), z.numel(), float(eps),
+                                            _ptr(norm_out), F32, _stream(stream)))
+    return out
+
+
+def _params(**kw):
+    p = SolveParams()
+    p.algo = ALGO_PD
+    p.max_iter = 200
+    p.theta = -1.0
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise ValueError("unknown solver parameter %s" % k)
+        setattr(p, k, v)
+    return p
+
+
+class Solver:
+    """Resident solver state (gbri_solver_create / step / get_x / report)."""
+
+    def __init__(self, plan, wav, y, plan_order=False, stream=None, **params):
+        _need(y, torch.complex64, (plan.M,), "y")
+        self.plan, self.wav = plan, wav
+        self.params = _params(**params)
+        h = C.c_void_p()
+        _lib.check(_lib.load().gbri_solver_create(C.byref(h), plan.handle, wav.handle, _ptr(y),
+                                                  C.byref(self.params), PLAN_ORDER if plan_order else 0,
+                                                  _stream(stream)))
+        self._h = h
+
+    def step(self, n_iter=1, stream=None):
+        _lib.check(_lib.load().gbri_solver_step(self._h, int(n_iter), _stream(stream)))
+
+    def x(self, out=None, stream=None):
+        if out is None:
+            out = torch.empty((self.plan.n_side, self.plan.n_side), dtype=torch.float32, device=self.plan.device)
+        _lib.check(_lib.load().gbri_solver_get_x(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def report(self, stream=None):
+        r = SolveReport()
+        _lib.check(_lib.load().gbri_solver_report(self._h, C.byref(r), _stream(stream)))
+        return {f: getattr(r, f) for f, _ in SolveReport._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().gbri_solver_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(plan, wav, y, x_out=None, plan_order=False, stream=None, **params):
+    """One-shot solve (gbri_solve); returns (x, report dict)."""
+    _need(y, torch.complex64, (plan.M,), "y")
+    if x_out is None:
+        x_out = torch.empty((plan.n_side, plan.n_side), dtype=torch.float32, device=y.device)
+    p = _params(**params)
+    r = SolveReport()
+    _lib.check(_lib.load().gbri_solve(plan.handle, wav.handle, _ptr(y), C.byref(p), _ptr(x_out), C.byref(r),
+                                      PLAN_ORDER if plan_order else 0, _stream(stream)))
+    return x_out, {f: getattr(r, f) for f, _ in SolveReport._fields_}
+
+
+def profile_enable(capacity):
+    _lib.check(_lib.load().gbri_profile_enable(int(capacity)))
+
+
+def profile_read(kind):
+    t, n = C.c_double(), C.c_int64()
+    _lib.check(_lib.load().gbri_profile_read(int(kind), C.byref(t), C.byref(n)))
+    return t.value, n.value
+
+
+def launch_count():
+    return int(_lib.load().gbri_launch_count())

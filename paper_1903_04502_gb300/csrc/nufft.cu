@@ -1,0 +1,221 @@
+// Measurement operator calls: Phi (Sec. 2, Eq. 2) = degrid(F(pad_correct(x))),
+// Phi^dagger = crop_correct(F^H(grid(y))), visibility reordering and the power
+// method for ||Phi||^2 (Sec. 6.3.1).
+#include <cmath>
+#include <vector>
+
+#include "nufft.cuh"
+
+namespace gbri {
+
+namespace {
+
+// Z S: padded[(q - n/2) mod K][(p - n/2) mod K] = corr[p] corr[q] x[q][p] * inv_scale
+__global__ void k_pad(const float* __restrict__ x, const float* __restrict__ corr, float2* __restrict__ padded,
+                      int n, int K, const double* __restrict__ d_norm) {
+  const float s = d_norm ? (float)(1.0 / *d_norm) : 1.0f;
+  const int total = n * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int q = i / n, p = i - q * n;
+    int r = q - n / 2; if (r < 0) r += K;
+    int c = p - n / 2; if (c < 0) c += K;
+    padded[(size_t)r * K + c] = make_float2(x[i] * corr[p] * corr[q] * s, 0.f);
+  }
+}
+
+// S^T Z^T and the real part: x[q][p] = corr[p] corr[q] Re(grid[(q - n/2) mod K][(p - n/2) mod K])
+__global__ void k_crop(const float2* __restrict__ grid, const float* __restrict__ corr, float* __restrict__ x,
+                       int n, int K) {
+  const int total = n * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int q = i / n, p = i - q * n;
+    int r = q - n / 2; if (r < 0) r += K;
+    int c = p - n / 2; if (c < 0) c += K;
+    x[i] = corr[p] * corr[q] * grid[(size_t)r * K + c].x;
+  }
+}
+
+__global__ void k_gather(const float2* __restrict__ in, const int32_t* __restrict__ perm, float2* __restrict__ out,
+                         int64_t M) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[perm[i]];
+}
+__global__ void k_scatter_vis(const float2* __restrict__ in, const int32_t* __restrict__ perm,
+                              float2* __restrict__ out, int64_t M) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+    out[perm[i]] = in[i];
+}
+
+// FP64 sum of squares of an image into partials[blockIdx.x] (per-thread FP32 Kahan partials).
+__global__ void k_image_sumsq(const float* __restrict__ x, int64_t n, double* __restrict__ partials) {
+  __shared__ double sh[40];
+  KahanF acc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc.add(x[i] * x[i]);
+  const double v = block_sum(acc.value(), sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v;
+}
+
+// norm = sqrt(sum partials) into out[0]
+__global__ void k_finish_norm(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  __shared__ double sh[40];
+  const double v = reduce_partials(partials, n, sh);
+  if (threadIdx.x == 0) out[0] = sqrt(v);
+}
+
+// start vector of the power method: 0.5 + U[0,1), U = top 53 bits of SplitMix64(seed + k golden), k = i + 1
+__global__ void k_power_start(float* __restrict__ b, int64_t n, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    b[i] = (float)(0.5 + (double)(z >> 11) * (1.0 / 9007199254740992.0));
+  }
+}
+
+int grid_blocks_for(int64_t n, int threads = 256) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), (int64_t)num_sms() * 8));
+}
+
+}  // namespace
+
+int32_t launch_pad(gbri_plan* p, const float* x, const double* d_norm, cudaStream_t s) {
+  launch_begin(GBRI_K_PAD, s);
+  k_pad<<<grid_blocks_for((int64_t)p->n_side * p->n_side), 256, 0, s>>>(x, p->corr, p->padded, p->n_side, p->K,
+                                                                         d_norm);
+  return launch_end(GBRI_K_PAD, s);
+}
+
+int32_t launch_crop(gbri_plan* p, float* x, cudaStream_t s) {
+  launch_begin(GBRI_K_CROP, s);
+  k_crop<<<grid_blocks_for((int64_t)p->n_side * p->n_side), 256, 0, s>>>(p->grid, p->corr, x, p->n_side, p->K);
+  return launch_end(GBRI_K_CROP, s);
+}
+
+int32_t fft_forward(gbri_plan* p, cudaStream_t s) {
+  if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cufftSetStream");
+  launch_begin(GBRI_K_FFT_FWD, s, false);
+  const cufftResult r = cufftExecC2C(p->fft, reinterpret_cast<cufftComplex*>(p->padded),
+                                     reinterpret_cast<cufftComplex*>(p->grid), CUFFT_FORWARD);
+  const int32_t st = launch_end(GBRI_K_FFT_FWD, s);
+  if (r != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cufftExecC2C forward");
+  return st;
+}
+
+int32_t fft_inverse(gbri_plan* p, cudaStream_t s) {
+  if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cufftSetStream");
+  launch_begin(GBRI_K_FFT_INV, s, false);
+  const cufftResult r = cufftExecC2C(p->fft, reinterpret_cast<cufftComplex*>(p->grid),
+                                     reinterpret_cast<cufftComplex*>(p->grid), CUFFT_INVERSE);
+  const int32_t st = launch_end(GBRI_K_FFT_INV, s);
+  if (r != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cufftExecC2C inverse");
+  return st;
+}
+
+int32_t normal_op(gbri_plan* p, const float* b, const double* d_norm, float* out, cudaStream_t s) {
+  GBRI_TRY(launch_pad(p, b, d_norm, s));
+  GBRI_TRY(fft_forward(p, s));
+  GBRI_TRY(launch_degrid(p, p->grid, EpiStorePlan{p->vis_tmp}, s));
+  GBRI_TRY(launch_grid(p, SrcPlan{p->vis_tmp}, s));
+  GBRI_TRY(fft_inverse(p, s));
+  return launch_crop(p, out, s);
+}
+
+int32_t image_norm(gbri_plan* p, const float* x, double* d_out, cudaStream_t s) {
+  const int64_t n = (int64_t)p->n_side * p->n_side;
+  const int blocks = std::min(grid_blocks_for(n), p->n_partials);
+  launch_begin(GBRI_K_OTHER, s);
+  k_image_sumsq<<<blocks, 256, 0, s>>>(x, n, p->partials);
+  GBRI_TRY(launch_end(GBRI_K_OTHER, s));
+  launch_begin(GBRI_K_OTHER, s);
+  k_finish_norm<<<1, 256, 0, s>>>(p->partials, blocks, d_out);
+  return launch_end(GBRI_K_OTHER, s);
+}
+
+}  // namespace gbri
+
+using namespace gbri;
+
+extern "C" {
+
+int32_t gbri_vis_reorder(const gbri_plan* pc, const float* d_in, float* d_out, int32_t to_plan, void* stream) {
+  GBRI_CHECK(pc, GBRI_EINVAL, "null plan");
+  if (pc->M == 0) return GBRI_OK;
+  GBRI_CHECK(d_in && d_out && d_in != d_out, GBRI_EINVAL, "bad buffers");
+  cudaStream_t s = (cudaStream_t)stream;
+  gbri_plan* p = const_cast<gbri_plan*>(pc);
+  launch_begin(GBRI_K_OTHER, s);
+  if (to_plan)
+    k_gather<<<grid_blocks_for(p->M), 256, 0, s>>>((const float2*)d_in, p->perm, (float2*)d_out, p->M);
+  else
+    k_scatter_vis<<<grid_blocks_for(p->M), 256, 0, s>>>((const float2*)d_in, p->perm, (float2*)d_out, p->M);
+  return launch_end(GBRI_K_OTHER, s);
+}
+
+int32_t gbri_phi(gbri_plan* p, const float* d_x, float* d_y, uint32_t flags, void* stream) {
+  GBRI_CHECK(p && d_x && (d_y || p->M == 0), GBRI_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  GBRI_TRY(launch_pad(p, d_x, nullptr, s));
+  GBRI_TRY(fft_forward(p, s));
+  if (p->M == 0) return GBRI_OK;
+  if (flags & GBRI_PLAN_ORDER) return launch_degrid(p, p->grid, EpiStorePlan{(float2*)d_y}, s);
+  return launch_degrid(p, p->grid, EpiStoreRaw{(float2*)d_y, p->perm}, s);
+}
+
+int32_t gbri_phi_adjoint(gbri_plan* p, const float* d_y, float* d_x, uint32_t flags, void* stream) {
+  GBRI_CHECK(p && d_x && (d_y || p->M == 0), GBRI_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (flags & GBRI_PLAN_ORDER)
+    GBRI_TRY(launch_grid(p, SrcPlan{(const float2*)d_y}, s));
+  else
+    GBRI_TRY(launch_grid(p, SrcRaw{(const float2*)d_y, p->perm}, s));
+  GBRI_TRY(fft_inverse(p, s));
+  return launch_crop(p, d_x, s);
+}
+
+int32_t gbri_op_norm(gbri_plan* p, int32_t max_iter, double tol, uint64_t seed, double* op_norm_sq,
+                     int32_t* iters, void* stream) {
+  GBRI_CHECK(p && op_norm_sq && max_iter > 0, GBRI_EINVAL, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = (int64_t)p->n_side * p->n_side;
+  float *b = nullptr, *c = nullptr;
+  double* d_norm = p->scalars + 8;  // scalars[8]: norm of the current vector
+  GBRI_CHECK_CUDA(cudaMallocAsync((void**)&b, sizeof(float) * n, s));
+  cudaError_t e = cudaMallocAsync((void**)&c, sizeof(float) * n, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(b, s);
+    return cuda_error(e, "cudaMallocAsync");
+  }
+  int32_t st = GBRI_OK;
+  launch_begin(GBRI_K_OTHER, s);
+  k_power_start<<<grid_blocks_for(n), 256, 0, s>>>(b, n, seed);
+  st = launch_end(GBRI_K_OTHER, s);
+  if (st == GBRI_OK) st = image_norm(p, b, d_norm, s);
+  double prev = 0.0, val = 0.0;
+  int it = 0;
+  for (it = 1; it <= max_iter && st == GBRI_OK; ++it) {
+    // c = Phi^dagger Phi (b / ||b||), then ||c||
+    st = normal_op(p, b, d_norm, c, s);
+    if (st != GBRI_OK) break;
+    st = image_norm(p, c, d_norm, s);
+    if (st != GBRI_OK) break;
+    e = cudaMemcpyAsync(&val, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = cuda_error(e, "power iteration");
+      break;
+    }
+    std::swap(b, c);
+    if (it > 1 && std::fabs(val - prev) <= tol * val) break;
+    prev = val;
+  }
+  cudaFreeAsync(b, s);
+  cudaFreeAsync(c, s);
+  if (st != GBRI_OK) return st;
+  *op_norm_sq = val;
+  if (iters) *iters = std::min(it, max_iter);
+  return GBRI_OK;
+}
+
+}  // extern "C"

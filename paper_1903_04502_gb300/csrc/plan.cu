@@ -1,0 +1,395 @@
+// Plan creation (once per problem): FP64 quantisation of (u, v) to fixed-point
+// grid coordinates, counting sort of the visibilities by (tile, cell), packed
+// per-visibility metadata, work chunks, the pre-sampled Kaiser-Bessel table
+// (Sec. 8.1) and the gridding correction (the S of Eq. 2), cuFFT plan.
+//
+// Kaiser-Bessel kernel (Sec. 7.3 names it, support J = 4; the formula is the
+// standard one): g(t) = I0(beta sqrt(1 - (2t/J)^2)) / I0(beta) for |t| < J/2,
+// 0 otherwise; its continuous Fourier transform is
+// ghat(nu) = J sinh(sqrt(beta^2 - (pi J nu)^2)) / (I0(beta) sqrt(beta^2 - (pi J nu)^2)).
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "nufft.cuh"
+
+namespace gbri {
+namespace {
+
+double kb_g(double t, int J, double beta) {
+  const double r = 2.0 * t / J;
+  if (!(std::fabs(r) < 1.0)) return 0.0;
+  return std::cyl_bessel_i(0.0, beta * std::sqrt(1.0 - r * r)) / std::cyl_bessel_i(0.0, beta);
+}
+
+double kb_ghat(double nu, int J, double beta) {
+  const double s = beta * beta - (M_PI * J * nu) * (M_PI * J * nu);
+  const double a = std::sqrt(std::fabs(s));
+  double ratio = 1.0;
+  if (a > 0.0) ratio = (s > 0.0) ? std::sinh(a) / a : std::sin(a) / a;
+  return J * ratio / std::cyl_bessel_i(0.0, beta);
+}
+
+// Per-visibility quantisation (Sec. 8.1, zeroth order): k~ = round_half_away(u * K S / (2 pi))
+// in FP64, tile-major cell key, tile-local packed coordinates.
+__global__ void k_quantise(const float4* __restrict__ uvw, int64_t M, double scale, int K, int log2S, int nT,
+                           int32_t* __restrict__ key, uint32_t* __restrict__ packed, float* __restrict__ wt,
+                           int32_t* __restrict__ counts, int32_t* __restrict__ err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int S = 1 << log2S;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+    const float4 r = uvw[i];
+    if (!isfinite(r.x) || !isfinite(r.y) || !isfinite(r.w)) {
+      atomicOr(err, 1);
+      key[i] = 0; packed[i] = 0; wt[i] = 0.f;
+      continue;
+    }
+    if (fabsf(r.x) > 50.2654825f || fabsf(r.y) > 50.2654825f) {  // 16 pi
+      atomicOr(err, 2);
+      key[i] = 0; packed[i] = 0; wt[i] = 0.f;
+      continue;
+    }
+    int q[2];
+    const float uv[2] = {r.x, r.y};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const double prod = __dmul_rn((double)uv[a], scale);
+      const double rnd = floor(__dadd_rn(fabs(prod), 0.5));
+      q[a] = (int)(prod < 0.0 ? -rnd : rnd);
+    }
+    // base cells floor(k~ / S) (arithmetic shift = floor for negatives), fraction k~ mod S
+    const int bx = q[0] >> log2S, by = q[1] >> log2S;
+    const int fx = q[0] & (S - 1), fy = q[1] & (S - 1);
+    int cx = bx % K; if (cx < 0) cx += K;
+    int cy = by % K; if (cy < 0) cy += K;
+    const int tx = cx / kTile, ty = cy / kTile;
+    const int lcx = cx - tx * kTile, lcy = cy - ty * kTile;
+    const int k = ((ty * nT + tx) * kTile + lcy) * kTile + lcx;
+    key[i] = k;
+    packed[i] = (uint32_t)(lcx * S + fx) | ((uint32_t)(lcy * S + fy) << 16);
+    wt[i] = r.w;
+    atomicAdd(counts + k, 1);
+  }
+}
+
+// ---- exclusive scan of int32 counts (3 phases) ---------------------------------
+constexpr int kScanThreads = 1024, kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ int block_exclusive_scan(int v, int* sh, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int n = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += n;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int n = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += n;
+    }
+    sh[lane] = s;  // inclusive over warps
+  }
+  __syncthreads();
+  const int warp_off = (w > 0) ? sh[w - 1] : 0;
+  *total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+__global__ void k_scan_tile_sums(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ sums) {
+  __shared__ int sh[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int v = 0;
+  for (int j = 0; j < kScanItems; ++j) v += (base + j < n) ? in[base + j] : 0;
+  int tot;
+  block_exclusive_scan(v, sh, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int32_t* __restrict__ sums, int n) {  // one block, in place, exclusive
+  __shared__ int sh[32];
+  int carry = 0;
+  for (int b = 0; b < n; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    const int v = (i < n) ? sums[i] : 0;
+    int tot;
+    const int ex = block_exclusive_scan(v, sh, &tot);
+    if (i < n) sums[i] = carry + ex;
+    carry += tot;
+  }
+}
+
+__global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ sums,
+                             int32_t* __restrict__ out /* n + 1 */) {
+  __shared__ int sh[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int loc[kScanItems];
+  int v = 0;
+  for (int j = 0; j < kScanItems; ++j) {
+    loc[j] = (base + j < n) ? in[base + j] : 0;
+    v += loc[j];
+  }
+  int tot;
+  int run = sums[blockIdx.x] + block_exclusive_scan(v, sh, &tot);
+  for (int j = 0; j < kScanItems; ++j) {
+    if (base + j < n) out[base + j] = run;
+    run += loc[j];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[blockIdx.x] + tot;
+}
+
+__global__ void k_scatter(const int32_t* __restrict__ key, const uint32_t* __restrict__ packed,
+                          const float* __restrict__ wt, int64_t M, int32_t* __restrict__ cursor,
+                          uint2* __restrict__ meta, int32_t* __restrict__ perm) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+    const int pos = atomicAdd(cursor + key[i], 1);
+    meta[pos] = make_uint2(packed[i], __float_as_uint(wt[i]));
+    perm[pos] = (int32_t)i;
+  }
+}
+
+__global__ void k_tile_starts(const int32_t* __restrict__ offsets, int n_tiles, int cells_per_tile,
+                              int32_t* __restrict__ starts) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= n_tiles) starts[t] = offsets[(int64_t)t * cells_per_tile];
+}
+
+template <class T>
+int32_t dmalloc(T** p, size_t n, int64_t* acct) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return set_error(GBRI_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  if (acct) *acct += (int64_t)(n * sizeof(T));
+  return GBRI_OK;
+}
+
+int32_t scan_counts(const int32_t* counts, int64_t n, int32_t* offsets, cudaStream_t s) {
+  const int64_t tiles = ceil_div(n, kScanTile);
+  int32_t* sums = nullptr;
+  GBRI_TRY(dmalloc(&sums, (size_t)tiles, nullptr));
+  launch_begin(GBRI_K_OTHER, s);
+  k_scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, s>>>(counts, n, sums);
+  int32_t st = launch_end(GBRI_K_OTHER, s);
+  if (st == GBRI_OK) {
+    launch_begin(GBRI_K_OTHER, s);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, (int)tiles);
+    st = launch_end(GBRI_K_OTHER, s);
+  }
+  if (st == GBRI_OK) {
+    launch_begin(GBRI_K_OTHER, s);
+    k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, s>>>(counts, n, sums, offsets);
+    st = launch_end(GBRI_K_OTHER, s);
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(sums);
+  return st;
+}
+
+void destroy_plan(gbri_plan* p) {
+  if (!p) return;
+  cudaFree(p->meta);
+  cudaFree(p->perm);
+  cudaFree(p->chunks);
+  cudaFree(p->wtab);
+  cudaFree(p->corr);
+  cudaFree(p->padded);
+  cudaFree(p->grid);
+  cudaFree(p->vis_tmp);
+  cudaFree(p->partials);
+  cudaFree(p->scalars);
+  if (p->fft_ok) cufftDestroy(p->fft);
+  delete p;
+}
+
+int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
+  const int K = p->K, S = p->S;
+  const int64_t M = p->M;
+  const int64_t cells = (int64_t)K * K;
+  const int n_tiles = p->nT * p->nT;
+
+  // tables on the host in FP64, stored FP32 (Sec. 8.1; the S factor of Eq. 2)
+  {
+    const int half = (p->J / 2) * S;
+    std::vector<double> tab(half + 1);
+    for (int i = 0; i <= half; ++i) tab[i] = kb_g((double)i / S, p->J, p->beta);
+    std::vector<float> w((size_t)S * p->J);
+    for (int f = 0; f < S; ++f)
+      for (int t = 0; t < p->J; ++t) {
+        const int d = std::abs(f + (p->J / 2 - 1 - t) * S);
+        w[(size_t)f * p->J + t] = (d <= half) ? (float)tab[d] : 0.f;
+      }
+    std::vector<float> corr(p->n_side);
+    for (int i = 0; i < p->n_side; ++i)
+      corr[i] = (float)(1.0 / kb_ghat((double)(i - p->n_side / 2) / K, p->J, p->beta));
+    GBRI_TRY(dmalloc(&p->wtab, w.size(), &p->device_bytes));
+    GBRI_TRY(dmalloc(&p->corr, corr.size(), &p->device_bytes));
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->wtab, w.data(), w.size() * 4, cudaMemcpyHostToDevice, s));
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->corr, corr.data(), corr.size() * 4, cudaMemcpyHostToDevice, s));
+  }
+
+  GBRI_TRY(dmalloc(&p->meta, (size_t)M, &p->device_bytes));
+  GBRI_TRY(dmalloc(&p->perm, (size_t)M, &p->device_bytes));
+  GBRI_TRY(dmalloc(&p->vis_tmp, (size_t)M, &p->device_bytes));
+  GBRI_TRY(dmalloc(&p->padded, (size_t)cells, &p->device_bytes));
+  GBRI_TRY(dmalloc(&p->grid, (size_t)cells, &p->device_bytes));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(p->padded, 0, sizeof(float2) * cells, s));
+
+  // work arrays for the sort
+  int32_t *key = nullptr, *counts = nullptr, *offsets = nullptr, *err = nullptr, *starts = nullptr;
+  uint32_t* packed = nullptr;
+  float* wt = nullptr;
+  int32_t st = GBRI_OK;
+  auto cleanup = [&]() {
+    cudaFree(key); cudaFree(counts); cudaFree(offsets); cudaFree(err); cudaFree(packed); cudaFree(wt);
+    cudaFree(starts);
+  };
+  if ((st = dmalloc(&key, (size_t)M, nullptr)) || (st = dmalloc(&packed, (size_t)M, nullptr)) ||
+      (st = dmalloc(&wt, (size_t)M, nullptr)) || (st = dmalloc(&counts, (size_t)cells, nullptr)) ||
+      (st = dmalloc(&offsets, (size_t)cells + 1, nullptr)) || (st = dmalloc(&err, 1, nullptr)) ||
+      (st = dmalloc(&starts, (size_t)n_tiles + 1, nullptr))) {
+    cleanup();
+    return st;
+  }
+  cudaMemsetAsync(counts, 0, sizeof(int32_t) * cells, s);
+  cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+  const double scale = (double)((int64_t)K * S) / (2.0 * M_PI);
+  const int vb = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(M, 256), 1), (int64_t)num_sms() * 16);
+  launch_begin(GBRI_K_OTHER, s);
+  k_quantise<<<vb, 256, 0, s>>>(reinterpret_cast<const float4*>(d_uvw), M, scale, K, p->log2S, p->nT, key,
+                                packed, wt, counts, err);
+  st = launch_end(GBRI_K_OTHER, s);
+  if (st == GBRI_OK) st = scan_counts(counts, cells, offsets, s);
+  int32_t herr = 0;
+  if (st == GBRI_OK) {
+    cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_error(e, "quantise status");
+    else if (herr & 1) st = set_error(GBRI_ENONFINITE, "non-finite u, v or weight");
+    else if (herr & 2) st = set_error(GBRI_EINVAL, "|u| or |v| exceeds 16 pi");
+  }
+  if (st == GBRI_OK) {
+    // cursor = offsets (reuse counts as the cursor array)
+    cudaMemcpyAsync(counts, offsets, sizeof(int32_t) * cells, cudaMemcpyDeviceToDevice, s);
+    launch_begin(GBRI_K_OTHER, s);
+    k_scatter<<<vb, 256, 0, s>>>(key, packed, wt, M, counts, p->meta, p->perm);
+    st = launch_end(GBRI_K_OTHER, s);
+  }
+  std::vector<int32_t> hst(n_tiles + 1);
+  if (st == GBRI_OK) {
+    launch_begin(GBRI_K_OTHER, s);
+    k_tile_starts<<<(n_tiles + 1 + 255) / 256, 256, 0, s>>>(offsets, n_tiles, kTile * kTile, starts);
+    st = launch_end(GBRI_K_OTHER, s);
+  }
+  if (st == GBRI_OK) {
+    cudaError_t e = cudaMemcpyAsync(hst.data(), starts, sizeof(int32_t) * (n_tiles + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_error(e, "tile starts");
+  }
+  cleanup();
+  if (st != GBRI_OK) return st;
+
+  // work chunks: at most kChunk visibilities of one tile each (built on the host)
+  std::vector<int4> ch;
+  for (int t = 0; t < n_tiles; ++t) {
+    const int a = hst[t], b = hst[t + 1];
+    for (int c = a; c < b; c += kChunk) ch.push_back(make_int4(t, c, std::min(kChunk, b - c), 0));
+  }
+  p->n_chunks = (int64_t)ch.size();
+  GBRI_TRY(dmalloc(&p->chunks, ch.size(), &p->device_bytes));
+  if (!ch.empty())
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+
+  // persistent grid sizes
+  const int sms = num_sms();
+  const int per_sm_dg = std::max(1, (int)((200 * 1024) / (degrid_smem(p) + 1024)));
+  const int per_sm_gr = std::max(1, (int)((200 * 1024) / (grid_smem(p) + 1024)));
+  p->degrid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_dg, 8)));
+  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_gr, 8)));
+  p->n_partials = std::max(p->degrid_blocks, 1024);
+  GBRI_TRY(dmalloc(&p->partials, (size_t)p->n_partials * 4, &p->device_bytes));
+  GBRI_TRY(dmalloc(&p->scalars, 64, &p->device_bytes));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(p->scalars, 0, 64 * sizeof(double), s));
+
+  if (cufftPlan2d(&p->fft, K, K, CUFFT_C2C) != CUFFT_SUCCESS)
+    return set_error(GBRI_ECUFFT, "cufftPlan2d failed");
+  p->fft_ok = true;
+  GBRI_CHECK_CUDA(cudaStreamSynchronize(s));
+  return GBRI_OK;
+}
+
+}  // namespace
+}  // namespace gbri
+
+using namespace gbri;
+
+extern "C" {
+
+int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* d_uvw, void* stream) {
+  GBRI_CHECK(out && d, GBRI_EINVAL, "null argument");
+  *out = nullptr;
+  GBRI_CHECK(d->reserved == 0, GBRI_EINVAL, "reserved must be 0");
+  GBRI_CHECK(d->precision == GBRI_F32, GBRI_EINVAL, "only GBRI_F32 plans are supported");
+  GBRI_CHECK(d->n_side >= 16 && d->n_side % 2 == 0, GBRI_EINVAL, "n_side must be even and >= 16");
+  GBRI_CHECK(d->oversample >= 2 && d->oversample <= 4, GBRI_EINVAL, "oversample must be in [2, 4]");
+  GBRI_CHECK(d->J == 4 || d->J == 6, GBRI_EINVAL, "J must be 4 or 6");
+  const int S = d->samples_per_unit;
+  GBRI_CHECK(S >= 16 && S <= 4096 && (S & (S - 1)) == 0, GBRI_EINVAL,
+             "samples_per_unit must be a power of two in [16, 4096]");
+  GBRI_CHECK(d->M >= 0 && d->M < (int64_t)1 << 31, GBRI_EINVAL, "M must be in [0, 2^31)");
+  GBRI_CHECK(d->M == 0 || d_uvw, GBRI_EINVAL, "null uvw");
+  const int64_t K = (int64_t)d->oversample * d->n_side;
+  GBRI_CHECK(K % kTile == 0, GBRI_EINVAL, "oversample * n_side must be a multiple of 16");
+  GBRI_CHECK(K <= 16384, GBRI_EINVAL, "grid larger than 16384^2 is not supported");
+  gbri_plan* p = new (std::nothrow) gbri_plan();
+  GBRI_CHECK(p, GBRI_ENOMEM, "host allocation");
+  p->n_side = d->n_side;
+  p->K = (int)K;
+  p->J = d->J;
+  p->S = S;
+  p->log2S = 0;
+  while ((1 << p->log2S) < S) ++p->log2S;
+  p->nT = (int)(K / kTile);
+  p->beta = d->kb_beta > 0 ? d->kb_beta : 2.34 * d->J;
+  p->M = d->M;
+  p->prec = d->precision;
+  const int32_t st = build_plan(p, d_uvw, (cudaStream_t)stream);
+  if (st != GBRI_OK) {
+    destroy_plan(p);
+    return st;
+  }
+  *out = p;
+  return GBRI_OK;
+}
+
+int32_t gbri_plan_destroy(gbri_plan* p) {
+  if (p) cudaDeviceSynchronize();
+  destroy_plan(p);
+  return GBRI_OK;
+}
+
+int32_t gbri_plan_info(const gbri_plan* p, int64_t* K, int64_t* M, int64_t* n_chunks, int64_t* bytes) {
+  GBRI_CHECK(p, GBRI_EINVAL, "null plan");
+  if (K) *K = p->K;
+  if (M) *M = p->M;
+  if (n_chunks) *n_chunks = p->n_chunks;
+  if (bytes) *bytes = p->device_bytes;
+  return GBRI_OK;
+}
+
+int32_t gbri_plan_permutation(const gbri_plan* p, int32_t* d_perm, void* stream) {
+  GBRI_CHECK(p && (d_perm || p->M == 0), GBRI_EINVAL, "null argument");
+  if (p->M == 0) return GBRI_OK;
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(d_perm, p->perm, sizeof(int32_t) * p->M, cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream));
+  return GBRI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,536 @@
+// Solvers of the constrained analysis problem (Sec. 3.1, Sec. 5):
+//     min ||Psi^dagger x||_1  s.t.  ||y - Phi x||_2 <= eps,  x >= 0.
+//
+// Primal-dual (Appendix A.4, Algorithm 7) with L = [Psi^dagger; Phi],
+// f = gamma ||.||_1 (+) iota_B(y, eps), g = iota_{R+}.  With the Moreau
+// decomposition the dual step is z1 <- clip(z1 + sigma1 Psi^dagger xhat, gamma) and
+// z2 <- t - sigma2 P_B(t / sigma2), t = z2 + sigma2 Phi xhat.  Writing
+// u = t - sigma2 y, the projection gives z2 = (1 - rho) u with
+// rho = min(1, eps / ||u / sigma2||), so the device keeps u and the scalar
+// c = 1 - rho instead of z2:
+//   degrid epilogue:  u <- c u + sigma2 (Phi xhat - y), partial ||u||^2  (FP64 block sums)
+//   scalar kernel:    c <- 1 - min(1, eps sigma2 / ||u||)
+//   gridding source:  u (Phi^dagger is linear; c scales the image)
+//   image epilogue:   x+ = max(x - tau (Psi z1 + c Re Phi^dagger u), 0), xhat = x+ + theta (x+ - x)
+//
+// Dual Forward-Backward ADMM (Sec. 5, Algorithm 1), with w = v + s - y, v = Phi x:
+//   r = y + rho_b w, rho_b = min(1, eps / ||w||)  (projection onto the ball around y)
+//   s+ = s + varrho (v - r) = s + varrho ((1 - rho_b) w - s)
+//   xt = x - rho Re Phi^dagger (v - r + s+),  v - r + s+ = (1 - rho_b) w - s + s+
+//   DualFB(xt): zbar = P_C(xt); repeat { d = clip(eta d + Psi^dagger zbar, gamma) / eta;
+//               zbar = P_C(xt - Psi d) }; x = zbar.
+// All global norms are FP64 (per-thread FP32 compensated partials, FP64 block sums).
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "nufft.cuh"
+#include "prox.cuh"
+#include "wavelet.cuh"
+
+namespace gbri {
+namespace {
+
+enum { SC_C = 0, SC_DIST = 1, SC_REL = 2, SC_XN = 3, SC_RES = 4, SC_MAX = 5, SC_N = 16 };
+
+struct EpiPD1 {
+  float2* u;
+  const float2* y;
+  const double* c;
+  double* partials;
+  float sigma2;
+  KahanF acc;
+  __device__ __forceinline__ void operator()(int pos, float2 phi) {
+    const float cc = (float)*c;  // broadcast load, cached
+    const float2 uo = u[pos], yy = y[pos];
+    const float2 un = make_float2(fmaf(cc, uo.x, sigma2 * (phi.x - yy.x)), fmaf(cc, uo.y, sigma2 * (phi.y - yy.y)));
+    u[pos] = un;
+    acc.add(fmaf(un.x, un.x, un.y * un.y));
+  }
+  __device__ __forceinline__ void finish() {
+    __shared__ double sh[40];
+    const double v = block_sum(acc.value(), sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+};
+
+struct EpiADMM1 {  // w = Phi x + s - y, partial ||w||^2
+  float2* w;
+  const float2* sv;
+  const float2* y;
+  double* partials;
+  KahanF acc;
+  __device__ __forceinline__ void operator()(int pos, float2 v) {
+    const float2 a = sv[pos], b = y[pos];
+    const float2 r = make_float2(v.x + a.x - b.x, v.y + a.y - b.y);
+    w[pos] = r;
+    acc.add(fmaf(r.x, r.x, r.y * r.y));
+  }
+  __device__ __forceinline__ void finish() {
+    __shared__ double sh[40];
+    const double v = block_sum(acc.value(), sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+};
+
+struct SrcADMM2 {  // s+ = s + varrho((1 - rho_b) w - s); source q = (1 - rho_b) w - s + s+
+  const float2* w;
+  float2* sv;
+  const double* rho_b;
+  float varrho;
+  __device__ __forceinline__ float2 operator()(int pos) const {
+    const float one_m = (float)(1.0 - *rho_b);
+    const float2 ww = w[pos], so = sv[pos];
+    const float2 pw = make_float2(one_m * ww.x, one_m * ww.y);
+    const float2 sn = make_float2(fmaf(varrho, pw.x - so.x, so.x), fmaf(varrho, pw.y - so.y, so.y));
+    sv[pos] = sn;
+    return make_float2(pw.x - so.x + sn.x, pw.y - so.y + sn.y);
+  }
+};
+
+// c = 1 - min(1, eps / (||u|| / sigma2))  (PD)   or   rho_b = min(1, eps / ||w||)  (ADMM, sigma2 = 1, want_rho)
+__global__ void k_ball_scalar(const double* __restrict__ partials, int n, double eps, double sigma2, bool want_rho,
+                              double* __restrict__ sc) {
+  __shared__ double sh[40];
+  const double dist = sqrt(reduce_partials(partials, n, sh)) / sigma2;
+  if (threadIdx.x == 0) {
+    const double rho = dist > eps ? eps / dist : 1.0;
+    sc[SC_C] = want_rho ? rho : 1.0 - rho;
+    sc[SC_DIST] = dist;
+  }
+}
+
+// PD primal update fused with S^T Z^T Re(.) of the gridded dual.
+__global__ void k_pd_update(const float2* __restrict__ grid, const float* __restrict__ corr,
+                            const float* __restrict__ psiz, float* __restrict__ x, float* __restrict__ xhat, int n,
+                            int K, float tau, float theta, const double* __restrict__ sc, double* __restrict__ partials) {
+  __shared__ double sh[40];
+  const float c = (float)sc[SC_C];
+  KahanF dd, xx;
+  const int total = n * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int q = i / n, p = i - q * n;
+    int r = q - n / 2; if (r < 0) r += K;
+    int cc = p - n / 2; if (cc < 0) cc += K;
+    const float phit = c * corr[p] * corr[q] * grid[(size_t)r * K + cc].x;
+    const float xo = x[i];
+    const float xn = fmaxf(xo - tau * (psiz[i] + phit), 0.f);
+    xhat[i] = fmaf(theta, xn - xo, xn);
+    x[i] = xn;
+    dd.add((xn - xo) * (xn - xo));
+    xx.add(xn * xn);
+  }
+  const double a = block_sum(dd.value(), sh);
+  const double b = block_sum(xx.value(), sh);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void k_rel_change(const double* __restrict__ partials, int n, double* __restrict__ sc) {
+  __shared__ double sh[40];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    const double dn = sqrt(a), xn = sqrt(b);
+    sc[SC_REL] = xn > 0 ? dn / xn : (dn == 0 ? 0.0 : INFINITY);
+    sc[SC_XN] = xn;
+  }
+}
+
+// ADMM: xt = x - rho * S^T Z^T Re(grid); zbar = max(xt, 0)
+__global__ void k_admm_xt(const float2* __restrict__ grid, const float* __restrict__ corr, const float* __restrict__ x,
+                          float* __restrict__ xt, float* __restrict__ zbar, int n, int K, float rho) {
+  const int total = n * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int q = i / n, p = i - q * n;
+    int r = q - n / 2; if (r < 0) r += K;
+    int cc = p - n / 2; if (cc < 0) cc += K;
+    const float v = x[i] - rho * corr[p] * corr[q] * grid[(size_t)r * K + cc].x;
+    xt[i] = v;
+    zbar[i] = fmaxf(v, 0.f);
+  }
+}
+
+// zbar = max(xt - Psi d, 0); on the last inner iteration also x = zbar with change partials.
+__global__ void k_admm_zbar(const float* __restrict__ xt, const float* __restrict__ psid, float* __restrict__ zbar,
+                            float* __restrict__ x, int64_t N, bool last, double* __restrict__ partials) {
+  __shared__ double sh[40];
+  KahanF dd, xx;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float z = fmaxf(xt[i] - psid[i], 0.f);
+    zbar[i] = z;
+    if (last) {
+      const float xo = x[i];
+      dd.add((z - xo) * (z - xo));
+      xx.add(z * z);
+      x[i] = z;
+    }
+  }
+  if (!last) return;
+  const double a = block_sum(dd.value(), sh);
+  const double b = block_sum(xx.value(), sh);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void k_absmax_partials(const float* __restrict__ a, int64_t n, double* __restrict__ partials) {
+  __shared__ float sh[32];
+  float m = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(a[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, sh[w]);
+    partials[blockIdx.x] = r;
+  }
+}
+
+__global__ void k_max_finish(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < n; ++i) m = fmax(m, partials[i]);
+    *out = m;
+  }
+}
+
+__global__ void k_residual_partials(const float2* __restrict__ a, const float2* __restrict__ b, int64_t M,
+                                    double* __restrict__ partials) {
+  __shared__ double sh[40];
+  KahanF acc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+    const float dr = a[i].x - b[i].x, di = a[i].y - b[i].y;
+    acc.add(fmaf(dr, dr, di * di));
+  }
+  const double v = block_sum(acc.value(), sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v;
+}
+
+__global__ void k_sqrt_sum(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  __shared__ double sh[40];
+  const double v = reduce_partials(partials, n, sh);
+  if (threadIdx.x == 0) *out = sqrt(v);
+}
+
+int img_blocks(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8));
+}
+
+}  // namespace
+}  // namespace gbri
+
+using namespace gbri;
+
+struct gbri_solver {
+  gbri_plan* plan = nullptr;
+  gbri_wavelet* wav = nullptr;
+  gbri_solve_params p{};
+  float2 *yp = nullptr, *u = nullptr, *w = nullptr;
+  float *x = nullptr, *xhat = nullptr, *psiz = nullptr, *z1 = nullptr, *xt = nullptr;
+  double* partials = nullptr;
+  double* sc = nullptr;
+  int n_partials = 0;
+  int iters = 0;
+  double ms_total = 0.0;
+};
+
+namespace {
+
+void free_solver(gbri_solver* s) {
+  if (!s) return;
+  cudaFree(s->yp); cudaFree(s->u); cudaFree(s->w);
+  cudaFree(s->x); cudaFree(s->xhat); cudaFree(s->psiz); cudaFree(s->z1); cudaFree(s->xt);
+  cudaFree(s->partials); cudaFree(s->sc);
+  delete s;
+}
+
+int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
+  gbri_plan* P = S->plan;
+  gbri_wavelet* W = S->wav;
+  const auto& p = S->p;
+  const int n = P->n_side;
+  const int64_t N = (int64_t)n * n;
+  // z1 <- clip(z1 + sigma1 Psi^dagger xhat, gamma)
+  GBRI_TRY(psi_adjoint_apply(W, S->xhat, S->z1, DualEpi{1, 1.f, (float)p.sigma1, (float)p.gamma, 1.f}, st));
+  // u <- c u + sigma2 (Phi xhat - y), ||u||^2
+  GBRI_TRY(launch_pad(P, S->xhat, nullptr, st));
+  GBRI_TRY(fft_forward(P, st));
+  EpiPD1 e1{S->u, S->yp, S->sc + SC_C, S->partials, (float)p.sigma2, KahanF{}};
+  GBRI_TRY(launch_degrid(P, P->grid, e1, st));
+  launch_begin(GBRI_K_OTHER, st);
+  k_ball_scalar<<<1, 256, 0, st>>>(S->partials, P->degrid_blocks, p.eps, p.sigma2, false, S->sc);
+  GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+  // Phi^dagger u (scaled by c in the update)
+  GBRI_TRY(launch_grid(P, SrcPlan{S->u}, st));
+  GBRI_TRY(fft_inverse(P, st));
+  // Psi z1
+  GBRI_TRY(psi_apply(W, S->z1, S->psiz, st));
+  const int ib = std::min(img_blocks(N), S->n_partials / 2);
+  launch_begin(GBRI_K_UPDATE, st);
+  k_pd_update<<<ib, 256, 0, st>>>(P->grid, P->corr, S->psiz, S->x, S->xhat, n, P->K, (float)p.tau, (float)p.theta,
+                                   S->sc, S->partials);
+  GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
+  launch_begin(GBRI_K_OTHER, st);
+  k_rel_change<<<1, 256, 0, st>>>(S->partials, ib, S->sc);
+  return launch_end(GBRI_K_OTHER, st);
+}
+
+int32_t admm_iteration(gbri_solver* S, cudaStream_t st) {
+  gbri_plan* P = S->plan;
+  gbri_wavelet* W = S->wav;
+  const auto& p = S->p;
+  const int n = P->n_side;
+  const int64_t N = (int64_t)n * n;
+  GBRI_TRY(launch_pad(P, S->x, nullptr, st));
+  GBRI_TRY(fft_forward(P, st));
+  EpiADMM1 e1{S->w, S->u, S->yp, S->partials, KahanF{}};
+  GBRI_TRY(launch_degrid(P, P->grid, e1, st));
+  launch_begin(GBRI_K_OTHER, st);
+  k_ball_scalar<<<1, 256, 0, st>>>(S->partials, P->degrid_blocks, p.eps, 1.0, true, S->sc);
+  GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+  GBRI_TRY(launch_grid(P, SrcADMM2{S->w, S->u, S->sc + SC_C, (float)p.varrho}, st));
+  GBRI_TRY(fft_inverse(P, st));
+  const int ib = std::min(img_blocks(N), S->n_partials / 2);
+  launch_begin(GBRI_K_UPDATE, st);
+  k_admm_xt<<<ib, 256, 0, st>>>(P->grid, P->corr, S->x, S->xt, S->xhat /* zbar */, n, P->K, (float)p.rho);
+  GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
+  for (int k = 0; k < p.dualfb_iters; ++k) {
+    GBRI_TRY(psi_adjoint_apply(W, S->xhat, S->z1 /* d */,
+                               DualEpi{1, (float)p.eta, 1.f, (float)p.gamma, (float)(1.0 / p.eta)}, st));
+    GBRI_TRY(psi_apply(W, S->z1, S->psiz, st));
+    const bool last = (k == p.dualfb_iters - 1);
+    launch_begin(GBRI_K_UPDATE, st);
+    k_admm_zbar<<<ib, 256, 0, st>>>(S->xt, S->psiz, S->xhat, S->x, N, last, S->partials);
+    GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
+  }
+  launch_begin(GBRI_K_OTHER, st);
+  k_rel_change<<<1, 256, 0, st>>>(S->partials, ib, S->sc);
+  return launch_end(GBRI_K_OTHER, st);
+}
+
+// ||y - Phi x|| into sc[SC_RES] (uses the plan's visibility scratch)
+int32_t residual(gbri_solver* S, cudaStream_t st) {
+  gbri_plan* P = S->plan;
+  GBRI_TRY(launch_pad(P, S->x, nullptr, st));
+  GBRI_TRY(fft_forward(P, st));
+  if (P->M > 0) GBRI_TRY(launch_degrid(P, P->grid, EpiStorePlan{P->vis_tmp}, st));
+  const int b = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(ceil_div(P->M, 2048), S->n_partials),
+                                                             (int64_t)num_sms() * 4));
+  launch_begin(GBRI_K_OTHER, st);
+  k_residual_partials<<<b, 256, 0, st>>>(P->vis_tmp, S->yp, P->M, S->partials);
+  GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+  launch_begin(GBRI_K_OTHER, st);
+  k_sqrt_sum<<<1, 256, 0, st>>>(S->partials, b, S->sc + SC_RES);
+  return launch_end(GBRI_K_OTHER, st);
+}
+
+// gamma = 1e-3 max|Psi^dagger Phi^dagger y| / ||Phi||^2
+int32_t default_gamma(gbri_solver* S, cudaStream_t st, double* out) {
+  gbri_plan* P = S->plan;
+  const int64_t N = (int64_t)P->n_side * P->n_side;
+  GBRI_TRY(launch_grid(P, SrcPlan{S->yp}, st));
+  GBRI_TRY(fft_inverse(P, st));
+  GBRI_TRY(launch_crop(P, S->psiz, st));
+  GBRI_TRY(psi_adjoint_apply(S->wav, S->psiz, S->z1, DualEpi{0, 0.f, 0.f, 0.f, 0.f}, st));
+  const int64_t tot = N * S->wav->nw;
+  const int b = std::min(img_blocks(tot), S->n_partials);
+  launch_begin(GBRI_K_OTHER, st);
+  k_absmax_partials<<<b, 256, 0, st>>>(S->z1, tot, S->partials);
+  GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+  launch_begin(GBRI_K_OTHER, st);
+  k_max_finish<<<1, 32, 0, st>>>(S->partials, b, S->sc + SC_MAX);
+  GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+  double m = 0;
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(&m, S->sc + SC_MAX, sizeof(double), cudaMemcpyDeviceToHost, st));
+  GBRI_CHECK_CUDA(cudaStreamSynchronize(st));
+  *out = 1e-3 * m / S->p.op_norm_sq;
+  return GBRI_OK;
+}
+
+template <class T>
+int32_t zalloc(T** p, size_t n, cudaStream_t s) {
+  if (n == 0) n = 1;
+  if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    return set_error(GBRI_ENOMEM, "cudaMalloc solver state");
+  }
+  GBRI_CHECK_CUDA(cudaMemsetAsync(*p, 0, n * sizeof(T), s));
+  return GBRI_OK;
+}
+
+int32_t create_solver(gbri_solver* S, const float* d_y, uint32_t flags, cudaStream_t st) {
+  gbri_plan* P = S->plan;
+  const int64_t N = (int64_t)P->n_side * P->n_side;
+  const int64_t M = P->M;
+  const int nw = S->wav->nw;
+  auto& p = S->p;
+  S->n_partials = std::max(std::max(P->degrid_blocks, 2 * img_blocks(N * nw)), 2048);
+  GBRI_TRY(zalloc(&S->partials, (size_t)S->n_partials * 2, st));
+  GBRI_TRY(zalloc(&S->sc, SC_N, st));
+  GBRI_TRY(zalloc(&S->yp, (size_t)M, st));
+  GBRI_TRY(zalloc(&S->u, (size_t)M, st));
+  if (p.algo == GBRI_ALGO_ADMM) GBRI_TRY(zalloc(&S->w, (size_t)M, st));
+  GBRI_TRY(zalloc(&S->x, (size_t)N, st));
+  GBRI_TRY(zalloc(&S->xhat, (size_t)N, st));
+  GBRI_TRY(zalloc(&S->psiz, (size_t)N, st));
+  GBRI_TRY(zalloc(&S->xt, (size_t)N, st));
+  GBRI_TRY(zalloc(&S->z1, (size_t)(N * nw), st));
+  if (M > 0) {
+    if (flags & GBRI_PLAN_ORDER)
+      GBRI_CHECK_CUDA(cudaMemcpyAsync(S->yp, d_y, sizeof(float2) * M, cudaMemcpyDeviceToDevice, st));
+    else
+      GBRI_TRY(gbri_vis_reorder(P, d_y, (float*)S->yp, 1, st));
+  }
+  // resolve defaults
+  if (p.max_iter < 0) return set_error(GBRI_EINVAL, "max_iter < 0");
+  if (!(p.eps > 0)) return set_error(GBRI_EINVAL, "eps must be > 0");
+  if (p.op_norm_sq <= 0) {
+    int32_t it = 0;
+    GBRI_TRY(gbri_op_norm(P, 200, 1e-8, p.seed, &p.op_norm_sq, &it, st));
+  }
+  if (p.tau <= 0) p.tau = 0.49;
+  if (p.sigma1 <= 0) p.sigma1 = 1.0;
+  if (p.sigma2 <= 0) p.sigma2 = 1.0 / p.op_norm_sq;
+  if (p.theta < 0) p.theta = 1.0;
+  if (p.rho <= 0) p.rho = 1.0 / p.op_norm_sq;
+  if (p.varrho <= 0) p.varrho = 1.0;
+  if (p.eta <= 0) p.eta = 1.0;
+  if (p.dualfb_iters <= 0) p.dualfb_iters = 1;
+  if (p.check_every <= 0) p.check_every = 10;
+  if (p.gamma <= 0) GBRI_TRY(default_gamma(S, st, &p.gamma));
+  // x = 0, xhat = 0, duals = 0, c = 0
+  GBRI_CHECK_CUDA(cudaMemsetAsync(S->z1, 0, sizeof(float) * N * nw, st));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(S->psiz, 0, sizeof(float) * N, st));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(S->sc, 0, sizeof(double) * SC_N, st));
+  return GBRI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav, const float* d_y,
+                           const gbri_solve_params* params, uint32_t flags, void* stream) {
+  GBRI_CHECK(out && plan && wav && params && (d_y || plan->M == 0), GBRI_EINVAL, "null argument");
+  *out = nullptr;
+  GBRI_CHECK(wav->n == plan->n_side, GBRI_EINVAL, "wavelet and plan image sizes differ");
+  GBRI_CHECK(params->algo == GBRI_ALGO_PD || params->algo == GBRI_ALGO_ADMM, GBRI_EINVAL, "unknown algo");
+  gbri_solver* S = new (std::nothrow) gbri_solver();
+  GBRI_CHECK(S, GBRI_ENOMEM, "host allocation");
+  S->plan = plan;
+  S->wav = wav;
+  S->p = *params;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t r = create_solver(S, d_y, flags, st);
+  if (r != GBRI_OK) {
+    cudaStreamSynchronize(st);
+    free_solver(S);
+    return r;
+  }
+  *out = S;
+  return GBRI_OK;
+}
+
+int32_t gbri_solver_destroy(gbri_solver* S) {
+  if (S) cudaDeviceSynchronize();
+  free_solver(S);
+  return GBRI_OK;
+}
+
+int32_t gbri_solver_step(gbri_solver* S, int32_t n_iter, void* stream) {
+  GBRI_CHECK(S && n_iter >= 0, GBRI_EINVAL, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int k = 0; k < n_iter; ++k) {
+    GBRI_TRY(S->p.algo == GBRI_ALGO_PD ? pd_iteration(S, st) : admm_iteration(S, st));
+    ++S->iters;
+  }
+  return GBRI_OK;
+}
+
+int32_t gbri_solver_get_x(gbri_solver* S, float* d_x, void* stream) {
+  GBRI_CHECK(S && d_x, GBRI_EINVAL, "null argument");
+  const int64_t N = (int64_t)S->plan->n_side * S->plan->n_side;
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(d_x, S->x, sizeof(float) * N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return GBRI_OK;
+}
+
+int32_t gbri_solver_report(gbri_solver* S, gbri_solve_report* r, void* stream) {
+  GBRI_CHECK(S && r, GBRI_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  GBRI_TRY(residual(S, st));
+  double sc[SC_N];
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(sc, S->sc, sizeof(sc), cudaMemcpyDeviceToHost, st));
+  GBRI_CHECK_CUDA(cudaStreamSynchronize(st));
+  r->iters = S->iters;
+  r->status = GBRI_OK;
+  r->rel_change = S->iters > 0 ? sc[SC_REL] : INFINITY;
+  r->residual_norm = sc[SC_RES];
+  r->op_norm_sq = S->p.op_norm_sq;
+  r->gamma = S->p.gamma;
+  r->ms_total = S->ms_total;
+  return GBRI_OK;
+}
+
+int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const float* d_y, const gbri_solve_params* params,
+                   float* d_x_out, gbri_solve_report* report, uint32_t flags, void* stream) {
+  GBRI_CHECK(d_x_out, GBRI_EINVAL, "null x");
+  gbri_solver* S = nullptr;
+  GBRI_TRY(gbri_solver_create(&S, plan, wav, d_y, params, flags, stream));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  int32_t rc = GBRI_OK;
+  bool converged = false;
+  const int every = S->p.check_every;
+  while (S->iters < S->p.max_iter) {
+    const int k = std::min(every, S->p.max_iter - S->iters);
+    rc = gbri_solver_step(S, k, stream);
+    if (rc != GBRI_OK) break;
+    if (S->p.rel_tol > 0) {
+      double rel = 0;
+      if (cudaMemcpyAsync(&rel, S->sc + SC_REL, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        rc = set_error(GBRI_ECUDA, "convergence read");
+        break;
+      }
+      if (rel < S->p.rel_tol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  cudaEventRecord(e1, st);
+  if (rc == GBRI_OK) rc = gbri_solver_get_x(S, d_x_out, stream);
+  if (rc == GBRI_OK) {
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    S->ms_total = ms;
+    gbri_solve_report r{};
+    rc = gbri_solver_report(S, &r, stream);
+    if (rc == GBRI_OK) {
+      r.status = (S->p.rel_tol > 0 && !converged) ? GBRI_ENOTCONV : GBRI_OK;
+      if (report) *report = r;
+      rc = r.status;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  gbri_solver_destroy(S);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,51 @@
+// SARA wavelet dictionary (Sec. 3.1, Sec. 6.4, Sec. 7.5): Dirac basis plus 2-D
+// separable periodic Daubechies transforms, batched over the bases in each launch.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace gbri {
+
+constexpr int kMaxTaps = 32;   // db16
+constexpr int kMaxBases = 16;
+
+// Filter bank of the non-Dirac bases, passed to the kernels by value.
+struct Filters {
+  float h[kMaxBases][kMaxTaps];
+  float g[kMaxBases][kMaxTaps];
+  int len[kMaxBases];
+  int aidx[kMaxBases];  // position of the basis in the coefficient stack
+};
+
+// How the analysis writes a final coefficient v (already scaled by 1/sqrt(n_w)):
+//   mode 0: out[q] = v
+//   mode 1: out[q] = clip(ca * out[q] + cb * v, [-lim, lim]) * ce   (dual updates of PD / DualFB)
+struct DualEpi {
+  int mode;
+  float ca, cb, lim, ce;
+};
+
+// Daubechies low-pass filter dbN (2N taps, minimum phase, sum = sqrt 2) by
+// spectral factorisation of the Daubechies polynomial (host, long double).
+std::vector<double> daubechies_lowpass(int N);
+
+}  // namespace gbri
+
+struct gbri_wavelet {
+  int n = 0, levels = 0, nw = 0, nb = 0;  // nb = number of non-Dirac bases
+  int dirac_idx = -1;
+  float scale = 1.f;                       // 1 / sqrt(n_w)
+  std::vector<int> orders;
+  gbri::Filters F;
+  float* tmp = nullptr;  // [nb][n][n]
+  float* ll = nullptr;   // [nb][n][n] LL carry (analysis) / reconstruction (synthesis)
+};
+
+namespace gbri {
+// Psi^dagger x with the epilogue applied to every final coefficient of the stack `out` [n_w][n][n].
+int32_t psi_adjoint_apply(gbri_wavelet* w, const float* x, float* out, DualEpi epi, cudaStream_t s);
+// x = Psi alpha (overwrites x).
+int32_t psi_apply(gbri_wavelet* w, const float* alpha, float* x, cudaStream_t s);
+}  // namespace gbri

@@ -1,0 +1,164 @@
+"""GPU parity of Phi / Phi^dagger (through the C ABI) against the FP64 oracle.
+
+Bar: relative L2 error <= 1e-5 per application in FP32 (table mode: both sides
+quantise the coordinates identically in FP64, so the tap indices and weights
+agree exactly up to the FP32 rounding of the table); integer work (quantisation,
+sort) bit-exact.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import measurement as me
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1903_04502_gb300 as g
+    g.library()
+    return g
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def make(n, M, J=4, seed=0, outliers=0.2, weights="uniform"):
+    x = synth.sky(n, 5, 3, seed=seed) + 0.01 * synth.uniform(n * n, seed=seed + 7).reshape(n, n)
+    uvw = synth.uv_coverage(M, seed=seed + 1, outlier_frac=outliers, weights=weights)
+    return x.astype(np.float32), uvw
+
+
+CASES = [  # (n_side, M, J): several tiles, ragged chunk tails
+    (128, 20_000, 4),
+    (64, 5_003, 6),
+    (96, 1_537, 4),
+    (256, 70_001, 4),
+]
+
+
+@pytest.mark.parametrize("n,M,J", CASES)
+def test_phi_and_adjoint_match_oracle(g, n, M, J):
+    x, uvw = make(n, M, J, seed=n + M)
+    geo = me.Geometry(uvw, n, 2, J, 4096)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, J=J, S=4096)
+    y = g.phi(plan, torch.from_numpy(x).cuda()).cpu().numpy()
+    y_ref = me.phi(x.astype(np.float64), geo)
+    assert rel(y, y_ref) <= TOL
+    yin = synth.complex_normal(M, seed=3).astype(np.complex64)
+    xa = g.phi_adjoint(plan, torch.from_numpy(yin).cuda()).cpu().numpy()
+    xa_ref = me.phi_adjoint(yin.astype(np.complex128), geo)
+    assert rel(xa, xa_ref) <= TOL
+
+
+def test_plan_order_and_permutation(g):
+    n, M = 128, 12_345
+    x, uvw = make(n, M)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    perm = plan.permutation().cpu().numpy()
+    assert np.array_equal(np.sort(perm), np.arange(M))
+    xd = torch.from_numpy(x).cuda()
+    y_raw = g.phi(plan, xd).cpu().numpy()
+    y_plan = g.phi(plan, xd, plan_order=True).cpu().numpy()
+    assert np.array_equal(y_plan, y_raw[perm])
+    back = g.vis_reorder(plan, torch.from_numpy(y_plan).cuda(), to_plan=False).cpu().numpy()
+    assert np.array_equal(back, y_raw)
+    # the adjoint in plan order equals the adjoint in caller order
+    yin = synth.complex_normal(M, seed=9).astype(np.complex64)
+    a = g.phi_adjoint(plan, torch.from_numpy(yin).cuda()).cpu().numpy()
+    b = g.phi_adjoint(plan, torch.from_numpy(yin[perm]).cuda(), plan_order=True).cpu().numpy()
+    assert rel(b, a) <= 1e-6
+
+
+def test_sort_is_bit_exact_tile_major(g):
+    """The plan's visibility order is sorted by the (tile, cell) key that the oracle's FP64
+    quantisation gives (integer work: compared exactly)."""
+    n, M, K, S, T = 128, 30_000, 256, 4096, 16
+    _, uvw = make(n, M)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, S=S)
+    perm = plan.permutation().cpu().numpy()
+    kx = me.quantise(uvw[:, 0], K, S)
+    ky = me.quantise(uvw[:, 1], K, S)
+    cx = np.mod(np.floor_divide(kx, S), K)
+    cy = np.mod(np.floor_divide(ky, S), K)
+    key = ((cy // T) * (K // T) + cx // T) * T * T + (cy % T) * T + (cx % T)
+    ks = key[perm]
+    assert np.all(np.diff(ks) >= 0)
+    assert plan.n_chunks >= len(np.unique(key // (T * T)))
+
+
+def test_adjoint_identity_on_gpu(g):
+    n, M = 256, 100_000
+    x, uvw = make(n, M, seed=5)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    y = synth.complex_normal(M, seed=6).astype(np.complex64)
+    px = g.phi(plan, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.complex128)
+    pty = g.phi_adjoint(plan, torch.from_numpy(y).cuda()).cpu().numpy().astype(np.float64)
+    lhs = np.real(np.vdot(px, y.astype(np.complex128)))
+    rhs = np.vdot(x.astype(np.float64), pty)
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_edge_cases(g):
+    n = 64
+    # empty visibility set
+    plan = g.Plan(torch.zeros((0, 4), dtype=torch.float32, device="cuda"), n)
+    x = torch.rand((n, n), device="cuda")
+    assert g.phi(plan, x).numel() == 0
+    assert float(g.phi_adjoint(plan, torch.zeros(0, dtype=torch.complex64, device="cuda")).abs().max()) == 0.0
+    # Nyquist edge (u, v = +-pi wrap), the origin, and a pile-up of identical points in one cell
+    pts = np.array([[np.pi, 0.3, 0, 1], [-np.pi, 0.3, 0, 1], [0.2, np.pi, 0, 0.5], [0.2, -np.pi, 0, 0.5],
+                    [0.0, 0.0, 0, 1.0]], dtype=np.float32)
+    pile = np.tile(np.array([[0.01, -0.02, 0, 0.75]], dtype=np.float32), (3000, 1))
+    uvw = np.concatenate([pts, pile])
+    xs = synth.uniform(n * n, seed=2).reshape(n, n).astype(np.float32)
+    geo = me.Geometry(uvw, n, 2, 4, 4096)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    y = g.phi(plan, torch.from_numpy(xs).cuda()).cpu().numpy()
+    assert rel(y, me.phi(xs.astype(np.float64), geo)) <= TOL
+    assert y[0] == pytest.approx(y[1], rel=1e-6)
+    yin = synth.complex_normal(len(uvw), seed=4).astype(np.complex64)
+    xa = g.phi_adjoint(plan, torch.from_numpy(yin).cuda()).cpu().numpy()
+    assert rel(xa, me.phi_adjoint(yin.astype(np.complex128), geo)) <= TOL
+
+
+def test_invalid_inputs_rejected(g):
+    n = 32
+    bad = np.array([[np.nan, 0, 0, 1]], dtype=np.float32)
+    with pytest.raises(g.GbriError) as e:
+        g.Plan(torch.from_numpy(bad).cuda(), n)
+    assert e.value.code == -6
+    far = np.array([[100.0, 0, 0, 1]], dtype=np.float32)
+    with pytest.raises(g.GbriError):
+        g.Plan(torch.from_numpy(far).cuda(), n)
+    with pytest.raises(g.GbriError):
+        g.Plan(torch.zeros((4, 4), device="cuda"), n, J=5)
+
+
+def test_full_size_sampled_parity(g):
+    """1024^2 image, 2048^2 grid, J = 4, M = 1e7 (the FP32 workload), same launch path as the
+    benchmark: sampled outputs of Phi against the oracle one by one, and the adjoint identity."""
+    cfg = synth.CONFIGS["large"]
+    n, M = cfg["n_side"], cfg["M"]
+    x = synth.sky(n, cfg["n_points"], cfg["n_blobs"], seed=0).astype(np.float32)
+    uvw = synth.uv_coverage(M, seed=1, outlier_frac=cfg["outlier_frac"], weights=cfg["weights"])
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, J=4, S=4096)
+    y = g.phi(plan, torch.from_numpy(x).cuda()).cpu().numpy()
+    idx = np.random.default_rng(0).choice(M, 4000, replace=False)
+    idx = np.concatenate([idx, [0, M - 1]])
+    geo = me.Geometry(uvw[idx], n, 2, 4, 4096)
+    y_ref = me.phi(x.astype(np.float64), geo)
+    assert rel(y[idx], y_ref) <= TOL
+    yin = torch.randn(M, dtype=torch.complex64, device="cuda")
+    pty = g.phi_adjoint(plan, yin).double()
+    lhs = torch.real(torch.vdot(torch.from_numpy(y).cuda().to(torch.complex128), yin.to(torch.complex128)))
+    rhs = torch.dot(torch.from_numpy(x).cuda().double().ravel(), pty.ravel())
+    assert abs(float(lhs - rhs)) <= 1e-5 * abs(float(lhs))

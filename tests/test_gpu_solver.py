@@ -1,0 +1,116 @@
+"""GPU parity of the power method and the solvers (through the C ABI) against the oracle.
+
+Bar: the image after the solver iterations within relative L2 1e-4 of the FP64
+oracle run with the same parameters (||Phi||^2, gamma, eps passed explicitly).
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import measurement as me, solvers as so, wavelets as wv
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1903_04502_gb300 as g
+    g.library()
+    return g
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def problem(n, M, orders, levels, seed=0, npts=5, nblobs=3):
+    x_true = synth.sky(n, npts, nblobs, seed=seed)
+    uvw = synth.uv_coverage(M, seed=seed + 1, outlier_frac=0.2, weights="uniform")
+    geo = me.Geometry(uvw, n, 2, 4, 4096)
+    ops = (lambda v: me.phi(v, geo), lambda v: me.phi_adjoint(v, geo),
+           lambda a: wv.psi(a, orders, levels), lambda v: wv.psi_adjoint(v, orders, levels))
+    y0 = ops[0](x_true)
+    sigma = 10 ** (-30 / 20) * np.linalg.norm(y0) / np.sqrt(M)
+    y = (y0 + sigma * synth.complex_normal(M, seed=seed + 2)).astype(np.complex64)
+    return uvw, geo, ops, y, so.epsilon_from_sigma(sigma, M)
+
+
+def test_power_method_matches_oracle(g):
+    n, M = 64, 8000
+    uvw, geo, ops, y, eps = problem(n, M, (0, 1), 2)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    val, it = g.op_norm(plan, 200, 1e-8, seed=7)
+    ref, rit = so.power_iteration(ops[0], ops[1], (n, n), seed=7)
+    assert val == pytest.approx(ref, rel=1e-5)
+
+
+@pytest.mark.parametrize("algo,iters", [("pd", 100), ("admm", 60)])
+def test_solver_iterations_match_oracle(g, algo, iters):
+    """Small FP64-plain workload: 128^2 sky, M = 2e4, SARA Dirac + db1..db4, 3 levels."""
+    n, M, orders, L = 128, 20_000, (0, 1, 2, 3, 4), 3
+    uvw, geo, ops, y, eps = problem(n, M, orders, L)
+    yd = y.astype(np.complex128)
+    opn, _ = so.power_iteration(ops[0], ops[1], (n, n))
+    gamma = so.default_gamma(yd, ops[1], ops[3], opn)
+    if algo == "pd":
+        x_ref, info = so.primal_dual(yd, *ops, so.PDParams(gamma=gamma, op_norm_sq=opn, eps=eps, max_iter=iters))
+        kw = dict(algo=g.ALGO_PD)
+    else:
+        x_ref, info = so.admm(yd, *ops, so.ADMMParams(gamma=gamma, eps=eps, rho=1.0 / opn, max_iter=iters))
+        kw = dict(algo=g.ALGO_ADMM)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    wav = g.Wavelet(n, L, orders)
+    s = g.Solver(plan, wav, torch.from_numpy(y).cuda(), eps=eps, gamma=gamma, op_norm_sq=opn, **kw)
+    s.step(iters)
+    x = s.x().cpu().numpy()
+    assert rel(x, x_ref) <= 1e-4, rel(x, x_ref)
+    r = s.report()
+    assert r["iters"] == iters
+    assert r["rel_change"] == pytest.approx(info["rel_change"], rel=1e-2, abs=1e-7)
+    assert r["residual_norm"] == pytest.approx(np.linalg.norm(yd - ops[0](x.astype(np.float64))), rel=1e-5)
+
+
+def test_default_gamma_and_op_norm_inside_solver(g):
+    n, M, orders, L = 64, 6000, (0, 1, 2), 2
+    uvw, geo, ops, y, eps = problem(n, M, orders, L, seed=3)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    wav = g.Wavelet(n, L, orders)
+    s = g.Solver(plan, wav, torch.from_numpy(y).cuda(), eps=eps, seed=0)
+    r = s.report()
+    opn, _ = so.power_iteration(ops[0], ops[1], (n, n), seed=0)
+    assert r["op_norm_sq"] == pytest.approx(opn, rel=1e-5)
+    gam = so.default_gamma(y.astype(np.complex128), ops[1], ops[3], opn)
+    assert r["gamma"] == pytest.approx(gam, rel=1e-5)
+
+
+def test_solve_converges_and_is_feasible(g):
+    n, M, orders, L = 64, 8000, (0, 1, 2, 3), 3
+    uvw, geo, ops, y, eps = problem(n, M, orders, L, seed=11)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    wav = g.Wavelet(n, L, orders)
+    x, rep = g.solve(plan, wav, torch.from_numpy(y).cuda(), eps=eps, max_iter=3000, rel_tol=1e-5, check_every=20)
+    assert rep["status"] == 0 and rep["iters"] < 3000
+    assert rep["residual_norm"] <= eps * 1.01
+    assert float(x.min()) >= 0.0
+    # the oracle's residual of the GPU image agrees with the library's FP64 norm
+    xr = x.cpu().numpy().astype(np.float64)
+    assert rep["residual_norm"] == pytest.approx(np.linalg.norm(y.astype(np.complex128) - ops[0](xr)), rel=1e-5)
+
+
+def test_dictionary_of_the_fp32_workload_short_run(g):
+    """SARA Dirac + db1..db8, 4 levels, on a 256^2 sky with 1e5 visibilities: 20 PD iterations."""
+    n, M, orders, L = 256, 100_000, tuple(range(9)), 4
+    uvw, geo, ops, y, eps = problem(n, M, orders, L, seed=21, npts=20, nblobs=8)
+    yd = y.astype(np.complex128)
+    opn, _ = so.power_iteration(ops[0], ops[1], (n, n), max_iter=50)
+    gamma = so.default_gamma(yd, ops[1], ops[3], opn)
+    x_ref, _ = so.primal_dual(yd, *ops, so.PDParams(gamma=gamma, op_norm_sq=opn, eps=eps, max_iter=20))
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    wav = g.Wavelet(n, L, orders)
+    s = g.Solver(plan, wav, torch.from_numpy(y).cuda(), eps=eps, gamma=gamma, op_norm_sq=opn)
+    s.step(20)
+    assert rel(s.x().cpu().numpy(), x_ref) <= 1e-4
