@@ -8,6 +8,160 @@
 
 namespace gbri {
 
+// Degridding (G then W, Sec. 2): for every visibility of every chunk,
+//   v = w * sum_{t'} wy[t'] sum_t wx[t] grid[row(t')][col(t)]
+// with the grid read through the read-only path and the kernel table in shared
+// memory; `Epi` consumes (plan position, v).  Persistent blocks stride over chunks.
+template <int J, class Epi>
+__global__ void __launch_bounds__(kThreads) k_degrid(VisGeom geo, const float2* __restrict__ grid, Epi epi) {
+  extern __shared__ float4 smem_dg[];
+  float* sw = reinterpret_cast<float*>(smem_dg);
+  const int S = 1 << geo.log2S;
+  copy_table_to_smem(sw, geo.wtab, S * J);
+  __syncthreads();
+  const int K = geo.K;
+  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
+    const int4 ch = geo.chunks[c];
+    const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
+    const int ox = tx * kTile - (J / 2 - 1), oy = ty * kTile - (J / 2 - 1);
+    for (int i = threadIdx.x; i < ch.z; i += blockDim.x) {
+      const int pos = ch.y + i;
+      const uint2 m = geo.meta[pos];
+      const int lx = m.x & 0xffff, ly = m.x >> 16;
+      const int cx = ox + (lx >> geo.log2S), cy = oy + (ly >> geo.log2S);
+      float wx[J], wy[J];
+      load_taps<J>(sw, lx & (S - 1), wx);
+      load_taps<J>(sw, ly & (S - 1), wy);
+      int col[J];
+#pragma unroll
+      for (int t = 0; t < J; ++t) col[t] = wrapK(cx + t, K);
+      float ar = 0.f, ai = 0.f;
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp) {
+        const float2* gr = grid + (size_t)wrapK(cy + tp, K) * K;
+        float rr = 0.f, ri = 0.f;
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+          const float2 g = __ldg(gr + col[t]);
+          rr = fmaf(wx[t], g.x, rr);
+          ri = fmaf(wx[t], g.y, ri);
+        }
+        ar = fmaf(wy[tp], rr, ar);
+        ai = fmaf(wy[tp], ri, ai);
+      }
+      const float w = __uint_as_float(m.y);
+      epi(pos, make_float2(w * ar, w * ai));
+    }
+  }
+  epi.finish();
+}
+
+// Gridding (W^T then G^T, Sec. 2): every visibility of a chunk adds
+// w * wy[t'] * wx[t] * v to its J x J cells in a shared (T+J-1)^2 accumulator
+// tile; the tile is then flushed to the global grid with one vector atomic per
+// non-zero cell.  `Src` gives the visibility value at a plan position.
+template <int J, class Src>
+__global__ void __launch_bounds__(kThreads) k_grid(VisGeom geo, float2* __restrict__ grid, Src src) {
+  extern __shared__ float4 smem_gr[];
+  constexpr int P = kTile + J - 1;
+  const int S = 1 << geo.log2S;
+  float* sw = reinterpret_cast<float*>(smem_gr);
+  float2* acc = reinterpret_cast<float2*>(sw + S * J);
+  copy_table_to_smem(sw, geo.wtab, S * J);
+  const int K = geo.K;
+  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int4 ch = geo.chunks[c];
+    const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
+    for (int i = threadIdx.x; i < ch.z; i += blockDim.x) {
+      const int pos = ch.y + i;
+      const uint2 m = geo.meta[pos];
+      const int lx = m.x & 0xffff, ly = m.x >> 16;
+      const int lcx = lx >> geo.log2S, lcy = ly >> geo.log2S;
+      float wx[J], wy[J];
+      load_taps<J>(sw, lx & (S - 1), wx);
+      load_taps<J>(sw, ly & (S - 1), wy);
+      float2 v = src(pos);
+      const float w = __uint_as_float(m.y);
+      v.x *= w;
+      v.y *= w;
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp) {
+        float* rowp = reinterpret_cast<float*>(acc + (lcy + tp) * P + lcx);
+        const float br = wy[tp] * v.x, bi = wy[tp] * v.y;
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+          atomicAdd(rowp + 2 * t, wx[t] * br);
+          atomicAdd(rowp + 2 * t + 1, wx[t] * bi);
+        }
+      }
+    }
+    __syncthreads();
+    const int ox = tx * kTile - (J / 2 - 1), oy = ty * kTile - (J / 2 - 1);
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+      const float2 a = acc[i];
+      if (a.x != 0.f || a.y != 0.f) {
+        const int r = i / P, cc = i - r * P;
+        atomicAdd(grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K), a);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+
+template <int J, class Epi>
+inline void degrid_instance(gbri_plan* p, const float2* grid, Epi epi, cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = degrid_smem(p);
+  if (!attr) {
+    cudaFuncSetAttribute(k_degrid<J, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_degrid<J, Epi><<<p->degrid_blocks, kThreads, smem, s>>>(vis_geom(p), grid, epi);
+}
+
+template <class Epi>
+int32_t launch_degrid(gbri_plan* p, const float2* grid, Epi epi, cudaStream_t s) {
+  launch_begin(GBRI_K_DEGRID, s);
+  if (p->J == 4) degrid_instance<4>(p, grid, epi, s);
+  else degrid_instance<6>(p, grid, epi, s);
+  return launch_end(GBRI_K_DEGRID, s);
+}
+
+template <int J, class Src>
+inline void grid_instance(gbri_plan* p, float2* grid, Src src, cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = grid_smem(p);
+  if (!attr) {
+    cudaFuncSetAttribute(k_grid<J, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_grid<J, Src><<<p->grid_blocks, kThreads, smem, s>>>(vis_geom(p), grid, src);
+}
+
+// Zeroes p->grid, then grids every visibility into it.
+template <class Src>
+int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s) {
+  GBRI_CHECK_CUDA(cudaMemsetAsync(p->grid, 0, sizeof(float2) * (size_t)p->K * p->K, s));
+  if (p->n_chunks == 0) return GBRI_OK;
+  launch_begin(GBRI_K_GRID, s);
+  if (p->J == 4) grid_instance<4>(p, p->grid, src, s);
+  else grid_instance<6>(p, p->grid, src, s);
+  return launch_end(GBRI_K_GRID, s);
+}
+
+
+// Every visibility kernel is instantiated here and only here.
+template int32_t launch_degrid<EpiStorePlan>(gbri_plan*, const float2*, EpiStorePlan, cudaStream_t);
+template int32_t launch_degrid<EpiStoreRaw>(gbri_plan*, const float2*, EpiStoreRaw, cudaStream_t);
+template int32_t launch_degrid<EpiPD1>(gbri_plan*, const float2*, EpiPD1, cudaStream_t);
+template int32_t launch_degrid<EpiADMM1>(gbri_plan*, const float2*, EpiADMM1, cudaStream_t);
+template int32_t launch_grid<SrcPlan>(gbri_plan*, SrcPlan, cudaStream_t);
+template int32_t launch_grid<SrcRaw>(gbri_plan*, SrcRaw, cudaStream_t);
+template int32_t launch_grid<SrcADMM2>(gbri_plan*, SrcADMM2, cudaStream_t);
+
 namespace {
 
 // Z S: padded[(q - n/2) mod K][(p - n/2) mod K] = corr[p] corr[q] x[q][p] * inv_scale

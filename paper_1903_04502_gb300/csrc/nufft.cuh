@@ -85,108 +85,6 @@ struct VisGeom {
   int n_chunks, K, log2S, nT;
 };
 
-// Degridding (G then W, Sec. 2): for every visibility of every chunk,
-//   v = w * sum_{t'} wy[t'] sum_t wx[t] grid[row(t')][col(t)]
-// with the grid read through the read-only path and the kernel table in shared
-// memory; `Epi` consumes (plan position, v).  Persistent blocks stride over chunks.
-template <int J, class Epi>
-__global__ void __launch_bounds__(kThreads) k_degrid(VisGeom geo, const float2* __restrict__ grid, Epi epi) {
-  extern __shared__ float4 smem_dg[];
-  float* sw = reinterpret_cast<float*>(smem_dg);
-  const int S = 1 << geo.log2S;
-  copy_table_to_smem(sw, geo.wtab, S * J);
-  __syncthreads();
-  const int K = geo.K;
-  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
-    const int4 ch = geo.chunks[c];
-    const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
-    const int ox = tx * kTile - (J / 2 - 1), oy = ty * kTile - (J / 2 - 1);
-    for (int i = threadIdx.x; i < ch.z; i += blockDim.x) {
-      const int pos = ch.y + i;
-      const uint2 m = geo.meta[pos];
-      const int lx = m.x & 0xffff, ly = m.x >> 16;
-      const int cx = ox + (lx >> geo.log2S), cy = oy + (ly >> geo.log2S);
-      float wx[J], wy[J];
-      load_taps<J>(sw, lx & (S - 1), wx);
-      load_taps<J>(sw, ly & (S - 1), wy);
-      int col[J];
-#pragma unroll
-      for (int t = 0; t < J; ++t) col[t] = wrapK(cx + t, K);
-      float ar = 0.f, ai = 0.f;
-#pragma unroll
-      for (int tp = 0; tp < J; ++tp) {
-        const float2* gr = grid + (size_t)wrapK(cy + tp, K) * K;
-        float rr = 0.f, ri = 0.f;
-#pragma unroll
-        for (int t = 0; t < J; ++t) {
-          const float2 g = __ldg(gr + col[t]);
-          rr = fmaf(wx[t], g.x, rr);
-          ri = fmaf(wx[t], g.y, ri);
-        }
-        ar = fmaf(wy[tp], rr, ar);
-        ai = fmaf(wy[tp], ri, ai);
-      }
-      const float w = __uint_as_float(m.y);
-      epi(pos, make_float2(w * ar, w * ai));
-    }
-  }
-  epi.finish();
-}
-
-// Gridding (W^T then G^T, Sec. 2): every visibility of a chunk adds
-// w * wy[t'] * wx[t] * v to its J x J cells in a shared (T+J-1)^2 accumulator
-// tile; the tile is then flushed to the global grid with one vector atomic per
-// non-zero cell.  `Src` gives the visibility value at a plan position.
-template <int J, class Src>
-__global__ void __launch_bounds__(kThreads) k_grid(VisGeom geo, float2* __restrict__ grid, Src src) {
-  extern __shared__ float4 smem_gr[];
-  constexpr int P = kTile + J - 1;
-  const int S = 1 << geo.log2S;
-  float* sw = reinterpret_cast<float*>(smem_gr);
-  float2* acc = reinterpret_cast<float2*>(sw + S * J);
-  copy_table_to_smem(sw, geo.wtab, S * J);
-  const int K = geo.K;
-  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
-    for (int i = threadIdx.x; i < P * P; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-    const int4 ch = geo.chunks[c];
-    const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
-    for (int i = threadIdx.x; i < ch.z; i += blockDim.x) {
-      const int pos = ch.y + i;
-      const uint2 m = geo.meta[pos];
-      const int lx = m.x & 0xffff, ly = m.x >> 16;
-      const int lcx = lx >> geo.log2S, lcy = ly >> geo.log2S;
-      float wx[J], wy[J];
-      load_taps<J>(sw, lx & (S - 1), wx);
-      load_taps<J>(sw, ly & (S - 1), wy);
-      float2 v = src(pos);
-      const float w = __uint_as_float(m.y);
-      v.x *= w;
-      v.y *= w;
-#pragma unroll
-      for (int tp = 0; tp < J; ++tp) {
-        float* rowp = reinterpret_cast<float*>(acc + (lcy + tp) * P + lcx);
-        const float br = wy[tp] * v.x, bi = wy[tp] * v.y;
-#pragma unroll
-        for (int t = 0; t < J; ++t) {
-          atomicAdd(rowp + 2 * t, wx[t] * br);
-          atomicAdd(rowp + 2 * t + 1, wx[t] * bi);
-        }
-      }
-    }
-    __syncthreads();
-    const int ox = tx * kTile - (J / 2 - 1), oy = ty * kTile - (J / 2 - 1);
-    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
-      const float2 a = acc[i];
-      if (a.x != 0.f || a.y != 0.f) {
-        const int r = i / P, cc = i - r * P;
-        atomicAdd(grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K), a);
-      }
-    }
-    __syncthreads();
-  }
-}
-
 inline size_t degrid_smem(const gbri_plan* p) { return (size_t)p->S * p->J * sizeof(float); }
 inline size_t grid_smem(const gbri_plan* p) {
   const int P = kTile + p->J - 1;
@@ -227,47 +125,69 @@ struct SrcRaw {
   __device__ __forceinline__ float2 operator()(int pos) const { return y[perm[pos]]; }
 };
 
-// ---- launch helpers -------------------------------------------------------------
-template <int J, class Epi>
-inline void degrid_instance(gbri_plan* p, const float2* grid, Epi epi, cudaStream_t s) {
-  static bool attr = false;
-  const size_t smem = degrid_smem(p);
-  if (!attr) {
-    cudaFuncSetAttribute(k_degrid<J, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
+// Solver epilogues (fused dual updates; see solver.cu for the algebra).
+struct EpiPD1 {
+  float2* u;
+  const float2* y;
+  const double* c;
+  double* partials;
+  float sigma2;
+  KahanF acc;
+  __device__ __forceinline__ void operator()(int pos, float2 phi) {
+    const float cc = (float)*c;  // broadcast load, cached
+    const float2 uo = u[pos], yy = y[pos];
+    const float2 un = make_float2(fmaf(cc, uo.x, sigma2 * (phi.x - yy.x)), fmaf(cc, uo.y, sigma2 * (phi.y - yy.y)));
+    u[pos] = un;
+    acc.add(fmaf(un.x, un.x, un.y * un.y));
   }
-  k_degrid<J, Epi><<<p->degrid_blocks, kThreads, smem, s>>>(vis_geom(p), grid, epi);
-}
+  __device__ __forceinline__ void finish() {
+    __shared__ double sh[40];
+    const double v = block_sum(acc.value(), sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+};
 
+struct EpiADMM1 {  // w = Phi x + s - y, partial ||w||^2
+  float2* w;
+  const float2* sv;
+  const float2* y;
+  double* partials;
+  KahanF acc;
+  __device__ __forceinline__ void operator()(int pos, float2 v) {
+    const float2 a = sv[pos], b = y[pos];
+    const float2 r = make_float2(v.x + a.x - b.x, v.y + a.y - b.y);
+    w[pos] = r;
+    acc.add(fmaf(r.x, r.x, r.y * r.y));
+  }
+  __device__ __forceinline__ void finish() {
+    __shared__ double sh[40];
+    const double v = block_sum(acc.value(), sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+};
+
+struct SrcADMM2 {  // s+ = s + varrho((1 - rho_b) w - s); source q = (1 - rho_b) w - s + s+
+  const float2* w;
+  float2* sv;
+  const double* rho_b;
+  float varrho;
+  __device__ __forceinline__ float2 operator()(int pos) const {
+    const float one_m = (float)(1.0 - *rho_b);
+    const float2 ww = w[pos], so = sv[pos];
+    const float2 pw = make_float2(one_m * ww.x, one_m * ww.y);
+    const float2 sn = make_float2(fmaf(varrho, pw.x - so.x, so.x), fmaf(varrho, pw.y - so.y, so.y));
+    sv[pos] = sn;
+    return make_float2(pw.x - so.x + sn.x, pw.y - so.y + sn.y);
+  }
+};
+
+// ---- launch helpers (defined in nufft.cu with explicit instantiations, so that each
+// kernel template is instantiated in exactly one translation unit) ----------------
 template <class Epi>
-inline int32_t launch_degrid(gbri_plan* p, const float2* grid, Epi epi, cudaStream_t s) {
-  launch_begin(GBRI_K_DEGRID, s);
-  if (p->J == 4) degrid_instance<4>(p, grid, epi, s);
-  else degrid_instance<6>(p, grid, epi, s);
-  return launch_end(GBRI_K_DEGRID, s);
-}
-
-template <int J, class Src>
-inline void grid_instance(gbri_plan* p, float2* grid, Src src, cudaStream_t s) {
-  static bool attr = false;
-  const size_t smem = grid_smem(p);
-  if (!attr) {
-    cudaFuncSetAttribute(k_grid<J, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  k_grid<J, Src><<<p->grid_blocks, kThreads, smem, s>>>(vis_geom(p), grid, src);
-}
-
+int32_t launch_degrid(gbri_plan* p, const float2* grid, Epi epi, cudaStream_t s);
 // Zeroes p->grid, then grids every visibility into it.
 template <class Src>
-inline int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s) {
-  GBRI_CHECK_CUDA(cudaMemsetAsync(p->grid, 0, sizeof(float2) * (size_t)p->K * p->K, s));
-  if (p->n_chunks == 0) return GBRI_OK;
-  launch_begin(GBRI_K_GRID, s);
-  if (p->J == 4) grid_instance<4>(p, p->grid, src, s);
-  else grid_instance<6>(p, p->grid, src, s);
-  return launch_end(GBRI_K_GRID, s);
-}
+int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s);
 
 // Z S x into p->padded; optional extra scaling by *d_scale (device, may be null).
 int32_t launch_pad(gbri_plan* p, const float* x, const double* d_inv_scale, cudaStream_t s);

@@ -33,61 +33,6 @@ namespace {
 
 enum { SC_C = 0, SC_DIST = 1, SC_REL = 2, SC_XN = 3, SC_RES = 4, SC_MAX = 5, SC_N = 16 };
 
-struct EpiPD1 {
-  float2* u;
-  const float2* y;
-  const double* c;
-  double* partials;
-  float sigma2;
-  KahanF acc;
-  __device__ __forceinline__ void operator()(int pos, float2 phi) {
-    const float cc = (float)*c;  // broadcast load, cached
-    const float2 uo = u[pos], yy = y[pos];
-    const float2 un = make_float2(fmaf(cc, uo.x, sigma2 * (phi.x - yy.x)), fmaf(cc, uo.y, sigma2 * (phi.y - yy.y)));
-    u[pos] = un;
-    acc.add(fmaf(un.x, un.x, un.y * un.y));
-  }
-  __device__ __forceinline__ void finish() {
-    __shared__ double sh[40];
-    const double v = block_sum(acc.value(), sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = v;
-  }
-};
-
-struct EpiADMM1 {  // w = Phi x + s - y, partial ||w||^2
-  float2* w;
-  const float2* sv;
-  const float2* y;
-  double* partials;
-  KahanF acc;
-  __device__ __forceinline__ void operator()(int pos, float2 v) {
-    const float2 a = sv[pos], b = y[pos];
-    const float2 r = make_float2(v.x + a.x - b.x, v.y + a.y - b.y);
-    w[pos] = r;
-    acc.add(fmaf(r.x, r.x, r.y * r.y));
-  }
-  __device__ __forceinline__ void finish() {
-    __shared__ double sh[40];
-    const double v = block_sum(acc.value(), sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = v;
-  }
-};
-
-struct SrcADMM2 {  // s+ = s + varrho((1 - rho_b) w - s); source q = (1 - rho_b) w - s + s+
-  const float2* w;
-  float2* sv;
-  const double* rho_b;
-  float varrho;
-  __device__ __forceinline__ float2 operator()(int pos) const {
-    const float one_m = (float)(1.0 - *rho_b);
-    const float2 ww = w[pos], so = sv[pos];
-    const float2 pw = make_float2(one_m * ww.x, one_m * ww.y);
-    const float2 sn = make_float2(fmaf(varrho, pw.x - so.x, so.x), fmaf(varrho, pw.y - so.y, so.y));
-    sv[pos] = sn;
-    return make_float2(pw.x - so.x + sn.x, pw.y - so.y + sn.y);
-  }
-};
-
 // c = 1 - min(1, eps / (||u|| / sigma2))  (PD)   or   rho_b = min(1, eps / ||w||)  (ADMM, sigma2 = 1, want_rho)
 __global__ void k_ball_scalar(const double* __restrict__ partials, int n, double eps, double sigma2, bool want_rho,
                               double* __restrict__ sc) {
