@@ -83,8 +83,8 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* desc, const floa
                          void* stream);
 int32_t gbri_plan_destroy(gbri_plan* plan);
 
-/* Plan facts: K, M, number of work chunks, device bytes held. Any pointer may be NULL. */
-int32_t gbri_plan_info(const gbri_plan* plan, int64_t* K, int64_t* M, int64_t* n_chunks,
+/* Plan facts: K, M, number of non-empty 16 x 16 grid tiles, device bytes held. Any pointer may be NULL. */
+int32_t gbri_plan_info(const gbri_plan* plan, int64_t* K, int64_t* M, int64_t* n_tiles,
                        int64_t* device_bytes);
 
 /* Copy the plan's permutation (plan position -> caller's visibility index) to d_perm [M] int32. */

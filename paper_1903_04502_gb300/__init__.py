@@ -68,7 +68,7 @@ class Plan:
         self._h = h
         K, M, nc, nb = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
         _lib.check(lib.gbri_plan_info(h, C.byref(K), C.byref(M), C.byref(nc), C.byref(nb)))
-        self.K, self.n_chunks, self.device_bytes = K.value, nc.value, nb.value
+        self.K, self.n_tiles, self.device_bytes = K.value, nc.value, nb.value
 
     @property
     def handle(self):

@@ -6,8 +6,9 @@
 //                      fixed-point coordinates (cell-in-tile * S + fraction),
 //                      .y = weight bits (float).  8 bytes per visibility.
 //   perm   [M] int32   plan position -> caller's visibility index.
-//   chunks [C] int4    {tile, first plan position, count, 0}; a chunk holds at
-//                      most kChunk visibilities of one T x T tile.
+//   cell_off [K*K+1]   plan positions of each grid cell's visibilities, cells in
+//                      tile-major order (tile, row in tile, column in tile).
+//   work   [W] int32   non-empty tiles, heaviest first (persistent-block work list).
 //   wtab   [S][J] f32  tap weights by fractional offset f = k~ mod S: entry t is
 //                      table[|f + (J/2 - 1 - t) S|] (Sec. 8.1 zeroth-order table,
 //                      re-indexed so one visibility reads one row per axis).
@@ -25,8 +26,7 @@
 namespace gbri {
 
 constexpr int kTile = 16;      // grid tile side in cells (T * S <= 65536 keeps 16-bit local coords)
-constexpr int kChunk = 1024;   // visibilities per work chunk
-constexpr int kThreads = 256;  // threads per block of the visibility kernels
+constexpr int kThreads = 256;  // threads per block of the visibility kernels: one per cell of a tile
 
 }  // namespace gbri
 
@@ -36,8 +36,9 @@ struct gbri_plan {
   int64_t M = 0;
   uint2* meta = nullptr;
   int32_t* perm = nullptr;
-  int4* chunks = nullptr;
-  int64_t n_chunks = 0;
+  int32_t* cell_off = nullptr;
+  int32_t* work = nullptr;
+  int64_t n_work = 0;
   float* wtab = nullptr;
   float* corr = nullptr;
   float2* padded = nullptr;
@@ -80,23 +81,28 @@ __device__ __forceinline__ void copy_table_to_smem(float* sw, const float* __res
 
 struct VisGeom {
   const uint2* __restrict__ meta;
-  const int4* __restrict__ chunks;
+  const int32_t* __restrict__ cell_off;
+  const int32_t* __restrict__ work;
   const float* __restrict__ wtab;
-  int n_chunks, K, log2S, nT;
+  int n_work, K, log2S, nT;
 };
 
 inline size_t degrid_smem(const gbri_plan* p) { return (size_t)p->S * p->J * sizeof(float); }
+// gridding accumulator: (T + J - 1) rows, planar re / im, row pitch kAccPitch (== 16 mod 32
+// so that the two tile rows of a warp fall on disjoint banks)
+constexpr int kAccPitch = 48;
 inline size_t grid_smem(const gbri_plan* p) {
   const int P = kTile + p->J - 1;
-  return (size_t)p->S * p->J * sizeof(float) + (size_t)P * P * sizeof(float2);
+  return (size_t)p->S * p->J * sizeof(float) + (size_t)2 * P * kAccPitch * sizeof(float);
 }
 
 inline VisGeom vis_geom(const gbri_plan* p) {
   VisGeom g;
   g.meta = p->meta;
-  g.chunks = p->chunks;
+  g.cell_off = p->cell_off;
+  g.work = p->work;
   g.wtab = p->wtab;
-  g.n_chunks = (int)p->n_chunks;
+  g.n_work = (int)p->n_work;
   g.K = p->K;
   g.log2S = p->log2S;
   g.nT = p->nT;

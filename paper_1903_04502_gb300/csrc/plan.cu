@@ -7,6 +7,7 @@
 // standard one): g(t) = I0(beta sqrt(1 - (2t/J)^2)) / I0(beta) for |t| < J/2,
 // 0 otherwise; its continuous Fourier transform is
 // ghat(nu) = J sinh(sqrt(beta^2 - (pi J nu)^2)) / (I0(beta) sqrt(beta^2 - (pi J nu)^2)).
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -197,7 +198,8 @@ void destroy_plan(gbri_plan* p) {
   if (!p) return;
   cudaFree(p->meta);
   cudaFree(p->perm);
-  cudaFree(p->chunks);
+  cudaFree(p->cell_off);
+  cudaFree(p->work);
   cudaFree(p->wtab);
   cudaFree(p->corr);
   cudaFree(p->padded);
@@ -243,17 +245,18 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   GBRI_CHECK_CUDA(cudaMemsetAsync(p->padded, 0, sizeof(float2) * cells, s));
 
   // work arrays for the sort
-  int32_t *key = nullptr, *counts = nullptr, *offsets = nullptr, *err = nullptr, *starts = nullptr;
+  int32_t *key = nullptr, *counts = nullptr, *err = nullptr, *starts = nullptr;
+  int32_t*& offsets = p->cell_off;  // kept: per-cell visibility ranges
   uint32_t* packed = nullptr;
   float* wt = nullptr;
   int32_t st = GBRI_OK;
   auto cleanup = [&]() {
-    cudaFree(key); cudaFree(counts); cudaFree(offsets); cudaFree(err); cudaFree(packed); cudaFree(wt);
+    cudaFree(key); cudaFree(counts); cudaFree(err); cudaFree(packed); cudaFree(wt);
     cudaFree(starts);
   };
   if ((st = dmalloc(&key, (size_t)M, nullptr)) || (st = dmalloc(&packed, (size_t)M, nullptr)) ||
       (st = dmalloc(&wt, (size_t)M, nullptr)) || (st = dmalloc(&counts, (size_t)cells, nullptr)) ||
-      (st = dmalloc(&offsets, (size_t)cells + 1, nullptr)) || (st = dmalloc(&err, 1, nullptr)) ||
+      (st = dmalloc(&offsets, (size_t)cells + 1, &p->device_bytes)) || (st = dmalloc(&err, 1, nullptr)) ||
       (st = dmalloc(&starts, (size_t)n_tiles + 1, nullptr))) {
     cleanup();
     return st;
@@ -296,23 +299,23 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   cleanup();
   if (st != GBRI_OK) return st;
 
-  // work chunks: at most kChunk visibilities of one tile each (built on the host)
-  std::vector<int4> ch;
-  for (int t = 0; t < n_tiles; ++t) {
-    const int a = hst[t], b = hst[t + 1];
-    for (int c = a; c < b; c += kChunk) ch.push_back(make_int4(t, c, std::min(kChunk, b - c), 0));
-  }
-  p->n_chunks = (int64_t)ch.size();
-  GBRI_TRY(dmalloc(&p->chunks, ch.size(), &p->device_bytes));
-  if (!ch.empty())
-    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  // work list: non-empty tiles, heaviest first (built on the host)
+  std::vector<int32_t> order;
+  for (int t = 0; t < n_tiles; ++t)
+    if (hst[t + 1] > hst[t]) order.push_back(t);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return hst[a + 1] - hst[a] > hst[b + 1] - hst[b]; });
+  p->n_work = (int64_t)order.size();
+  GBRI_TRY(dmalloc(&p->work, order.size(), &p->device_bytes));
+  if (!order.empty())
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->work, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
 
   // persistent grid sizes
   const int sms = num_sms();
-  const int per_sm_dg = std::max(1, (int)((200 * 1024) / (degrid_smem(p) + 1024)));
-  const int per_sm_gr = std::max(1, (int)((200 * 1024) / (grid_smem(p) + 1024)));
-  p->degrid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_dg, 8)));
-  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_gr, 8)));
+  const int per_sm_dg = std::max(1, (int)((227 * 1024) / (degrid_smem(p) + 1024)));
+  const int per_sm_gr = std::max(1, (int)((227 * 1024) / (grid_smem(p) + 1024)));
+  p->degrid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_work, (int64_t)sms * std::min(per_sm_dg, 8)));
+  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_work, (int64_t)sms * std::min(per_sm_gr, 8)));
   p->n_partials = std::max(p->degrid_blocks, 1024);
   GBRI_TRY(dmalloc(&p->partials, (size_t)p->n_partials * 4, &p->device_bytes));
   GBRI_TRY(dmalloc(&p->scalars, 64, &p->device_bytes));
@@ -375,11 +378,11 @@ int32_t gbri_plan_destroy(gbri_plan* p) {
   return GBRI_OK;
 }
 
-int32_t gbri_plan_info(const gbri_plan* p, int64_t* K, int64_t* M, int64_t* n_chunks, int64_t* bytes) {
+int32_t gbri_plan_info(const gbri_plan* p, int64_t* K, int64_t* M, int64_t* n_tiles, int64_t* bytes) {
   GBRI_CHECK(p, GBRI_EINVAL, "null plan");
   if (K) *K = p->K;
   if (M) *M = p->M;
-  if (n_chunks) *n_chunks = p->n_chunks;
+  if (n_tiles) *n_tiles = p->n_work;
   if (bytes) *bytes = p->device_bytes;
   return GBRI_OK;
 }
