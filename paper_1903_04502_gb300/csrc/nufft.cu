@@ -8,52 +8,55 @@
 
 namespace gbri {
 
-// Degridding (G then W, Sec. 2), one thread per base grid cell of a 16 x 16 tile.
-// The thread loads the J x J patch of the grid that every visibility of its cell
-// touches into registers once, then for each of its visibilities computes
-//   v = w * sum_{t'} wy[t'] sum_t wx[t] patch[t'][t]
-// with the two J-tap weight rows read from the shared-memory table.  A warp's
-// patch loads are row-contiguous (coalesced).  `Epi` consumes (plan position, v).
-// Persistent blocks stride over the non-empty tiles, heaviest first.
+// Degridding (G then W, Sec. 2).  A block takes one chunk (<= kChunk visibilities
+// of one 16 x 16 tile), copies the tile's (T + J - 1)^2 grid window into shared
+// memory and then gives one thread per visibility (coalesced metadata and
+// epilogue streams):
+//   v = w * sum_{t'} wy[t'] sum_t wx[t] win[cy + t'][cx + t]
+// with the two J-tap weight rows read from the shared-memory table.  Within a
+// tile the plan orders visibilities rank-major (the first visibility of every
+// cell, then the second, ...), so the lanes of a warp read distinct, row-adjacent
+// cells.  `Epi` consumes (plan position, v).  Persistent blocks stride over chunks.
 template <int J, class Epi>
 __global__ void __launch_bounds__(kThreads) k_degrid(VisGeom geo, const float2* __restrict__ grid, Epi epi) {
   extern __shared__ float4 smem_dg[];
+  constexpr int P = kTile + J - 1;
   float* sw = reinterpret_cast<float*>(smem_dg);
   const int S = 1 << geo.log2S;
+  float2* win = reinterpret_cast<float2*>(sw + S * J);
   copy_table_to_smem(sw, geo.wtab, S * J);
-  __syncthreads();
   const int K = geo.K;
-  const int lcy = threadIdx.x >> 4, lcx = threadIdx.x & 15;
-  for (int wi = blockIdx.x; wi < geo.n_work; wi += gridDim.x) {
-    const int tile = geo.work[wi];
-    const int cell = tile * (kTile * kTile) + threadIdx.x;
-    const int beg = geo.cell_off[cell], end = geo.cell_off[cell + 1];
-    if (beg >= end) continue;
-    const int ty = tile / geo.nT, tx = tile - ty * geo.nT;
-    const int cx = tx * kTile + lcx - (J / 2 - 1), cy = ty * kTile + lcy - (J / 2 - 1);
-    int col[J];
-#pragma unroll
-    for (int t = 0; t < J; ++t) col[t] = wrapK(cx + t, K);
-    float2 pt[J][J];
-#pragma unroll
-    for (int tp = 0; tp < J; ++tp) {
-      const float2* gr = grid + (size_t)wrapK(cy + tp, K) * K;
-#pragma unroll
-      for (int t = 0; t < J; ++t) pt[tp][t] = __ldg(gr + col[t]);
+  int cur_tile = -1;
+  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
+    const int4 ch = geo.chunks[c];
+    if (ch.x != cur_tile) {
+      __syncthreads();
+      const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
+      const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
+      for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int r = i / P, cc = i - r * P;
+        win[r * kWinPitch + cc] = __ldg(grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K));
+      }
+      cur_tile = ch.x;
+      __syncthreads();
     }
-    for (int pos = beg; pos < end; ++pos) {
+    for (int i = threadIdx.x; i < ch.z; i += blockDim.x) {
+      const int pos = ch.y + i;
       const uint2 m = geo.meta[pos];
+      const int lx = m.x & 0xffff, ly = m.x >> 16;
       float wx[J], wy[J];
-      load_taps<J>(sw, (m.x & 0xffff) & (S - 1), wx);
-      load_taps<J>(sw, (m.x >> 16) & (S - 1), wy);
+      load_taps<J>(sw, lx & (S - 1), wx);
+      load_taps<J>(sw, ly & (S - 1), wy);
+      const float2* base = win + (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
       float ar = 0.f, ai = 0.f;
 #pragma unroll
       for (int tp = 0; tp < J; ++tp) {
         float rr = 0.f, ri = 0.f;
 #pragma unroll
         for (int t = 0; t < J; ++t) {
-          rr = fmaf(wx[t], pt[tp][t].x, rr);
-          ri = fmaf(wx[t], pt[tp][t].y, ri);
+          const float2 gv = base[tp * kWinPitch + t];
+          rr = fmaf(wx[t], gv.x, rr);
+          ri = fmaf(wx[t], gv.y, ri);
         }
         ar = fmaf(wy[tp], rr, ar);
         ai = fmaf(wy[tp], ri, ai);
@@ -65,14 +68,13 @@ __global__ void __launch_bounds__(kThreads) k_degrid(VisGeom geo, const float2* 
   epi.finish();
 }
 
-// Gridding (W^T then G^T, Sec. 2), one thread per base grid cell of a tile: the
-// thread sums w * v * wy[t'] wx[t] over its cell's visibilities into a J x J
-// register patch, then adds the patch to a shared (T+J-1)^2 accumulator (planar
-// re / im).  In one atomic instruction the 32 lanes own 32 distinct cells (two
-// tile rows, 16 adjacent columns) at distinct banks: no address or bank conflict.
-// The accumulator is written to the global grid with plain stores for the cells
-// no other tile touches and vector atomics for the shared border.
-// `Src` gives the visibility value at a plan position.
+// Gridding (W^T then G^T, Sec. 2).  A block takes one chunk; each thread takes one
+// visibility (coalesced) and adds w * v * wy[t'] wx[t] to the J x J cells of a
+// shared (T + J - 1)^2 accumulator (planar re / im, row pitch == 16 mod 32).
+// Rank-major order within the tile makes the 32 lanes of an atomic instruction hit
+// 32 distinct cells on distinct banks.  The accumulator is then written to the
+// global grid: plain stores for the cells that no other tile touches when the tile
+// is a single chunk, vector atomics otherwise.  `Src` gives the visibility value.
 template <int J, class Src>
 __global__ void __launch_bounds__(kThreads) k_grid(VisGeom geo, float2* __restrict__ grid, Src src) {
   extern __shared__ float4 smem_gr[];
@@ -83,60 +85,46 @@ __global__ void __launch_bounds__(kThreads) k_grid(VisGeom geo, float2* __restri
   float* acc_im = acc_re + P * kAccPitch;
   copy_table_to_smem(sw, geo.wtab, S * J);
   const int K = geo.K;
-  const int lcy = threadIdx.x >> 4, lcx = threadIdx.x & 15;
-  for (int wi = blockIdx.x; wi < geo.n_work; wi += gridDim.x) {
+  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
     for (int i = threadIdx.x; i < P * kAccPitch; i += blockDim.x) {
       acc_re[i] = 0.f;
       acc_im[i] = 0.f;
     }
     __syncthreads();
-    const int tile = geo.work[wi];
-    const int cell = tile * (kTile * kTile) + threadIdx.x;
-    const int beg = geo.cell_off[cell], end = geo.cell_off[cell + 1];
-    if (beg < end) {
-      float2 pt[J][J];
+    const int4 ch = geo.chunks[c];
+    for (int i = threadIdx.x; i < ch.z; i += blockDim.x) {
+      const int pos = ch.y + i;
+      const uint2 m = geo.meta[pos];
+      const int lx = m.x & 0xffff, ly = m.x >> 16;
+      float wx[J], wy[J];
+      load_taps<J>(sw, lx & (S - 1), wx);
+      load_taps<J>(sw, ly & (S - 1), wy);
+      float2 v = src(pos);
+      const float w = __uint_as_float(m.y);
+      v.x *= w;
+      v.y *= w;
+      const int a0 = (ly >> geo.log2S) * kAccPitch + (lx >> geo.log2S);
 #pragma unroll
-      for (int tp = 0; tp < J; ++tp)
-#pragma unroll
-        for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
-      for (int pos = beg; pos < end; ++pos) {
-        const uint2 m = geo.meta[pos];
-        float wx[J], wy[J];
-        load_taps<J>(sw, (m.x & 0xffff) & (S - 1), wx);
-        load_taps<J>(sw, (m.x >> 16) & (S - 1), wy);
-        float2 v = src(pos);
-        const float w = __uint_as_float(m.y);
-        v.x *= w;
-        v.y *= w;
-#pragma unroll
-        for (int tp = 0; tp < J; ++tp) {
-          const float br = wy[tp] * v.x, bi = wy[tp] * v.y;
-#pragma unroll
-          for (int t = 0; t < J; ++t) {
-            pt[tp][t].x = fmaf(wx[t], br, pt[tp][t].x);
-            pt[tp][t].y = fmaf(wx[t], bi, pt[tp][t].y);
-          }
-        }
-      }
-#pragma unroll
-      for (int tp = 0; tp < J; ++tp)
+      for (int tp = 0; tp < J; ++tp) {
+        const float br = wy[tp] * v.x, bi = wy[tp] * v.y;
 #pragma unroll
         for (int t = 0; t < J; ++t) {
-          const int a = (lcy + tp) * kAccPitch + lcx + t;
-          atomicAdd(acc_re + a, pt[tp][t].x);
-          atomicAdd(acc_im + a, pt[tp][t].y);
+          atomicAdd(acc_re + a0 + tp * kAccPitch + t, wx[t] * br);
+          atomicAdd(acc_im + a0 + tp * kAccPitch + t, wx[t] * bi);
         }
+      }
     }
     __syncthreads();
-    const int ty = tile / geo.nT, tx = tile - ty * geo.nT;
+    const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
     const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
-    // cells of this tile that no neighbouring tile's accumulator covers
-    constexpr int lo = J - 1, hi = kTile;  // accumulator rows/cols [lo, hi) are exclusive
+    // accumulator rows / cols [lo, hi) belong to no other tile's window
+    constexpr int lo = J - 1, hi = kTile;
+    const bool single = ch.w != 0;
     for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
-      const int r = i / P, c = i - r * P;
-      const float2 a = make_float2(acc_re[r * kAccPitch + c], acc_im[r * kAccPitch + c]);
-      float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + c, K);
-      if (r >= lo && r < hi && c >= lo && c < hi) *dst = a;
+      const int r = i / P, cc = i - r * P;
+      const float2 a = make_float2(acc_re[r * kAccPitch + cc], acc_im[r * kAccPitch + cc]);
+      float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      if (single && r >= lo && r < hi && cc >= lo && cc < hi) *dst = a;
       else if (a.x != 0.f || a.y != 0.f) atomicAdd(dst, a);
     }
     __syncthreads();
@@ -177,7 +165,7 @@ inline void grid_instance(gbri_plan* p, float2* grid, Src src, cudaStream_t s) {
 template <class Src>
 int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s) {
   GBRI_CHECK_CUDA(cudaMemsetAsync(p->grid, 0, sizeof(float2) * (size_t)p->K * p->K, s));
-  if (p->n_work == 0) return GBRI_OK;
+  if (p->n_chunks == 0) return GBRI_OK;
   launch_begin(GBRI_K_GRID, s);
   if (p->J == 4) grid_instance<4>(p, p->grid, src, s);
   else grid_instance<6>(p, p->grid, src, s);

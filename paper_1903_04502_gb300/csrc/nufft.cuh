@@ -6,9 +6,10 @@
 //                      fixed-point coordinates (cell-in-tile * S + fraction),
 //                      .y = weight bits (float).  8 bytes per visibility.
 //   perm   [M] int32   plan position -> caller's visibility index.
-//   cell_off [K*K+1]   plan positions of each grid cell's visibilities, cells in
-//                      tile-major order (tile, row in tile, column in tile).
-//   work   [W] int32   non-empty tiles, heaviest first (persistent-block work list).
+//   chunks [C] int4    {tile, first plan position, count, single}: at most kChunk
+//                      visibilities of one T x T tile; single = the tile is one chunk.
+//   Within a tile the visibilities are ordered rank-major: the first visibility of
+//   every non-empty cell (cells in row-major order), then the second, and so on.
 //   wtab   [S][J] f32  tap weights by fractional offset f = k~ mod S: entry t is
 //                      table[|f + (J/2 - 1 - t) S|] (Sec. 8.1 zeroth-order table,
 //                      re-indexed so one visibility reads one row per axis).
@@ -26,7 +27,9 @@
 namespace gbri {
 
 constexpr int kTile = 16;      // grid tile side in cells (T * S <= 65536 keeps 16-bit local coords)
-constexpr int kThreads = 256;  // threads per block of the visibility kernels: one per cell of a tile
+constexpr int kThreads = 256;  // threads per block of the visibility kernels
+constexpr int kChunk = 4096;   // visibilities per work chunk
+constexpr int kWinPitch = 24;  // float2 pitch of the degridding window (== 8 mod 16: two rows per warp on disjoint banks)
 
 }  // namespace gbri
 
@@ -36,9 +39,10 @@ struct gbri_plan {
   int64_t M = 0;
   uint2* meta = nullptr;
   int32_t* perm = nullptr;
-  int32_t* cell_off = nullptr;
-  int32_t* work = nullptr;
-  int64_t n_work = 0;
+  int4* chunks = nullptr;
+  int64_t n_chunks = 0;
+  int64_t n_tiles = 0;  // non-empty tiles
+  int32_t* cell_off = nullptr;  // plan creation only
   float* wtab = nullptr;
   float* corr = nullptr;
   float2* padded = nullptr;
@@ -81,13 +85,14 @@ __device__ __forceinline__ void copy_table_to_smem(float* sw, const float* __res
 
 struct VisGeom {
   const uint2* __restrict__ meta;
-  const int32_t* __restrict__ cell_off;
-  const int32_t* __restrict__ work;
+  const int4* __restrict__ chunks;
   const float* __restrict__ wtab;
-  int n_work, K, log2S, nT;
+  int n_chunks, K, log2S, nT;
 };
 
-inline size_t degrid_smem(const gbri_plan* p) { return (size_t)p->S * p->J * sizeof(float); }
+inline size_t degrid_smem(const gbri_plan* p) {
+  return (size_t)p->S * p->J * sizeof(float) + (size_t)(kTile + p->J - 1) * kWinPitch * sizeof(float2);
+}
 // gridding accumulator: (T + J - 1) rows, planar re / im, row pitch kAccPitch (== 16 mod 32
 // so that the two tile rows of a warp fall on disjoint banks)
 constexpr int kAccPitch = 48;
@@ -99,10 +104,9 @@ inline size_t grid_smem(const gbri_plan* p) {
 inline VisGeom vis_geom(const gbri_plan* p) {
   VisGeom g;
   g.meta = p->meta;
-  g.cell_off = p->cell_off;
-  g.work = p->work;
+  g.chunks = p->chunks;
   g.wtab = p->wtab;
-  g.n_work = (int)p->n_work;
+  g.n_chunks = (int)p->n_chunks;
   g.K = p->K;
   g.log2S = p->log2S;
   g.nT = p->nT;

@@ -96,31 +96,6 @@ __device__ __forceinline__ int pmod(int v, int m) {
   return v < 0 ? v + m : v;
 }
 
-// Row pass of the analysis at block size m (pitch n): out[r][k] = a, out[r][m/2 + k] = d.
-__global__ void k_dwt_rows(const float* __restrict__ in, size_t in_stride, float* __restrict__ out, int m, int n,
-                           const Filters F) {
-  const int j = blockIdx.y;
-  const int L = F.len[j];
-  const int half = m >> 1;
-  const float* src = in + in_stride * j;
-  float* dst = out + (size_t)n * n * j;
-  const int total = m * half;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int r = t / half, k = t - r * half;
-    const float* row = src + (size_t)r * n;
-    float a = 0.f, d = 0.f;
-    for (int i = 0; i < L; ++i) {
-      int idx = 2 * k + i;
-      idx = (idx < m) ? idx : pmod(idx, m);
-      const float v = row[idx];
-      a = fmaf(F.h[j][i], v, a);
-      d = fmaf(F.g[j][i], v, d);
-    }
-    dst[(size_t)r * n + k] = a;
-    dst[(size_t)r * n + half + k] = d;
-  }
-}
-
 __device__ __forceinline__ void emit(float* __restrict__ out, size_t q, float v, const DualEpi& e) {
   if (e.mode == 0) {
     out[q] = v;
@@ -130,76 +105,144 @@ __device__ __forceinline__ void emit(float* __restrict__ out, size_t q, float v,
   }
 }
 
-// Column pass: rows k (a) and m/2 + k (d) of column c.  The LL quadrant goes to
-// the carry buffer unless this is the last level; every other coefficient is final.
-__global__ void k_dwt_cols(const float* __restrict__ tmp, float* __restrict__ ll, float* __restrict__ out, int m,
-                           int n, bool last, float scale, const Filters F, const DualEpi e) {
-  const int j = blockIdx.y;
+constexpr int kAB = 16;                       // analysis: output coefficients per block side (per quadrant)
+constexpr int kATile = 2 * kAB + kMaxTaps - 2;  // input rows / cols a block reads
+constexpr int kSB = 32;                       // synthesis: output samples per block side
+constexpr int kSK = kSB / 2 + kMaxTaps / 2 - 1;  // coefficient rows / cols per half a block reads
+
+// One analysis level at block size m (pitch n) for basis blockIdx.z, fused rows + columns:
+// the block reads the (2*16 + L - 2)^2 input window (periodic), filters its rows into
+// [a | d] halves in shared memory, then its columns, and writes a 16 x 16 block of each
+// quadrant.  The LL quadrant goes to the carry buffer unless this is the last level;
+// every other coefficient is final and goes through the epilogue.
+__global__ void __launch_bounds__(256) k_dwt_level(const float* __restrict__ in, size_t in_stride,
+                                                   float* __restrict__ ll, float* __restrict__ out, int m, int n,
+                                                   bool last, float scale, const Filters F, const DualEpi e) {
+  __shared__ float tin[kATile][kATile + 1];
+  __shared__ float trow[kATile][2 * kAB + 1];
+  const int j = blockIdx.z;
   const int L = F.len[j];
   const int half = m >> 1;
-  const float* src = tmp + (size_t)n * n * j;
-  float* carry = ll + (size_t)n * n * j;
-  float* dst = out + (size_t)n * n * F.aidx[j];
-  const int total = half * m;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int k = t / m, c = t - k * m;
+  const int k0 = blockIdx.y * kAB, l0 = blockIdx.x * kAB;
+  const int T = 2 * kAB + L - 2;
+  const float* src = in + in_stride * j;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int rr = idx / T, cc = idx - rr * T;
+    int gr = 2 * k0 + rr, gc = 2 * l0 + cc;
+    gr = gr < m ? gr : gr % m;
+    gc = gc < m ? gc : gc % m;
+    tin[rr][cc] = src[(size_t)gr * n + gc];
+  }
+  __syncthreads();
+  const float* h = F.h[j];
+  const float* g = F.g[j];
+  for (int idx = threadIdx.x; idx < T * kAB; idx += blockDim.x) {
+    const int rr = idx / kAB, l = idx - rr * kAB;
     float a = 0.f, d = 0.f;
     for (int i = 0; i < L; ++i) {
-      int idx = 2 * k + i;
-      idx = (idx < m) ? idx : pmod(idx, m);
-      const float v = src[(size_t)idx * n + c];
-      a = fmaf(F.h[j][i], v, a);
-      d = fmaf(F.g[j][i], v, d);
+      const float v = tin[rr][2 * l + i];
+      a = fmaf(h[i], v, a);
+      d = fmaf(g[i], v, d);
     }
-    if (c < half && !last) carry[(size_t)k * n + c] = a;
-    else emit(dst, (size_t)k * n + c, scale * a, e);
-    emit(dst, (size_t)(half + k) * n + c, scale * d, e);
+    trow[rr][l] = a;
+    trow[rr][kAB + l] = d;
+  }
+  __syncthreads();
+  float* carry = ll + (size_t)n * n * j;
+  float* dst = out + (size_t)n * n * F.aidx[j];
+  for (int idx = threadIdx.x; idx < kAB * 2 * kAB; idx += blockDim.x) {
+    const int k = idx / (2 * kAB), c = idx - k * (2 * kAB);  // c < 16: low-pass columns, else high-pass
+    const int kk = k0 + k, ll_ = l0 + (c & (kAB - 1));
+    if (kk >= half || ll_ >= half) continue;
+    float lo = 0.f, hi = 0.f;
+    for (int i = 0; i < L; ++i) {
+      const float v = trow[2 * k + i][c];
+      lo = fmaf(h[i], v, lo);
+      hi = fmaf(g[i], v, hi);
+    }
+    const int col = (c < kAB) ? ll_ : half + ll_;
+    if (c < kAB && !last) carry[(size_t)kk * n + col] = lo;
+    else emit(dst, (size_t)kk * n + col, scale * lo, e);
+    emit(dst, (size_t)(half + kk) * n + col, scale * hi, e);
   }
 }
 
-// Synthesis, column pass at block size m: tmp[r][c] = sum over taps i with (r - i) even of
-// h[i] A[k_i][c] + g[i] A[m/2 + k_i][c], k_i = ((r - i)/2) mod (m/2).  A's LL quadrant comes from
-// the reconstruction buffer (from_rec) or from the coefficients (coarsest level).
-__global__ void k_idwt_cols(const float* __restrict__ alpha, const float* __restrict__ rec, bool from_rec,
-                            float* __restrict__ tmp, int m, int n, const Filters F) {
-  const int j = blockIdx.y;
-  const int L = F.len[j];
+// One synthesis level at block size m, fused columns + rows (the transpose of the
+// analysis): the block reconstructs a 32 x 32 window of the m x m block from the
+// 2 x (16 + L/2 - 1) coefficient rows and columns it touches (periodic).  The LL
+// quadrant is read from the reconstruction of the coarser level (from_rec) or from
+// the coefficients.  With sum_bases (finest level) the block loops over every basis,
+// adds the Dirac coefficients and writes scale * sum into x; otherwise it writes the
+// reconstruction of basis blockIdx.z into rec.
+__global__ void __launch_bounds__(256) k_idwt_level(const float* __restrict__ alpha, const float* __restrict__ rec_in,
+                                                    bool from_rec, float* __restrict__ rec_out, int m, int n,
+                                                    int nb, bool sum_bases, const float* __restrict__ dirac,
+                                                    float* __restrict__ x, float scale, const Filters F) {
+  __shared__ float tc[2 * kSK][2 * kSK + 1];  // [a|d rows][a|d cols]
+  __shared__ float tm[kSB][2 * kSK + 1];      // after the column synthesis
   const int half = m >> 1;
-  const float* coef = alpha + (size_t)n * n * F.aidx[j];
-  const float* llsrc = from_rec ? rec + (size_t)n * n * j : coef;
-  float* dst = tmp + (size_t)n * n * j;
-  const int total = m * m;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int r = t / m, c = t - r * m;
-    const float* lo = (c < half) ? llsrc : coef;
-    float v = 0.f;
-    for (int i = r & 1; i < L; i += 2) {
-      const int k = pmod((r - i) >> 1, half);
-      v = fmaf(F.h[j][i], lo[(size_t)k * n + c], v);
-      v = fmaf(F.g[j][i], coef[(size_t)(half + k) * n + c], v);
+  const int r0 = blockIdx.y * kSB, c0 = blockIdx.x * kSB;
+  float accv[kSB * kSB / 256];
+#pragma unroll
+  for (int q = 0; q < kSB * kSB / 256; ++q) accv[q] = 0.f;
+  const int jb = sum_bases ? 0 : blockIdx.z, je = sum_bases ? nb : blockIdx.z + 1;
+  for (int j = jb; j < je; ++j) {
+    const int L = F.len[j];
+    const int KB = kSB / 2 + L / 2 - 1;
+    const int kr_lo = r0 / 2 - L / 2 + 1, kc_lo = c0 / 2 - L / 2 + 1;
+    const float* coef = alpha + (size_t)n * n * F.aidx[j];
+    const float* llsrc = from_rec ? rec_in + (size_t)n * n * j : coef;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 4 * KB * KB; idx += blockDim.x) {
+      const int sr = idx / (2 * KB), sc = idx - sr * (2 * KB);
+      const int pr = sr >= KB, pc = sc >= KB;
+      int kr = (kr_lo + sr - pr * KB) % half; if (kr < 0) kr += half;
+      int kc = (kc_lo + sc - pc * KB) % half; if (kc < 0) kc += half;
+      const float* srcp = (pr == 0 && pc == 0) ? llsrc : coef;
+      tc[pr * KB + (sr - pr * KB)][pc * KB + (sc - pc * KB)] = srcp[(size_t)(pr * half + kr) * n + pc * half + kc];
     }
-    dst[(size_t)r * n + c] = v;
+    __syncthreads();
+    const float* h = F.h[j];
+    const float* g = F.g[j];
+    for (int idx = threadIdx.x; idx < kSB * 2 * KB; idx += blockDim.x) {
+      const int r = idx / (2 * KB), sc = idx - r * (2 * KB);
+      const int R = r0 + r;
+      float v = 0.f;
+      for (int i = R & 1; i < L; i += 2) {
+        const int kq = ((R - i) >> 1) - kr_lo;
+        v = fmaf(h[i], tc[kq][sc], v);
+        v = fmaf(g[i], tc[KB + kq][sc], v);
+      }
+      tm[r][sc] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kSB * kSB / 256; ++q) {
+      const int idx = threadIdx.x + q * 256;
+      const int r = idx / kSB, c = idx - r * kSB;
+      const int C = c0 + c;
+      float v = 0.f;
+      for (int i = C & 1; i < L; i += 2) {
+        const int kq = ((C - i) >> 1) - kc_lo;
+        v = fmaf(h[i], tm[r][kq], v);
+        v = fmaf(g[i], tm[r][KB + kq], v);
+      }
+      accv[q] += v;
+    }
   }
-}
-
-// Synthesis, row pass: rec[r][c] = sum over taps with (c - i) even of h[i] tmp[r][k_i] + g[i] tmp[r][m/2 + k_i].
-__global__ void k_idwt_rows(const float* __restrict__ tmp, float* __restrict__ rec, int m, int n, const Filters F) {
-  const int j = blockIdx.y;
-  const int L = F.len[j];
-  const int half = m >> 1;
-  const float* src = tmp + (size_t)n * n * j;
-  float* dst = rec + (size_t)n * n * j;
-  const int total = m * m;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int r = t / m, c = t - r * m;
-    const float* row = src + (size_t)r * n;
-    float v = 0.f;
-    for (int i = c & 1; i < L; i += 2) {
-      const int k = pmod((c - i) >> 1, half);
-      v = fmaf(F.h[j][i], row[k], v);
-      v = fmaf(F.g[j][i], row[half + k], v);
+#pragma unroll
+  for (int q = 0; q < kSB * kSB / 256; ++q) {
+    const int idx = threadIdx.x + q * 256;
+    const int r = idx / kSB, c = idx - r * kSB;
+    const int R = r0 + r, C = c0 + c;
+    if (R >= m || C >= m) continue;
+    if (sum_bases) {
+      float v = accv[q];
+      if (dirac) v += dirac[(size_t)R * n + C];
+      x[(size_t)R * n + C] = scale * v;
+    } else {
+      rec_out[(size_t)n * n * blockIdx.z + (size_t)R * n + C] = accv[q];
     }
-    dst[(size_t)r * n + c] = v;
   }
 }
 
@@ -209,14 +252,10 @@ __global__ void k_dirac(const float* __restrict__ x, float* __restrict__ out, in
     emit(out, (size_t)q, scale * x[q], e);
 }
 
-// x[q] = scale * (sum_j rec[j][q] + alpha[dirac][q])
-__global__ void k_psi_sum(const float* __restrict__ rec, int nb, const float* __restrict__ dirac, float* __restrict__ x,
-                          int64_t N, float scale) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-    float v = dirac ? dirac[q] : 0.f;
-    for (int j = 0; j < nb; ++j) v += rec[(size_t)N * j + q];
-    x[q] = scale * v;
-  }
+// x[q] = scale * dirac[q] (a dictionary that holds only the Dirac basis)
+__global__ void k_scale_copy(const float* __restrict__ a, float* __restrict__ x, int64_t N, float scale) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
+    x[q] = scale * a[q];
 }
 
 int blocks_for(int64_t work) {
@@ -236,14 +275,12 @@ int32_t psi_adjoint_apply(gbri_wavelet* w, const float* x, float* out, DualEpi e
   if (w->nb == 0) return GBRI_OK;
   for (int lev = 0; lev < w->levels; ++lev) {
     const int m = n >> lev;
+    const int bq = (int)ceil_div(m / 2, kAB);
     const float* in = (lev == 0) ? x : w->ll;
     const size_t in_stride = (lev == 0) ? 0 : (size_t)N;
-    dim3 gr(blocks_for((int64_t)m * m / 2 / std::max(1, w->nb) + 1), w->nb);
     launch_begin(GBRI_K_PSI_ADJ, s);
-    k_dwt_rows<<<gr, 256, 0, s>>>(in, in_stride, w->tmp, m, n, w->F);
-    GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
-    launch_begin(GBRI_K_PSI_ADJ, s);
-    k_dwt_cols<<<gr, 256, 0, s>>>(w->tmp, w->ll, out, m, n, lev == w->levels - 1, w->scale, w->F, epi);
+    k_dwt_level<<<dim3(bq, bq, w->nb), 256, 0, s>>>(in, in_stride, w->ll, out, m, n, lev == w->levels - 1, w->scale,
+                                                    w->F, epi);
     GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
   }
   return GBRI_OK;
@@ -252,20 +289,26 @@ int32_t psi_adjoint_apply(gbri_wavelet* w, const float* x, float* out, DualEpi e
 int32_t psi_apply(gbri_wavelet* w, const float* alpha, float* x, cudaStream_t s) {
   const int n = w->n;
   const int64_t N = (int64_t)n * n;
-  for (int lev = w->levels - 1; lev >= 0 && w->nb > 0; --lev) {
-    const int m = n >> lev;
-    dim3 gr(blocks_for((int64_t)m * m / std::max(1, w->nb) + 1), w->nb);
+  const float* dirac = w->dirac_idx >= 0 ? alpha + (size_t)N * w->dirac_idx : nullptr;
+  if (w->nb == 0) {
     launch_begin(GBRI_K_PSI, s);
-    k_idwt_cols<<<gr, 256, 0, s>>>(alpha, w->ll, lev != w->levels - 1, w->tmp, m, n, w->F);
-    GBRI_TRY(launch_end(GBRI_K_PSI, s));
-    launch_begin(GBRI_K_PSI, s);
-    k_idwt_rows<<<gr, 256, 0, s>>>(w->tmp, w->ll, m, n, w->F);
-    GBRI_TRY(launch_end(GBRI_K_PSI, s));
+    k_scale_copy<<<blocks_for(N), 256, 0, s>>>(dirac, x, N, w->scale);
+    return launch_end(GBRI_K_PSI, s);
   }
-  launch_begin(GBRI_K_PSI, s);
-  k_psi_sum<<<blocks_for(N), 256, 0, s>>>(w->ll, w->nb, w->dirac_idx >= 0 ? alpha + (size_t)N * w->dirac_idx : nullptr,
-                                          x, N, w->scale);
-  return launch_end(GBRI_K_PSI, s);
+  // ping-pong reconstruction buffers: level l reads the coarser level's output
+  float* bufs[2] = {w->ll, w->tmp};
+  int cur = 0;
+  for (int lev = w->levels - 1; lev >= 0; --lev) {
+    const int m = n >> lev;
+    const int bs = (int)ceil_div(m, kSB);
+    const bool finest = (lev == 0);
+    launch_begin(GBRI_K_PSI, s);
+    k_idwt_level<<<dim3(bs, bs, finest ? 1 : w->nb), 256, 0, s>>>(
+        alpha, bufs[cur ^ 1], lev != w->levels - 1, bufs[cur], m, n, w->nb, finest, dirac, x, w->scale, w->F);
+    GBRI_TRY(launch_end(GBRI_K_PSI, s));
+    cur ^= 1;
+  }
+  return GBRI_OK;
 }
 
 }  // namespace gbri
