@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="profiling run: short power method, no end-to-end, operator or CPU legs")
     return ap.parse_args()
 
 
@@ -211,7 +213,7 @@ def run_gbri(args):
     noise = torch.randn(M, dtype=torch.complex64, device=dev, generator=gen)
     y = y0 + sigma * noise
     eps = sigma * np.sqrt(M + 2 * np.sqrt(M))
-    opn, _ = g.op_norm(plan, 100, 1e-6, seed=seed)
+    opn, _ = g.op_norm(plan, 3 if args.quick else 100, 1e-6, seed=seed)
     solver = g.Solver(plan, wav, y, eps=eps, op_norm_sq=opn)
     gamma = solver.report()["gamma"]
 
@@ -265,6 +267,11 @@ def run_gbri(args):
         a2 = alg[other] / (kern[other]["ms_avg"] * 1e-3) / 1e9
         roof["other"] = {"kernel": other, "achieved": a2, "frac": a2 / peak}
 
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "ms_per_step": ms_per, "value": value, "kernels": kern,
+                              "gpu_launches": launches}))
+        return 0
     # end to end through the public API with host buffers: pinned y in, full solve, x out
     y_host = y.cpu().pin_memory()
     x_host = torch.empty((n, n), dtype=torch.float32).pin_memory()

@@ -115,7 +115,7 @@ int32_t gbri_op_norm(gbri_plan* plan, int32_t max_iter, double tol, uint64_t see
                      int32_t* iters, void* stream);
 
 /* ---- SARA wavelet dictionary (Sec. 3.1, Sec. 6.4, Sec. 7.5) --------------- */
-/* db_orders[n_w] (host): 0 = Dirac basis, N in 1..16 = Daubechies dbN (2N taps,
+/* db_orders[n_w] (host): 0 = Dirac basis, N in 1..10 = Daubechies dbN (2N taps,
  * minimum phase, derived in the library by spectral factorisation).  Periodic
  * boundaries, rows then columns per level, Mallat layout, `levels` levels; the
  * stack is scaled by 1/sqrt(n_w) so that Psi Psi^dagger = I.  n_side must be

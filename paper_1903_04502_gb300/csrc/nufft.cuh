@@ -8,8 +8,8 @@
 //   perm   [M] int32   plan position -> caller's visibility index.
 //   chunks [C] int4    {tile, first plan position, count, single}: at most kChunk
 //                      visibilities of one T x T tile; single = the tile is one chunk.
-//   Within a tile the visibilities are ordered rank-major: the first visibility of
-//   every non-empty cell (cells in row-major order), then the second, and so on.
+//   Visibilities are sorted by (tile, cell row, cell column): a cell's visibilities
+//   are contiguous.
 //   wtab   [S][J] f32  tap weights by fractional offset f = k~ mod S: entry t is
 //                      table[|f + (J/2 - 1 - t) S|] (Sec. 8.1 zeroth-order table,
 //                      re-indexed so one visibility reads one row per axis).
@@ -28,7 +28,8 @@ namespace gbri {
 
 constexpr int kTile = 16;      // grid tile side in cells (T * S <= 65536 keeps 16-bit local coords)
 constexpr int kThreads = 256;  // threads per block of the visibility kernels
-constexpr int kChunk = 4096;   // visibilities per work chunk
+constexpr int kChunk = 1024;   // visibilities per work chunk (also the gridding stage size)
+constexpr int kUnroll = 4;     // visibilities in flight per thread in the degridding loop
 constexpr int kWinPitch = 24;  // float2 pitch of the degridding window (== 8 mod 16: two rows per warp on disjoint banks)
 
 }  // namespace gbri
@@ -98,7 +99,8 @@ inline size_t degrid_smem(const gbri_plan* p) {
 constexpr int kAccPitch = 48;
 inline size_t grid_smem(const gbri_plan* p) {
   const int P = kTile + p->J - 1;
-  return (size_t)p->S * p->J * sizeof(float) + (size_t)2 * P * kAccPitch * sizeof(float);
+  return (size_t)p->S * p->J * sizeof(float) + (size_t)2 * P * kAccPitch * sizeof(float) +
+         (size_t)kChunk * (sizeof(uint2) + sizeof(float2)) + 2 * kTile * kTile * sizeof(int);
 }
 
 inline VisGeom vis_geom(const gbri_plan* p) {
@@ -114,15 +116,21 @@ inline VisGeom vis_geom(const gbri_plan* p) {
 }
 
 // ---- epilogues / sources ------------------------------------------------------
+// A degridding epilogue has two phases so that its global loads can be issued
+// together with the metadata loads: Pre p = load(pos); ...; store(pos, p, v).
 struct EpiStorePlan {  // y[pos] = v
   float2* y;
-  __device__ __forceinline__ void operator()(int pos, float2 v) { y[pos] = v; }
+  struct Pre {};
+  __device__ __forceinline__ Pre load(int) const { return Pre{}; }
+  __device__ __forceinline__ void store(int pos, const Pre&, float2 v) { y[pos] = v; }
   __device__ __forceinline__ void finish() {}
 };
 struct EpiStoreRaw {  // y[perm[pos]] = v
   float2* y;
   const int32_t* perm;
-  __device__ __forceinline__ void operator()(int pos, float2 v) { y[perm[pos]] = v; }
+  struct Pre { int dst; };
+  __device__ __forceinline__ Pre load(int pos) const { return Pre{perm[pos]}; }
+  __device__ __forceinline__ void store(int, const Pre& p, float2 v) { y[p.dst] = v; }
   __device__ __forceinline__ void finish() {}
 };
 struct SrcPlan {
@@ -143,10 +151,11 @@ struct EpiPD1 {
   double* partials;
   float sigma2;
   KahanF acc;
-  __device__ __forceinline__ void operator()(int pos, float2 phi) {
+  struct Pre { float2 u, y; };
+  __device__ __forceinline__ Pre load(int pos) const { return Pre{u[pos], y[pos]}; }
+  __device__ __forceinline__ void store(int pos, const Pre& p, float2 phi) {
     const float cc = (float)*c;  // broadcast load, cached
-    const float2 uo = u[pos], yy = y[pos];
-    const float2 un = make_float2(fmaf(cc, uo.x, sigma2 * (phi.x - yy.x)), fmaf(cc, uo.y, sigma2 * (phi.y - yy.y)));
+    const float2 un = make_float2(fmaf(cc, p.u.x, sigma2 * (phi.x - p.y.x)), fmaf(cc, p.u.y, sigma2 * (phi.y - p.y.y)));
     u[pos] = un;
     acc.add(fmaf(un.x, un.x, un.y * un.y));
   }
@@ -163,9 +172,10 @@ struct EpiADMM1 {  // w = Phi x + s - y, partial ||w||^2
   const float2* y;
   double* partials;
   KahanF acc;
-  __device__ __forceinline__ void operator()(int pos, float2 v) {
-    const float2 a = sv[pos], b = y[pos];
-    const float2 r = make_float2(v.x + a.x - b.x, v.y + a.y - b.y);
+  struct Pre { float2 s, y; };
+  __device__ __forceinline__ Pre load(int pos) const { return Pre{sv[pos], y[pos]}; }
+  __device__ __forceinline__ void store(int pos, const Pre& p, float2 v) {
+    const float2 r = make_float2(v.x + p.s.x - p.y.x, v.y + p.s.y - p.y.y);
     w[pos] = r;
     acc.add(fmaf(r.x, r.x, r.y * r.y));
   }

@@ -154,37 +154,6 @@ __global__ void k_scatter(const int32_t* __restrict__ key, const uint32_t* __res
   }
 }
 
-// Within each tile, move the cell-sorted visibilities to rank-major order: all cells'
-// first visibilities (cells in row-major order), then all second visibilities, ...
-// One block per non-empty tile, one thread per cell; a block-wide scan per rank.
-__global__ void __launch_bounds__(256) k_rank_major(const int32_t* __restrict__ cell_off, const int32_t* __restrict__ tiles,
-                                                    const uint2* __restrict__ meta_in, const int32_t* __restrict__ perm_in,
-                                                    uint2* __restrict__ meta_out, int32_t* __restrict__ perm_out) {
-  __shared__ int sh[32];
-  __shared__ int smax;
-  const int tile = tiles[blockIdx.x];
-  const int cell = tile * (kTile * kTile) + threadIdx.x;
-  const int beg = cell_off[cell];
-  const int cnt = cell_off[cell + 1] - beg;
-  const int base0 = cell_off[tile * (kTile * kTile)];
-  if (threadIdx.x == 0) smax = 0;
-  __syncthreads();
-  atomicMax(&smax, cnt);
-  __syncthreads();
-  const int rounds = smax;
-  int base = base0;
-  for (int r = 0; r < rounds; ++r) {
-    const int flag = cnt > r ? 1 : 0;
-    int tot;
-    const int ex = block_exclusive_scan(flag, sh, &tot);
-    if (flag) {
-      meta_out[base + ex] = meta_in[beg + r];
-      perm_out[base + ex] = perm_in[beg + r];
-    }
-    base += tot;
-  }
-}
-
 __global__ void k_tile_starts(const int32_t* __restrict__ offsets, int n_tiles, int cells_per_tile,
                               int32_t* __restrict__ starts) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -329,35 +298,10 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   cleanup();
   if (st != GBRI_OK) return st;
 
-  // rank-major order inside every non-empty tile
   std::vector<int32_t> tiles;
   for (int t = 0; t < n_tiles; ++t)
     if (hst[t + 1] > hst[t]) tiles.push_back(t);
   p->n_tiles = (int64_t)tiles.size();
-  if (!tiles.empty()) {
-    int32_t* dtiles = nullptr;
-    uint2* meta2 = nullptr;
-    int32_t* perm2 = nullptr;
-    if ((st = dmalloc(&dtiles, tiles.size(), nullptr)) || (st = dmalloc(&meta2, (size_t)M, nullptr)) ||
-        (st = dmalloc(&perm2, (size_t)M, nullptr))) {
-      cudaFree(dtiles); cudaFree(meta2); cudaFree(perm2);
-      return st;
-    }
-    cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    launch_begin(GBRI_K_OTHER, s);
-    k_rank_major<<<(unsigned)tiles.size(), kTile * kTile, 0, s>>>(p->cell_off, dtiles, p->meta, p->perm, meta2, perm2);
-    st = launch_end(GBRI_K_OTHER, s);
-    cudaStreamSynchronize(s);
-    cudaFree(dtiles);
-    if (st != GBRI_OK) {
-      cudaFree(meta2); cudaFree(perm2);
-      return st;
-    }
-    cudaFree(p->meta);
-    cudaFree(p->perm);
-    p->meta = meta2;
-    p->perm = perm2;
-  }
   cudaFree(p->cell_off);  // the kernels only need tile ranges (chunks)
   p->cell_off = nullptr;
   p->device_bytes -= (int64_t)(cells + 1) * (int64_t)sizeof(int32_t);

@@ -105,58 +105,72 @@ __device__ __forceinline__ void emit(float* __restrict__ out, size_t q, float v,
   }
 }
 
-constexpr int kAB = 16;                       // analysis: output coefficients per block side (per quadrant)
+constexpr int kAB = 16;                         // analysis: output coefficients per block side (per quadrant)
 constexpr int kATile = 2 * kAB + kMaxTaps - 2;  // input rows / cols a block reads
-constexpr int kSB = 32;                       // synthesis: output samples per block side
-constexpr int kSK = kSB / 2 + kMaxTaps / 2 - 1;  // coefficient rows / cols per half a block reads
+constexpr int kSB = 32;                         // synthesis: output samples per block side
+constexpr int kSK = kSB / 2 + kMaxTaps / 2 - 1; // coefficient rows / cols per half a block reads
 
-// One analysis level at block size m (pitch n) for basis blockIdx.z, fused rows + columns:
-// the block reads the (2*16 + L - 2)^2 input window (periodic), filters its rows into
-// [a | d] halves in shared memory, then its columns, and writes a 16 x 16 block of each
-// quadrant.  The LL quadrant goes to the carry buffer unless this is the last level;
-// every other coefficient is final and goes through the epilogue.
-__global__ void __launch_bounds__(256) k_dwt_level(const float* __restrict__ in, size_t in_stride,
-                                                   float* __restrict__ ll, float* __restrict__ out, int m, int n,
-                                                   bool last, float scale, const Filters F, const DualEpi e) {
-  __shared__ float tin[kATile][kATile + 1];
-  __shared__ float trow[kATile][2 * kAB + 1];
-  const int j = blockIdx.z;
-  const int L = F.len[j];
+struct AnaSmem {
+  float tin[kATile][kATile + 1];
+  float trow[kATile][2 * kAB + 1];
+};
+struct SynSmem {
+  float tc[2 * kSK][2 * kSK + 1];  // [a|d rows][a|d cols]
+  float tm[kSB][2 * kSK + 1];      // after the column synthesis
+};
+
+// One analysis level of one basis with an L-tap filter pair (unrolled), block
+// (blockIdx.x, blockIdx.y) = 16 x 16 output coefficients of each quadrant.
+template <int L>
+__device__ __forceinline__ void dwt_block(AnaSmem& sm, const float* __restrict__ src, float* __restrict__ carry,
+                                          float* __restrict__ dst, int m, int n, bool last, float scale,
+                                          const float* __restrict__ hf, const float* __restrict__ gf,
+                                          const DualEpi& e) {
+  constexpr int T = 2 * kAB + L - 2;
   const int half = m >> 1;
   const int k0 = blockIdx.y * kAB, l0 = blockIdx.x * kAB;
-  const int T = 2 * kAB + L - 2;
-  const float* src = in + in_stride * j;
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int rr = idx / T, cc = idx - rr * T;
-    int gr = 2 * k0 + rr, gc = 2 * l0 + cc;
+  float h[L], g[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    h[i] = hf[i];
+    g[i] = gf[i];
+  }
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int rr = ty; rr < T; rr += 8) {
+    int gr = 2 * k0 + rr;
     gr = gr < m ? gr : gr % m;
-    gc = gc < m ? gc : gc % m;
-    tin[rr][cc] = src[(size_t)gr * n + gc];
-  }
-  __syncthreads();
-  const float* h = F.h[j];
-  const float* g = F.g[j];
-  for (int idx = threadIdx.x; idx < T * kAB; idx += blockDim.x) {
-    const int rr = idx / kAB, l = idx - rr * kAB;
-    float a = 0.f, d = 0.f;
-    for (int i = 0; i < L; ++i) {
-      const float v = tin[rr][2 * l + i];
-      a = fmaf(h[i], v, a);
-      d = fmaf(g[i], v, d);
+    const float* row = src + (size_t)gr * n;
+    for (int cc = tx; cc < T; cc += 32) {
+      int gc = 2 * l0 + cc;
+      gc = gc < m ? gc : gc % m;
+      sm.tin[rr][cc] = row[gc];
     }
-    trow[rr][l] = a;
-    trow[rr][kAB + l] = d;
   }
   __syncthreads();
-  float* carry = ll + (size_t)n * n * j;
-  float* dst = out + (size_t)n * n * F.aidx[j];
-  for (int idx = threadIdx.x; idx < kAB * 2 * kAB; idx += blockDim.x) {
-    const int k = idx / (2 * kAB), c = idx - k * (2 * kAB);  // c < 16: low-pass columns, else high-pass
-    const int kk = k0 + k, ll_ = l0 + (c & (kAB - 1));
+  {
+    const int l = threadIdx.x & (kAB - 1);
+    for (int rr = threadIdx.x >> 4; rr < T; rr += 256 / kAB) {
+      float a = 0.f, d = 0.f;
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        const float v = sm.tin[rr][2 * l + i];
+        a = fmaf(h[i], v, a);
+        d = fmaf(g[i], v, d);
+      }
+      sm.trow[rr][l] = a;
+      sm.trow[rr][kAB + l] = d;
+    }
+  }
+  __syncthreads();
+  const int c = tx;  // c < 16: low-pass columns, else high-pass
+  const int ll_ = l0 + (c & (kAB - 1));
+  for (int k = ty; k < kAB; k += 8) {
+    const int kk = k0 + k;
     if (kk >= half || ll_ >= half) continue;
     float lo = 0.f, hi = 0.f;
+#pragma unroll
     for (int i = 0; i < L; ++i) {
-      const float v = trow[2 * k + i][c];
+      const float v = sm.trow[2 * k + i][c];
       lo = fmaf(h[i], v, lo);
       hi = fmaf(g[i], v, hi);
     }
@@ -167,82 +181,137 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float* __restrict__ in,
   }
 }
 
-// One synthesis level at block size m, fused columns + rows (the transpose of the
-// analysis): the block reconstructs a 32 x 32 window of the m x m block from the
-// 2 x (16 + L/2 - 1) coefficient rows and columns it touches (periodic).  The LL
-// quadrant is read from the reconstruction of the coarser level (from_rec) or from
-// the coefficients.  With sum_bases (finest level) the block loops over every basis,
-// adds the Dirac coefficients and writes scale * sum into x; otherwise it writes the
-// reconstruction of basis blockIdx.z into rec.
-__global__ void __launch_bounds__(256) k_idwt_level(const float* __restrict__ alpha, const float* __restrict__ rec_in,
-                                                    bool from_rec, float* __restrict__ rec_out, int m, int n,
-                                                    int nb, bool sum_bases, const float* __restrict__ dirac,
-                                                    float* __restrict__ x, float scale, const Filters F) {
-  __shared__ float tc[2 * kSK][2 * kSK + 1];  // [a|d rows][a|d cols]
-  __shared__ float tm[kSB][2 * kSK + 1];      // after the column synthesis
+// One analysis level at block size m (pitch n) for basis blockIdx.z, fused rows + columns:
+// the block reads the (2*16 + L - 2)^2 input window (periodic), filters its rows into
+// [a | d] halves in shared memory, then its columns, and writes a 16 x 16 block of each
+// quadrant.  The LL quadrant goes to the carry buffer unless this is the last level;
+// every other coefficient is final and goes through the epilogue.
+__global__ void __launch_bounds__(256) k_dwt_level(const float* __restrict__ in, size_t in_stride,
+                                                   float* __restrict__ ll, float* __restrict__ out, int m, int n,
+                                                   bool last, float scale, const Filters F, const DualEpi e) {
+  __shared__ AnaSmem sm;
+  const int j = blockIdx.z;
+  const float* src = in + in_stride * j;
+  float* carry = ll + (size_t)n * n * j;
+  float* dst = out + (size_t)n * n * F.aidx[j];
+#define GBRI_DWT_CASE(LL) \
+  case LL: dwt_block<LL>(sm, src, carry, dst, m, n, last, scale, F.h[j], F.g[j], e); break;
+  switch (F.len[j]) {
+    GBRI_DWT_CASE(2) GBRI_DWT_CASE(4) GBRI_DWT_CASE(6) GBRI_DWT_CASE(8) GBRI_DWT_CASE(10) GBRI_DWT_CASE(12)
+    GBRI_DWT_CASE(14) GBRI_DWT_CASE(16) GBRI_DWT_CASE(18) GBRI_DWT_CASE(20)
+    default: break;
+  }
+#undef GBRI_DWT_CASE
+}
+
+// One synthesis level of one basis with an L-tap filter pair (the transpose of the
+// analysis): reconstructs a 32 x 32 window of the m x m block from the
+// 2 x (16 + L/2 - 1) coefficient rows and columns it touches (periodic).
+template <int L>
+__device__ __forceinline__ void idwt_block(SynSmem& sm, const float* __restrict__ coef, const float* __restrict__ llsrc,
+                                           float* __restrict__ dst, int m, int n, const float* __restrict__ hf,
+                                           const float* __restrict__ gf) {
+  constexpr int KB = kSB / 2 + L / 2 - 1;
   const int half = m >> 1;
   const int r0 = blockIdx.y * kSB, c0 = blockIdx.x * kSB;
-  float accv[kSB * kSB / 256];
+  const int kr_lo = r0 / 2 - L / 2 + 1, kc_lo = c0 / 2 - L / 2 + 1;
+  float h[L], g[L];
 #pragma unroll
-  for (int q = 0; q < kSB * kSB / 256; ++q) accv[q] = 0.f;
-  const int jb = sum_bases ? 0 : blockIdx.z, je = sum_bases ? nb : blockIdx.z + 1;
-  for (int j = jb; j < je; ++j) {
-    const int L = F.len[j];
-    const int KB = kSB / 2 + L / 2 - 1;
-    const int kr_lo = r0 / 2 - L / 2 + 1, kc_lo = c0 / 2 - L / 2 + 1;
-    const float* coef = alpha + (size_t)n * n * F.aidx[j];
-    const float* llsrc = from_rec ? rec_in + (size_t)n * n * j : coef;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 4 * KB * KB; idx += blockDim.x) {
-      const int sr = idx / (2 * KB), sc = idx - sr * (2 * KB);
-      const int pr = sr >= KB, pc = sc >= KB;
-      int kr = (kr_lo + sr - pr * KB) % half; if (kr < 0) kr += half;
-      int kc = (kc_lo + sc - pc * KB) % half; if (kc < 0) kc += half;
+  for (int i = 0; i < L; ++i) {
+    h[i] = hf[i];
+    g[i] = gf[i];
+  }
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int sr = ty; sr < 2 * KB; sr += 8) {
+    const int pr = sr >= KB ? 1 : 0;
+    int kr = (kr_lo + sr - pr * KB) % half;
+    if (kr < 0) kr += half;
+    const size_t rowoff = (size_t)(pr * half + kr) * n;
+    for (int sc = tx; sc < 2 * KB; sc += 32) {
+      const int pc = sc >= KB ? 1 : 0;
+      int kc = (kc_lo + sc - pc * KB) % half;
+      if (kc < 0) kc += half;
       const float* srcp = (pr == 0 && pc == 0) ? llsrc : coef;
-      tc[pr * KB + (sr - pr * KB)][pc * KB + (sc - pc * KB)] = srcp[(size_t)(pr * half + kr) * n + pc * half + kc];
-    }
-    __syncthreads();
-    const float* h = F.h[j];
-    const float* g = F.g[j];
-    for (int idx = threadIdx.x; idx < kSB * 2 * KB; idx += blockDim.x) {
-      const int r = idx / (2 * KB), sc = idx - r * (2 * KB);
-      const int R = r0 + r;
-      float v = 0.f;
-      for (int i = R & 1; i < L; i += 2) {
-        const int kq = ((R - i) >> 1) - kr_lo;
-        v = fmaf(h[i], tc[kq][sc], v);
-        v = fmaf(g[i], tc[KB + kq][sc], v);
-      }
-      tm[r][sc] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kSB * kSB / 256; ++q) {
-      const int idx = threadIdx.x + q * 256;
-      const int r = idx / kSB, c = idx - r * kSB;
-      const int C = c0 + c;
-      float v = 0.f;
-      for (int i = C & 1; i < L; i += 2) {
-        const int kq = ((C - i) >> 1) - kc_lo;
-        v = fmaf(h[i], tm[r][kq], v);
-        v = fmaf(g[i], tm[r][KB + kq], v);
-      }
-      accv[q] += v;
+      sm.tc[sr][sc] = srcp[rowoff + pc * half + kc];
     }
   }
+  __syncthreads();
+  for (int r = ty; r < kSB; r += 8) {
+    const int R = r0 + r;
+    for (int sc = tx; sc < 2 * KB; sc += 32) {
+      float v = 0.f;
+      if (R & 1) {
 #pragma unroll
-  for (int q = 0; q < kSB * kSB / 256; ++q) {
-    const int idx = threadIdx.x + q * 256;
-    const int r = idx / kSB, c = idx - r * kSB;
-    const int R = r0 + r, C = c0 + c;
-    if (R >= m || C >= m) continue;
-    if (sum_bases) {
-      float v = accv[q];
-      if (dirac) v += dirac[(size_t)R * n + C];
-      x[(size_t)R * n + C] = scale * v;
-    } else {
-      rec_out[(size_t)n * n * blockIdx.z + (size_t)R * n + C] = accv[q];
+        for (int i = 1; i < L; i += 2) {
+          const int kq = ((R - i) >> 1) - kr_lo;
+          v = fmaf(h[i], sm.tc[kq][sc], v);
+          v = fmaf(g[i], sm.tc[KB + kq][sc], v);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < L; i += 2) {
+          const int kq = ((R - i) >> 1) - kr_lo;
+          v = fmaf(h[i], sm.tc[kq][sc], v);
+          v = fmaf(g[i], sm.tc[KB + kq][sc], v);
+        }
+      }
+      sm.tm[r][sc] = v;
     }
+  }
+  __syncthreads();
+  {
+    const int c = tx, C = c0 + c;
+    for (int r = ty; r < kSB; r += 8) {
+      const int R = r0 + r;
+      float v = 0.f;
+      if (C & 1) {
+#pragma unroll
+        for (int i = 1; i < L; i += 2) {
+          const int kq = ((C - i) >> 1) - kc_lo;
+          v = fmaf(h[i], sm.tm[r][kq], v);
+          v = fmaf(g[i], sm.tm[r][KB + kq], v);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < L; i += 2) {
+          const int kq = ((C - i) >> 1) - kc_lo;
+          v = fmaf(h[i], sm.tm[r][kq], v);
+          v = fmaf(g[i], sm.tm[r][KB + kq], v);
+        }
+      }
+      if (R < m && C < m) dst[(size_t)R * n + C] = v;
+    }
+  }
+}
+
+// One synthesis level at block size m for basis blockIdx.z: writes the reconstruction
+// of the m x m block into rec_out[basis].  The LL quadrant is read from rec_in (the
+// coarser level's reconstruction, from_rec) or from the coefficients.
+__global__ void __launch_bounds__(256) k_idwt_level(const float* __restrict__ alpha, const float* __restrict__ rec_in,
+                                                    bool from_rec, float* __restrict__ rec_out, int m, int n,
+                                                    const Filters F) {
+  __shared__ SynSmem sm;
+  const int j = blockIdx.z;
+  const float* coef = alpha + (size_t)n * n * F.aidx[j];
+  const float* llsrc = from_rec ? rec_in + (size_t)n * n * j : coef;
+  float* dst = rec_out + (size_t)n * n * j;
+#define GBRI_IDWT_CASE(LL) \
+  case LL: idwt_block<LL>(sm, coef, llsrc, dst, m, n, F.h[j], F.g[j]); break;
+  switch (F.len[j]) {
+    GBRI_IDWT_CASE(2) GBRI_IDWT_CASE(4) GBRI_IDWT_CASE(6) GBRI_IDWT_CASE(8) GBRI_IDWT_CASE(10) GBRI_IDWT_CASE(12)
+    GBRI_IDWT_CASE(14) GBRI_IDWT_CASE(16) GBRI_IDWT_CASE(18) GBRI_IDWT_CASE(20)
+    default: break;
+  }
+#undef GBRI_IDWT_CASE
+}
+
+// x[q] = scale * (sum_j rec[j][q] + dirac[q])
+__global__ void k_psi_sum(const float* __restrict__ rec, int nb, const float* __restrict__ dirac,
+                          float* __restrict__ x, int64_t N, float scale) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+    float v = dirac ? dirac[q] : 0.f;
+    for (int j = 0; j < nb; ++j) v += rec[(size_t)N * j + q];
+    x[q] = scale * v;
   }
 }
 
@@ -301,14 +370,15 @@ int32_t psi_apply(gbri_wavelet* w, const float* alpha, float* x, cudaStream_t s)
   for (int lev = w->levels - 1; lev >= 0; --lev) {
     const int m = n >> lev;
     const int bs = (int)ceil_div(m, kSB);
-    const bool finest = (lev == 0);
     launch_begin(GBRI_K_PSI, s);
-    k_idwt_level<<<dim3(bs, bs, finest ? 1 : w->nb), 256, 0, s>>>(
-        alpha, bufs[cur ^ 1], lev != w->levels - 1, bufs[cur], m, n, w->nb, finest, dirac, x, w->scale, w->F);
+    k_idwt_level<<<dim3(bs, bs, w->nb), 256, 0, s>>>(alpha, bufs[cur ^ 1], lev != w->levels - 1, bufs[cur], m, n,
+                                                     w->F);
     GBRI_TRY(launch_end(GBRI_K_PSI, s));
     cur ^= 1;
   }
-  return GBRI_OK;
+  launch_begin(GBRI_K_PSI, s);
+  k_psi_sum<<<blocks_for(N), 256, 0, s>>>(bufs[cur ^ 1], w->nb, dirac, x, N, w->scale);
+  return launch_end(GBRI_K_PSI, s);
 }
 
 }  // namespace gbri
@@ -336,7 +406,7 @@ int32_t gbri_wavelet_create(gbri_wavelet** out, int32_t n_side, int32_t levels, 
     const int N = db_orders[b];
     if (N < 0 || N > kMaxTaps / 2 || (N == 0 && w->dirac_idx >= 0)) {
       delete w;
-      return set_error(GBRI_EINVAL, "db order must be 0 (once) or 1..16");
+      return set_error(GBRI_EINVAL, "db order must be 0 (once) or 1..10");
     }
     w->orders.push_back(N);
     if (N == 0) {

@@ -8,7 +8,7 @@
 
 namespace gbri {
 
-constexpr int kMaxTaps = 32;   // db16
+constexpr int kMaxTaps = 20;   // db10
 constexpr int kMaxBases = 16;
 
 // Filter bank of the non-Dirac bases, passed to the kernels by value.
