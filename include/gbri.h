@@ -145,6 +145,24 @@ int32_t gbri_prox_l1(const float* d_in, float* d_out, int64_t n, double lambda, 
 int32_t gbri_proj_l2ball(const float* d_z, const float* d_center, float* d_out, int64_t M, double eps,
                          double* d_norm_out, int32_t precision, void* stream);
 
+/* Allocation-free variant of gbri_proj_l2ball (the paper has no counterpart; this is
+ * a library convenience).  Same arguments, result and error behaviour, but the FP64
+ * reduction scratch is a fixed 1024-entry (8 KB) device array inside the library
+ * instead of a stream-ordered allocation, for callers that cannot allocate device
+ * memory at that point (their own pool already holds the memory, an out-of-memory
+ * handler, a loop that must not synchronise).  No cudaMalloc or cudaFree is made.
+ *  - The array lives on every GPU that loads the library until the process exits.
+ *  - The first call on a device resolves the array's device address for that device
+ *    (cudaGetSymbolAddress, with the device current); make that first call before
+ *    any stream capture.
+ *  - Every call shares the one array: calls that overlap on the GPU (different
+ *    streams, or devices sharing nothing but the same call in flight) race.  Each
+ *    call writes every scratch entry it reads, so nothing needs clearing.
+ *  - Returns GBRI_EINVAL if a launch would need more than 1024 partials (one per
+ *    reduction block; at most 4 per SM, so only GPUs with more than 256 SMs). */
+int32_t gbri_proj_l2ball_noalloc(const float* d_z, const float* d_center, float* d_out, int64_t M, double eps,
+                                 double* d_norm_out, void* stream);
+
 /* ---- solvers (Appendix A.4 Algorithm 7; Sec. 5 Algorithm 1) --------------- */
 #define GBRI_ALGO_PD 0
 #define GBRI_ALGO_ADMM 1

@@ -206,6 +206,22 @@ def proj_l2ball(z, center, eps, out=None, norm_out=None, stream=None):
     return out
 
 
+def proj_l2ball_noalloc(z, center, eps, out=None, norm_out=None, stream=None):
+    """Allocation-free projection onto the l2 ball (gbri_proj_l2ball_noalloc): same result as
+    ``proj_l2ball``, with the reduction scratch in a fixed device array inside the library, for
+    callers that cannot allocate device memory at that point.  Concurrent calls race."""
+    _need(z, torch.complex64, name="z")
+    _need(center, torch.complex64, tuple(z.shape), "center")
+    if out is None:
+        out = torch.empty_like(z)
+    _need(out, torch.complex64, tuple(z.shape), "out")
+    if norm_out is not None:
+        _need(norm_out, torch.float64, (1,), "norm_out")
+    _lib.check(_lib.load().gbri_proj_l2ball_noalloc(_ptr(z), _ptr(center), _ptr(out), z.numel(), float(eps),
+                                                    _ptr(norm_out), _stream(stream)))
+    return out
+
+
 def _params(**kw):
     p = SolveParams()
     p.algo = ALGO_PD
