@@ -342,14 +342,17 @@ int32_t psi_adjoint_apply(gbri_wavelet* w, const float* x, float* out, DualEpi e
     GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
   }
   if (w->nb == 0) return GBRI_OK;
+  // the LL carry ping-pongs between the two buffers: a level must not overwrite the
+  // window another block of the same level still has to read
+  float* carry[2] = {w->ll, w->tmp};
   for (int lev = 0; lev < w->levels; ++lev) {
     const int m = n >> lev;
     const int bq = (int)ceil_div(m / 2, kAB);
-    const float* in = (lev == 0) ? x : w->ll;
+    const float* in = (lev == 0) ? x : carry[(lev - 1) & 1];
     const size_t in_stride = (lev == 0) ? 0 : (size_t)N;
     launch_begin(GBRI_K_PSI_ADJ, s);
-    k_dwt_level<<<dim3(bq, bq, w->nb), 256, 0, s>>>(in, in_stride, w->ll, out, m, n, lev == w->levels - 1, w->scale,
-                                                    w->F, epi);
+    k_dwt_level<<<dim3(bq, bq, w->nb), 256, 0, s>>>(in, in_stride, carry[lev & 1], out, m, n, lev == w->levels - 1,
+                                                    w->scale, w->F, epi);
     GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
   }
   return GBRI_OK;
