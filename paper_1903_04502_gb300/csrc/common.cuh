@@ -43,6 +43,12 @@ void launch_begin(int kind, cudaStream_t s, bool own = true);
 int32_t launch_end(int kind, cudaStream_t s);  // checks cudaGetLastError
 
 int num_sms();
+// True while per-kernel event timing is on (graph replay is then avoided so that
+// every kernel launch gets its own event pair).
+bool profiling_enabled();
+// Account for kernels launched by a graph replay (captured launches are not launches).
+void add_launches(int64_t n);
+int64_t launch_counter();
 
 // ---- device helpers ----------------------------------------------------------
 // Block-wide sum of a double; result valid in thread 0.  blockDim.x must be a

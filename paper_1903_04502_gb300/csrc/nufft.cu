@@ -2,6 +2,7 @@
 // Phi^dagger = crop_correct(F^H(grid(y))), visibility reordering and the power
 // method for ||Phi||^2 (Sec. 6.3.1).
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "nufft.cuh"
@@ -208,13 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_grid(VisGeom geo, float2* __restri
 
 template <int J, class Epi>
 inline void degrid_instance(gbri_plan* p, const float2* grid, Epi epi, cudaStream_t s) {
-  static bool attr = false;
-  const size_t smem = degrid_smem(p);
-  if (!attr) {
-    cudaFuncSetAttribute(k_degrid<J, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  k_degrid<J, Epi><<<p->degrid_blocks, kThreads, smem, s>>>(vis_geom(p), grid, epi);
+  k_degrid<J, Epi><<<p->degrid_blocks, kThreads, degrid_smem(p), s>>>(vis_geom(p), grid, epi);
 }
 
 template <class Epi>
@@ -227,13 +222,7 @@ int32_t launch_degrid(gbri_plan* p, const float2* grid, Epi epi, cudaStream_t s)
 
 template <int J, class Src>
 inline void grid_instance(gbri_plan* p, float2* grid, Src src, cudaStream_t s) {
-  static bool attr = false;
-  const size_t smem = grid_smem(p);
-  if (!attr) {
-    cudaFuncSetAttribute(k_grid<J, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  k_grid<J, Src><<<p->grid_blocks, kThreads, smem, s>>>(vis_geom(p), grid, src);
+  k_grid<J, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(vis_geom(p), grid, src);
 }
 
 // Zeroes p->grid, then grids every visibility into it.
@@ -247,6 +236,28 @@ int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s) {
   return launch_end(GBRI_K_GRID, s);
 }
 
+
+// Dynamic shared memory above 48 KB needs a per-kernel attribute; it is set once
+// for every instantiation before any launch (so never inside a stream capture).
+int32_t prepare_visibility_kernels() {
+  static int32_t status = -100;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int lim = 200 * 1024;
+    cudaError_t e = cudaSuccess;
+#define GBRI_ATTR(kern) if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+    GBRI_ATTR((k_degrid<4, EpiStorePlan>)); GBRI_ATTR((k_degrid<6, EpiStorePlan>));
+    GBRI_ATTR((k_degrid<4, EpiStoreRaw>)); GBRI_ATTR((k_degrid<6, EpiStoreRaw>));
+    GBRI_ATTR((k_degrid<4, EpiPD1>)); GBRI_ATTR((k_degrid<6, EpiPD1>));
+    GBRI_ATTR((k_degrid<4, EpiADMM1>)); GBRI_ATTR((k_degrid<6, EpiADMM1>));
+    GBRI_ATTR((k_grid<4, SrcPlan>)); GBRI_ATTR((k_grid<6, SrcPlan>));
+    GBRI_ATTR((k_grid<4, SrcRaw>)); GBRI_ATTR((k_grid<6, SrcRaw>));
+    GBRI_ATTR((k_grid<4, SrcADMM2>)); GBRI_ATTR((k_grid<6, SrcADMM2>));
+#undef GBRI_ATTR
+    status = (e == cudaSuccess) ? GBRI_OK : cuda_error(e, "cudaFuncSetAttribute");
+  });
+  return status;
+}
 
 // Every visibility kernel is instantiated here and only here.
 template int32_t launch_degrid<EpiStorePlan>(gbri_plan*, const float2*, EpiStorePlan, cudaStream_t);

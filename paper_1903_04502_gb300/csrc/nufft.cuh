@@ -209,6 +209,8 @@ int32_t launch_degrid(gbri_plan* p, const float2* grid, Epi epi, cudaStream_t s)
 template <class Src>
 int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s);
 
+// Sets the shared-memory attributes of every visibility kernel (once per process).
+int32_t prepare_visibility_kernels();
 // Z S x into p->padded; optional extra scaling by *d_scale (device, may be null).
 int32_t launch_pad(gbri_plan* p, const float* x, const double* d_inv_scale, cudaStream_t s);
 // F: padded -> grid (forward, unnormalised); F^H: grid in place (inverse, unnormalised).

@@ -211,6 +211,7 @@ void destroy_plan(gbri_plan* p) {
 }
 
 int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
+  GBRI_TRY(prepare_visibility_kernels());
   const int K = p->K, S = p->S;
   const int64_t M = p->M;
   const int64_t cells = (int64_t)K * K;

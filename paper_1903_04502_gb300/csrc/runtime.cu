@@ -66,6 +66,21 @@ int32_t launch_end(int kind, cudaStream_t s) {
   return GBRI_OK;
 }
 
+bool profiling_enabled() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_prof_cap > 0;
+}
+
+void add_launches(int64_t n) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_launches += n;
+}
+
+int64_t launch_counter() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_launches;
+}
+
 int num_sms() {
   static int n = 0;
   if (n == 0) {

@@ -22,6 +22,7 @@
 // All global norms are FP64 (per-thread FP32 compensated partials, FP64 block sums).
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <new>
 
 #include "nufft.cuh"
@@ -188,12 +189,21 @@ struct gbri_solver {
   int n_partials = 0;
   int iters = 0;
   double ms_total = 0.0;
+  // one iteration captured as a CUDA graph and replayed (no host work per kernel)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t launches_per_iter = 0;
+  bool graph_failed = false;
 };
 
 namespace {
 
 void free_solver(gbri_solver* s) {
   if (!s) return;
+  if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   cudaFree(s->yp); cudaFree(s->u); cudaFree(s->w);
   cudaFree(s->x); cudaFree(s->xhat); cudaFree(s->psiz); cudaFree(s->z1); cudaFree(s->xt);
   cudaFree(s->partials); cudaFree(s->sc);
@@ -303,6 +313,39 @@ int32_t default_gamma(gbri_solver* S, cudaStream_t st, double* out) {
   return GBRI_OK;
 }
 
+bool use_graphs() {
+  const char* e = getenv("GBRI_GRAPHS");
+  return !(e && e[0] == '0');
+}
+
+// Capture one iteration on a private stream (the caller's stream may be the legacy
+// default stream, which cannot be captured) and instantiate it.
+int32_t capture_iteration(gbri_solver* S) {
+  if (!S->cap_stream) GBRI_CHECK_CUDA(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
+  const int64_t before = launch_counter();
+  GBRI_CHECK_CUDA(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int32_t r = S->p.algo == GBRI_ALGO_PD ? pd_iteration(S, S->cap_stream) : admm_iteration(S, S->cap_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
+  const int64_t captured = launch_counter() - before;
+  add_launches(-captured);  // capturing launches nothing
+  if (r != GBRI_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&ex, g, 0);
+  if (e2 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_error(e2, "cudaGraphInstantiate");
+  }
+  S->graph = g;
+  S->graph_exec = ex;
+  S->launches_per_iter = captured;
+  return GBRI_OK;
+}
+
 template <class T>
 int32_t zalloc(T** p, size_t n, cudaStream_t s) {
   if (n == 0) n = 1;
@@ -396,6 +439,21 @@ int32_t gbri_solver_destroy(gbri_solver* S) {
 int32_t gbri_solver_step(gbri_solver* S, int32_t n_iter, void* stream) {
   GBRI_CHECK(S && n_iter >= 0, GBRI_EINVAL, "bad argument");
   cudaStream_t st = (cudaStream_t)stream;
+  if (n_iter == 0) return GBRI_OK;
+  if (use_graphs() && !profiling_enabled() && !S->graph_failed) {
+    if (!S->graph_exec) {
+      const int32_t r = capture_iteration(S);
+      if (r != GBRI_OK) S->graph_failed = true;  // fall back to direct launches
+    }
+    if (S->graph_exec) {
+      for (int k = 0; k < n_iter; ++k) {
+        GBRI_CHECK_CUDA(cudaGraphLaunch(S->graph_exec, st));
+        ++S->iters;
+      }
+      add_launches(S->launches_per_iter * n_iter);
+      return GBRI_OK;
+    }
+  }
   for (int k = 0; k < n_iter; ++k) {
     GBRI_TRY(S->p.algo == GBRI_ALGO_PD ? pd_iteration(S, st) : admm_iteration(S, st));
     ++S->iters;
