@@ -9,16 +9,17 @@
 
 namespace gbri {
 
-// Degridding (G then W, Sec. 2).  A block takes one chunk (<= kChunk visibilities
-// of one 16 x 16 tile), copies the tile's (T + J - 1)^2 grid window into shared
-// memory and gives one thread per visibility (coalesced metadata and epilogue
-// streams, kUnroll visibilities in flight per thread):
-//   v = w * sum_{t'} wy[t'] sum_t wx[t] win[cy + t'][cx + t]
-// with the two J-tap weight rows read from the shared-memory table.  Visibilities
-// are cell-sorted, so lanes that share a cell read the same window words
-// (broadcast).  Persistent blocks stride over the chunks, heaviest tiles first.
+// Degridding (G then W, Sec. 2).  A block takes one chunk (<= kChunk visibilities of
+// one 16 x 16 tile) and copies the tile's (T + J - 1)^2 grid window into shared
+// memory.  Thread t owns the run of kRun consecutive (cell-sorted) visibilities
+// starting at chunk position kRun * t: it issues all their metadata and epilogue
+// loads at once, reads the J x J window patch of a cell into registers only when
+// the cell changes along the run, and computes
+//   v = w * sum_{t'} wy[t'] sum_t wx[t] patch[t'][t]
+// with the two J-tap weight rows from the shared-memory table.  `Epi` consumes
+// (plan position, v).  Persistent blocks stride over the chunks.
 template <int J, class Epi>
-__global__ void __launch_bounds__(kThreads) k_degrid(VisGeom geo, const float2* __restrict__ grid, Epi epi) {
+__global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_degrid(VisGeom geo, const float2* __restrict__ grid, Epi epi) {
   extern __shared__ float4 smem_dg[];
   constexpr int P = kTile + J - 1;
   float* sw = reinterpret_cast<float*>(smem_dg);
@@ -40,155 +41,138 @@ __global__ void __launch_bounds__(kThreads) k_degrid(VisGeom geo, const float2* 
       cur_tile = ch.x;
       __syncthreads();
     }
-    for (int i0 = threadIdx.x; i0 < ch.z; i0 += blockDim.x * kUnroll) {
-      uint2 m[kUnroll];
-      typename Epi::Pre pre[kUnroll];
+    const int j0 = threadIdx.x * kRun;
+    const int n = min(kRun, ch.z - j0);
+    if (n <= 0) continue;
+    uint2 m[kRun];
+    typename Epi::Pre pre[kRun];
 #pragma unroll
-      for (int k = 0; k < kUnroll; ++k) {
-        const int i = i0 + k * blockDim.x;
-        if (i < ch.z) {
-          m[k] = geo.meta[ch.y + i];
-          pre[k] = epi.load(ch.y + i);
-        }
+    for (int k = 0; k < kRun; ++k)
+      if (k < n) {
+        m[k] = geo.meta[ch.y + j0 + k];
+        pre[k] = epi.load(ch.y + j0 + k);
       }
+    float2 pt[J][J];
+    int cur = -1;
 #pragma unroll
-      for (int k = 0; k < kUnroll; ++k) {
-        const int i = i0 + k * blockDim.x;
-        if (i >= ch.z) break;
-        const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
-        float wx[J], wy[J];
-        load_taps<J>(sw, lx & (S - 1), wx);
-        load_taps<J>(sw, ly & (S - 1), wy);
-        const float2* base = win + (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
-        float ar = 0.f, ai = 0.f;
+    for (int k = 0; k < kRun; ++k) {
+      if (k >= n) break;
+      const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
+      const int ci = (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
+      if (ci != cur) {
 #pragma unroll
-        for (int tp = 0; tp < J; ++tp) {
-          float rr = 0.f, ri = 0.f;
+        for (int tp = 0; tp < J; ++tp)
 #pragma unroll
-          for (int t = 0; t < J; ++t) {
-            const float2 gv = base[tp * kWinPitch + t];
-            rr = fmaf(wx[t], gv.x, rr);
-            ri = fmaf(wx[t], gv.y, ri);
-          }
-          ar = fmaf(wy[tp], rr, ar);
-          ai = fmaf(wy[tp], ri, ai);
-        }
-        const float w = __uint_as_float(m[k].y);
-        epi.store(ch.y + i, pre[k], make_float2(w * ar, w * ai));
+          for (int t = 0; t < J; ++t) pt[tp][t] = win[ci + tp * kWinPitch + t];
+        cur = ci;
       }
+      float wx[J], wy[J];
+      load_taps<J>(sw, lx & (S - 1), wx);
+      load_taps<J>(sw, ly & (S - 1), wy);
+      float ar = 0.f, ai = 0.f;
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp) {
+        float rr = 0.f, ri = 0.f;
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+          rr = fmaf(wx[t], pt[tp][t].x, rr);
+          ri = fmaf(wx[t], pt[tp][t].y, ri);
+        }
+        ar = fmaf(wy[tp], rr, ar);
+        ai = fmaf(wy[tp], ri, ai);
+      }
+      const float w = __uint_as_float(m[k].y);
+      epi.store(ch.y + j0 + k, pre[k], make_float2(w * ar, w * ai));
     }
   }
   epi.finish();
 }
 
-// Gridding (W^T then G^T, Sec. 2).  A block takes one chunk of one tile:
-//  1. stages the chunk's metadata and weighted values w * v in shared memory
-//     (coalesced, kUnroll loads in flight per thread);
-//  2. finds each cell's range in the (cell-sorted) chunk;
-//  3. one thread per cell of the tile sums wy[t'] wx[t] w v over its cell's
-//     visibilities into a J x J register patch;
-//  4. adds the patches to a shared (T + J - 1)^2 accumulator (planar re / im,
-//     row pitch == 16 mod 32): in one atomic instruction the 32 lanes own 32
-//     distinct cells (two tile rows) on distinct banks;
-//  5. writes the accumulator to the global grid: plain stores for the cells no
-//     other tile touches when the tile is a single chunk, vector atomics otherwise.
+// Gridding (W^T then G^T, Sec. 2).  A block takes one chunk of one tile.  Thread t
+// owns the run of kRun consecutive (cell-sorted) visibilities starting at chunk
+// position kRun * t: it loads them at once, sums w * v * wy[t'] wx[t] over the run
+// into a J x J register patch and adds the patch to a shared (T + J - 1)^2
+// accumulator (planar re / im) only when the cell changes and at the end of the
+// run, so dense cells cost one shared atomic per tap per run instead of per
+// visibility.  The accumulator is then written to the global grid: plain stores
+// for the cells that no other tile touches when the tile is a single chunk, vector
+// atomics otherwise.  `Src` gives the visibility value at a plan position.
+template <int J>
+__device__ __forceinline__ void flush_patch(float* acc_re, float* acc_im, int a0, const float2 (&pt)[J][J]) {
+#pragma unroll
+  for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+    for (int t = 0; t < J; ++t) {
+      atomicAdd(acc_re + a0 + tp * kAccPitch + t, pt[tp][t].x);
+      atomicAdd(acc_im + a0 + tp * kAccPitch + t, pt[tp][t].y);
+    }
+}
+
 template <int J, class Src>
-__global__ void __launch_bounds__(kThreads) k_grid(VisGeom geo, float2* __restrict__ grid, Src src) {
+__global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_grid(VisGeom geo, float2* __restrict__ grid, Src src) {
   extern __shared__ float4 smem_gr[];
   constexpr int P = kTile + J - 1;
-  constexpr int NC = kTile * kTile;
   const int S = 1 << geo.log2S;
   float* sw = reinterpret_cast<float*>(smem_gr);
   float* acc_re = sw + S * J;
   float* acc_im = acc_re + P * kAccPitch;
-  uint2* sm_meta = reinterpret_cast<uint2*>(acc_im + P * kAccPitch);
-  float2* sm_val = reinterpret_cast<float2*>(sm_meta + kChunk);
-  int* cbeg = reinterpret_cast<int*>(sm_val + kChunk);
-  int* cend = cbeg + NC;
   copy_table_to_smem(sw, geo.wtab, S * J);
   const int K = geo.K;
-  const int lcy = threadIdx.x >> 4, lcx = threadIdx.x & 15;
   for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
     const int4 ch = geo.chunks[c];
     for (int i = threadIdx.x; i < P * kAccPitch; i += blockDim.x) {
       acc_re[i] = 0.f;
       acc_im[i] = 0.f;
     }
-    for (int i = threadIdx.x; i < NC; i += blockDim.x) {
-      cbeg[i] = 0;
-      cend[i] = 0;
-    }
-    for (int i0 = threadIdx.x; i0 < ch.z; i0 += blockDim.x * kUnroll) {
-      uint2 m[kUnroll];
-      float2 v[kUnroll];
-#pragma unroll
-      for (int k = 0; k < kUnroll; ++k) {
-        const int i = i0 + k * blockDim.x;
-        if (i < ch.z) {
-          m[k] = geo.meta[ch.y + i];
-          v[k] = src(ch.y + i);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < kUnroll; ++k) {
-        const int i = i0 + k * blockDim.x;
-        if (i < ch.z) {
-          const float w = __uint_as_float(m[k].y);
-          sm_meta[i] = m[k];
-          sm_val[i] = make_float2(w * v[k].x, w * v[k].y);
-        }
-      }
-    }
     __syncthreads();
-    for (int i = threadIdx.x; i < ch.z; i += blockDim.x) {
-      const uint32_t x = sm_meta[i].x;
-      const int cell = ((int)(x >> 16) >> geo.log2S) * kTile + ((int)(x & 0xffff) >> geo.log2S);
-      int prev = -1, next = -1;
-      if (i > 0) {
-        const uint32_t xp = sm_meta[i - 1].x;
-        prev = ((int)(xp >> 16) >> geo.log2S) * kTile + ((int)(xp & 0xffff) >> geo.log2S);
-      }
-      if (i + 1 < ch.z) {
-        const uint32_t xn = sm_meta[i + 1].x;
-        next = ((int)(xn >> 16) >> geo.log2S) * kTile + ((int)(xn & 0xffff) >> geo.log2S);
-      }
-      if (cell != prev) cbeg[cell] = i;
-      if (cell != next) cend[cell] = i + 1;
-    }
-    __syncthreads();
-    {
-      const int b = cbeg[threadIdx.x], e = cend[threadIdx.x];
-      if (b < e) {
-        float2 pt[J][J];
+    const int j0 = threadIdx.x * kRun;
+    const int n = min(kRun, ch.z - j0);
+    if (n > 0) {
+      uint2 m[kRun];
+      float2 v[kRun];
 #pragma unroll
-        for (int tp = 0; tp < J; ++tp)
+      for (int k = 0; k < kRun; ++k)
+        if (k < n) {
+          m[k] = geo.meta[ch.y + j0 + k];
+          v[k] = src(ch.y + j0 + k);
+        }
+      float2 pt[J][J];
 #pragma unroll
-          for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
-        for (int j = b; j < e; ++j) {
-          const uint32_t x = sm_meta[j].x;
-          float wx[J], wy[J];
-          load_taps<J>(sw, (x & 0xffff) & (S - 1), wx);
-          load_taps<J>(sw, (x >> 16) & (S - 1), wy);
-          const float2 vv = sm_val[j];
+      for (int tp = 0; tp < J; ++tp)
 #pragma unroll
-          for (int tp = 0; tp < J; ++tp) {
-            const float br = wy[tp] * vv.x, bi = wy[tp] * vv.y;
+        for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
+      int cur = -1;
 #pragma unroll
-            for (int t = 0; t < J; ++t) {
-              pt[tp][t].x = fmaf(wx[t], br, pt[tp][t].x);
-              pt[tp][t].y = fmaf(wx[t], bi, pt[tp][t].y);
-            }
+      for (int k = 0; k < kRun; ++k) {
+        if (k >= n) break;
+        const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
+        const int a0 = (ly >> geo.log2S) * kAccPitch + (lx >> geo.log2S);
+        if (a0 != cur) {
+          if (cur >= 0) {
+            flush_patch<J>(acc_re, acc_im, cur, pt);
+#pragma unroll
+            for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+              for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
           }
+          cur = a0;
         }
+        float wx[J], wy[J];
+        load_taps<J>(sw, lx & (S - 1), wx);
+        load_taps<J>(sw, ly & (S - 1), wy);
+        const float w = __uint_as_float(m[k].y);
+        const float vr = w * v[k].x, vi = w * v[k].y;
 #pragma unroll
-        for (int tp = 0; tp < J; ++tp)
+        for (int tp = 0; tp < J; ++tp) {
+          const float br = wy[tp] * vr, bi = wy[tp] * vi;
 #pragma unroll
           for (int t = 0; t < J; ++t) {
-            const int a = (lcy + tp) * kAccPitch + lcx + t;
-            atomicAdd(acc_re + a, pt[tp][t].x);
-            atomicAdd(acc_im + a, pt[tp][t].y);
+            pt[tp][t].x = fmaf(wx[t], br, pt[tp][t].x);
+            pt[tp][t].y = fmaf(wx[t], bi, pt[tp][t].y);
           }
+        }
       }
+      flush_patch<J>(acc_re, acc_im, cur, pt);
     }
     __syncthreads();
     const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;

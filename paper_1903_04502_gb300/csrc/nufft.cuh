@@ -28,8 +28,8 @@ namespace gbri {
 
 constexpr int kTile = 16;      // grid tile side in cells (T * S <= 65536 keeps 16-bit local coords)
 constexpr int kThreads = 256;  // threads per block of the visibility kernels
-constexpr int kChunk = 1024;   // visibilities per work chunk (also the gridding stage size)
-constexpr int kUnroll = 4;     // visibilities in flight per thread in the degridding loop
+constexpr int kRun = 4;        // consecutive visibilities a thread owns within a chunk
+constexpr int kChunk = kThreads * kRun;  // visibilities per work chunk
 constexpr int kWinPitch = 24;  // float2 pitch of the degridding window (== 8 mod 16: two rows per warp on disjoint banks)
 
 }  // namespace gbri
@@ -99,8 +99,7 @@ inline size_t degrid_smem(const gbri_plan* p) {
 constexpr int kAccPitch = 48;
 inline size_t grid_smem(const gbri_plan* p) {
   const int P = kTile + p->J - 1;
-  return (size_t)p->S * p->J * sizeof(float) + (size_t)2 * P * kAccPitch * sizeof(float) +
-         (size_t)kChunk * (sizeof(uint2) + sizeof(float2)) + 2 * kTile * kTile * sizeof(int);
+  return (size_t)p->S * p->J * sizeof(float) + (size_t)2 * P * kAccPitch * sizeof(float);
 }
 
 inline VisGeom vis_geom(const gbri_plan* p) {

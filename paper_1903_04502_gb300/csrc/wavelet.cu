@@ -222,15 +222,22 @@ __device__ __forceinline__ void idwt_block(SynSmem& sm, const float* __restrict_
     g[i] = gf[i];
   }
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  // coefficient indexes stay within [-half, 2 half) once half >= 16 and half >= L: one
+  // conditional wrap instead of an integer modulo per element
+  const bool small = half < 16 || half < L;
   for (int sr = ty; sr < 2 * KB; sr += 8) {
     const int pr = sr >= KB ? 1 : 0;
-    int kr = (kr_lo + sr - pr * KB) % half;
+    int kr = kr_lo + sr - pr * KB;
+    if (small) kr %= half;
     if (kr < 0) kr += half;
+    if (kr >= half) kr -= half;
     const size_t rowoff = (size_t)(pr * half + kr) * n;
     for (int sc = tx; sc < 2 * KB; sc += 32) {
       const int pc = sc >= KB ? 1 : 0;
-      int kc = (kc_lo + sc - pc * KB) % half;
+      int kc = kc_lo + sc - pc * KB;
+      if (small) kc %= half;
       if (kc < 0) kc += half;
+      if (kc >= half) kc -= half;
       const float* srcp = (pr == 0 && pc == 0) ? llsrc : coef;
       sm.tc[sr][sc] = srcp[rowoff + pc * half + kc];
     }
