@@ -9,12 +9,11 @@
 
 namespace gbri {
 
-// Degridding (G then W, Sec. 2).  A block takes one chunk (<= kChunk visibilities of
-// one 16 x 16 tile) and copies the tile's (T + J - 1)^2 grid window into shared
-// memory.  Thread t owns the run of kRun consecutive (cell-sorted) visibilities
-// starting at chunk position kRun * t: it issues all their metadata and epilogue
-// loads at once, reads the J x J window patch of a cell into registers only when
-// the cell changes along the run, and computes
+// Degridding (G then W, Sec. 2).  A block takes one chunk (<= kThreads sub-runs of one
+// 16 x 16 tile) and copies the tile's (T + J - 1)^2 grid window into shared memory.
+// Thread t owns sub-run t (<= kRun consecutive visibilities of one cell; the lanes of
+// a warp hold distinct cells): it issues all their metadata and epilogue loads at
+// once, reads the cell's J x J window patch into registers once, and computes
 //   v = w * sum_{t'} wy[t'] sum_t wx[t] patch[t'][t]
 // with the two J-tap weight rows from the shared-memory table.  `Epi` consumes
 // (plan position, v).  Persistent blocks stride over the chunks.
@@ -41,34 +40,30 @@ __global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_degrid(VisGeom g
       cur_tile = ch.x;
       __syncthreads();
     }
-    const int j0 = threadIdx.x * kRun;
-    const int n = min(kRun, ch.z - j0);
-    if (n <= 0) continue;
+    if ((int)threadIdx.x >= ch.z) continue;
+    const int2 sr = geo.subruns[ch.y + threadIdx.x];
+    const int p0 = sr.x, n = sr.y;
     uint2 m[kRun];
     typename Epi::Pre pre[kRun];
 #pragma unroll
     for (int k = 0; k < kRun; ++k)
       if (k < n) {
-        m[k] = geo.meta[ch.y + j0 + k];
-        pre[k] = epi.load(ch.y + j0 + k);
+        m[k] = geo.meta[p0 + k];
+        pre[k] = epi.load(p0 + k);
       }
+    // all visibilities of a sub-run share one cell: its J x J window patch, once
+    const int ci = ((int)(m[0].x >> 16) >> geo.log2S) * kWinPitch + ((int)(m[0].x & 0xffff) >> geo.log2S);
     float2 pt[J][J];
-    int cur = -1;
+#pragma unroll
+    for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+      for (int t = 0; t < J; ++t) pt[tp][t] = win[ci + tp * kWinPitch + t];
 #pragma unroll
     for (int k = 0; k < kRun; ++k) {
       if (k >= n) break;
-      const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
-      const int ci = (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
-      if (ci != cur) {
-#pragma unroll
-        for (int tp = 0; tp < J; ++tp)
-#pragma unroll
-          for (int t = 0; t < J; ++t) pt[tp][t] = win[ci + tp * kWinPitch + t];
-        cur = ci;
-      }
       float wx[J], wy[J];
-      load_taps<J>(sw, lx & (S - 1), wx);
-      load_taps<J>(sw, ly & (S - 1), wy);
+      load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), wx);
+      load_taps<J>(sw, (m[k].x >> 16) & (S - 1), wy);
       float ar = 0.f, ai = 0.f;
 #pragma unroll
       for (int tp = 0; tp < J; ++tp) {
@@ -82,19 +77,18 @@ __global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_degrid(VisGeom g
         ai = fmaf(wy[tp], ri, ai);
       }
       const float w = __uint_as_float(m[k].y);
-      epi.store(ch.y + j0 + k, pre[k], make_float2(w * ar, w * ai));
+      epi.store(p0 + k, pre[k], make_float2(w * ar, w * ai));
     }
   }
   epi.finish();
 }
 
 // Gridding (W^T then G^T, Sec. 2).  A block takes one chunk of one tile.  Thread t
-// owns the run of kRun consecutive (cell-sorted) visibilities starting at chunk
-// position kRun * t: it loads them at once, sums w * v * wy[t'] wx[t] over the run
-// into a J x J register patch and adds the patch to a shared (T + J - 1)^2
-// accumulator (planar re / im) only when the cell changes and at the end of the
-// run, so dense cells cost one shared atomic per tap per run instead of per
-// visibility.  The accumulator is then written to the global grid: plain stores
+// owns sub-run t (<= kRun visibilities of one cell; the lanes of a warp hold
+// distinct cells): it loads them at once, sums w * v * wy[t'] wx[t] into a J x J
+// register patch and adds the patch to a shared (T + J - 1)^2 accumulator (planar
+// re / im) with one atomic per tap: kRun times fewer shared atomics than one per
+// visibility, and no two lanes of an atomic instruction on the same cell.  The accumulator is then written to the global grid: plain stores
 // for the cells that no other tile touches when the tile is a single chunk, vector
 // atomics otherwise.  `Src` gives the visibility value at a plan position.
 template <int J>
@@ -125,41 +119,28 @@ __global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_grid(VisGeom geo
       acc_im[i] = 0.f;
     }
     __syncthreads();
-    const int j0 = threadIdx.x * kRun;
-    const int n = min(kRun, ch.z - j0);
-    if (n > 0) {
+    if ((int)threadIdx.x < ch.z) {
+      const int2 sr = geo.subruns[ch.y + threadIdx.x];
+      const int p0 = sr.x, n = sr.y;
       uint2 m[kRun];
       float2 v[kRun];
 #pragma unroll
       for (int k = 0; k < kRun; ++k)
         if (k < n) {
-          m[k] = geo.meta[ch.y + j0 + k];
-          v[k] = src(ch.y + j0 + k);
+          m[k] = geo.meta[p0 + k];
+          v[k] = src(p0 + k);
         }
       float2 pt[J][J];
 #pragma unroll
       for (int tp = 0; tp < J; ++tp)
 #pragma unroll
         for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
-      int cur = -1;
 #pragma unroll
       for (int k = 0; k < kRun; ++k) {
         if (k >= n) break;
-        const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
-        const int a0 = (ly >> geo.log2S) * kAccPitch + (lx >> geo.log2S);
-        if (a0 != cur) {
-          if (cur >= 0) {
-            flush_patch<J>(acc_re, acc_im, cur, pt);
-#pragma unroll
-            for (int tp = 0; tp < J; ++tp)
-#pragma unroll
-              for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
-          }
-          cur = a0;
-        }
         float wx[J], wy[J];
-        load_taps<J>(sw, lx & (S - 1), wx);
-        load_taps<J>(sw, ly & (S - 1), wy);
+        load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), wx);
+        load_taps<J>(sw, (m[k].x >> 16) & (S - 1), wy);
         const float w = __uint_as_float(m[k].y);
         const float vr = w * v[k].x, vi = w * v[k].y;
 #pragma unroll
@@ -172,7 +153,9 @@ __global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_grid(VisGeom geo
           }
         }
       }
-      flush_patch<J>(acc_re, acc_im, cur, pt);
+      // one cell per sub-run; the lanes of a warp hold distinct cells
+      const int a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch + ((int)(m[0].x & 0xffff) >> geo.log2S);
+      flush_patch<J>(acc_re, acc_im, a0, pt);
     }
     __syncthreads();
     const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;

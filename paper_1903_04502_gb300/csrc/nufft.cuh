@@ -6,8 +6,11 @@
 //                      fixed-point coordinates (cell-in-tile * S + fraction),
 //                      .y = weight bits (float).  8 bytes per visibility.
 //   perm   [M] int32   plan position -> caller's visibility index.
-//   chunks [C] int4    {tile, first plan position, count, single}: at most kChunk
-//                      visibilities of one T x T tile; single = the tile is one chunk.
+//   subruns [R] int2   {first plan position, count <= kRun}: consecutive visibilities
+//                      of one cell; within a tile listed rank-major (all cells' first
+//                      sub-runs in cell order, then all second sub-runs, ...).
+//   chunks [C] int4    {tile, first sub-run, sub-runs (<= kThreads), single}; single =
+//                      the tile is one chunk.
 //   Visibilities are sorted by (tile, cell row, cell column): a cell's visibilities
 //   are contiguous.
 //   wtab   [S][J] f32  tap weights by fractional offset f = k~ mod S: entry t is
@@ -41,6 +44,7 @@ struct gbri_plan {
   uint2* meta = nullptr;
   int32_t* perm = nullptr;
   int4* chunks = nullptr;
+  int2* subruns = nullptr;  // {first plan position, count <= kRun}: visibilities of one cell
   int64_t n_chunks = 0;
   int64_t n_tiles = 0;  // non-empty tiles
   int32_t* cell_off = nullptr;  // plan creation only
@@ -87,6 +91,7 @@ __device__ __forceinline__ void copy_table_to_smem(float* sw, const float* __res
 struct VisGeom {
   const uint2* __restrict__ meta;
   const int4* __restrict__ chunks;
+  const int2* __restrict__ subruns;
   const float* __restrict__ wtab;
   int n_chunks, K, log2S, nT;
 };
@@ -106,6 +111,7 @@ inline VisGeom vis_geom(const gbri_plan* p) {
   VisGeom g;
   g.meta = p->meta;
   g.chunks = p->chunks;
+  g.subruns = p->subruns;
   g.wtab = p->wtab;
   g.n_chunks = (int)p->n_chunks;
   g.K = p->K;

@@ -199,6 +199,7 @@ void destroy_plan(gbri_plan* p) {
   cudaFree(p->meta);
   cudaFree(p->perm);
   cudaFree(p->chunks);
+  cudaFree(p->subruns);
   cudaFree(p->wtab);
   cudaFree(p->corr);
   cudaFree(p->padded);
@@ -303,24 +304,57 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   for (int t = 0; t < n_tiles; ++t)
     if (hst[t + 1] > hst[t]) tiles.push_back(t);
   p->n_tiles = (int64_t)tiles.size();
-  cudaFree(p->cell_off);  // the kernels only need tile ranges (chunks)
+
+  // Sub-runs: at most kRun consecutive visibilities of one cell.  Within a tile they are
+  // listed rank-major (every cell's first sub-run in cell order, then every second one,
+  // ...), so the lanes of a warp take sub-runs of distinct cells.  A chunk is up to
+  // kThreads sub-runs of one tile (one per thread), heaviest tiles first.
+  std::vector<int32_t> hoff((size_t)cells + 1);
+  {
+    cudaError_t e = cudaMemcpyAsync(hoff.data(), p->cell_off, sizeof(int32_t) * (cells + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "cell offsets");
+  }
+  cudaFree(p->cell_off);  // the kernels only need the sub-runs and chunks
   p->cell_off = nullptr;
   p->device_bytes -= (int64_t)(cells + 1) * (int64_t)sizeof(int32_t);
-
-  // work chunks: at most kChunk visibilities of one tile each, heaviest tiles first
   std::vector<int32_t> order(tiles);
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return hst[a + 1] - hst[a] > hst[b + 1] - hst[b]; });
+  std::vector<int2> sub;
+  sub.reserve((size_t)(M / kRun + order.size() * 64 + 16));
   std::vector<int4> ch;
+  constexpr int NC = kTile * kTile;
+  int nsub[NC];
   for (int t : order) {
-    const int a = hst[t], b = hst[t + 1];
-    const int single = (b - a) <= kChunk ? 1 : 0;
-    for (int c = a; c < b; c += kChunk) ch.push_back(make_int4(t, c, std::min(kChunk, b - c), single));
+    const int64_t base = (int64_t)t * NC;
+    int maxsub = 0;
+    for (int c = 0; c < NC; ++c) {
+      const int cnt = hoff[base + c + 1] - hoff[base + c];
+      nsub[c] = (cnt + kRun - 1) / kRun;
+      maxsub = std::max(maxsub, nsub[c]);
+    }
+    const int64_t first = (int64_t)sub.size();
+    for (int r = 0; r < maxsub; ++r)
+      for (int c = 0; c < NC; ++c)
+        if (nsub[c] > r) {
+          const int st0 = hoff[base + c] + r * kRun;
+          sub.push_back(make_int2(st0, std::min(kRun, hoff[base + c + 1] - st0)));
+        }
+    const int64_t nt = (int64_t)sub.size() - first;
+    const int single = nt <= kThreads ? 1 : 0;
+    for (int64_t k = 0; k < nt; k += kThreads)
+      ch.push_back(make_int4(t, (int)(first + k), (int)std::min<int64_t>(kThreads, nt - k), single));
   }
+  GBRI_CHECK((int64_t)sub.size() < ((int64_t)1 << 31), GBRI_EINVAL, "too many sub-runs");
   p->n_chunks = (int64_t)ch.size();
   GBRI_TRY(dmalloc(&p->chunks, ch.size(), &p->device_bytes));
-  if (!ch.empty())
+  GBRI_TRY(dmalloc(&p->subruns, sub.size(), &p->device_bytes));
+  if (!ch.empty()) {
     GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->subruns, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  }
+  GBRI_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
 
   // persistent grid sizes
   const int sms = num_sms();
