@@ -9,28 +9,36 @@
 
 namespace gbri {
 
-// Degridding (G then W, Sec. 2).  A block takes one chunk (<= kThreads sub-runs of one
-// 16 x 16 tile) and copies the tile's (T + J - 1)^2 grid window into shared memory.
-// Thread t owns sub-run t (<= kRun consecutive visibilities of one cell; the lanes of
-// a warp hold distinct cells): it issues all their metadata and epilogue loads at
-// once, reads the cell's J x J window patch into registers once, and computes
-//   v = w * sum_{t'} wy[t'] sum_t wx[t] patch[t'][t]
-// with the two J-tap weight rows from the shared-memory table.  `Epi` consumes
-// (plan position, v).  Persistent blocks stride over the chunks.
+// Degridding (G then W, Sec. 2).  A block takes one chunk: up to kThreads sub-runs
+// (<= kRun visibilities of one cell each) of one 16 x 16 tile, stored as one
+// contiguous range.  Per chunk:
+//  1. the tile's (T + J - 1)^2 grid window is copied into shared memory (when the
+//     tile changes), the chunk's metadata is staged in shared memory and the
+//     epilogue's operands are prefetched, all with coalesced loads;
+//  2. thread t takes sub-run t (the lanes of a warp hold distinct cells), reads its
+//     cell's J x J window patch into registers once and computes, for each visibility,
+//       v = w * sum_{t'} wy[t'] sum_t wx[t] patch[t'][t]
+//     with the two J-tap weight rows from the shared-memory table;
+//  3. the epilogue consumes (plan position, v) in a coalesced pass.
+// Persistent blocks stride over the chunks, heaviest tiles first.
 template <int J, class Epi>
-__global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_degrid(VisGeom geo, const float2* __restrict__ grid, Epi epi) {
+__global__ void __launch_bounds__(kThreads, 2) k_degrid(VisGeom geo, const float2* __restrict__ grid, Epi epi) {
   extern __shared__ float4 smem_dg[];
   constexpr int P = kTile + J - 1;
   float* sw = reinterpret_cast<float*>(smem_dg);
   const int S = 1 << geo.log2S;
   float2* win = reinterpret_cast<float2*>(sw + S * J);
+  uint2* sm_meta = reinterpret_cast<uint2*>(win + P * kWinPitch);
+  float2* sm_phi = reinterpret_cast<float2*>(sm_meta + kChunk);
   copy_table_to_smem(sw, geo.wtab, S * J);
   const int K = geo.K;
   int cur_tile = -1;
   for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
     const int4 ch = geo.chunks[c];
+    const int2 s0 = geo.subruns[ch.y], s1 = geo.subruns[ch.y + ch.z - 1];
+    const int lo = s0.x, cnt = s1.x + s1.y - s0.x;
+    __syncthreads();  // the previous chunk is done with the shared buffers
     if (ch.x != cur_tile) {
-      __syncthreads();
       const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
       const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
       for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
@@ -38,59 +46,60 @@ __global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_degrid(VisGeom g
         win[r * kWinPitch + cc] = __ldg(grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K));
       }
       cur_tile = ch.x;
-      __syncthreads();
     }
-    if ((int)threadIdx.x >= ch.z) continue;
-    const int2 sr = geo.subruns[ch.y + threadIdx.x];
-    const int p0 = sr.x, n = sr.y;
-    uint2 m[kRun];
     typename Epi::Pre pre[kRun];
 #pragma unroll
-    for (int k = 0; k < kRun; ++k)
-      if (k < n) {
-        m[k] = geo.meta[p0 + k];
-        pre[k] = epi.load(p0 + k);
+    for (int k = 0; k < kRun; ++k) {
+      const int i = threadIdx.x + k * kThreads;
+      if (i < cnt) {
+        sm_meta[i] = geo.meta[lo + i];
+        pre[k] = epi.load(lo + i);
       }
-    // all visibilities of a sub-run share one cell: its J x J window patch, once
-    const int ci = ((int)(m[0].x >> 16) >> geo.log2S) * kWinPitch + ((int)(m[0].x & 0xffff) >> geo.log2S);
-    float2 pt[J][J];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < ch.z) {
+      const int2 sr = geo.subruns[ch.y + threadIdx.x];
+      const int l0 = sr.x - lo;
+      const uint32_t x0 = sm_meta[l0].x;
+      const int ci = ((int)(x0 >> 16) >> geo.log2S) * kWinPitch + ((int)(x0 & 0xffff) >> geo.log2S);
+      float2 pt[J][J];
 #pragma unroll
-    for (int tp = 0; tp < J; ++tp)
+      for (int tp = 0; tp < J; ++tp)
 #pragma unroll
-      for (int t = 0; t < J; ++t) pt[tp][t] = win[ci + tp * kWinPitch + t];
+        for (int t = 0; t < J; ++t) pt[tp][t] = win[ci + tp * kWinPitch + t];
+#pragma unroll
+      for (int k = 0; k < kRun; ++k) {
+        if (k >= sr.y) break;
+        const uint2 m = sm_meta[l0 + k];
+        float wx[J], wy[J];
+        load_taps<J>(sw, (m.x & 0xffff) & (S - 1), wx);
+        load_taps<J>(sw, (m.x >> 16) & (S - 1), wy);
+        float ar = 0.f, ai = 0.f;
+#pragma unroll
+        for (int tp = 0; tp < J; ++tp) {
+          float rr = 0.f, ri = 0.f;
+#pragma unroll
+          for (int t = 0; t < J; ++t) {
+            rr = fmaf(wx[t], pt[tp][t].x, rr);
+            ri = fmaf(wx[t], pt[tp][t].y, ri);
+          }
+          ar = fmaf(wy[tp], rr, ar);
+          ai = fmaf(wy[tp], ri, ai);
+        }
+        const float w = __uint_as_float(m.y);
+        sm_phi[l0 + k] = make_float2(w * ar, w * ai);
+      }
+    }
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRun; ++k) {
-      if (k >= n) break;
-      float wx[J], wy[J];
-      load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), wx);
-      load_taps<J>(sw, (m[k].x >> 16) & (S - 1), wy);
-      float ar = 0.f, ai = 0.f;
-#pragma unroll
-      for (int tp = 0; tp < J; ++tp) {
-        float rr = 0.f, ri = 0.f;
-#pragma unroll
-        for (int t = 0; t < J; ++t) {
-          rr = fmaf(wx[t], pt[tp][t].x, rr);
-          ri = fmaf(wx[t], pt[tp][t].y, ri);
-        }
-        ar = fmaf(wy[tp], rr, ar);
-        ai = fmaf(wy[tp], ri, ai);
-      }
-      const float w = __uint_as_float(m[k].y);
-      epi.store(p0 + k, pre[k], make_float2(w * ar, w * ai));
+      const int i = threadIdx.x + k * kThreads;
+      if (i < cnt) epi.store(lo + i, pre[k], sm_phi[i]);
     }
   }
   epi.finish();
 }
 
-// Gridding (W^T then G^T, Sec. 2).  A block takes one chunk of one tile.  Thread t
-// owns sub-run t (<= kRun visibilities of one cell; the lanes of a warp hold
-// distinct cells): it loads them at once, sums w * v * wy[t'] wx[t] into a J x J
-// register patch and adds the patch to a shared (T + J - 1)^2 accumulator (planar
-// re / im) with one atomic per tap: kRun times fewer shared atomics than one per
-// visibility, and no two lanes of an atomic instruction on the same cell.  The accumulator is then written to the global grid: plain stores
-// for the cells that no other tile touches when the tile is a single chunk, vector
-// atomics otherwise.  `Src` gives the visibility value at a plan position.
 template <int J>
 __device__ __forceinline__ void flush_patch(float* acc_re, float* acc_im, int a0, const float2 (&pt)[J][J]) {
 #pragma unroll
@@ -102,50 +111,80 @@ __device__ __forceinline__ void flush_patch(float* acc_re, float* acc_im, int a0
     }
 }
 
+// Gridding (W^T then G^T, Sec. 2).  A block takes one chunk (one contiguous range of
+// up to kThreads sub-runs of one tile):
+//  1. the chunk's metadata and weighted values w * v are staged in shared memory
+//     with coalesced loads;
+//  2. thread t takes sub-run t (<= kRun visibilities of one cell; the lanes of a
+//     warp hold distinct cells), sums wy[t'] wx[t] w v into a J x J register patch
+//     and adds it to a shared (T + J - 1)^2 accumulator (planar re / im) with one
+//     atomic per tap: no two lanes of an atomic instruction on the same cell;
+//  3. the accumulator goes to the global grid: plain stores for the cells no other
+//     tile touches when the tile is a single chunk, vector atomics otherwise.
+// `Src` gives the visibility value at a plan position.
 template <int J, class Src>
-__global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_grid(VisGeom geo, float2* __restrict__ grid, Src src) {
+__global__ void __launch_bounds__(kThreads, 2) k_grid(VisGeom geo, float2* __restrict__ grid, Src src) {
   extern __shared__ float4 smem_gr[];
   constexpr int P = kTile + J - 1;
   const int S = 1 << geo.log2S;
   float* sw = reinterpret_cast<float*>(smem_gr);
   float* acc_re = sw + S * J;
   float* acc_im = acc_re + P * kAccPitch;
+  uint2* sm_meta = reinterpret_cast<uint2*>(acc_im + P * kAccPitch);
+  float2* sm_val = reinterpret_cast<float2*>(sm_meta + kChunk);
   copy_table_to_smem(sw, geo.wtab, S * J);
   const int K = geo.K;
   for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
     const int4 ch = geo.chunks[c];
+    const int2 s0 = geo.subruns[ch.y], s1 = geo.subruns[ch.y + ch.z - 1];
+    const int lo = s0.x, cnt = s1.x + s1.y - s0.x;
     for (int i = threadIdx.x; i < P * kAccPitch; i += blockDim.x) {
       acc_re[i] = 0.f;
       acc_im[i] = 0.f;
     }
-    __syncthreads();
-    if ((int)threadIdx.x < ch.z) {
-      const int2 sr = geo.subruns[ch.y + threadIdx.x];
-      const int p0 = sr.x, n = sr.y;
+    {
       uint2 m[kRun];
       float2 v[kRun];
 #pragma unroll
-      for (int k = 0; k < kRun; ++k)
-        if (k < n) {
-          m[k] = geo.meta[p0 + k];
-          v[k] = src(p0 + k);
+      for (int k = 0; k < kRun; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        if (i < cnt) {
+          m[k] = geo.meta[lo + i];
+          v[k] = src(lo + i);
         }
+      }
+#pragma unroll
+      for (int k = 0; k < kRun; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        if (i < cnt) {
+          const float w = __uint_as_float(m[k].y);
+          sm_meta[i] = m[k];
+          sm_val[i] = make_float2(w * v[k].x, w * v[k].y);
+        }
+      }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < ch.z) {
+      const int2 sr = geo.subruns[ch.y + threadIdx.x];
+      const int l0 = sr.x - lo;
       float2 pt[J][J];
 #pragma unroll
       for (int tp = 0; tp < J; ++tp)
 #pragma unroll
         for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
+      uint32_t x0 = 0;
 #pragma unroll
       for (int k = 0; k < kRun; ++k) {
-        if (k >= n) break;
+        if (k >= sr.y) break;
+        const uint32_t x = sm_meta[l0 + k].x;
+        x0 = x;
         float wx[J], wy[J];
-        load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), wx);
-        load_taps<J>(sw, (m[k].x >> 16) & (S - 1), wy);
-        const float w = __uint_as_float(m[k].y);
-        const float vr = w * v[k].x, vi = w * v[k].y;
+        load_taps<J>(sw, (x & 0xffff) & (S - 1), wx);
+        load_taps<J>(sw, (x >> 16) & (S - 1), wy);
+        const float2 vv = sm_val[l0 + k];
 #pragma unroll
         for (int tp = 0; tp < J; ++tp) {
-          const float br = wy[tp] * vr, bi = wy[tp] * vi;
+          const float br = wy[tp] * vv.x, bi = wy[tp] * vv.y;
 #pragma unroll
           for (int t = 0; t < J; ++t) {
             pt[tp][t].x = fmaf(wx[t], br, pt[tp][t].x);
@@ -153,21 +192,20 @@ __global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_grid(VisGeom geo
           }
         }
       }
-      // one cell per sub-run; the lanes of a warp hold distinct cells
-      const int a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch + ((int)(m[0].x & 0xffff) >> geo.log2S);
+      const int a0 = ((int)(x0 >> 16) >> geo.log2S) * kAccPitch + ((int)(x0 & 0xffff) >> geo.log2S);
       flush_patch<J>(acc_re, acc_im, a0, pt);
     }
     __syncthreads();
     const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
     const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
-    // accumulator rows / cols [lo, hi) belong to no other tile's window
-    constexpr int lo = J - 1, hi = kTile;
+    // accumulator rows / cols [lo_x, hi_x) belong to no other tile's window
+    constexpr int lo_x = J - 1, hi_x = kTile;
     const bool single = ch.w != 0;
     for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
       const int r = i / P, cc = i - r * P;
       const float2 a = make_float2(acc_re[r * kAccPitch + cc], acc_im[r * kAccPitch + cc]);
       float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
-      if (single && r >= lo && r < hi && cc >= lo && cc < hi) *dst = a;
+      if (single && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) *dst = a;
       else if (a.x != 0.f || a.y != 0.f) atomicAdd(dst, a);
     }
     __syncthreads();

@@ -97,14 +97,16 @@ struct VisGeom {
 };
 
 inline size_t degrid_smem(const gbri_plan* p) {
-  return (size_t)p->S * p->J * sizeof(float) + (size_t)(kTile + p->J - 1) * kWinPitch * sizeof(float2);
+  return (size_t)p->S * p->J * sizeof(float) + (size_t)(kTile + p->J - 1) * kWinPitch * sizeof(float2) +
+         (size_t)kChunk * (sizeof(uint2) + sizeof(float2));
 }
 // gridding accumulator: (T + J - 1) rows, planar re / im, row pitch kAccPitch (== 16 mod 32
 // so that the two tile rows of a warp fall on disjoint banks)
 constexpr int kAccPitch = 48;
 inline size_t grid_smem(const gbri_plan* p) {
   const int P = kTile + p->J - 1;
-  return (size_t)p->S * p->J * sizeof(float) + (size_t)2 * P * kAccPitch * sizeof(float);
+  return (size_t)p->S * p->J * sizeof(float) + (size_t)2 * P * kAccPitch * sizeof(float) +
+         (size_t)kChunk * (sizeof(uint2) + sizeof(float2));
 }
 
 inline VisGeom vis_geom(const gbri_plan* p) {

@@ -154,6 +154,22 @@ __global__ void k_scatter(const int32_t* __restrict__ key, const uint32_t* __res
   }
 }
 
+// Move every sub-run (<= kRun visibilities of one cell) from its cell-sorted place to
+// its place in the sub-run order: one thread per sub-run.
+__global__ void k_relayout(const int2* __restrict__ old_sub, const int32_t* __restrict__ new_start, int64_t n_sub,
+                           const uint2* __restrict__ meta_in, const int32_t* __restrict__ perm_in,
+                           uint2* __restrict__ meta_out, int32_t* __restrict__ perm_out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sub; i += stride) {
+    const int2 o = old_sub[i];
+    const int d = new_start[i];
+    for (int k = 0; k < o.y; ++k) {
+      meta_out[d + k] = meta_in[o.x + k];
+      perm_out[d + k] = perm_in[o.x + k];
+    }
+  }
+}
+
 __global__ void k_tile_starts(const int32_t* __restrict__ offsets, int n_tiles, int cells_per_tile,
                               int32_t* __restrict__ starts) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -347,13 +363,50 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
       ch.push_back(make_int4(t, (int)(first + k), (int)std::min<int64_t>(kThreads, nt - k), single));
   }
   GBRI_CHECK((int64_t)sub.size() < ((int64_t)1 << 31), GBRI_EINVAL, "too many sub-runs");
+  // physical layout = sub-run order: a chunk's sub-runs form one contiguous range
+  std::vector<int32_t> nstart(sub.size());
+  {
+    int64_t run = 0;
+    for (size_t i = 0; i < sub.size(); ++i) {
+      nstart[i] = (int32_t)run;
+      run += sub[i].y;
+    }
+  }
   p->n_chunks = (int64_t)ch.size();
   GBRI_TRY(dmalloc(&p->chunks, ch.size(), &p->device_bytes));
   GBRI_TRY(dmalloc(&p->subruns, sub.size(), &p->device_bytes));
-  if (!ch.empty()) {
-    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  if (!sub.empty()) {
+    int2* dold = nullptr;
+    int32_t* dnew = nullptr;
+    uint2* meta2 = nullptr;
+    int32_t* perm2 = nullptr;
+    if ((st = dmalloc(&dold, sub.size(), nullptr)) || (st = dmalloc(&dnew, sub.size(), nullptr)) ||
+        (st = dmalloc(&meta2, (size_t)M, nullptr)) || (st = dmalloc(&perm2, (size_t)M, nullptr))) {
+      cudaFree(dold); cudaFree(dnew); cudaFree(meta2); cudaFree(perm2);
+      return st;
+    }
+    cudaMemcpyAsync(dold, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dnew, nstart.data(), nstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    launch_begin(GBRI_K_OTHER, s);
+    k_relayout<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)sub.size(), 256), (int64_t)num_sms() * 16), 256, 0, s>>>(
+        dold, dnew, (int64_t)sub.size(), p->meta, p->perm, meta2, perm2);
+    st = launch_end(GBRI_K_OTHER, s);
+    cudaStreamSynchronize(s);
+    cudaFree(dold);
+    cudaFree(dnew);
+    if (st != GBRI_OK) {
+      cudaFree(meta2); cudaFree(perm2);
+      return st;
+    }
+    cudaFree(p->meta);
+    cudaFree(p->perm);
+    p->meta = meta2;
+    p->perm = perm2;
+    for (size_t i = 0; i < sub.size(); ++i) sub[i].x = nstart[i];
     GBRI_CHECK_CUDA(cudaMemcpyAsync(p->subruns, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
   }
+  if (!ch.empty())
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   GBRI_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
 
   // persistent grid sizes

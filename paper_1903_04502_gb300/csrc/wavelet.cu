@@ -243,50 +243,37 @@ __device__ __forceinline__ void idwt_block(SynSmem& sm, const float* __restrict_
     }
   }
   __syncthreads();
-  for (int r = ty; r < kSB; r += 8) {
-    const int R = r0 + r;
-    for (int sc = tx; sc < 2 * KB; sc += 32) {
-      float v = 0.f;
-      if (R & 1) {
+  // column synthesis, two output rows (2p, 2p + 1) per item: both read the same L/2
+  // coefficient rows kq = p + L/2 - 1 - s of the a and d halves
+  for (int idx = threadIdx.x; idx < (kSB / 2) * 2 * KB; idx += blockDim.x) {
+    const int pr = idx / (2 * KB), sc = idx - pr * (2 * KB);
+    float ve = 0.f, vo = 0.f;
 #pragma unroll
-        for (int i = 1; i < L; i += 2) {
-          const int kq = ((R - i) >> 1) - kr_lo;
-          v = fmaf(h[i], sm.tc[kq][sc], v);
-          v = fmaf(g[i], sm.tc[KB + kq][sc], v);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < L; i += 2) {
-          const int kq = ((R - i) >> 1) - kr_lo;
-          v = fmaf(h[i], sm.tc[kq][sc], v);
-          v = fmaf(g[i], sm.tc[KB + kq][sc], v);
-        }
-      }
-      sm.tm[r][sc] = v;
+    for (int q = 0; q < L / 2; ++q) {
+      const int kq = pr + L / 2 - 1 - q;
+      const float a = sm.tc[kq][sc], d = sm.tc[KB + kq][sc];
+      ve = fmaf(h[2 * q], a, fmaf(g[2 * q], d, ve));
+      vo = fmaf(h[2 * q + 1], a, fmaf(g[2 * q + 1], d, vo));
     }
+    sm.tm[2 * pr][sc] = ve;
+    sm.tm[2 * pr + 1][sc] = vo;
   }
   __syncthreads();
-  {
-    const int c = tx, C = c0 + c;
-    for (int r = ty; r < kSB; r += 8) {
-      const int R = r0 + r;
-      float v = 0.f;
-      if (C & 1) {
+  // row synthesis, two output columns per item
+  for (int idx = threadIdx.x; idx < kSB * (kSB / 2); idx += blockDim.x) {
+    const int r = idx / (kSB / 2), pc = idx - r * (kSB / 2);
+    float ve = 0.f, vo = 0.f;
 #pragma unroll
-        for (int i = 1; i < L; i += 2) {
-          const int kq = ((C - i) >> 1) - kc_lo;
-          v = fmaf(h[i], sm.tm[r][kq], v);
-          v = fmaf(g[i], sm.tm[r][KB + kq], v);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < L; i += 2) {
-          const int kq = ((C - i) >> 1) - kc_lo;
-          v = fmaf(h[i], sm.tm[r][kq], v);
-          v = fmaf(g[i], sm.tm[r][KB + kq], v);
-        }
-      }
-      if (R < m && C < m) dst[(size_t)R * n + C] = v;
+    for (int q = 0; q < L / 2; ++q) {
+      const int kq = pc + L / 2 - 1 - q;
+      const float a = sm.tm[r][kq], d = sm.tm[r][KB + kq];
+      ve = fmaf(h[2 * q], a, fmaf(g[2 * q], d, ve));
+      vo = fmaf(h[2 * q + 1], a, fmaf(g[2 * q + 1], d, vo));
+    }
+    const int R = r0 + r, C = c0 + 2 * pc;
+    if (R < m) {
+      if (C < m) dst[(size_t)R * n + C] = ve;
+      if (C + 1 < m) dst[(size_t)R * n + C + 1] = vo;
     }
   }
 }

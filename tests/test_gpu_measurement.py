@@ -80,19 +80,34 @@ def test_plan_order_and_permutation(g):
 
 def test_sort_is_bit_exact_tile_major(g):
     """The plan's visibility order follows the oracle's FP64 quantisation exactly (integer work,
-    compared exactly): sorted by (tile, cell row, cell column) of the base grid cell."""
-    n, M, K, S, T = 128, 30_000, 256, 4096, 16
+    compared exactly): non-empty 16 x 16 tiles heaviest first (ties by tile index), and inside a
+    tile the sub-runs (up to 4 visibilities of one base cell) listed rank-major: every cell's
+    first sub-run in cell order, then every second one, and so on."""
+    n, M, K, S, T, R = 128, 30_000, 256, 4096, 16, 4
     _, uvw = make(n, M)
     plan = g.Plan(torch.from_numpy(uvw).cuda(), n, S=S)
     perm = plan.permutation().cpu().numpy()
+    assert np.array_equal(np.sort(perm), np.arange(M))
     kx = me.quantise(uvw[:, 0], K, S)
     ky = me.quantise(uvw[:, 1], K, S)
     cx = np.mod(np.floor_divide(kx, S), K)
     cy = np.mod(np.floor_divide(ky, S), K)
-    key = ((cy // T) * (K // T) + cx // T) * T * T + (cy % T) * T + (cx % T)
-    assert np.all(np.diff(key[perm]) >= 0)
-    assert np.array_equal(np.bincount(key, minlength=K * K), np.bincount(key[perm], minlength=K * K))
-    assert plan.n_tiles == len(np.unique(key // (T * T)))
+    tile = (cy // T) * (K // T) + cx // T
+    cell = (cy % T) * T + (cx % T)
+    counts = np.bincount(tile, minlength=(K // T) ** 2)
+    tiles = np.nonzero(counts)[0]
+    order = tiles[np.argsort(-counts[tiles], kind="stable")]
+    expect_tiles, expect_cells = [], []
+    for t in order:
+        cc = np.bincount(cell[tile == t], minlength=T * T)
+        for r in range(int(-(-cc.max() // R))):
+            for c in np.nonzero(cc > r * R)[0]:
+                k = min(R, cc[c] - r * R)
+                expect_tiles += [t] * k
+                expect_cells += [c] * k
+    assert np.array_equal(tile[perm], np.array(expect_tiles))
+    assert np.array_equal(cell[perm], np.array(expect_cells))
+    assert plan.n_tiles == len(tiles)
 
 
 def test_adjoint_identity_on_gpu(g):
