@@ -9,36 +9,32 @@
 
 namespace gbri {
 
-// Degridding (G then W, Sec. 2).  A block takes one chunk: up to kThreads sub-runs
-// (<= kRun visibilities of one cell each) of one 16 x 16 tile, stored as one
-// contiguous range.  Per chunk:
-//  1. the tile's (T + J - 1)^2 grid window is copied into shared memory (when the
-//     tile changes), the chunk's metadata is staged in shared memory and the
-//     epilogue's operands are prefetched, all with coalesced loads;
-//  2. thread t takes sub-run t (the lanes of a warp hold distinct cells), reads its
-//     cell's J x J window patch into registers once and computes, for each visibility,
-//       v = w * sum_{t'} wy[t'] sum_t wx[t] patch[t'][t]
-//     with the two J-tap weight rows from the shared-memory table;
-//  3. the epilogue consumes (plan position, v) in a coalesced pass.
-// Persistent blocks stride over the chunks, heaviest tiles first.
+// Degridding (G then W, Sec. 2).  A block takes one chunk (one contiguous range of
+// at most kThreads * kRun visibilities of one 16 x 16 tile), copies the tile's
+// (T + J - 1)^2 grid window into shared memory when the tile changes, and gives one
+// thread per visibility with kRun visibilities in flight per thread (coalesced
+// metadata and epilogue streams):
+//   v = w * sum_{t'} wy[t'] sum_t wx[t] win[cy + t'][cx + t]
+// with the two J-tap weight rows from the shared-memory table.  The visibilities of
+// a sub-run share a cell, so neighbouring lanes often read the same window words.
+// `Epi` consumes (plan position, v).  Persistent blocks stride over the chunks.
 template <int J, class Epi>
-__global__ void __launch_bounds__(kThreads, 2) k_degrid(VisGeom geo, const float2* __restrict__ grid, Epi epi) {
+__global__ void __launch_bounds__(kThreads, (J == 4 ? 4 : 3)) k_degrid(VisGeom geo, const float2* __restrict__ grid,
+                                                                       Epi epi) {
   extern __shared__ float4 smem_dg[];
   constexpr int P = kTile + J - 1;
   float* sw = reinterpret_cast<float*>(smem_dg);
   const int S = 1 << geo.log2S;
-  float2* win = reinterpret_cast<float2*>(sw + S * J);
-  uint2* sm_meta = reinterpret_cast<uint2*>(win + P * kWinPitch);
-  float2* sm_phi = reinterpret_cast<float2*>(sm_meta + kChunk);
-  copy_table_to_smem(sw, geo.wtab, S * J);
+  float2* win = reinterpret_cast<float2*>(sw + table_floats(S, J));
+  copy_table_to_smem(sw, geo.wtab, table_floats(S, J));
   const int K = geo.K;
   int cur_tile = -1;
   for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
     const int4 ch = geo.chunks[c];
     const int2 s0 = geo.subruns[ch.y], s1 = geo.subruns[ch.y + ch.z - 1];
     const int lo = s0.x, cnt = s1.x + s1.y - s0.x;
-    __syncthreads();  // the previous chunk is done with the shared buffers
     if (ch.x != cur_tile) {
+      __syncthreads();
       const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
       const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
       for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
@@ -46,154 +42,117 @@ __global__ void __launch_bounds__(kThreads, 2) k_degrid(VisGeom geo, const float
         win[r * kWinPitch + cc] = __ldg(grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K));
       }
       cur_tile = ch.x;
+      __syncthreads();
     }
+    uint2 m[kRun];
     typename Epi::Pre pre[kRun];
 #pragma unroll
     for (int k = 0; k < kRun; ++k) {
       const int i = threadIdx.x + k * kThreads;
       if (i < cnt) {
-        sm_meta[i] = geo.meta[lo + i];
+        m[k] = geo.meta[lo + i];
         pre[k] = epi.load(lo + i);
       }
     }
-    __syncthreads();
-    if ((int)threadIdx.x < ch.z) {
-      const int2 sr = geo.subruns[ch.y + threadIdx.x];
-      const int l0 = sr.x - lo;
-      const uint32_t x0 = sm_meta[l0].x;
-      const int ci = ((int)(x0 >> 16) >> geo.log2S) * kWinPitch + ((int)(x0 & 0xffff) >> geo.log2S);
-      float2 pt[J][J];
-#pragma unroll
-      for (int tp = 0; tp < J; ++tp)
-#pragma unroll
-        for (int t = 0; t < J; ++t) pt[tp][t] = win[ci + tp * kWinPitch + t];
-#pragma unroll
-      for (int k = 0; k < kRun; ++k) {
-        if (k >= sr.y) break;
-        const uint2 m = sm_meta[l0 + k];
-        float wx[J], wy[J];
-        load_taps<J>(sw, (m.x & 0xffff) & (S - 1), wx);
-        load_taps<J>(sw, (m.x >> 16) & (S - 1), wy);
-        float ar = 0.f, ai = 0.f;
-#pragma unroll
-        for (int tp = 0; tp < J; ++tp) {
-          float rr = 0.f, ri = 0.f;
-#pragma unroll
-          for (int t = 0; t < J; ++t) {
-            rr = fmaf(wx[t], pt[tp][t].x, rr);
-            ri = fmaf(wx[t], pt[tp][t].y, ri);
-          }
-          ar = fmaf(wy[tp], rr, ar);
-          ai = fmaf(wy[tp], ri, ai);
-        }
-        const float w = __uint_as_float(m.y);
-        sm_phi[l0 + k] = make_float2(w * ar, w * ai);
-      }
-    }
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRun; ++k) {
       const int i = threadIdx.x + k * kThreads;
-      if (i < cnt) epi.store(lo + i, pre[k], sm_phi[i]);
+      if (i >= cnt) break;
+      const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
+      float wx[J], wy[J];
+      load_taps<J>(sw, lx & (S - 1), S, wx);
+      load_taps<J>(sw, ly & (S - 1), S, wy);
+      const float2* base = win + (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
+      float ar = 0.f, ai = 0.f;
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp) {
+        float rr = 0.f, ri = 0.f;
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+          const float2 gv = base[tp * kWinPitch + t];
+          rr = fmaf(wx[t], gv.x, rr);
+          ri = fmaf(wx[t], gv.y, ri);
+        }
+        ar = fmaf(wy[tp], rr, ar);
+        ai = fmaf(wy[tp], ri, ai);
+      }
+      const float w = __uint_as_float(m[k].y);
+      epi.store(lo + i, pre[k], make_float2(w * ar, w * ai));
     }
   }
   epi.finish();
 }
 
-template <int J>
-__device__ __forceinline__ void flush_patch(float* acc_re, float* acc_im, int a0, const float2 (&pt)[J][J]) {
-#pragma unroll
-  for (int tp = 0; tp < J; ++tp)
-#pragma unroll
-    for (int t = 0; t < J; ++t) {
-      atomicAdd(acc_re + a0 + tp * kAccPitch + t, pt[tp][t].x);
-      atomicAdd(acc_im + a0 + tp * kAccPitch + t, pt[tp][t].y);
-    }
-}
-
-// Gridding (W^T then G^T, Sec. 2).  A block takes one chunk (one contiguous range of
-// up to kThreads sub-runs of one tile):
-//  1. the chunk's metadata and weighted values w * v are staged in shared memory
-//     with coalesced loads;
-//  2. thread t takes sub-run t (<= kRun visibilities of one cell; the lanes of a
-//     warp hold distinct cells), sums wy[t'] wx[t] w v into a J x J register patch
-//     and adds it to a shared (T + J - 1)^2 accumulator (planar re / im) with one
-//     atomic per tap: no two lanes of an atomic instruction on the same cell;
-//  3. the accumulator goes to the global grid: plain stores for the cells no other
-//     tile touches when the tile is a single chunk, vector atomics otherwise.
+// Gridding (W^T then G^T, Sec. 2).  A block takes one chunk (up to kThreads sub-run
+// slots of one tile; each round of the rank-major order starts at a warp boundary,
+// so the 32 lanes of a warp hold sub-runs of 32 distinct cells).  Thread t loads
+// its sub-run (<= kRun visibilities of one cell) at once, sums w * v * wy[t'] wx[t]
+// into a J x J register patch and adds it to its warp's private (T + J - 1)^2
+// accumulator in shared memory with plain read-modify-writes: the lanes of one
+// instruction touch distinct cells, and successive instructions of a warp are
+// ordered, so no atomics are needed.  The block then sums the warp accumulators and
+// writes the tile window to the global grid: plain stores for the cells no other
+// tile touches when the tile is a single chunk, vector atomics otherwise.
 // `Src` gives the visibility value at a plan position.
 template <int J, class Src>
-__global__ void __launch_bounds__(kThreads, 2) k_grid(VisGeom geo, float2* __restrict__ grid, Src src) {
+__global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_grid(VisGeom geo, float2* __restrict__ grid, Src src) {
   extern __shared__ float4 smem_gr[];
   constexpr int P = kTile + J - 1;
+  constexpr int W = kThreads / 32;
   const int S = 1 << geo.log2S;
   float* sw = reinterpret_cast<float*>(smem_gr);
-  float* acc_re = sw + S * J;
-  float* acc_im = acc_re + P * kAccPitch;
-  uint2* sm_meta = reinterpret_cast<uint2*>(acc_im + P * kAccPitch);
-  float2* sm_val = reinterpret_cast<float2*>(sm_meta + kChunk);
-  copy_table_to_smem(sw, geo.wtab, S * J);
+  float2* accs = reinterpret_cast<float2*>(sw + table_floats(S, J));
+  copy_table_to_smem(sw, geo.wtab, table_floats(S, J));
+  float2* acc = accs + (threadIdx.x >> 5) * (P * kAccPitch2);
   const int K = geo.K;
   for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
     const int4 ch = geo.chunks[c];
-    const int2 s0 = geo.subruns[ch.y], s1 = geo.subruns[ch.y + ch.z - 1];
-    const int lo = s0.x, cnt = s1.x + s1.y - s0.x;
-    for (int i = threadIdx.x; i < P * kAccPitch; i += blockDim.x) {
-      acc_re[i] = 0.f;
-      acc_im[i] = 0.f;
-    }
-    {
-      uint2 m[kRun];
-      float2 v[kRun];
-#pragma unroll
-      for (int k = 0; k < kRun; ++k) {
-        const int i = threadIdx.x + k * kThreads;
-        if (i < cnt) {
-          m[k] = geo.meta[lo + i];
-          v[k] = src(lo + i);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < kRun; ++k) {
-        const int i = threadIdx.x + k * kThreads;
-        if (i < cnt) {
-          const float w = __uint_as_float(m[k].y);
-          sm_meta[i] = m[k];
-          sm_val[i] = make_float2(w * v[k].x, w * v[k].y);
-        }
-      }
-    }
+    for (int i = threadIdx.x; i < W * P * kAccPitch2; i += blockDim.x) accs[i] = make_float2(0.f, 0.f);
     __syncthreads();
     if ((int)threadIdx.x < ch.z) {
       const int2 sr = geo.subruns[ch.y + threadIdx.x];
-      const int l0 = sr.x - lo;
-      float2 pt[J][J];
+      if (sr.y > 0) {
+        uint2 m[kRun];
+        float2 v[kRun];
 #pragma unroll
-      for (int tp = 0; tp < J; ++tp)
+        for (int k = 0; k < kRun; ++k)
+          if (k < sr.y) {
+            m[k] = geo.meta[sr.x + k];
+            v[k] = src(sr.x + k);
+          }
+        float2 pt[J][J];
 #pragma unroll
-        for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
-      uint32_t x0 = 0;
+        for (int tp = 0; tp < J; ++tp)
 #pragma unroll
-      for (int k = 0; k < kRun; ++k) {
-        if (k >= sr.y) break;
-        const uint32_t x = sm_meta[l0 + k].x;
-        x0 = x;
-        float wx[J], wy[J];
-        load_taps<J>(sw, (x & 0xffff) & (S - 1), wx);
-        load_taps<J>(sw, (x >> 16) & (S - 1), wy);
-        const float2 vv = sm_val[l0 + k];
+          for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int tp = 0; tp < J; ++tp) {
-          const float br = wy[tp] * vv.x, bi = wy[tp] * vv.y;
+        for (int k = 0; k < kRun; ++k) {
+          if (k >= sr.y) break;
+          float wx[J], wy[J];
+          load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
+          load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
+          const float w = __uint_as_float(m[k].y);
+          const float vr = w * v[k].x, vi = w * v[k].y;
 #pragma unroll
-          for (int t = 0; t < J; ++t) {
-            pt[tp][t].x = fmaf(wx[t], br, pt[tp][t].x);
-            pt[tp][t].y = fmaf(wx[t], bi, pt[tp][t].y);
+          for (int tp = 0; tp < J; ++tp) {
+            const float br = wy[tp] * vr, bi = wy[tp] * vi;
+#pragma unroll
+            for (int t = 0; t < J; ++t) {
+              pt[tp][t].x = fmaf(wx[t], br, pt[tp][t].x);
+              pt[tp][t].y = fmaf(wx[t], bi, pt[tp][t].y);
+            }
           }
         }
+        const int a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S);
+#pragma unroll
+        for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+          for (int t = 0; t < J; ++t) {
+            float2* q = acc + a0 + tp * kAccPitch2 + t;
+            const float2 o = *q;
+            *q = make_float2(o.x + pt[tp][t].x, o.y + pt[tp][t].y);
+          }
       }
-      const int a0 = ((int)(x0 >> 16) >> geo.log2S) * kAccPitch + ((int)(x0 & 0xffff) >> geo.log2S);
-      flush_patch<J>(acc_re, acc_im, a0, pt);
     }
     __syncthreads();
     const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
@@ -203,7 +162,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(VisGeom geo, float2* __res
     const bool single = ch.w != 0;
     for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
       const int r = i / P, cc = i - r * P;
-      const float2 a = make_float2(acc_re[r * kAccPitch + cc], acc_im[r * kAccPitch + cc]);
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int wq = 0; wq < W; ++wq) {
+        const float2 b = accs[wq * (P * kAccPitch2) + r * kAccPitch2 + cc];
+        a.x += b.x;
+        a.y += b.y;
+      }
       float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
       if (single && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) *dst = a;
       else if (a.x != 0.f || a.y != 0.f) atomicAdd(dst, a);

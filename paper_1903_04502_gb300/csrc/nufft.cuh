@@ -66,21 +66,31 @@ namespace gbri {
 
 __device__ __forceinline__ int wrapK(int v, int K) { return v < 0 ? v + K : (v >= K ? v - K : v); }
 
-// Load the J tap weights of one axis for fractional offset f from the shared table.
+// Load the J tap weights of one axis for fractional offset f (0 <= f < S) from the
+// shared table.  The table stores rows f = 0 .. S/2 only: row S - f is row f reversed
+// (entry t of row f is table[|f + (J/2 - 1 - t) S|]).
 template <int J>
-__device__ __forceinline__ void load_taps(const float* sw, int f, float (&w)[J]) {
+__device__ __forceinline__ void load_taps(const float* sw, int f, int S, float (&w)[J]) {
+  const bool rev = f > (S >> 1);
+  const int row = rev ? S - f : f;
+  float v[J];
   if constexpr (J == 4) {
-    float4 v = reinterpret_cast<const float4*>(sw)[f];
-    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    const float4 q = reinterpret_cast<const float4*>(sw)[row];
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   } else if constexpr (J == 6) {
-    const float2* p = reinterpret_cast<const float2*>(sw + f * 6);
-    float2 a = p[0], b = p[1], c = p[2];
-    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y; w[4] = c.x; w[5] = c.y;
+    const float2* p = reinterpret_cast<const float2*>(sw + row * 6);
+    const float2 a = p[0], b = p[1], c = p[2];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
   } else {
 #pragma unroll
-    for (int t = 0; t < J; ++t) w[t] = sw[f * J + t];
+    for (int t = 0; t < J; ++t) v[t] = sw[row * J + t];
   }
+#pragma unroll
+  for (int t = 0; t < J; ++t) w[t] = rev ? v[J - 1 - t] : v[t];
 }
+
+// floats of the stored tap table (rows 0 .. S/2), rounded up to a whole float4
+__host__ __device__ inline int table_floats(int S, int J) { return (((S / 2 + 1) * J) + 3) & ~3; }
 
 __device__ __forceinline__ void copy_table_to_smem(float* sw, const float* __restrict__ g, int nfloats) {
   const float4* g4 = reinterpret_cast<const float4*>(g);
@@ -97,16 +107,16 @@ struct VisGeom {
 };
 
 inline size_t degrid_smem(const gbri_plan* p) {
-  return (size_t)p->S * p->J * sizeof(float) + (size_t)(kTile + p->J - 1) * kWinPitch * sizeof(float2) +
-         (size_t)kChunk * (sizeof(uint2) + sizeof(float2));
+  return (size_t)table_floats(p->S, p->J) * sizeof(float) + (size_t)(kTile + p->J - 1) * kWinPitch * sizeof(float2);
 }
 // gridding accumulator: (T + J - 1) rows, planar re / im, row pitch kAccPitch (== 16 mod 32
 // so that the two tile rows of a warp fall on disjoint banks)
 constexpr int kAccPitch = 48;
+// warp-private gridding accumulators: float2 cells, row pitch kAccPitch2 (>= T + J - 1)
+constexpr int kAccPitch2 = 21;
 inline size_t grid_smem(const gbri_plan* p) {
   const int P = kTile + p->J - 1;
-  return (size_t)p->S * p->J * sizeof(float) + (size_t)2 * P * kAccPitch * sizeof(float) +
-         (size_t)kChunk * (sizeof(uint2) + sizeof(float2));
+  return (size_t)table_floats(p->S, p->J) * sizeof(float) + (size_t)(kThreads / 32) * P * kAccPitch2 * sizeof(float2);
 }
 
 inline VisGeom vis_geom(const gbri_plan* p) {

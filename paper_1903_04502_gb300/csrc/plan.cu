@@ -239,8 +239,8 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     const int half = (p->J / 2) * S;
     std::vector<double> tab(half + 1);
     for (int i = 0; i <= half; ++i) tab[i] = kb_g((double)i / S, p->J, p->beta);
-    std::vector<float> w((size_t)S * p->J);
-    for (int f = 0; f < S; ++f)
+    std::vector<float> w((size_t)table_floats(S, p->J), 0.f);
+    for (int f = 0; f <= S / 2; ++f)
       for (int t = 0; t < p->J; ++t) {
         const int d = std::abs(f + (p->J / 2 - 1 - t) * S);
         w[(size_t)f * p->J + t] = (d <= half) ? (float)tab[d] : 0.f;
@@ -323,7 +323,8 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
 
   // Sub-runs: at most kRun consecutive visibilities of one cell.  Within a tile they are
   // listed rank-major (every cell's first sub-run in cell order, then every second one,
-  // ...), so the lanes of a warp take sub-runs of distinct cells.  A chunk is up to
+  // ...), each round padded to a multiple of 32 slots, so the lanes of a warp take
+  // sub-runs of distinct cells.  A chunk is up to
   // kThreads sub-runs of one tile (one per thread), heaviest tiles first.
   std::vector<int32_t> hoff((size_t)cells + 1);
   {
@@ -351,12 +352,16 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
       maxsub = std::max(maxsub, nsub[c]);
     }
     const int64_t first = (int64_t)sub.size();
-    for (int r = 0; r < maxsub; ++r)
+    for (int r = 0; r < maxsub; ++r) {
       for (int c = 0; c < NC; ++c)
         if (nsub[c] > r) {
           const int st0 = hoff[base + c] + r * kRun;
           sub.push_back(make_int2(st0, std::min(kRun, hoff[base + c + 1] - st0)));
         }
+      // each round starts at a warp boundary: the 32 lanes of a warp never hold two
+      // sub-runs of one cell (empty slots pad the round)
+      while ((sub.size() - first) % 32) sub.push_back(make_int2(0, 0));
+    }
     const int64_t nt = (int64_t)sub.size() - first;
     const int single = nt <= kThreads ? 1 : 0;
     for (int64_t k = 0; k < nt; k += kThreads)
@@ -413,8 +418,10 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   const int sms = num_sms();
   const int per_sm_dg = std::max(1, (int)((227 * 1024) / (degrid_smem(p) + 1024)));
   const int per_sm_gr = std::max(1, (int)((227 * 1024) / (grid_smem(p) + 1024)));
-  p->degrid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_dg, 8)));
-  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_gr, 8)));
+  // resident blocks per SM: the smaller of the shared-memory and the launch-bounds limits
+  const int reg_dg = p->J == 4 ? 4 : 3, reg_gr = p->J == 4 ? 3 : 2;
+  p->degrid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_dg, reg_dg)));
+  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_gr, reg_gr)));
   p->n_partials = std::max(p->degrid_blocks, 1024);
   GBRI_TRY(dmalloc(&p->partials, (size_t)p->n_partials * 4, &p->device_bytes));
   GBRI_TRY(dmalloc(&p->scalars, 64, &p->device_bytes));
