@@ -215,6 +215,25 @@ int32_t gbri_solver_report(gbri_solver* s, gbri_solve_report* report, void* stre
 int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const float* d_y, const gbri_solve_params* params,
                    float* d_x_out, gbri_solve_report* report, uint32_t flags, void* stream);
 
+/* ---- batched execution (many independent problems in one graph launch) ----- */
+/* A batch holds resident solvers of independent problems (each with its own plan
+ * and wavelet object; sizes, visibility counts and kernel supports may differ).
+ * gbri_batch_step runs n_iter iterations of every member: each iteration is one
+ * launch of a CUDA graph whose branches are the members' captured iterations, so
+ * the problems share the device.  Members may be added and removed between steps
+ * (continuous batching; the graph is rebuilt on the next step).  Remove a solver
+ * before destroying it.  No paper counterpart: the paper distributes one problem
+ * over cluster nodes (Sec. 6); on one GPU the independent problems share it. */
+typedef struct gbri_batch gbri_batch;
+int32_t gbri_batch_create(gbri_batch** out);
+int32_t gbri_batch_destroy(gbri_batch* b);
+/* Errors: EINVAL if the solver is already a member or shares a plan or wavelet object with one. */
+int32_t gbri_batch_add(gbri_batch* b, gbri_solver* s);
+int32_t gbri_batch_remove(gbri_batch* b, gbri_solver* s);
+int32_t gbri_batch_size(const gbri_batch* b);
+/* No host synchronisation.  EINVAL while kernel timing (gbri_profile_enable) is on. */
+int32_t gbri_batch_step(gbri_batch* b, int32_t n_iter, void* stream);
+
 /* ---- diagnostics ------------------------------------------------------------ */
 /* Kernel timing with CUDA events recorded around each library kernel launch on its
  * own stream.  capacity = events per kind to keep (0 disables).  Kinds: */

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (ALGO_ADMM, ALGO_PD, F32, PLAN_ORDER, GbriError, SolveParams, SolveReport,  # noqa: F401
                    K_NAMES)
 
-__all__ = ["Plan", "Wavelet", "Solver", "phi", "phi_adjoint", "op_norm", "psi", "psi_adjoint", "prox_l1",
+__all__ = ["Plan", "Wavelet", "Solver", "Batch", "phi", "phi_adjoint", "op_norm", "psi", "psi_adjoint", "prox_l1",
            "proj_l2ball", "solve", "vis_reorder", "profile_enable", "profile_read", "launch_count",
            "GbriError", "library"]
 
@@ -264,6 +264,43 @@ class Solver:
     def close(self):
         if getattr(self, "_h", None):
             _lib.load().gbri_solver_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Resident solvers of independent problems stepped together (gbri_batch_*): every
+    iteration of every member is one CUDA-graph launch; members may join and leave
+    between steps."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        _lib.check(_lib.load().gbri_batch_create(C.byref(h)))
+        self._h = h
+        self.members = []
+
+    def add(self, solver):
+        _lib.check(_lib.load().gbri_batch_add(self._h, solver._h))
+        self.members.append(solver)
+
+    def remove(self, solver):
+        _lib.check(_lib.load().gbri_batch_remove(self._h, solver._h))
+        self.members.remove(solver)
+
+    def __len__(self):
+        return int(_lib.load().gbri_batch_size(self._h))
+
+    def step(self, n_iter=1, stream=None):
+        _lib.check(_lib.load().gbri_batch_step(self._h, int(n_iter), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().gbri_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -67,6 +67,12 @@ SIGNATURES = {
     "gbri_solver_get_x": (I32, [P, P, P]),
     "gbri_solver_report": (I32, [P, C.POINTER(SolveReport), P]),
     "gbri_solve": (I32, [P, P, P, C.POINTER(SolveParams), P, C.POINTER(SolveReport), U32, P]),
+    "gbri_batch_create": (I32, [C.POINTER(P)]),
+    "gbri_batch_destroy": (I32, [P]),
+    "gbri_batch_add": (I32, [P, P]),
+    "gbri_batch_remove": (I32, [P, P]),
+    "gbri_batch_size": (I32, [P]),
+    "gbri_batch_step": (I32, [P, I32, P]),
     "gbri_profile_enable": (I32, [I32]),
     "gbri_profile_read": (I32, [I32, C.POINTER(D), C.POINTER(I64)]),
     "gbri_launch_count": (I64, []),

@@ -109,50 +109,56 @@ __global__ void __launch_bounds__(kThreads, (J == 4 ? 3 : 2)) k_grid(VisGeom geo
     const int4 ch = geo.chunks[c];
     for (int i = threadIdx.x; i < W * P * kAccPitch2; i += blockDim.x) accs[i] = make_float2(0.f, 0.f);
     __syncthreads();
-    if ((int)threadIdx.x < ch.z) {
-      const int2 sr = geo.subruns[ch.y + threadIdx.x];
-      if (sr.y > 0) {
-        uint2 m[kRun];
-        float2 v[kRun];
+    {
+      const int2 sr = ((int)threadIdx.x < ch.z) ? geo.subruns[ch.y + threadIdx.x] : make_int2(0, 0);
+      const bool active = sr.y > 0;
+      uint2 m[kRun];
+      float2 v[kRun];
 #pragma unroll
-        for (int k = 0; k < kRun; ++k)
-          if (k < sr.y) {
-            m[k] = geo.meta[sr.x + k];
-            v[k] = src(sr.x + k);
-          }
-        float2 pt[J][J];
-#pragma unroll
-        for (int tp = 0; tp < J; ++tp)
-#pragma unroll
-          for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < kRun; ++k) {
-          if (k >= sr.y) break;
-          float wx[J], wy[J];
-          load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
-          load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
-          const float w = __uint_as_float(m[k].y);
-          const float vr = w * v[k].x, vi = w * v[k].y;
-#pragma unroll
-          for (int tp = 0; tp < J; ++tp) {
-            const float br = wy[tp] * vr, bi = wy[tp] * vi;
-#pragma unroll
-            for (int t = 0; t < J; ++t) {
-              pt[tp][t].x = fmaf(wx[t], br, pt[tp][t].x);
-              pt[tp][t].y = fmaf(wx[t], bi, pt[tp][t].y);
-            }
-          }
+      for (int k = 0; k < kRun; ++k)
+        if (k < sr.y) {
+          m[k] = geo.meta[sr.x + k];
+          v[k] = src(sr.x + k);
         }
-        const int a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S);
+      float2 pt[J][J];
 #pragma unroll
-        for (int tp = 0; tp < J; ++tp)
+      for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+        for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < kRun; ++k) {
+        if (k >= sr.y) break;
+        float wx[J], wy[J];
+        load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
+        load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
+        const float w = __uint_as_float(m[k].y);
+        const float vr = w * v[k].x, vi = w * v[k].y;
+#pragma unroll
+        for (int tp = 0; tp < J; ++tp) {
+          const float br = wy[tp] * vr, bi = wy[tp] * vi;
 #pragma unroll
           for (int t = 0; t < J; ++t) {
+            pt[tp][t].x = fmaf(wx[t], br, pt[tp][t].x);
+            pt[tp][t].y = fmaf(wx[t], bi, pt[tp][t].y);
+          }
+        }
+      }
+      const int a0 = active ? ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S)
+                            : 0;
+      // all 32 lanes walk the taps in lockstep: within one tap the active lanes touch
+      // distinct cells, and the warp barrier orders one tap's stores before the next
+      // tap's loads (a neighbour cell's patch overlaps this one)
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+          if (active) {
             float2* q = acc + a0 + tp * kAccPitch2 + t;
             const float2 o = *q;
             *q = make_float2(o.x + pt[tp][t].x, o.y + pt[tp][t].y);
           }
-      }
+          __syncwarp();
+        }
     }
     __syncthreads();
     const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;

@@ -27,6 +27,7 @@
 
 #include "nufft.cuh"
 #include "prox.cuh"
+#include "solver.cuh"
 #include "wavelet.cuh"
 
 namespace gbri {
@@ -405,6 +406,21 @@ int32_t create_solver(gbri_solver* S, const float* d_y, uint32_t flags, cudaStre
 }
 
 }  // namespace
+
+namespace gbri {
+
+int32_t solver_iteration_graph(gbri_solver* s) {
+  if (s->graph_exec) return GBRI_OK;
+  GBRI_CHECK(!profiling_enabled(), GBRI_EINVAL, "batched graphs cannot run while kernel timing is on");
+  return capture_iteration(s);
+}
+cudaGraph_t solver_graph(gbri_solver* s) { return s->graph; }
+int64_t solver_launches_per_iteration(gbri_solver* s) { return s->launches_per_iter; }
+const gbri_plan* solver_plan(const gbri_solver* s) { return s->plan; }
+const gbri_wavelet* solver_wavelet(const gbri_solver* s) { return s->wav; }
+void solver_add_iterations(gbri_solver* s, int n) { s->iters += n; }
+
+}  // namespace gbri
 
 extern "C" {
 
