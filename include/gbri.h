@@ -206,6 +206,9 @@ int32_t gbri_solver_destroy(gbri_solver* s);
 int32_t gbri_solver_step(gbri_solver* s, int32_t n_iter, void* stream);
 /* Copy the current iterate x to d_x (image). */
 int32_t gbri_solver_get_x(gbri_solver* s, float* d_x, void* stream);
+/* Iterations run and the last FP64 relative change ||x+ - x|| / ||x+|| (host; INFINITY before the
+ * first iteration).  Reads one device scalar: synchronises `stream`, no other work. */
+int32_t gbri_solver_status(gbri_solver* s, int32_t* iters, double* rel_change, void* stream);
 /* Fill *report (host) with the iteration count, last relative change and residual. Synchronises. */
 int32_t gbri_solver_report(gbri_solver* s, gbri_solve_report* report, void* stream);
 

@@ -256,6 +256,12 @@ class Solver:
         _lib.check(_lib.load().gbri_solver_get_x(self._h, _ptr(out), _stream(stream)))
         return out
 
+    def status(self, stream=None):
+        """(iterations run, last relative iterate change) -- one scalar read (gbri_solver_status)."""
+        it, rel = C.c_int32(), C.c_double()
+        _lib.check(_lib.load().gbri_solver_status(self._h, C.byref(it), C.byref(rel), _stream(stream)))
+        return it.value, rel.value
+
     def report(self, stream=None):
         r = SolveReport()
         _lib.check(_lib.load().gbri_solver_report(self._h, C.byref(r), _stream(stream)))

@@ -484,6 +484,19 @@ int32_t gbri_solver_get_x(gbri_solver* S, float* d_x, void* stream) {
   return GBRI_OK;
 }
 
+int32_t gbri_solver_status(gbri_solver* S, int32_t* iters, double* rel_change, void* stream) {
+  GBRI_CHECK(S, GBRI_EINVAL, "null solver");
+  double rel = INFINITY;
+  if (S->iters > 0) {
+    cudaStream_t st = (cudaStream_t)stream;
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(&rel, S->sc + SC_REL, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GBRI_CHECK_CUDA(cudaStreamSynchronize(st));
+  }
+  if (iters) *iters = S->iters;
+  if (rel_change) *rel_change = rel;
+  return GBRI_OK;
+}
+
 int32_t gbri_solver_report(gbri_solver* S, gbri_solve_report* r, void* stream) {
   GBRI_CHECK(S && r, GBRI_EINVAL, "null argument");
   cudaStream_t st = (cudaStream_t)stream;

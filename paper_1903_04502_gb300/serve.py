@@ -1,0 +1,224 @@
+"""Request loop for imaging jobs: HBM-budget admission and continuous batching.
+
+Jobs (one imaging problem each: coverage, data, dictionary, stopping rule) arrive
+over time.  The server admits queued jobs in arrival order while their estimated
+device footprint fits the HBM budget, keeps each admitted job's plan, data,
+iterate and dual variables resident on the device, and advances every resident
+job together: each step is one launch of the batch graph (``Batch.step``), so jobs
+of different sizes share the GPU.  Every ``check_every`` iterations the server
+reads each job's FP64 relative iterate change, retires the jobs that converged or
+reached their iteration cap (image copied to the host), frees their memory and
+admits waiting jobs at once -- jobs join and leave the running batch between
+steps.  Latency is measured from arrival to result on the host.
+
+The device work is behind a small engine interface so that the scheduling logic
+(admission, ordering, retirement, failures, latency bookkeeping) can be exercised
+without a GPU.
+"""
+
+import collections
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass(eq=False)
+class Job:
+    """One reconstruction request.  uvw: float32 [M, 4] {u, v, w, weight}; y: complex64 [M]."""
+    uvw: np.ndarray
+    y: np.ndarray
+    n_side: int
+    eps: float
+    J: int = 4
+    db_orders: tuple = (0, 1, 2, 3, 4, 5, 6, 7, 8)
+    levels: int = 4
+    max_iter: int = 300
+    rel_tol: float = 1e-3
+    op_norm_sq: float = 0.0
+    gamma: float = 0.0
+    arrival: float = 0.0
+    job_id: int = -1
+    # filled by the server
+    result: object = None
+    iters: int = 0
+    rel_change: float = float("inf")
+    error: str = ""
+    admitted_at: float = 0.0
+    done_at: float = 0.0
+
+    @property
+    def M(self):
+        return int(self.uvw.shape[0])
+
+    @property
+    def latency(self):
+        return self.done_at - self.arrival
+
+
+def device_footprint(n_side, M, J=4, n_w=9, oversample=2):
+    """Upper estimate of the device bytes a resident job holds (plan, wavelets, solver state)."""
+    K = oversample * n_side
+    N = n_side * n_side
+    plan = M * (8 + 4 + 8) + M // 2 * 8 + 2 * 8 * K * K + (8 * K * K // 64) + (1 << 20)
+    plan_build = M * (16 + 4 + 4 + 4 + 8 + 4) + 8 * K * K  # transient during plan creation
+    wav = 2 * max(1, n_w - 1) * 4 * N
+    solver = M * 8 * 2 + N * 4 * (5 + n_w) + (1 << 20)
+    return plan + max(plan_build - plan, 0) + wav + solver
+
+
+class GpuEngine:
+    """Device side of the server: resident solvers stepped together in one batch graph."""
+
+    def __init__(self, device=0):
+        import torch
+        import paper_1903_04502_gb300 as g
+        self.torch, self.g = torch, g
+        self.device = torch.device("cuda", device)
+        self.batch = g.Batch()
+        self.state = {}
+
+    def start(self, job):
+        torch, g = self.torch, self.g
+        uvw = torch.from_numpy(np.ascontiguousarray(job.uvw, dtype=np.float32)).to(self.device)
+        plan = g.Plan(uvw, job.n_side, J=job.J)
+        del uvw
+        wav = g.Wavelet(job.n_side, job.levels, job.db_orders)
+        y = torch.from_numpy(np.ascontiguousarray(job.y, dtype=np.complex64)).to(self.device)
+        s = g.Solver(plan, wav, y, eps=job.eps, op_norm_sq=job.op_norm_sq, gamma=job.gamma, max_iter=job.max_iter,
+                     rel_tol=job.rel_tol)
+        self.batch.add(s)
+        self.state[job.job_id] = (plan, wav, s)
+
+    def step(self, n_iter):
+        self.batch.step(n_iter)
+
+    def status(self, job):
+        return self.state[job.job_id][2].status()
+
+    def finish(self, job):
+        plan, wav, s = self.state.pop(job.job_id)
+        x = s.x().cpu().numpy()
+        self.batch.remove(s)
+        s.close()
+        wav.close()
+        plan.close()
+        return x
+
+    def abort(self, job):
+        st = self.state.pop(job.job_id, None)
+        if st is None:
+            return
+        plan, wav, s = st
+        try:
+            self.batch.remove(s)
+        except Exception:
+            pass
+        s.close()
+        wav.close()
+        plan.close()
+
+
+class Server:
+    """Continuous-batching request loop with HBM-footprint admission (see the module docstring)."""
+
+    def __init__(self, engine, hbm_budget, check_every=10, clock=time.perf_counter):
+        self.engine = engine
+        self.budget = int(hbm_budget)
+        self.check_every = int(check_every)
+        self.clock = clock
+        self.queue = collections.deque()
+        self.active = []
+        self.done = []
+        self.failed = []
+        self.used = 0
+        self.iterations = 0          # solver iterations run, summed over jobs
+        self.vis_iterations = 0      # visibilities through Phi and Phi^dagger, summed
+        self.max_resident = 0
+        self._next_id = 0
+        self._fp = {}
+
+    def submit(self, job):
+        job.job_id = self._next_id
+        self._next_id += 1
+        if not job.arrival:
+            job.arrival = self.clock()
+        self._fp[job.job_id] = device_footprint(job.n_side, job.M, job.J, len(job.db_orders))
+        if self._fp[job.job_id] > self.budget:
+            job.error = "job needs %d bytes, more than the whole budget of %d" % (self._fp[job.job_id], self.budget)
+            job.done_at = self.clock()
+            self.failed.append(job)
+            return job
+        self.queue.append(job)
+        return job
+
+    def _admit(self):
+        # arrival order: the head of the queue waits until it fits (no overtaking)
+        while self.queue and self.used + self._fp[self.queue[0].job_id] <= self.budget:
+            job = self.queue.popleft()
+            try:
+                self.engine.start(job)
+            except Exception as e:  # bad input, allocation failure: the job fails, the server goes on
+                job.error = "%s: %s" % (type(e).__name__, e)
+                job.done_at = self.clock()
+                self.failed.append(job)
+                self.engine.abort(job)
+                continue
+            job.admitted_at = self.clock()
+            self.used += self._fp[job.job_id]
+            self.active.append(job)
+        self.max_resident = max(self.max_resident, len(self.active))
+
+    def _retire(self):
+        keep = []
+        for job in self.active:
+            it, rel = self.engine.status(job)
+            job.iters, job.rel_change = it, rel
+            if it >= job.max_iter or (job.rel_tol > 0 and rel < job.rel_tol):
+                job.result = self.engine.finish(job)
+                job.done_at = self.clock()
+                self.used -= self._fp[job.job_id]
+                self.done.append(job)
+            else:
+                keep.append(job)
+        self.active = keep
+
+    def tick(self):
+        """Admit what fits, advance every resident job, retire finished ones.  Returns the
+        number of iterations each resident job advanced (0 when idle)."""
+        self._admit()
+        if not self.active:
+            return 0
+        k = min(self.check_every, min(j.max_iter - j.iters for j in self.active))
+        k = max(1, k)
+        self.engine.step(k)
+        for j in self.active:
+            self.iterations += k
+            self.vis_iterations += k * j.M
+        self._retire()
+        return k
+
+    def run(self, arrivals=(), idle_sleep=1e-3):
+        """Serve ``arrivals`` (jobs with ``arrival`` times relative to the start, in order) and
+        every job already queued, until all are done.  Returns the finished jobs."""
+        pending = collections.deque(sorted(arrivals, key=lambda j: j.arrival))
+        t0 = self.clock()
+        for j in pending:
+            j.arrival += t0
+        while pending or self.queue or self.active:
+            now = self.clock()
+            while pending and pending[0].arrival <= now:
+                self.submit(pending.popleft())
+            if self.tick() == 0 and pending:
+                time.sleep(min(idle_sleep, max(0.0, pending[0].arrival - self.clock())))
+        return self.done
+
+    def stats(self):
+        lat = np.array([j.latency for j in self.done]) if self.done else np.zeros(0)
+        return {
+            "jobs": len(self.done),
+            "failed": len(self.failed),
+            "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+            "max_resident": self.max_resident,
+        }

@@ -1,0 +1,52 @@
+"""The request loop on the GPU: jobs that arrive while others run join the running batch,
+memory admission holds the rest back, and every job's image is the same as when the job
+runs alone for the same number of iterations."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import measurement as me, solvers as so
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1903_04502_gb300 as g
+    g.library()
+    return g
+
+
+def make_job(serve, n, M, J, seed, arrival):
+    x = synth.sky(n, 3, 2, seed=seed)
+    uvw = synth.uv_coverage(M, seed=seed + 100, outlier_frac=0.2, weights="uniform")
+    y0 = me.phi(x, me.Geometry(uvw, n, 2, J, 4096))
+    sigma = 10 ** (-30 / 20) * np.linalg.norm(y0) / np.sqrt(M)
+    y = (y0 + sigma * synth.complex_normal(M, seed=seed + 200)).astype(np.complex64)
+    return serve.Job(uvw=uvw, y=y, n_side=n, eps=so.epsilon_from_sigma(sigma, M), J=J, db_orders=(0, 1, 2, 3),
+                     levels=2, max_iter=60, rel_tol=2e-3, op_norm_sq=float(M), gamma=1e-3, arrival=arrival)
+
+
+def test_served_jobs_match_alone(g):
+    from paper_1903_04502_gb300 import serve
+    specs = [(64, 6000, 4), (32, 2000, 6), (96, 12000, 4), (64, 4000, 6), (32, 3000, 4), (128, 20000, 4)]
+    jobs = [make_job(serve, n, M, J, seed=i + 1, arrival=0.02 * i) for i, (n, M, J) in enumerate(specs)]
+    budget = 3 * max(serve.device_footprint(n, M, J, 4) for n, M, J in specs)
+    srv = serve.Server(serve.GpuEngine(), hbm_budget=budget, check_every=5)
+    done = srv.run(jobs)
+    assert len(done) == len(jobs) and not srv.failed
+    assert srv.max_resident >= 2                      # jobs overlapped on the device
+    st = srv.stats()
+    assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]
+    for j in done:
+        plan = g.Plan(torch.from_numpy(j.uvw).cuda(), j.n_side, J=j.J)
+        wav = g.Wavelet(j.n_side, j.levels, j.db_orders)
+        s = g.Solver(plan, wav, torch.from_numpy(j.y).cuda(), eps=j.eps, op_norm_sq=j.op_norm_sq, gamma=j.gamma)
+        s.step(j.iters)
+        xa = s.x().cpu().numpy()
+        assert np.linalg.norm(j.result - xa) <= 1e-5 * np.linalg.norm(xa)
+        assert j.iters == 60 or j.rel_change < 2e-3
