@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=10.0, help="Poisson job arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window of the serving leg (0: skip)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: short power method, no end-to-end, operator or CPU legs")
     return ap.parse_args()
@@ -185,6 +187,62 @@ def run_reference(args):
     return 0
 
 
+def serving_leg(args, dev, seed=1000):
+    """Request loop under Poisson arrivals: jobs of mixed size (image side in {256, 512, 1024},
+    M log-uniform in [1e5, 2e6], J in {4, 6}, SARA Dirac + db1..db8 over 4 levels, at most 300
+    primal-dual iterations or relative change < 1e-3), 150 GB admission budget.  Reports job
+    latency p50 / p99 and throughput, and the same jobs run one at a time."""
+    import torch
+    import paper_1903_04502_gb300 as g
+    from paper_1903_04502_gb300 import serve
+    rng = np.random.default_rng(seed)
+    n_jobs = max(1, int(round(args.serve_rate * args.serve_seconds)))
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n_jobs))
+    jobs = []
+    for i in range(n_jobs):
+        n = int(rng.choice([256, 512, 1024]))
+        M = int(np.exp(rng.uniform(np.log(1e5), np.log(2e6))))
+        J = int(rng.choice([4, 6]))
+        x = synth.sky(n, 10, 4, seed=seed + i)
+        uvw = synth.uv_coverage(M, seed=seed + i + 1, outlier_frac=0.2, weights="uniform")
+        plan = g.Plan(torch.from_numpy(uvw).to(dev), n, J=J)
+        y0 = g.phi(plan, torch.from_numpy(x.astype(np.float32)).to(dev))
+        sigma = 10 ** (-30 / 20) * float(torch.linalg.vector_norm(y0.to(torch.complex128))) / np.sqrt(M)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed + i + 2)
+        y = (y0 + sigma * torch.randn(M, dtype=torch.complex64, device=dev, generator=gen)).cpu().numpy()
+        plan.close()
+        jobs.append(serve.Job(uvw=uvw, y=y, n_side=n, eps=sigma * np.sqrt(M + 2 * np.sqrt(M)), J=J,
+                              db_orders=tuple(range(9)), levels=4, max_iter=300, rel_tol=1e-3,
+                              arrival=float(arrivals[i])))
+    torch.cuda.synchronize()
+    srv = serve.Server(serve.GpuEngine(dev.index or 0), hbm_budget=150e9, check_every=10)
+    t0 = time.perf_counter()
+    srv.run(jobs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    # the same jobs, one at a time, back to back (no arrivals: pure device throughput)
+    t1 = time.perf_counter()
+    seq_vis = 0
+    for j in jobs:
+        plan = g.Plan(torch.from_numpy(j.uvw).to(dev), j.n_side, J=j.J)
+        wav = g.Wavelet(j.n_side, j.levels, j.db_orders)
+        s = g.Solver(plan, wav, torch.from_numpy(j.y).to(dev), eps=j.eps)
+        s.step(j.iters)
+        s.x().cpu()
+        seq_vis += j.iters * j.M
+        s.close(); wav.close(); plan.close()
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t1
+    busy = max(1e-9, max(j.done_at for j in srv.done) - min(j.admitted_at for j in srv.done))
+    return {"rate_jobs_per_s": args.serve_rate, "jobs": st["jobs"], "failed": st["failed"],
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_resident": st["max_resident"],
+            "iterations_per_s": srv.iterations / busy, "vis_per_s": srv.vis_iterations / busy,
+            "wall_s": wall, "one_at_a_time_vis_per_s": seq_vis / seq, "one_at_a_time_s": seq,
+            "budget_gb": 150, "jobs_mix": "n in {256,512,1024}, M log-uniform [1e5, 2e6], J in {4,6}"}
+
+
 def run_gbri(args):
     import torch
     import paper_1903_04502_gb300 as g
@@ -327,6 +385,10 @@ def run_gbri(args):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(cfg, x_true, uvw, args.cpu_sample)
+    serving = None
+    if args.serve_seconds > 0 and ws == 1:
+        solver.close()
+        serving = serving_leg(args, dev)
     ws_bytes = plan.device_bytes + 2 * M * 8 + cfg["n_side"] ** 2 * 4 * (len(cfg["db_orders"]) + 8)
     line = {
         "metric": "Phi+Phi-dagger visibilities/s per primal-dual iteration", "value": value, "unit": "vis/s",
@@ -338,7 +400,7 @@ def run_gbri(args):
                    % (ws_bytes / 1e9), "plan_s": t_plan, "op_norm_sq": opn, "gamma": gamma},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "profiled_region": {"steps": k_prof, "ms_per_step": ms_prof, "launch": "kernel by kernel with events"},
-        "clocks": clk, "kernels": kern, "operators": ops, "impl": "gbri",
+        "clocks": clk, "kernels": kern, "operators": ops, "serving": serving, "impl": "gbri",
     }
     print(json.dumps(line))
     if ws > 1:
