@@ -34,7 +34,7 @@ def make_job(serve, n, M, J, seed, arrival):
 def test_served_jobs_match_alone(g):
     from paper_1903_04502_gb300 import serve
     specs = [(64, 6000, 4), (32, 2000, 6), (96, 12000, 4), (64, 4000, 6), (32, 3000, 4), (128, 20000, 4)]
-    jobs = [make_job(serve, n, M, J, seed=i + 1, arrival=0.02 * i) for i, (n, M, J) in enumerate(specs)]
+    jobs = [make_job(serve, n, M, J, seed=i + 1, arrival=0.0 if i < 3 else 0.005 * i) for i, (n, M, J) in enumerate(specs)]
     budget = 3 * max(serve.device_footprint(n, M, J, 4) for n, M, J in specs)
     srv = serve.Server(serve.GpuEngine(), hbm_budget=budget, check_every=5)
     done = srv.run(jobs)
