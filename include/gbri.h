@@ -66,6 +66,10 @@ typedef struct {
   double kb_beta;            /* Kaiser-Bessel shape; <= 0 selects 2.34 * J */
   int64_t M;                 /* number of visibilities, >= 0 */
   int32_t precision;         /* GBRI_F32 */
+  int32_t vis_per_run;       /* visibilities of one grid cell a thread takes at once: 1..4; 0 selects 4 */
+  int32_t autotune;          /* 1: time the run lengths 1, 2, 4 and the resident blocks per SM of the
+                                visibility kernels at plan creation and keep the fastest (cached per
+                                problem shape for the process); 0: vis_per_run and the occupancy limit */
   int32_t reserved;          /* must be 0 */
 } gbri_plan_desc;
 
@@ -82,6 +86,11 @@ typedef struct {
 int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* desc, const float* d_uvw_weight,
                          void* stream);
 int32_t gbri_plan_destroy(gbri_plan* plan);
+
+/* Launch configuration the plan uses (after autotuning, if requested): visibilities per run and
+ * persistent blocks of the degridding and gridding kernels.  Any pointer may be NULL. */
+int32_t gbri_plan_launch_config(const gbri_plan* plan, int32_t* vis_per_run, int32_t* degrid_blocks,
+                                int32_t* grid_blocks);
 
 /* Plan facts: K, M, number of non-empty 16 x 16 grid tiles, device bytes held. Any pointer may be NULL. */
 int32_t gbri_plan_info(const gbri_plan* plan, int64_t* K, int64_t* M, int64_t* n_tiles,

@@ -54,7 +54,8 @@ class Plan:
     uvw: float32 CUDA tensor [M, 4] of {u, v, w, weight}.
     """
 
-    def __init__(self, uvw, n_side, oversample=2, J=4, S=4096, beta=0.0, stream=None):
+    def __init__(self, uvw, n_side, oversample=2, J=4, S=4096, beta=0.0, vis_per_run=0, autotune=False,
+                 stream=None):
         lib = _lib.load()
         _need(uvw, torch.float32, name="uvw")
         if uvw.dim() != 2 or uvw.shape[1] != 4:
@@ -62,7 +63,8 @@ class Plan:
         self.n_side, self.J, self.S = int(n_side), int(J), int(S)
         self.M = int(uvw.shape[0])
         self.device = uvw.device
-        d = _lib.PlanDesc(self.n_side, int(oversample), self.J, self.S, float(beta), self.M, F32, 0)
+        d = _lib.PlanDesc(self.n_side, int(oversample), self.J, self.S, float(beta), self.M, F32, int(vis_per_run),
+                          1 if autotune else 0, 0)
         h = C.c_void_p()
         _lib.check(lib.gbri_plan_create(C.byref(h), C.byref(d), _ptr(uvw), _stream(stream)))
         self._h = h
@@ -73,6 +75,12 @@ class Plan:
     @property
     def handle(self):
         return self._h
+
+    def launch_config(self):
+        """(visibilities per run, degridding blocks, gridding blocks) in use (gbri_plan_launch_config)."""
+        r, d, g_ = C.c_int32(), C.c_int32(), C.c_int32()
+        _lib.check(_lib.load().gbri_plan_launch_config(self._h, C.byref(r), C.byref(d), C.byref(g_)))
+        return r.value, d.value, g_.value
 
     def permutation(self, stream=None):
         out = torch.empty(self.M, dtype=torch.int32, device=self.device)

@@ -24,7 +24,8 @@ K_NAMES = ["pad", "fft_fwd", "degrid", "grid", "fft_inv", "crop", "psi_adjoint",
 class PlanDesc(C.Structure):
     _fields_ = [("n_side", C.c_int32), ("oversample", C.c_int32), ("J", C.c_int32),
                 ("samples_per_unit", C.c_int32), ("kb_beta", C.c_double), ("M", C.c_int64),
-                ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("precision", C.c_int32), ("vis_per_run", C.c_int32), ("autotune", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class SolveParams(C.Structure):
@@ -49,6 +50,7 @@ SIGNATURES = {
     "gbri_plan_create": (I32, [C.POINTER(P), C.POINTER(PlanDesc), P, P]),
     "gbri_plan_destroy": (I32, [P]),
     "gbri_plan_info": (I32, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
+    "gbri_plan_launch_config": (I32, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
     "gbri_plan_permutation": (I32, [P, P, P]),
     "gbri_vis_reorder": (I32, [P, P, P, I32, P]),
     "gbri_phi": (I32, [P, P, P, U32, P]),

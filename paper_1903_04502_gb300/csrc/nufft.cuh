@@ -59,7 +59,10 @@ struct gbri_plan {
   cufftHandle fft = 0;
   bool fft_ok = false;
   int64_t device_bytes = 0;
+  int64_t layout_bytes = 0;
   int degrid_blocks = 0, grid_blocks = 0;
+  int run_len = 4;  // visibilities per sub-run (<= kRun)
+  int autotune = 0;
 };
 
 namespace gbri {

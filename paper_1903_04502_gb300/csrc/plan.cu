@@ -8,8 +8,12 @@
 // 0 otherwise; its continuous Fourier transform is
 // ghat(nu) = J sinh(sqrt(beta^2 - (pi J nu)^2)) / (I0(beta) sqrt(beta^2 - (pi J nu)^2)).
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "nufft.cuh"
@@ -227,6 +231,113 @@ void destroy_plan(gbri_plan* p) {
   delete p;
 }
 
+// Sub-runs: at most R consecutive visibilities of one cell.  Within a tile they are
+// listed rank-major (every cell's first sub-run in cell order, then every second one,
+// ...), each round padded to a multiple of 32 slots, so the lanes of a warp take
+// sub-runs of distinct cells.  A chunk is up to kThreads sub-runs of one tile (one per
+// thread), heaviest tiles first.  The visibilities are stored in sub-run order, so a
+// chunk is one contiguous range.  (Re)builds p->meta, p->perm, p->subruns, p->chunks
+// from the cell-sorted arrays.
+int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector<int32_t>& hst,
+               const std::vector<int32_t>& order, int R, const uint2* meta_cell, const int32_t* perm_cell,
+               cudaStream_t s) {
+  const int64_t M = p->M;
+  constexpr int NC = kTile * kTile;
+  cudaFree(p->meta); cudaFree(p->perm); cudaFree(p->subruns); cudaFree(p->chunks);
+  p->meta = nullptr; p->perm = nullptr; p->subruns = nullptr; p->chunks = nullptr;
+  std::vector<int2> sub;
+  sub.reserve((size_t)(M / R + order.size() * 64 + 16));
+  std::vector<int4> ch;
+  int nsub[NC];
+  for (int t : order) {
+    const int64_t base = (int64_t)t * NC;
+    int maxsub = 0;
+    for (int c = 0; c < NC; ++c) {
+      const int cnt = hoff[base + c + 1] - hoff[base + c];
+      nsub[c] = (cnt + R - 1) / R;
+      maxsub = std::max(maxsub, nsub[c]);
+    }
+    const int64_t first = (int64_t)sub.size();
+    for (int r = 0; r < maxsub; ++r) {
+      for (int c = 0; c < NC; ++c)
+        if (nsub[c] > r) {
+          const int st0 = hoff[base + c] + r * R;
+          sub.push_back(make_int2(st0, std::min(R, hoff[base + c + 1] - st0)));
+        }
+      while ((sub.size() - first) % 32) sub.push_back(make_int2(0, 0));
+    }
+    const int64_t nt = (int64_t)sub.size() - first;
+    const int single = nt <= kThreads ? 1 : 0;
+    for (int64_t k = 0; k < nt; k += kThreads)
+      ch.push_back(make_int4(t, (int)(first + k), (int)std::min<int64_t>(kThreads, nt - k), single));
+  }
+  GBRI_CHECK((int64_t)sub.size() < ((int64_t)1 << 31), GBRI_EINVAL, "too many sub-runs");
+  (void)hst;
+  std::vector<int32_t> nstart(sub.size());
+  int64_t run = 0;
+  for (size_t i = 0; i < sub.size(); ++i) {
+    nstart[i] = (int32_t)run;
+    run += sub[i].y;
+  }
+  p->n_chunks = (int64_t)ch.size();
+  int32_t st = GBRI_OK;
+  if ((st = dmalloc(&p->meta, (size_t)M, nullptr)) || (st = dmalloc(&p->perm, (size_t)M, nullptr)) ||
+      (st = dmalloc(&p->chunks, ch.size(), nullptr)) || (st = dmalloc(&p->subruns, sub.size(), nullptr)))
+    return st;
+  if (!sub.empty()) {
+    int2* dold = nullptr;
+    int32_t* dnew = nullptr;
+    if ((st = dmalloc(&dold, sub.size(), nullptr)) || (st = dmalloc(&dnew, sub.size(), nullptr))) {
+      cudaFree(dold);
+      return st;
+    }
+    cudaMemcpyAsync(dold, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dnew, nstart.data(), nstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    launch_begin(GBRI_K_OTHER, s);
+    k_relayout<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)sub.size(), 256), (int64_t)num_sms() * 16), 256, 0, s>>>(
+        dold, dnew, (int64_t)sub.size(), meta_cell, perm_cell, p->meta, p->perm);
+    st = launch_end(GBRI_K_OTHER, s);
+    cudaStreamSynchronize(s);
+    cudaFree(dold);
+    cudaFree(dnew);
+    if (st != GBRI_OK) return st;
+    for (size_t i = 0; i < sub.size(); ++i) sub[i].x = nstart[i];
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->subruns, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  }
+  if (!ch.empty())
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  GBRI_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+  p->layout_bytes = (int64_t)(sub.size() * sizeof(int2) + ch.size() * sizeof(int4));
+  return GBRI_OK;
+}
+
+// Autotuner results per problem shape (grid size, support, table density, visibility
+// count, non-empty tiles): run length and resident blocks per SM of both kernels.
+struct TuneKey {
+  int K, J, S;
+  int64_t M, tiles;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(K, J, S, M, tiles) < std::tie(o.K, o.J, o.S, o.M, o.tiles);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, 3>> g_tune;
+
+bool tune_cache_get(const TuneKey& k, int* run, int* dg, int* gr) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *run = it->second[0];
+  *dg = it->second[1];
+  *gr = it->second[2];
+  return true;
+}
+
+void tune_cache_put(const TuneKey& k, int run, int dg, int gr) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[k] = {run, dg, gr};
+}
+
 int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   GBRI_TRY(prepare_visibility_kernels());
   const int K = p->K, S = p->S;
@@ -320,12 +431,6 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   for (int t = 0; t < n_tiles; ++t)
     if (hst[t + 1] > hst[t]) tiles.push_back(t);
   p->n_tiles = (int64_t)tiles.size();
-
-  // Sub-runs: at most kRun consecutive visibilities of one cell.  Within a tile they are
-  // listed rank-major (every cell's first sub-run in cell order, then every second one,
-  // ...), each round padded to a multiple of 32 slots, so the lanes of a warp take
-  // sub-runs of distinct cells.  A chunk is up to
-  // kThreads sub-runs of one tile (one per thread), heaviest tiles first.
   std::vector<int32_t> hoff((size_t)cells + 1);
   {
     cudaError_t e = cudaMemcpyAsync(hoff.data(), p->cell_off, sizeof(int32_t) * (cells + 1), cudaMemcpyDeviceToHost, s);
@@ -338,98 +443,88 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   std::vector<int32_t> order(tiles);
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return hst[a + 1] - hst[a] > hst[b + 1] - hst[b]; });
-  std::vector<int2> sub;
-  sub.reserve((size_t)(M / kRun + order.size() * 64 + 16));
-  std::vector<int4> ch;
-  constexpr int NC = kTile * kTile;
-  int nsub[NC];
-  for (int t : order) {
-    const int64_t base = (int64_t)t * NC;
-    int maxsub = 0;
-    for (int c = 0; c < NC; ++c) {
-      const int cnt = hoff[base + c + 1] - hoff[base + c];
-      nsub[c] = (cnt + kRun - 1) / kRun;
-      maxsub = std::max(maxsub, nsub[c]);
-    }
-    const int64_t first = (int64_t)sub.size();
-    for (int r = 0; r < maxsub; ++r) {
-      for (int c = 0; c < NC; ++c)
-        if (nsub[c] > r) {
-          const int st0 = hoff[base + c] + r * kRun;
-          sub.push_back(make_int2(st0, std::min(kRun, hoff[base + c + 1] - st0)));
-        }
-      // each round starts at a warp boundary: the 32 lanes of a warp never hold two
-      // sub-runs of one cell (empty slots pad the round)
-      while ((sub.size() - first) % 32) sub.push_back(make_int2(0, 0));
-    }
-    const int64_t nt = (int64_t)sub.size() - first;
-    const int single = nt <= kThreads ? 1 : 0;
-    for (int64_t k = 0; k < nt; k += kThreads)
-      ch.push_back(make_int4(t, (int)(first + k), (int)std::min<int64_t>(kThreads, nt - k), single));
-  }
-  GBRI_CHECK((int64_t)sub.size() < ((int64_t)1 << 31), GBRI_EINVAL, "too many sub-runs");
-  // physical layout = sub-run order: a chunk's sub-runs form one contiguous range
-  std::vector<int32_t> nstart(sub.size());
-  {
-    int64_t run = 0;
-    for (size_t i = 0; i < sub.size(); ++i) {
-      nstart[i] = (int32_t)run;
-      run += sub[i].y;
-    }
-  }
-  p->n_chunks = (int64_t)ch.size();
-  GBRI_TRY(dmalloc(&p->chunks, ch.size(), &p->device_bytes));
-  GBRI_TRY(dmalloc(&p->subruns, sub.size(), &p->device_bytes));
-  if (!sub.empty()) {
-    int2* dold = nullptr;
-    int32_t* dnew = nullptr;
-    uint2* meta2 = nullptr;
-    int32_t* perm2 = nullptr;
-    if ((st = dmalloc(&dold, sub.size(), nullptr)) || (st = dmalloc(&dnew, sub.size(), nullptr)) ||
-        (st = dmalloc(&meta2, (size_t)M, nullptr)) || (st = dmalloc(&perm2, (size_t)M, nullptr))) {
-      cudaFree(dold); cudaFree(dnew); cudaFree(meta2); cudaFree(perm2);
-      return st;
-    }
-    cudaMemcpyAsync(dold, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(dnew, nstart.data(), nstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    launch_begin(GBRI_K_OTHER, s);
-    k_relayout<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)sub.size(), 256), (int64_t)num_sms() * 16), 256, 0, s>>>(
-        dold, dnew, (int64_t)sub.size(), p->meta, p->perm, meta2, perm2);
-    st = launch_end(GBRI_K_OTHER, s);
-    cudaStreamSynchronize(s);
-    cudaFree(dold);
-    cudaFree(dnew);
-    if (st != GBRI_OK) {
-      cudaFree(meta2); cudaFree(perm2);
-      return st;
-    }
-    cudaFree(p->meta);
-    cudaFree(p->perm);
-    p->meta = meta2;
-    p->perm = perm2;
-    for (size_t i = 0; i < sub.size(); ++i) sub[i].x = nstart[i];
-    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->subruns, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-  }
-  if (!ch.empty())
-    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-  GBRI_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
-
-  // persistent grid sizes
+  // the cell-sorted arrays stay the source of every layout tried below
+  uint2* meta_cell = p->meta;
+  int32_t* perm_cell = p->perm;
+  p->meta = nullptr;
+  p->perm = nullptr;
+  p->device_bytes -= (int64_t)M * 12;
   const int sms = num_sms();
-  const int per_sm_dg = std::max(1, (int)((227 * 1024) / (degrid_smem(p) + 1024)));
-  const int per_sm_gr = std::max(1, (int)((227 * 1024) / (grid_smem(p) + 1024)));
-  // resident blocks per SM: the smaller of the shared-memory and the launch-bounds limits
-  const int reg_dg = p->J == 4 ? 4 : 3, reg_gr = p->J == 4 ? 3 : 2;
-  p->degrid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_dg, reg_dg)));
-  p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * std::min(per_sm_gr, reg_gr)));
-  p->n_partials = std::max(p->degrid_blocks, 1024);
+  const int lim_dg = std::min(std::max(1, (int)((227 * 1024) / (degrid_smem(p) + 1024))), p->J == 4 ? 4 : 3);
+  const int lim_gr = std::min(std::max(1, (int)((227 * 1024) / (grid_smem(p) + 1024))), p->J == 4 ? 3 : 2);
+  p->n_partials = std::max(sms * 8, 1024);
   GBRI_TRY(dmalloc(&p->partials, (size_t)p->n_partials * 4, &p->device_bytes));
   GBRI_TRY(dmalloc(&p->scalars, 64, &p->device_bytes));
   GBRI_CHECK_CUDA(cudaMemsetAsync(p->scalars, 0, 64 * sizeof(double), s));
-
-  if (cufftPlan2d(&p->fft, K, K, CUFFT_C2C) != CUFFT_SUCCESS)
+  if (cufftPlan2d(&p->fft, K, K, CUFFT_C2C) != CUFFT_SUCCESS) {
+    cudaFree(meta_cell); cudaFree(perm_cell);
     return set_error(GBRI_ECUFFT, "cufftPlan2d failed");
+  }
   p->fft_ok = true;
+
+  auto set_blocks = [&](int bpm_dg, int bpm_gr) {
+    p->degrid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * bpm_dg));
+    p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * bpm_gr));
+  };
+  int best_run = p->run_len, best_dg = lim_dg, best_gr = lim_gr;
+  const TuneKey tkey{K, p->J, S, M, p->n_tiles};
+  bool cached = false;
+  if (p->autotune) cached = tune_cache_get(tkey, &best_run, &best_dg, &best_gr);
+  if (p->autotune && !cached && M > 0) {
+    // time the plain degridding and gridding kernels for every run length and
+    // persistent-grid size, keep the pair with the smallest summed time
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int runs[3] = {1, 2, 4};
+    for (int R : runs) {
+      st = layout(p, hoff, hst, order, R, meta_cell, perm_cell, s);
+      if (st != GBRI_OK) break;
+      float tdg[8] = {0}, tgr[8] = {0};
+      for (int b = 1; b <= std::max(lim_dg, lim_gr); ++b) {
+        set_blocks(std::min(b, lim_dg), std::min(b, lim_gr));
+        for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up
+          cudaEventRecord(e0, s);
+          if (b <= lim_dg) launch_degrid(p, p->grid, EpiStorePlan{p->vis_tmp}, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep) tdg[b] += ms;
+          cudaEventRecord(e0, s);
+          if (b <= lim_gr) launch_grid(p, SrcPlan{p->vis_tmp}, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep) tgr[b] += ms;
+        }
+      }
+      int bd = 1, bg = 1;
+      for (int b = 1; b <= lim_dg; ++b)
+        if (tdg[b] < tdg[bd]) bd = b;
+      for (int b = 1; b <= lim_gr; ++b)
+        if (tgr[b] < tgr[bg]) bg = b;
+      if (tdg[bd] + tgr[bg] < best) {
+        best = tdg[bd] + tgr[bg];
+        best_run = R;
+        best_dg = bd;
+        best_gr = bg;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == GBRI_OK) tune_cache_put(tkey, best_run, best_dg, best_gr);
+  }
+  if (st == GBRI_OK) st = layout(p, hoff, hst, order, best_run, meta_cell, perm_cell, s);
+  cudaStreamSynchronize(s);
+  cudaFree(meta_cell);
+  cudaFree(perm_cell);
+  if (st != GBRI_OK) return st;
+  p->run_len = best_run;
+  set_blocks(best_dg, best_gr);
+  p->device_bytes += (int64_t)M * 12 + p->layout_bytes;
+  GBRI_CHECK_CUDA(cudaMemsetAsync(p->grid, 0, sizeof(float2) * cells, s));
   GBRI_CHECK_CUDA(cudaStreamSynchronize(s));
   return GBRI_OK;
 }
@@ -469,6 +564,10 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* 
   p->beta = d->kb_beta > 0 ? d->kb_beta : 2.34 * d->J;
   p->M = d->M;
   p->prec = d->precision;
+  GBRI_CHECK(d->vis_per_run >= 0 && d->vis_per_run <= kRun, GBRI_EINVAL, "vis_per_run must be in [0, 4]");
+  GBRI_CHECK(d->autotune == 0 || d->autotune == 1, GBRI_EINVAL, "autotune must be 0 or 1");
+  p->run_len = d->vis_per_run ? d->vis_per_run : kRun;
+  p->autotune = d->autotune;
   const int32_t st = build_plan(p, d_uvw, (cudaStream_t)stream);
   if (st != GBRI_OK) {
     destroy_plan(p);
@@ -481,6 +580,14 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* 
 int32_t gbri_plan_destroy(gbri_plan* p) {
   if (p) cudaDeviceSynchronize();
   destroy_plan(p);
+  return GBRI_OK;
+}
+
+int32_t gbri_plan_launch_config(const gbri_plan* p, int32_t* run, int32_t* dg, int32_t* gr) {
+  GBRI_CHECK(p, GBRI_EINVAL, "null plan");
+  if (run) *run = p->run_len;
+  if (dg) *dg = p->degrid_blocks;
+  if (gr) *gr = p->grid_blocks;
   return GBRI_OK;
 }
 

@@ -177,3 +177,31 @@ def test_full_size_sampled_parity(g):
     lhs = torch.real(torch.vdot(torch.from_numpy(y).cuda().to(torch.complex128), yin.to(torch.complex128)))
     rhs = torch.dot(torch.from_numpy(x).cuda().double().ravel(), pty.ravel())
     assert abs(float(lhs - rhs)) <= 1e-5 * abs(float(lhs))
+
+
+@pytest.mark.parametrize("vis_per_run", [1, 2])
+def test_run_length_variants_match_oracle(g, vis_per_run):
+    n, M = 128, 25_000
+    x, uvw = make(n, M, seed=77)
+    geo = me.Geometry(uvw, n, 2, 4, 4096)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, vis_per_run=vis_per_run)
+    assert plan.launch_config()[0] == vis_per_run
+    y = g.phi(plan, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, me.phi(x.astype(np.float64), geo)) <= TOL
+    yin = synth.complex_normal(M, seed=78).astype(np.complex64)
+    xa = g.phi_adjoint(plan, torch.from_numpy(yin).cuda()).cpu().numpy()
+    assert rel(xa, me.phi_adjoint(yin.astype(np.complex128), geo)) <= TOL
+
+
+def test_autotuned_plan_matches_oracle_and_is_cached(g):
+    n, M = 256, 200_000
+    x, uvw = make(n, M, seed=79)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, autotune=True)
+    run, dg, gr = plan.launch_config()
+    assert run in (1, 2, 4) and dg >= 1 and gr >= 1
+    idx = np.arange(0, M, 97)
+    geo = me.Geometry(uvw[idx], n, 2, 4, 4096)
+    y = g.phi(plan, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y[idx], me.phi(x.astype(np.float64), geo)) <= TOL
+    again = g.Plan(torch.from_numpy(uvw).cuda(), n, autotune=True)   # same shape: cached choice
+    assert again.launch_config() == (run, dg, gr)
