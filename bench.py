@@ -33,7 +33,7 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernels at the 1024^2 / M = 1e7 workload; set to None
 # whenever a kernel changes after its capture.
-KERNEL_TRAFFIC = {"degrid": 344.2e6, "grid": 232.6e6}
+KERNEL_TRAFFIC = {"degrid": None, "grid": None}
 
 
 def parse():
@@ -66,6 +66,22 @@ def workload(cfg_name, rank=0):
     x_true = synth.sky(cfg["n_side"], cfg["n_points"], cfg["n_blobs"], seed=seed)
     uvw = synth.uv_coverage(cfg["M"], seed=seed + 1, outlier_frac=cfg["outlier_frac"], weights=cfg["weights"])
     return cfg, seed, x_true, uvw
+
+
+def aggregate_replicas(ms_local, units_local, steps):
+    """Weak-scaling aggregate over ranks: the slowest rank's time and the sum of the units all
+    ranks processed (whole-job throughput).  Works with any initialised process group."""
+    import torch
+    import torch.distributed as dist
+    ms, units = float(ms_local), float(units_local)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = float(t.item()), float(u.item())
+    return ms, units * steps / (ms / 1e3)
 
 
 def describe(cfg):
@@ -298,11 +314,7 @@ def run_gbri(args):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = g.launch_count() - n0
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = aggregate_replicas(e0.elapsed_time(e1), M, args.steps)
     clk = clocks.stop() if rank == 0 else None
     # profiled timed region: the same iterations launched kernel by kernel, each kernel
     # bracketed by CUDA events on its launching stream (graph replay is off while timing)
@@ -323,7 +335,6 @@ def run_gbri(args):
             kern[name] = {"ms_total": tot, "launches": cnt, "ms_avg": tot / cnt}
     g.profile_enable(0)
     ms_per = ms / args.steps
-    value = ws * M * args.steps / (ms / 1e3)
 
     # roofline of the dominant visibility kernel (algorithmic bytes per launch)
     K = plan.K

@@ -33,7 +33,7 @@ constexpr int kTile = 16;      // grid tile side in cells (T * S <= 65536 keeps 
 constexpr int kThreads = 256;  // threads per block of the visibility kernels
 constexpr int kRun = 4;        // consecutive visibilities a thread owns within a chunk
 constexpr int kChunk = kThreads * kRun;  // visibilities per work chunk
-constexpr int kWinPitch = 24;  // float2 pitch of the degridding window (== 8 mod 16: two rows per warp on disjoint banks)
+constexpr int kWinPitch = 21;  // float2 pitch of the degridding window (same bank-slot map as the gridding accumulators)
 
 }  // namespace gbri
 

@@ -259,11 +259,27 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
     }
     const int64_t first = (int64_t)sub.size();
     for (int r = 0; r < maxsub; ++r) {
+      // order inside the round: round robin over the 16 eight-byte shared-memory bank
+      // slots of the cells' first accumulator / window word, so that the 16 lanes of a
+      // half-warp hit distinct slots while enough slots are left
+      int bucket[16][NC];
+      int nb[16] = {0};
       for (int c = 0; c < NC; ++c)
         if (nsub[c] > r) {
-          const int st0 = hoff[base + c] + r * R;
-          sub.push_back(make_int2(st0, std::min(R, hoff[base + c + 1] - st0)));
+          const int slot = ((c / kTile) * kAccPitch2 + (c % kTile)) & 15;
+          bucket[slot][nb[slot]++] = c;
         }
+      int taken[16] = {0};
+      for (bool any = true; any;) {
+        any = false;
+        for (int q = 0; q < 16; ++q)
+          if (taken[q] < nb[q]) {
+            const int c = bucket[q][taken[q]++];
+            const int st0 = hoff[base + c] + r * R;
+            sub.push_back(make_int2(st0, std::min(R, hoff[base + c + 1] - st0)));
+            any = true;
+          }
+      }
       while ((sub.size() - first) % 32) sub.push_back(make_int2(0, 0));
     }
     const int64_t nt = (int64_t)sub.size() - first;

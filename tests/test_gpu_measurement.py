@@ -82,7 +82,8 @@ def test_sort_is_bit_exact_tile_major(g):
     """The plan's visibility order follows the oracle's FP64 quantisation exactly (integer work,
     compared exactly): non-empty 16 x 16 tiles heaviest first (ties by tile index), and inside a
     tile the sub-runs (up to 4 visibilities of one base cell) listed rank-major: every cell's
-    first sub-run in cell order, then every second one, and so on."""
+    first sub-run, then every second one, and so on; inside a round the cells go round robin
+    over the 16 shared-memory bank slots of their first word, in cell order within a slot."""
     n, M, K, S, T, R = 128, 30_000, 256, 4096, 16, 4
     _, uvw = make(n, M)
     plan = g.Plan(torch.from_numpy(uvw).cuda(), n, S=S)
@@ -101,10 +102,16 @@ def test_sort_is_bit_exact_tile_major(g):
     for t in order:
         cc = np.bincount(cell[tile == t], minlength=T * T)
         for r in range(int(-(-cc.max() // R))):
-            for c in np.nonzero(cc > r * R)[0]:
-                k = min(R, cc[c] - r * R)
-                expect_tiles += [t] * k
-                expect_cells += [c] * k
+            # inside a round: round robin over the 16 bank slots ((row * 21 + col) mod 16)
+            buckets = [[c for c in np.nonzero(cc > r * R)[0] if ((c // T) * 21 + c % T) % 16 == q]
+                       for q in range(16)]
+            while any(buckets):
+                for q in range(16):
+                    if buckets[q]:
+                        c = buckets[q].pop(0)
+                        k = min(R, cc[c] - r * R)
+                        expect_tiles += [t] * k
+                        expect_cells += [c] * k
     assert np.array_equal(tile[perm], np.array(expect_tiles))
     assert np.array_equal(cell[perm], np.array(expect_cells))
     assert plan.n_tiles == len(tiles)
