@@ -33,7 +33,7 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernels at the 1024^2 / M = 1e7 workload; set to None
 # whenever a kernel changes after its capture.
-KERNEL_TRAFFIC = {"degrid": 343.77e6, "grid": 233.28e6}
+KERNEL_TRAFFIC = {"degrid": 343.66e6, "grid": 232.99e6}
 
 
 def parse():
@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=10.0, help="Poisson job arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window of the serving leg (0: skip)")
+    ap.add_argument("--fp64-steps", type=int, default=50,
+                    help="timed iterations of the plain FP64 path (0: skip the precision leg)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: short power method, no end-to-end, operator or CPU legs")
     return ap.parse_args()
@@ -264,6 +266,56 @@ def serving_leg(args, dev, seed=1000):
             "budget_gb": 150, "jobs_mix": "n in {256,512,1024}, M log-uniform [1e5, 2e6], J in {4,6}"}
 
 
+def precision_leg(args, g, cfg, uvw_dev, y, eps, opn, gamma, ms_mixed, stream):
+    """The plain FP64 path on the same workload: ms per primal-dual iteration (graph replays,
+    CUDA events) and, after the workload's iteration count from x = 0 on both paths, the
+    relative L2 distance of the mixed-precision image from the FP64 image."""
+    import torch
+    n, M = cfg["n_side"], cfg["M"]
+    kw = dict(oversample=cfg["oversample"], J=cfg["J"], S=cfg["S"])
+    p64 = g.Plan(uvw_dev, n, precision=g.F64, **kw)
+    w64 = g.Wavelet(n, cfg["levels"], cfg["db_orders"], precision=g.F64)
+    y64 = y.to(torch.complex128)
+    s64 = g.Solver(p64, w64, y64, eps=eps, op_norm_sq=opn, gamma=gamma)
+    s64.step(3)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s64.step(args.fp64_steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms64 = a.elapsed_time(b) / args.fp64_steps
+    # per-kernel breakdown of the FP64 iteration (kernel by kernel, events on the stream)
+    from paper_1903_04502_gb300 import _lib
+    k = min(args.fp64_steps, 20)
+    g.profile_enable(k + 8)
+    s64.step(k)
+    torch.cuda.synchronize()
+    kern64 = {}
+    for i, name in enumerate(_lib.K_NAMES):
+        tot, cnt = g.profile_read(i)
+        if cnt:
+            kern64[name] = {"ms_avg": tot / cnt, "launches": cnt}
+    g.profile_enable(0)
+    s64.close()
+    iters = cfg["iters"]
+    s64 = g.Solver(p64, w64, y64, eps=eps, op_norm_sq=opn, gamma=gamma)
+    s64.step(iters)
+    p32 = g.Plan(uvw_dev, n, **kw)
+    w32 = g.Wavelet(n, cfg["levels"], cfg["db_orders"])
+    s32 = g.Solver(p32, w32, y, eps=eps, op_norm_sq=opn, gamma=gamma)
+    s32.step(iters)
+    x64 = s64.x()
+    x32 = s32.x().to(torch.float64)
+    err = float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))
+    for o in (s32, w32, p32, s64, w64, p64):
+        o.close()
+    return {"fp64_ms_per_step": ms64, "fp64_value": M / (ms64 * 1e-3), "mixed_ms_per_step": ms_mixed,
+            "speedup_mixed_over_fp64": ms64 / ms_mixed, "iterations_compared": iters,
+            "final_image_rel_err_mixed_vs_fp64": err, "fp64_steps": args.fp64_steps, "fp64_kernels": kern64,
+            "note": "both paths from x = 0 with the same data, ||Phi||^2, gamma and eps; CUDA-graph replays"}
+
+
 def run_gbri(args):
     import torch
     import paper_1903_04502_gb300 as g
@@ -394,6 +446,9 @@ def run_gbri(args):
     torch.cuda.synchronize()
     ops = {"phi_vis_per_s": M * reps / (a.elapsed_time(b) * 1e-3),
            "phi_adjoint_vis_per_s": M * reps / (b.elapsed_time(c) * 1e-3)}
+    precision = None
+    if args.fp64_steps > 0:
+        precision = precision_leg(args, g, cfg, torch.from_numpy(uvw).to(dev), y, eps, opn, gamma, ms_per, stream)
 
     if ws > 1:
         torch.distributed.barrier()
@@ -417,7 +472,8 @@ def run_gbri(args):
                    % (ws_bytes / 1e9), "plan_s": t_plan, "op_norm_sq": opn, "gamma": gamma},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "profiled_region": {"steps": k_prof, "ms_per_step": ms_prof, "launch": "kernel by kernel with events"},
-        "clocks": clk, "kernels": kern, "operators": ops, "serving": serving, "impl": "gbri",
+        "clocks": clk, "kernels": kern, "operators": ops, "precision": precision, "serving": serving,
+        "impl": "gbri",
     }
     print(json.dumps(line))
     if ws > 1:

@@ -18,9 +18,13 @@
  *     call returns (except where a create call documents a copy).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Work is enqueued on it; nothing synchronises unless the call says so.
- *   - Precision: GBRI_F32 (float / interleaved complex64) for the bulk, with FP64
- *     global norms.  Images are row-major [n_side][n_side] float; visibilities
- *     are interleaved complex {re, im} float pairs.
+ *   - Precision is fixed per object (plan, wavelet; a solver takes its plan's):
+ *     GBRI_F32 = float images and interleaved complex64 {re, im} visibilities,
+ *     FP32 arithmetic for the bulk with FP64 global norms, ball test, power
+ *     method and convergence test (the mixed-precision path); GBRI_F64 = double
+ *     images and complex128 visibilities, FP64 throughout (the plain FP64 path).
+ *     Data pointers are void*: their element type is the object's precision.
+ *     Images are row-major [n_side][n_side].
  *   - Return value: GBRI_OK (0) or a negative gbri_status.  On error nothing has
  *     been enqueued unless the status is GBRI_ECUDA / GBRI_ECUFFT, in which case
  *     the stream may hold partial work.  gbri_last_error() gives a message
@@ -65,7 +69,7 @@ typedef struct {
   int32_t samples_per_unit;  /* table samples per grid cell S: power of two, 16 <= S <= 4096 */
   double kb_beta;            /* Kaiser-Bessel shape; <= 0 selects 2.34 * J */
   int64_t M;                 /* number of visibilities, >= 0 */
-  int32_t precision;         /* GBRI_F32 */
+  int32_t precision;         /* GBRI_F32 or GBRI_F64: tables, grids and data in float or double */
   int32_t vis_per_run;       /* visibilities of one grid cell a thread takes at once: 1..4; 0 selects 4 */
   int32_t autotune;          /* 1: time the run lengths 1, 2, 4 and the resident blocks per SM of the
                                 visibility kernels at plan creation and keep the fastest (cached per
@@ -102,17 +106,17 @@ int32_t gbri_plan_permutation(const gbri_plan* plan, int32_t* d_perm, void* stre
 /* Reorder a complex visibility vector [M] between the caller's order and plan order.
  * to_plan = 1: d_out[pos] = d_in[perm[pos]]; to_plan = 0: d_out[perm[pos]] = d_in[pos].
  * d_in and d_out must not overlap. */
-int32_t gbri_vis_reorder(const gbri_plan* plan, const float* d_in, float* d_out, int32_t to_plan,
+int32_t gbri_vis_reorder(const gbri_plan* plan, const void* d_in, void* d_out, int32_t to_plan,
                          void* stream);
 
-/* y = Phi x = W G F Z S x (Sec. 2, Eq. 2).  d_x: [n_side][n_side] float image.
+/* y = Phi x = W G F Z S x (Sec. 2, Eq. 2).  d_x: [n_side][n_side] real image.
  * d_y: [M] complex, written (caller's order unless flags has GBRI_PLAN_ORDER). */
-int32_t gbri_phi(gbri_plan* plan, const float* d_x, float* d_y, uint32_t flags, void* stream);
+int32_t gbri_phi(gbri_plan* plan, const void* d_x, void* d_y, uint32_t flags, void* stream);
 
 /* x = Phi^dagger y = Re(S^T Z^T F^H G^T W^T y) (Sec. 2; real part because the sky
  * is real).  d_y: [M] complex (caller's order unless GBRI_PLAN_ORDER); d_x:
- * [n_side][n_side] float, overwritten. */
-int32_t gbri_phi_adjoint(gbri_plan* plan, const float* d_y, float* d_x, uint32_t flags, void* stream);
+ * [n_side][n_side] real, overwritten. */
+int32_t gbri_phi_adjoint(gbri_plan* plan, const void* d_y, void* d_x, uint32_t flags, void* stream);
 
 /* ||Phi||^2 by the power method on Phi^dagger Phi (Sec. 6.3.1), FP64 norms.
  * Start vector 0.5 + U[0,1) with U from SplitMix64 at counters seed + k * 0x9E3779B97F4A7C15
@@ -134,28 +138,30 @@ int32_t gbri_wavelet_create(gbri_wavelet** out, int32_t n_side, int32_t levels, 
 int32_t gbri_wavelet_destroy(gbri_wavelet* wav);
 
 /* x = Psi alpha = sum_b IDWT_b(alpha_b) / sqrt(n_w).  d_alpha: [n_w][n_side][n_side]; d_x: image. */
-int32_t gbri_psi(gbri_wavelet* wav, const float* d_alpha, float* d_x, void* stream);
+int32_t gbri_psi(gbri_wavelet* wav, const void* d_alpha, void* d_x, void* stream);
 
 /* alpha = Psi^dagger x: alpha_b = DWT_b(x) / sqrt(n_w). */
-int32_t gbri_psi_adjoint(gbri_wavelet* wav, const float* d_x, float* d_alpha, void* stream);
+int32_t gbri_psi_adjoint(gbri_wavelet* wav, const void* d_x, void* d_alpha, void* stream);
 
 /* ---- proximal operators (Sec. 4) ------------------------------------------ */
 /* Soft thresholding (Sec. 4.3): out_i = 0 if |in_i| <= lambda, else in_i (|in_i| - lambda) / |in_i|.
- * n elements of float (is_complex = 0) or complex (is_complex = 1).  d_in == d_out allowed. */
-int32_t gbri_prox_l1(const float* d_in, float* d_out, int64_t n, double lambda, int32_t is_complex,
+ * n elements of real (is_complex = 0) or complex (is_complex = 1) type of the given precision.
+ * d_in == d_out allowed. */
+int32_t gbri_prox_l1(const void* d_in, void* d_out, int64_t n, double lambda, int32_t is_complex,
                      int32_t precision, void* stream);
 
 /* Projection onto the l2 ball of radius eps centred at d_center (Sec. 4.2 and the
  * global constraint of Sec. 6.8): out = z if ||z - c|| <= eps, else c + eps (z - c) / ||z - c||.
- * Complex vectors of length M; the norm is accumulated in FP64 (per-thread partial
- * sums in FP32, compensated).  d_norm_out (device double, may be NULL) receives
- * ||z - c||.  d_out may alias d_z.  Uses a temporary device buffer from the
- * stream-ordered allocator. */
-int32_t gbri_proj_l2ball(const float* d_z, const float* d_center, float* d_out, int64_t M, double eps,
+ * Complex vectors of length M in the given precision; the norm is accumulated in
+ * FP64 (GBRI_F32: per-thread partial sums in FP32, compensated).  d_norm_out (device
+ * double, may be NULL) receives ||z - c||.  d_out may alias d_z.  Uses a temporary
+ * device buffer from the stream-ordered allocator. */
+int32_t gbri_proj_l2ball(const void* d_z, const void* d_center, void* d_out, int64_t M, double eps,
                          double* d_norm_out, int32_t precision, void* stream);
 
-/* Allocation-free variant of gbri_proj_l2ball (the paper has no counterpart; this is
- * a library convenience).  Same arguments, result and error behaviour, but the FP64
+/* Allocation-free variant of gbri_proj_l2ball for GBRI_F32 complex64 vectors (the paper
+ * has no counterpart; this is a library convenience).  Same arguments (without the
+ * precision), result and error behaviour, but the FP64
  * reduction scratch is a fixed 1024-entry (8 KB) device array inside the library
  * instead of a stream-ordered allocation, for callers that cannot allocate device
  * memory at that point (their own pool already holds the memory, an out-of-memory
@@ -206,15 +212,16 @@ typedef struct {
 } gbri_solve_report;
 
 /* Stateful solver: keeps the iterate and dual variables resident on the device.
- * d_y: [M] complex data (caller's order unless GBRI_PLAN_ORDER); it is copied.
+ * The plan and the wavelet object must have the same precision, which the solver
+ * takes.  d_y: [M] complex data (caller's order unless GBRI_PLAN_ORDER); it is copied.
  * Synchronises `stream` (power method / gamma when requested). */
-int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav, const float* d_y,
+int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav, const void* d_y,
                            const gbri_solve_params* params, uint32_t flags, void* stream);
 int32_t gbri_solver_destroy(gbri_solver* s);
 /* Run n_iter iterations without any host synchronisation. */
 int32_t gbri_solver_step(gbri_solver* s, int32_t n_iter, void* stream);
 /* Copy the current iterate x to d_x (image). */
-int32_t gbri_solver_get_x(gbri_solver* s, float* d_x, void* stream);
+int32_t gbri_solver_get_x(gbri_solver* s, void* d_x, void* stream);
 /* Iterations run and the last FP64 relative change ||x+ - x|| / ||x+|| (host; INFINITY before the
  * first iteration).  Reads one device scalar: synchronises `stream`, no other work. */
 int32_t gbri_solver_status(gbri_solver* s, int32_t* iters, double* rel_change, void* stream);
@@ -224,8 +231,8 @@ int32_t gbri_solver_report(gbri_solver* s, gbri_solve_report* report, void* stre
 /* One-shot solve: create, iterate up to max_iter (checking rel_tol every check_every
  * iterations on the host), write x to d_x_out, fill *report (host, may be NULL), destroy.
  * Returns GBRI_OK, GBRI_ENOTCONV (max_iter reached with rel_tol > 0) or an error. */
-int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const float* d_y, const gbri_solve_params* params,
-                   float* d_x_out, gbri_solve_report* report, uint32_t flags, void* stream);
+int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const void* d_y, const gbri_solve_params* params,
+                   void* d_x_out, gbri_solve_report* report, uint32_t flags, void* stream);
 
 /* ---- batched execution (many independent problems in one graph launch) ----- */
 /* A batch holds resident solvers of independent problems (each with its own plan

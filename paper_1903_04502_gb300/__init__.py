@@ -16,7 +16,7 @@ import ctypes as C
 import torch
 
 from . import _lib
-from ._lib import (ALGO_ADMM, ALGO_PD, F32, PLAN_ORDER, GbriError, SolveParams, SolveReport,  # noqa: F401
+from ._lib import (ALGO_ADMM, ALGO_PD, F32, F64, PLAN_ORDER, GbriError, SolveParams, SolveReport,  # noqa: F401
                    K_NAMES)
 
 __all__ = ["Plan", "Wavelet", "Solver", "Batch", "phi", "phi_adjoint", "op_norm", "psi", "psi_adjoint", "prox_l1",
@@ -37,6 +37,21 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
 
 
+_REAL = {F32: torch.float32, F64: torch.float64}
+_CPLX = {F32: torch.complex64, F64: torch.complex128}
+
+
+def _precision(p):
+    """Precision code from F32 / F64, "f32" / "f64" or a torch dtype."""
+    if p in (F32, F64):
+        return p
+    if p in ("f32", "fp32", torch.float32, torch.complex64):
+        return F32
+    if p in ("f64", "fp64", torch.float64, torch.complex128):
+        return F64
+    raise ValueError("precision must be F32 or F64, got %r" % (p,))
+
+
 def _need(t, dtype, shape=None, name="tensor"):
     if not t.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % name)
@@ -51,11 +66,12 @@ def _need(t, dtype, shape=None, name="tensor"):
 class Plan:
     """Measurement-operator plan for one problem (gbri_plan_create).
 
-    uvw: float32 CUDA tensor [M, 4] of {u, v, w, weight}.
+    uvw: float32 CUDA tensor [M, 4] of {u, v, w, weight}.  precision: F32 (float images,
+    complex64 visibilities, FP64 global norms) or F64 (double / complex128, FP64 throughout).
     """
 
     def __init__(self, uvw, n_side, oversample=2, J=4, S=4096, beta=0.0, vis_per_run=0, autotune=False,
-                 stream=None):
+                 precision=F32, stream=None):
         lib = _lib.load()
         _need(uvw, torch.float32, name="uvw")
         if uvw.dim() != 2 or uvw.shape[1] != 4:
@@ -63,8 +79,10 @@ class Plan:
         self.n_side, self.J, self.S = int(n_side), int(J), int(S)
         self.M = int(uvw.shape[0])
         self.device = uvw.device
-        d = _lib.PlanDesc(self.n_side, int(oversample), self.J, self.S, float(beta), self.M, F32, int(vis_per_run),
-                          1 if autotune else 0, 0)
+        self.precision = _precision(precision)
+        self.real_dtype, self.complex_dtype = _REAL[self.precision], _CPLX[self.precision]
+        d = _lib.PlanDesc(self.n_side, int(oversample), self.J, self.S, float(beta), self.M, self.precision,
+                          int(vis_per_run), 1 if autotune else 0, 0)
         h = C.c_void_p()
         _lib.check(lib.gbri_plan_create(C.byref(h), C.byref(d), _ptr(uvw), _stream(stream)))
         self._h = h
@@ -100,29 +118,29 @@ class Plan:
 
 
 def phi(plan, x, y=None, plan_order=False, stream=None):
-    """y = Phi x (gbri_phi).  x: float32 [n_side, n_side]; returns complex64 [M]."""
-    _need(x, torch.float32, (plan.n_side, plan.n_side), "x")
+    """y = Phi x (gbri_phi).  x: real [n_side, n_side]; returns complex [M] (plan precision)."""
+    _need(x, plan.real_dtype, (plan.n_side, plan.n_side), "x")
     if y is None:
-        y = torch.empty(plan.M, dtype=torch.complex64, device=x.device)
-    _need(y, torch.complex64, (plan.M,), "y")
+        y = torch.empty(plan.M, dtype=plan.complex_dtype, device=x.device)
+    _need(y, plan.complex_dtype, (plan.M,), "y")
     _lib.check(_lib.load().gbri_phi(plan.handle, _ptr(x), _ptr(y), PLAN_ORDER if plan_order else 0, _stream(stream)))
     return y
 
 
 def phi_adjoint(plan, y, x=None, plan_order=False, stream=None):
-    """x = Phi^dagger y (gbri_phi_adjoint).  y: complex64 [M]; returns float32 [n_side, n_side]."""
-    _need(y, torch.complex64, (plan.M,), "y")
+    """x = Phi^dagger y (gbri_phi_adjoint).  y: complex [M]; returns real [n_side, n_side] (plan precision)."""
+    _need(y, plan.complex_dtype, (plan.M,), "y")
     if x is None:
-        x = torch.empty((plan.n_side, plan.n_side), dtype=torch.float32, device=y.device)
-    _need(x, torch.float32, (plan.n_side, plan.n_side), "x")
+        x = torch.empty((plan.n_side, plan.n_side), dtype=plan.real_dtype, device=y.device)
+    _need(x, plan.real_dtype, (plan.n_side, plan.n_side), "x")
     _lib.check(_lib.load().gbri_phi_adjoint(plan.handle, _ptr(y), _ptr(x), PLAN_ORDER if plan_order else 0,
                                             _stream(stream)))
     return x
 
 
 def vis_reorder(plan, vis, to_plan=True, out=None, stream=None):
-    """Reorder a complex64 [M] vector between caller order and plan order (gbri_vis_reorder)."""
-    _need(vis, torch.complex64, (plan.M,), "vis")
+    """Reorder a complex [M] vector between caller order and plan order (gbri_vis_reorder)."""
+    _need(vis, plan.complex_dtype, (plan.M,), "vis")
     if out is None:
         out = torch.empty_like(vis)
     _lib.check(_lib.load().gbri_vis_reorder(plan.handle, _ptr(vis), _ptr(out), 1 if to_plan else 0, _stream(stream)))
@@ -138,16 +156,18 @@ def op_norm(plan, max_iter=200, tol=1e-8, seed=0, stream=None):
 
 
 class Wavelet:
-    """SARA dictionary (gbri_wavelet_create): db_orders with 0 = Dirac, N = dbN."""
+    """SARA dictionary (gbri_wavelet_create): db_orders with 0 = Dirac, N = dbN; precision F32 or F64."""
 
-    def __init__(self, n_side, levels, db_orders):
+    def __init__(self, n_side, levels, db_orders, precision=F32):
         lib = _lib.load()
         self.n_side, self.levels = int(n_side), int(levels)
         self.db_orders = tuple(int(o) for o in db_orders)
         self.n_w = len(self.db_orders)
+        self.precision = _precision(precision)
+        self.real_dtype = _REAL[self.precision]
         arr = (C.c_int32 * self.n_w)(*self.db_orders)
         h = C.c_void_p()
-        _lib.check(lib.gbri_wavelet_create(C.byref(h), self.n_side, self.levels, arr, self.n_w, F32))
+        _lib.check(lib.gbri_wavelet_create(C.byref(h), self.n_side, self.levels, arr, self.n_w, self.precision))
         self._h = h
 
     @property
@@ -167,50 +187,52 @@ class Wavelet:
 
 
 def psi(wav, alpha, x=None, stream=None):
-    """x = Psi alpha (gbri_psi).  alpha: float32 [n_w, n, n]."""
-    _need(alpha, torch.float32, (wav.n_w, wav.n_side, wav.n_side), "alpha")
+    """x = Psi alpha (gbri_psi).  alpha: real [n_w, n, n] (wavelet precision)."""
+    _need(alpha, wav.real_dtype, (wav.n_w, wav.n_side, wav.n_side), "alpha")
     if x is None:
-        x = torch.empty((wav.n_side, wav.n_side), dtype=torch.float32, device=alpha.device)
-    _need(x, torch.float32, (wav.n_side, wav.n_side), "x")
+        x = torch.empty((wav.n_side, wav.n_side), dtype=wav.real_dtype, device=alpha.device)
+    _need(x, wav.real_dtype, (wav.n_side, wav.n_side), "x")
     _lib.check(_lib.load().gbri_psi(wav.handle, _ptr(alpha), _ptr(x), _stream(stream)))
     return x
 
 
 def psi_adjoint(wav, x, alpha=None, stream=None):
     """alpha = Psi^dagger x (gbri_psi_adjoint)."""
-    _need(x, torch.float32, (wav.n_side, wav.n_side), "x")
+    _need(x, wav.real_dtype, (wav.n_side, wav.n_side), "x")
     if alpha is None:
-        alpha = torch.empty((wav.n_w, wav.n_side, wav.n_side), dtype=torch.float32, device=x.device)
-    _need(alpha, torch.float32, (wav.n_w, wav.n_side, wav.n_side), "alpha")
+        alpha = torch.empty((wav.n_w, wav.n_side, wav.n_side), dtype=wav.real_dtype, device=x.device)
+    _need(alpha, wav.real_dtype, (wav.n_w, wav.n_side, wav.n_side), "alpha")
     _lib.check(_lib.load().gbri_psi_adjoint(wav.handle, _ptr(x), _ptr(alpha), _stream(stream)))
     return alpha
 
 
 def prox_l1(x, lam, out=None, stream=None):
-    """Soft thresholding (gbri_prox_l1) of a float32 or complex64 CUDA tensor."""
-    if x.dtype not in (torch.float32, torch.complex64):
-        raise ValueError("prox_l1 takes float32 or complex64")
+    """Soft thresholding (gbri_prox_l1) of a float32 / float64 / complex64 / complex128 CUDA tensor."""
+    if x.dtype not in (torch.float32, torch.float64, torch.complex64, torch.complex128):
+        raise ValueError("prox_l1 takes float32, float64, complex64 or complex128")
     _need(x, x.dtype, name="x")
     if out is None:
         out = torch.empty_like(x)
     _need(out, x.dtype, tuple(x.shape), "out")
-    _lib.check(_lib.load().gbri_prox_l1(_ptr(x), _ptr(out), x.numel(), float(lam),
-                                        1 if x.dtype == torch.complex64 else 0, F32, _stream(stream)))
+    _lib.check(_lib.load().gbri_prox_l1(_ptr(x), _ptr(out), x.numel(), float(lam), 1 if x.is_complex() else 0,
+                                        _precision(x.dtype), _stream(stream)))
     return out
 
 
 def proj_l2ball(z, center, eps, out=None, norm_out=None, stream=None):
-    """Projection of complex64 z onto the l2 ball of radius eps around center (gbri_proj_l2ball).
-    norm_out: optional float64 CUDA tensor of one element receiving ||z - center||."""
-    _need(z, torch.complex64, name="z")
-    _need(center, torch.complex64, tuple(z.shape), "center")
+    """Projection of complex64 / complex128 z onto the l2 ball of radius eps around center
+    (gbri_proj_l2ball).  norm_out: optional float64 CUDA tensor of one element receiving ||z - center||."""
+    if z.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError("proj_l2ball takes complex64 or complex128")
+    _need(z, z.dtype, name="z")
+    _need(center, z.dtype, tuple(z.shape), "center")
     if out is None:
         out = torch.empty_like(z)
-    _need(out, torch.complex64, tuple(z.shape), "out")
+    _need(out, z.dtype, tuple(z.shape), "out")
     if norm_out is not None:
         _need(norm_out, torch.float64, (1,), "norm_out")
     _lib.check(_lib.load().gbri_proj_l2ball(_ptr(z), _ptr(center), _ptr(out), z.numel(), float(eps),
-                                            _ptr(norm_out), F32, _stream(stream)))
+                                            _ptr(norm_out), _precision(z.dtype), _stream(stream)))
     return out
 
 
@@ -246,7 +268,7 @@ class Solver:
     """Resident solver state (gbri_solver_create / step / get_x / report)."""
 
     def __init__(self, plan, wav, y, plan_order=False, stream=None, **params):
-        _need(y, torch.complex64, (plan.M,), "y")
+        _need(y, plan.complex_dtype, (plan.M,), "y")
         self.plan, self.wav = plan, wav
         self.params = _params(**params)
         h = C.c_void_p()
@@ -260,7 +282,9 @@ class Solver:
 
     def x(self, out=None, stream=None):
         if out is None:
-            out = torch.empty((self.plan.n_side, self.plan.n_side), dtype=torch.float32, device=self.plan.device)
+            out = torch.empty((self.plan.n_side, self.plan.n_side), dtype=self.plan.real_dtype,
+                              device=self.plan.device)
+        _need(out, self.plan.real_dtype, (self.plan.n_side, self.plan.n_side), "out")
         _lib.check(_lib.load().gbri_solver_get_x(self._h, _ptr(out), _stream(stream)))
         return out
 
@@ -326,9 +350,9 @@ class Batch:
 
 def solve(plan, wav, y, x_out=None, plan_order=False, stream=None, **params):
     """One-shot solve (gbri_solve); returns (x, report dict)."""
-    _need(y, torch.complex64, (plan.M,), "y")
+    _need(y, plan.complex_dtype, (plan.M,), "y")
     if x_out is None:
-        x_out = torch.empty((plan.n_side, plan.n_side), dtype=torch.float32, device=y.device)
+        x_out = torch.empty((plan.n_side, plan.n_side), dtype=plan.real_dtype, device=y.device)
     p = _params(**params)
     r = SolveReport()
     _lib.check(_lib.load().gbri_solve(plan.handle, wav.handle, _ptr(y), C.byref(p), _ptr(x_out), C.byref(r),

@@ -82,6 +82,45 @@ struct KahanF {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// Plain FP64 accumulator (the FP64 path needs no compensation).
+struct SumD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// ---- arithmetic type of a path ------------------------------------------------
+// R = float: FP32 bulk with FP64 global sums (per-thread compensated FP32 partials);
+// R = double: the plain FP64 path.  cplx<R> is the interleaved complex type.
+template <class R> struct RealT;
+template <> struct RealT<float> { using C = float2; using Acc = KahanF; };
+template <> struct RealT<double> { using C = double2; using Acc = SumD; };
+template <class R> using cplx = typename RealT<R>::C;
+template <class R> using acc_t = typename RealT<R>::Acc;
+
+template <class R>
+__host__ __device__ __forceinline__ cplx<R> mkc(R re, R im) {
+  cplx<R> v;
+  v.x = re;
+  v.y = im;
+  return v;
+}
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float max_r(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double max_r(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float min_r(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double min_r(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float abs_r(float a) { return fabsf(a); }
+__device__ __forceinline__ double abs_r(double a) { return fabs(a); }
+__device__ __forceinline__ float copysign_r(float a, float b) { return copysignf(a, b); }
+__device__ __forceinline__ double copysign_r(double a, double b) { return copysign(a, b); }
+__device__ __forceinline__ float hypot_r(float a, float b) { return hypotf(a, b); }
+__device__ __forceinline__ double hypot_r(double a, double b) { return hypot(a, b); }
+
+// element size in bytes of a precision code (GBRI_F32 / GBRI_F64)
+inline size_t real_bytes(int prec) { return prec == GBRI_F64 ? 8 : 4; }
+
 // Sum a fixed-length array of double partials in a fixed order (deterministic);
 // all threads of the block get the result.
 __device__ __forceinline__ double reduce_partials(const double* p, int n, double* sh) {

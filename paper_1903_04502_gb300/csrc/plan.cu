@@ -192,6 +192,32 @@ int32_t dmalloc(T** p, size_t n, int64_t* acct) {
   return GBRI_OK;
 }
 
+int32_t bmalloc(void** p, size_t bytes, int64_t* acct) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return set_error(GBRI_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  if (acct) *acct += (int64_t)bytes;
+  return GBRI_OK;
+}
+
+// Device copy of an FP64 host table in the plan's precision (rounded once for FP32).
+int32_t upload_real(void** dst, const std::vector<double>& v, int prec, int64_t* acct, cudaStream_t s) {
+  const size_t rb = real_bytes(prec);
+  GBRI_TRY(bmalloc(dst, v.size() * rb, acct));
+  if (prec == GBRI_F64) {
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(*dst, v.data(), v.size() * rb, cudaMemcpyHostToDevice, s));
+    GBRI_CHECK_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::vector<float> f(v.begin(), v.end());
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(*dst, f.data(), f.size() * rb, cudaMemcpyHostToDevice, s));
+    GBRI_CHECK_CUDA(cudaStreamSynchronize(s));
+  }
+  return GBRI_OK;
+}
+
 int32_t scan_counts(const int32_t* counts, int64_t n, int32_t* offsets, cudaStream_t s) {
   const int64_t tiles = ceil_div(n, kScanTile);
   int32_t* sums = nullptr;
@@ -330,10 +356,10 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
 // Autotuner results per problem shape (grid size, support, table density, visibility
 // count, non-empty tiles): run length and resident blocks per SM of both kernels.
 struct TuneKey {
-  int K, J, S;
+  int K, J, S, prec;
   int64_t M, tiles;
   bool operator<(const TuneKey& o) const {
-    return std::tie(K, J, S, M, tiles) < std::tie(o.K, o.J, o.S, o.M, o.tiles);
+    return std::tie(K, J, S, prec, M, tiles) < std::tie(o.K, o.J, o.S, o.prec, o.M, o.tiles);
   }
 };
 std::mutex g_tune_mu;
@@ -354,39 +380,47 @@ void tune_cache_put(const TuneKey& k, int run, int dg, int gr) {
   g_tune[k] = {run, dg, gr};
 }
 
+// Plain degridding / gridding of the plan's scratch (autotuner timing).
+void plain_degrid(gbri_plan* p, cudaStream_t s) {
+  if (p->prec == GBRI_F64) launch_degrid(p, EpiStorePlan<double>{p->as<double2>(p->vis_tmp)}, s);
+  else launch_degrid(p, EpiStorePlan<float>{p->as<float2>(p->vis_tmp)}, s);
+}
+void plain_grid(gbri_plan* p, cudaStream_t s) {
+  if (p->prec == GBRI_F64) launch_grid(p, SrcPlan<double>{p->as<const double2>(p->vis_tmp)}, s);
+  else launch_grid(p, SrcPlan<float>{p->as<const float2>(p->vis_tmp)}, s);
+}
+
 int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
-  GBRI_TRY(prepare_visibility_kernels());
+  GBRI_TRY(p->prec == GBRI_F64 ? prepare_visibility_kernels<double>() : prepare_visibility_kernels<float>());
   const int K = p->K, S = p->S;
   const int64_t M = p->M;
   const int64_t cells = (int64_t)K * K;
   const int n_tiles = p->nT * p->nT;
 
-  // tables on the host in FP64, stored FP32 (Sec. 8.1; the S factor of Eq. 2)
+  // tables on the host in FP64, stored in the plan's precision (Sec. 8.1; the S factor of Eq. 2)
+  const size_t rb = real_bytes(p->prec);
   {
     const int half = (p->J / 2) * S;
     std::vector<double> tab(half + 1);
     for (int i = 0; i <= half; ++i) tab[i] = kb_g((double)i / S, p->J, p->beta);
-    std::vector<float> w((size_t)table_floats(S, p->J), 0.f);
+    std::vector<double> w((size_t)table_elems(S, p->J), 0.0);
     for (int f = 0; f <= S / 2; ++f)
       for (int t = 0; t < p->J; ++t) {
         const int d = std::abs(f + (p->J / 2 - 1 - t) * S);
-        w[(size_t)f * p->J + t] = (d <= half) ? (float)tab[d] : 0.f;
+        w[(size_t)f * p->J + t] = (d <= half) ? tab[d] : 0.0;
       }
-    std::vector<float> corr(p->n_side);
-    for (int i = 0; i < p->n_side; ++i)
-      corr[i] = (float)(1.0 / kb_ghat((double)(i - p->n_side / 2) / K, p->J, p->beta));
-    GBRI_TRY(dmalloc(&p->wtab, w.size(), &p->device_bytes));
-    GBRI_TRY(dmalloc(&p->corr, corr.size(), &p->device_bytes));
-    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->wtab, w.data(), w.size() * 4, cudaMemcpyHostToDevice, s));
-    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->corr, corr.data(), corr.size() * 4, cudaMemcpyHostToDevice, s));
+    std::vector<double> corr(p->n_side);
+    for (int i = 0; i < p->n_side; ++i) corr[i] = 1.0 / kb_ghat((double)(i - p->n_side / 2) / K, p->J, p->beta);
+    GBRI_TRY(upload_real(&p->wtab, w, p->prec, &p->device_bytes, s));
+    GBRI_TRY(upload_real(&p->corr, corr, p->prec, &p->device_bytes, s));
   }
 
   GBRI_TRY(dmalloc(&p->meta, (size_t)M, &p->device_bytes));
   GBRI_TRY(dmalloc(&p->perm, (size_t)M, &p->device_bytes));
-  GBRI_TRY(dmalloc(&p->vis_tmp, (size_t)M, &p->device_bytes));
-  GBRI_TRY(dmalloc(&p->padded, (size_t)cells, &p->device_bytes));
-  GBRI_TRY(dmalloc(&p->grid, (size_t)cells, &p->device_bytes));
-  GBRI_CHECK_CUDA(cudaMemsetAsync(p->padded, 0, sizeof(float2) * cells, s));
+  GBRI_TRY(bmalloc(&p->vis_tmp, (size_t)M * 2 * rb, &p->device_bytes));
+  GBRI_TRY(bmalloc(&p->padded, (size_t)cells * 2 * rb, &p->device_bytes));
+  GBRI_TRY(bmalloc(&p->grid, (size_t)cells * 2 * rb, &p->device_bytes));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(p->padded, 0, (size_t)cells * 2 * rb, s));
 
   // work arrays for the sort
   int32_t *key = nullptr, *counts = nullptr, *err = nullptr, *starts = nullptr;
@@ -466,13 +500,15 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   p->perm = nullptr;
   p->device_bytes -= (int64_t)M * 12;
   const int sms = num_sms();
-  const int lim_dg = std::min(std::max(1, (int)((227 * 1024) / (degrid_smem(p) + 1024))), p->J == 4 ? 4 : 3);
-  const int lim_gr = std::min(std::max(1, (int)((227 * 1024) / (grid_smem(p) + 1024))), p->J == 4 ? 3 : 2);
+  const int lim_dg =
+      std::min(std::max(1, (int)((227 * 1024) / (degrid_smem(p) + 1024))), degrid_occupancy((int)rb, p->J));
+  const int lim_gr =
+      std::min(std::max(1, (int)((227 * 1024) / (grid_smem(p) + 1024))), grid_occupancy((int)rb, p->J));
   p->n_partials = std::max(sms * 8, 1024);
   GBRI_TRY(dmalloc(&p->partials, (size_t)p->n_partials * 4, &p->device_bytes));
   GBRI_TRY(dmalloc(&p->scalars, 64, &p->device_bytes));
   GBRI_CHECK_CUDA(cudaMemsetAsync(p->scalars, 0, 64 * sizeof(double), s));
-  if (cufftPlan2d(&p->fft, K, K, CUFFT_C2C) != CUFFT_SUCCESS) {
+  if (cufftPlan2d(&p->fft, K, K, p->prec == GBRI_F64 ? CUFFT_Z2Z : CUFFT_C2C) != CUFFT_SUCCESS) {
     cudaFree(meta_cell); cudaFree(perm_cell);
     return set_error(GBRI_ECUFFT, "cufftPlan2d failed");
   }
@@ -483,7 +519,7 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * bpm_gr));
   };
   int best_run = p->run_len, best_dg = lim_dg, best_gr = lim_gr;
-  const TuneKey tkey{K, p->J, S, M, p->n_tiles};
+  const TuneKey tkey{K, p->J, S, p->prec, M, p->n_tiles};
   bool cached = false;
   if (p->autotune) cached = tune_cache_get(tkey, &best_run, &best_dg, &best_gr);
   if (p->autotune && !cached && M > 0) {
@@ -502,14 +538,14 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
         set_blocks(std::min(b, lim_dg), std::min(b, lim_gr));
         for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up
           cudaEventRecord(e0, s);
-          if (b <= lim_dg) launch_degrid(p, p->grid, EpiStorePlan{p->vis_tmp}, s);
+          if (b <= lim_dg) plain_degrid(p, s);
           cudaEventRecord(e1, s);
           cudaEventSynchronize(e1);
           float ms = 0.f;
           cudaEventElapsedTime(&ms, e0, e1);
           if (rep) tdg[b] += ms;
           cudaEventRecord(e0, s);
-          if (b <= lim_gr) launch_grid(p, SrcPlan{p->vis_tmp}, s);
+          if (b <= lim_gr) plain_grid(p, s);
           cudaEventRecord(e1, s);
           cudaEventSynchronize(e1);
           cudaEventElapsedTime(&ms, e0, e1);
@@ -540,7 +576,7 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   p->run_len = best_run;
   set_blocks(best_dg, best_gr);
   p->device_bytes += (int64_t)M * 12 + p->layout_bytes;
-  GBRI_CHECK_CUDA(cudaMemsetAsync(p->grid, 0, sizeof(float2) * cells, s));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(p->grid, 0, (size_t)cells * 2 * rb, s));
   GBRI_CHECK_CUDA(cudaStreamSynchronize(s));
   return GBRI_OK;
 }
@@ -556,7 +592,7 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* 
   GBRI_CHECK(out && d, GBRI_EINVAL, "null argument");
   *out = nullptr;
   GBRI_CHECK(d->reserved == 0, GBRI_EINVAL, "reserved must be 0");
-  GBRI_CHECK(d->precision == GBRI_F32, GBRI_EINVAL, "only GBRI_F32 plans are supported");
+  GBRI_CHECK(d->precision == GBRI_F32 || d->precision == GBRI_F64, GBRI_EINVAL, "precision must be GBRI_F32 or GBRI_F64");
   GBRI_CHECK(d->n_side >= 16 && d->n_side % 2 == 0, GBRI_EINVAL, "n_side must be even and >= 16");
   GBRI_CHECK(d->oversample >= 2 && d->oversample <= 4, GBRI_EINVAL, "oversample must be in [2, 4]");
   GBRI_CHECK(d->J == 4 || d->J == 6, GBRI_EINVAL, "J must be 4 or 6");

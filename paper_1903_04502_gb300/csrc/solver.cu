@@ -19,7 +19,9 @@
 //   xt = x - rho Re Phi^dagger (v - r + s+),  v - r + s+ = (1 - rho_b) w - s + s+
 //   DualFB(xt): zbar = P_C(xt); repeat { d = clip(eta d + Psi^dagger zbar, gamma) / eta;
 //               zbar = P_C(xt - Psi d) }; x = zbar.
-// All global norms are FP64 (per-thread FP32 compensated partials, FP64 block sums).
+// All global norms are FP64 (FP32 path: per-thread compensated FP32 partials, FP64
+// block sums).  Every kernel is templated on the real type R of the plan: float for
+// the mixed-precision path, double for the plain FP64 path.
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -48,21 +50,22 @@ __global__ void k_ball_scalar(const double* __restrict__ partials, int n, double
 }
 
 // PD primal update fused with S^T Z^T Re(.) of the gridded dual.
-__global__ void k_pd_update(const float2* __restrict__ grid, const float* __restrict__ corr,
-                            const float* __restrict__ psiz, float* __restrict__ x, float* __restrict__ xhat, int n,
-                            int K, float tau, float theta, const double* __restrict__ sc, double* __restrict__ partials) {
+template <class R>
+__global__ void k_pd_update(const cplx<R>* __restrict__ grid, const R* __restrict__ corr, const R* __restrict__ psiz,
+                            R* __restrict__ x, R* __restrict__ xhat, int n, int K, R tau, R theta,
+                            const double* __restrict__ sc, double* __restrict__ partials) {
   __shared__ double sh[40];
-  const float c = (float)sc[SC_C];
-  KahanF dd, xx;
+  const R c = (R)sc[SC_C];
+  acc_t<R> dd, xx;
   const int total = n * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int q = i / n, p = i - q * n;
     int r = q - n / 2; if (r < 0) r += K;
     int cc = p - n / 2; if (cc < 0) cc += K;
-    const float phit = c * corr[p] * corr[q] * grid[(size_t)r * K + cc].x;
-    const float xo = x[i];
-    const float xn = fmaxf(xo - tau * (psiz[i] + phit), 0.f);
-    xhat[i] = fmaf(theta, xn - xo, xn);
+    const R phit = c * corr[p] * corr[q] * grid[(size_t)r * K + cc].x;
+    const R xo = x[i];
+    const R xn = max_r(xo - tau * (psiz[i] + phit), (R)0);
+    xhat[i] = fma_r(theta, xn - xo, xn);
     x[i] = xn;
     dd.add((xn - xo) * (xn - xo));
     xx.add(xn * xn);
@@ -92,29 +95,31 @@ __global__ void k_rel_change(const double* __restrict__ partials, int n, double*
 }
 
 // ADMM: xt = x - rho * S^T Z^T Re(grid); zbar = max(xt, 0)
-__global__ void k_admm_xt(const float2* __restrict__ grid, const float* __restrict__ corr, const float* __restrict__ x,
-                          float* __restrict__ xt, float* __restrict__ zbar, int n, int K, float rho) {
+template <class R>
+__global__ void k_admm_xt(const cplx<R>* __restrict__ grid, const R* __restrict__ corr, const R* __restrict__ x,
+                          R* __restrict__ xt, R* __restrict__ zbar, int n, int K, R rho) {
   const int total = n * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int q = i / n, p = i - q * n;
     int r = q - n / 2; if (r < 0) r += K;
     int cc = p - n / 2; if (cc < 0) cc += K;
-    const float v = x[i] - rho * corr[p] * corr[q] * grid[(size_t)r * K + cc].x;
+    const R v = x[i] - rho * corr[p] * corr[q] * grid[(size_t)r * K + cc].x;
     xt[i] = v;
-    zbar[i] = fmaxf(v, 0.f);
+    zbar[i] = max_r(v, (R)0);
   }
 }
 
 // zbar = max(xt - Psi d, 0); on the last inner iteration also x = zbar with change partials.
-__global__ void k_admm_zbar(const float* __restrict__ xt, const float* __restrict__ psid, float* __restrict__ zbar,
-                            float* __restrict__ x, int64_t N, bool last, double* __restrict__ partials) {
+template <class R>
+__global__ void k_admm_zbar(const R* __restrict__ xt, const R* __restrict__ psid, R* __restrict__ zbar,
+                            R* __restrict__ x, int64_t N, bool last, double* __restrict__ partials) {
   __shared__ double sh[40];
-  KahanF dd, xx;
+  acc_t<R> dd, xx;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const float z = fmaxf(xt[i] - psid[i], 0.f);
+    const R z = max_r(xt[i] - psid[i], (R)0);
     zbar[i] = z;
     if (last) {
-      const float xo = x[i];
+      const R xo = x[i];
       dd.add((z - xo) * (z - xo));
       xx.add(z * z);
       x[i] = z;
@@ -129,17 +134,18 @@ __global__ void k_admm_zbar(const float* __restrict__ xt, const float* __restric
   }
 }
 
-__global__ void k_absmax_partials(const float* __restrict__ a, int64_t n, double* __restrict__ partials) {
-  __shared__ float sh[32];
-  float m = 0.f;
+template <class R>
+__global__ void k_absmax_partials(const R* __restrict__ a, int64_t n, double* __restrict__ partials) {
+  __shared__ R sh[32];
+  R m = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf(a[i]));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    m = max_r(m, abs_r(a[i]));
+  for (int o = 16; o > 0; o >>= 1) m = max_r(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float r = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, sh[w]);
+    R r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max_r(r, sh[w]);
     partials[blockIdx.x] = r;
   }
 }
@@ -152,13 +158,14 @@ __global__ void k_max_finish(const double* __restrict__ partials, int n, double*
   }
 }
 
-__global__ void k_residual_partials(const float2* __restrict__ a, const float2* __restrict__ b, int64_t M,
+template <class R>
+__global__ void k_residual_partials(const cplx<R>* __restrict__ a, const cplx<R>* __restrict__ b, int64_t M,
                                     double* __restrict__ partials) {
   __shared__ double sh[40];
-  KahanF acc;
+  acc_t<R> acc;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-    const float dr = a[i].x - b[i].x, di = a[i].y - b[i].y;
-    acc.add(fmaf(dr, dr, di * di));
+    const R dr = a[i].x - b[i].x, di = a[i].y - b[i].y;
+    acc.add(fma_r(dr, dr, di * di));
   }
   const double v = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = v;
@@ -183,8 +190,9 @@ struct gbri_solver {
   gbri_plan* plan = nullptr;
   gbri_wavelet* wav = nullptr;
   gbri_solve_params p{};
-  float2 *yp = nullptr, *u = nullptr, *w = nullptr;
-  float *x = nullptr, *xhat = nullptr, *psiz = nullptr, *z1 = nullptr, *xt = nullptr;
+  int prec = 0;  // the plan's precision: element type R of every vector below
+  void *yp = nullptr, *u = nullptr, *w = nullptr;                            // complex [M], plan order
+  void *x = nullptr, *xhat = nullptr, *psiz = nullptr, *z1 = nullptr, *xt = nullptr;  // real images / stacks
   double* partials = nullptr;
   double* sc = nullptr;
   int n_partials = 0;
@@ -211,6 +219,10 @@ void free_solver(gbri_solver* s) {
   delete s;
 }
 
+template <class R> R* vec(void* p) { return static_cast<R*>(p); }
+template <class R> cplx<R>* cvec(void* p) { return static_cast<cplx<R>*>(p); }
+
+template <class R>
 int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   gbri_plan* P = S->plan;
   gbri_wavelet* W = S->wav;
@@ -218,56 +230,60 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   const int n = P->n_side;
   const int64_t N = (int64_t)n * n;
   // z1 <- clip(z1 + sigma1 Psi^dagger xhat, gamma)
-  GBRI_TRY(psi_adjoint_apply(W, S->xhat, S->z1, DualEpi{1, 1.f, (float)p.sigma1, (float)p.gamma, 1.f}, st));
+  GBRI_TRY(psi_adjoint_apply<R>(W, vec<R>(S->xhat), vec<R>(S->z1), DualEpi{1, 1.0, p.sigma1, p.gamma, 1.0}, st));
   // u <- c u + sigma2 (Phi xhat - y), ||u||^2
-  GBRI_TRY(launch_pad(P, S->xhat, nullptr, st));
+  GBRI_TRY(launch_pad<R>(P, vec<R>(S->xhat), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
-  EpiPD1 e1{S->u, S->yp, S->sc + SC_C, S->partials, (float)p.sigma2, KahanF{}};
-  GBRI_TRY(launch_degrid(P, P->grid, e1, st));
+  EpiPD1<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->sc + SC_C, S->partials, (R)p.sigma2, acc_t<R>{}};
+  GBRI_TRY(launch_degrid(P, e1, st));
   launch_begin(GBRI_K_OTHER, st);
   k_ball_scalar<<<1, 256, 0, st>>>(S->partials, P->degrid_blocks, p.eps, p.sigma2, false, S->sc);
   GBRI_TRY(launch_end(GBRI_K_OTHER, st));
   // Phi^dagger u (scaled by c in the update)
-  GBRI_TRY(launch_grid(P, SrcPlan{S->u}, st));
+  GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st));
   GBRI_TRY(fft_inverse(P, st));
   // Psi z1
-  GBRI_TRY(psi_apply(W, S->z1, S->psiz, st));
+  GBRI_TRY(psi_apply<R>(W, vec<R>(S->z1), vec<R>(S->psiz), st));
   const int ib = std::min(img_blocks(N), S->n_partials / 2);
   launch_begin(GBRI_K_UPDATE, st);
-  k_pd_update<<<ib, 256, 0, st>>>(P->grid, P->corr, S->psiz, S->x, S->xhat, n, P->K, (float)p.tau, (float)p.theta,
-                                   S->sc, S->partials);
+  k_pd_update<R><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz),
+                                     vec<R>(S->x), vec<R>(S->xhat), n, P->K, (R)p.tau, (R)p.theta, S->sc,
+                                     S->partials);
   GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
   launch_begin(GBRI_K_OTHER, st);
   k_rel_change<<<1, 256, 0, st>>>(S->partials, ib, S->sc);
   return launch_end(GBRI_K_OTHER, st);
 }
 
+template <class R>
 int32_t admm_iteration(gbri_solver* S, cudaStream_t st) {
   gbri_plan* P = S->plan;
   gbri_wavelet* W = S->wav;
   const auto& p = S->p;
   const int n = P->n_side;
   const int64_t N = (int64_t)n * n;
-  GBRI_TRY(launch_pad(P, S->x, nullptr, st));
+  GBRI_TRY(launch_pad<R>(P, vec<R>(S->x), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
-  EpiADMM1 e1{S->w, S->u, S->yp, S->partials, KahanF{}};
-  GBRI_TRY(launch_degrid(P, P->grid, e1, st));
+  EpiADMM1<R> e1{cvec<R>(S->w), cvec<R>(S->u), cvec<R>(S->yp), S->partials, acc_t<R>{}};
+  GBRI_TRY(launch_degrid(P, e1, st));
   launch_begin(GBRI_K_OTHER, st);
   k_ball_scalar<<<1, 256, 0, st>>>(S->partials, P->degrid_blocks, p.eps, 1.0, true, S->sc);
   GBRI_TRY(launch_end(GBRI_K_OTHER, st));
-  GBRI_TRY(launch_grid(P, SrcADMM2{S->w, S->u, S->sc + SC_C, (float)p.varrho}, st));
+  GBRI_TRY(launch_grid(P, SrcADMM2<R>{cvec<R>(S->w), cvec<R>(S->u), S->sc + SC_C, (R)p.varrho}, st));
   GBRI_TRY(fft_inverse(P, st));
   const int ib = std::min(img_blocks(N), S->n_partials / 2);
   launch_begin(GBRI_K_UPDATE, st);
-  k_admm_xt<<<ib, 256, 0, st>>>(P->grid, P->corr, S->x, S->xt, S->xhat /* zbar */, n, P->K, (float)p.rho);
+  k_admm_xt<R><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->x),
+                                   vec<R>(S->xt), vec<R>(S->xhat) /* zbar */, n, P->K, (R)p.rho);
   GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
   for (int k = 0; k < p.dualfb_iters; ++k) {
-    GBRI_TRY(psi_adjoint_apply(W, S->xhat, S->z1 /* d */,
-                               DualEpi{1, (float)p.eta, 1.f, (float)p.gamma, (float)(1.0 / p.eta)}, st));
-    GBRI_TRY(psi_apply(W, S->z1, S->psiz, st));
+    GBRI_TRY(psi_adjoint_apply<R>(W, vec<R>(S->xhat), vec<R>(S->z1) /* d */,
+                                  DualEpi{1, p.eta, 1.0, p.gamma, 1.0 / p.eta}, st));
+    GBRI_TRY(psi_apply<R>(W, vec<R>(S->z1), vec<R>(S->psiz), st));
     const bool last = (k == p.dualfb_iters - 1);
     launch_begin(GBRI_K_UPDATE, st);
-    k_admm_zbar<<<ib, 256, 0, st>>>(S->xt, S->psiz, S->xhat, S->x, N, last, S->partials);
+    k_admm_zbar<R><<<ib, 256, 0, st>>>(vec<R>(S->xt), vec<R>(S->psiz), vec<R>(S->xhat), vec<R>(S->x), N, last,
+                                       S->partials);
     GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
   }
   launch_begin(GBRI_K_OTHER, st);
@@ -275,16 +291,23 @@ int32_t admm_iteration(gbri_solver* S, cudaStream_t st) {
   return launch_end(GBRI_K_OTHER, st);
 }
 
+int32_t iteration(gbri_solver* S, cudaStream_t st) {
+  if (S->prec == GBRI_F64)
+    return S->p.algo == GBRI_ALGO_PD ? pd_iteration<double>(S, st) : admm_iteration<double>(S, st);
+  return S->p.algo == GBRI_ALGO_PD ? pd_iteration<float>(S, st) : admm_iteration<float>(S, st);
+}
+
 // ||y - Phi x|| into sc[SC_RES] (uses the plan's visibility scratch)
+template <class R>
 int32_t residual(gbri_solver* S, cudaStream_t st) {
   gbri_plan* P = S->plan;
-  GBRI_TRY(launch_pad(P, S->x, nullptr, st));
+  GBRI_TRY(launch_pad<R>(P, vec<R>(S->x), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
-  if (P->M > 0) GBRI_TRY(launch_degrid(P, P->grid, EpiStorePlan{P->vis_tmp}, st));
+  if (P->M > 0) GBRI_TRY(launch_degrid(P, EpiStorePlan<R>{P->as<cplx<R>>(P->vis_tmp)}, st));
   const int b = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(ceil_div(P->M, 2048), S->n_partials),
                                                              (int64_t)num_sms() * 4));
   launch_begin(GBRI_K_OTHER, st);
-  k_residual_partials<<<b, 256, 0, st>>>(P->vis_tmp, S->yp, P->M, S->partials);
+  k_residual_partials<R><<<b, 256, 0, st>>>(P->as<const cplx<R>>(P->vis_tmp), cvec<R>(S->yp), P->M, S->partials);
   GBRI_TRY(launch_end(GBRI_K_OTHER, st));
   launch_begin(GBRI_K_OTHER, st);
   k_sqrt_sum<<<1, 256, 0, st>>>(S->partials, b, S->sc + SC_RES);
@@ -292,17 +315,18 @@ int32_t residual(gbri_solver* S, cudaStream_t st) {
 }
 
 // gamma = 1e-3 max|Psi^dagger Phi^dagger y| / ||Phi||^2
+template <class R>
 int32_t default_gamma(gbri_solver* S, cudaStream_t st, double* out) {
   gbri_plan* P = S->plan;
   const int64_t N = (int64_t)P->n_side * P->n_side;
-  GBRI_TRY(launch_grid(P, SrcPlan{S->yp}, st));
+  GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->yp)}, st));
   GBRI_TRY(fft_inverse(P, st));
-  GBRI_TRY(launch_crop(P, S->psiz, st));
-  GBRI_TRY(psi_adjoint_apply(S->wav, S->psiz, S->z1, DualEpi{0, 0.f, 0.f, 0.f, 0.f}, st));
+  GBRI_TRY(launch_crop<R>(P, vec<R>(S->psiz), st));
+  GBRI_TRY(psi_adjoint_apply<R>(S->wav, vec<R>(S->psiz), vec<R>(S->z1), DualEpi{0, 0.0, 0.0, 0.0, 0.0}, st));
   const int64_t tot = N * S->wav->nw;
   const int b = std::min(img_blocks(tot), S->n_partials);
   launch_begin(GBRI_K_OTHER, st);
-  k_absmax_partials<<<b, 256, 0, st>>>(S->z1, tot, S->partials);
+  k_absmax_partials<R><<<b, 256, 0, st>>>(vec<R>(S->z1), tot, S->partials);
   GBRI_TRY(launch_end(GBRI_K_OTHER, st));
   launch_begin(GBRI_K_OTHER, st);
   k_max_finish<<<1, 32, 0, st>>>(S->partials, b, S->sc + SC_MAX);
@@ -325,7 +349,7 @@ int32_t capture_iteration(gbri_solver* S) {
   if (!S->cap_stream) GBRI_CHECK_CUDA(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
   const int64_t before = launch_counter();
   GBRI_CHECK_CUDA(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
-  const int32_t r = S->p.algo == GBRI_ALGO_PD ? pd_iteration(S, S->cap_stream) : admm_iteration(S, S->cap_stream);
+  const int32_t r = iteration(S, S->cap_stream);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
   const int64_t captured = launch_counter() - before;
@@ -358,28 +382,40 @@ int32_t zalloc(T** p, size_t n, cudaStream_t s) {
   return GBRI_OK;
 }
 
-int32_t create_solver(gbri_solver* S, const float* d_y, uint32_t flags, cudaStream_t st) {
+// zeroed device buffer of `bytes` bytes
+int32_t zalloc_bytes(void** p, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    return set_error(GBRI_ENOMEM, "cudaMalloc solver state");
+  }
+  GBRI_CHECK_CUDA(cudaMemsetAsync(*p, 0, bytes, s));
+  return GBRI_OK;
+}
+
+int32_t create_solver(gbri_solver* S, const void* d_y, uint32_t flags, cudaStream_t st) {
   gbri_plan* P = S->plan;
   const int64_t N = (int64_t)P->n_side * P->n_side;
   const int64_t M = P->M;
   const int nw = S->wav->nw;
+  const size_t rb = real_bytes(S->prec);
   auto& p = S->p;
   S->n_partials = std::max(std::max(P->degrid_blocks, 2 * img_blocks(N * nw)), 2048);
   GBRI_TRY(zalloc(&S->partials, (size_t)S->n_partials * 2, st));
   GBRI_TRY(zalloc(&S->sc, SC_N, st));
-  GBRI_TRY(zalloc(&S->yp, (size_t)M, st));
-  GBRI_TRY(zalloc(&S->u, (size_t)M, st));
-  if (p.algo == GBRI_ALGO_ADMM) GBRI_TRY(zalloc(&S->w, (size_t)M, st));
-  GBRI_TRY(zalloc(&S->x, (size_t)N, st));
-  GBRI_TRY(zalloc(&S->xhat, (size_t)N, st));
-  GBRI_TRY(zalloc(&S->psiz, (size_t)N, st));
-  GBRI_TRY(zalloc(&S->xt, (size_t)N, st));
-  GBRI_TRY(zalloc(&S->z1, (size_t)(N * nw), st));
+  GBRI_TRY(zalloc_bytes(&S->yp, (size_t)M * 2 * rb, st));
+  GBRI_TRY(zalloc_bytes(&S->u, (size_t)M * 2 * rb, st));
+  if (p.algo == GBRI_ALGO_ADMM) GBRI_TRY(zalloc_bytes(&S->w, (size_t)M * 2 * rb, st));
+  GBRI_TRY(zalloc_bytes(&S->x, (size_t)N * rb, st));
+  GBRI_TRY(zalloc_bytes(&S->xhat, (size_t)N * rb, st));
+  GBRI_TRY(zalloc_bytes(&S->psiz, (size_t)N * rb, st));
+  GBRI_TRY(zalloc_bytes(&S->xt, (size_t)N * rb, st));
+  GBRI_TRY(zalloc_bytes(&S->z1, (size_t)(N * nw) * rb, st));
   if (M > 0) {
     if (flags & GBRI_PLAN_ORDER)
-      GBRI_CHECK_CUDA(cudaMemcpyAsync(S->yp, d_y, sizeof(float2) * M, cudaMemcpyDeviceToDevice, st));
+      GBRI_CHECK_CUDA(cudaMemcpyAsync(S->yp, d_y, (size_t)M * 2 * rb, cudaMemcpyDeviceToDevice, st));
     else
-      GBRI_TRY(gbri_vis_reorder(P, d_y, (float*)S->yp, 1, st));
+      GBRI_TRY(gbri_vis_reorder(P, d_y, S->yp, 1, st));
   }
   // resolve defaults
   if (p.max_iter < 0) return set_error(GBRI_EINVAL, "max_iter < 0");
@@ -397,10 +433,11 @@ int32_t create_solver(gbri_solver* S, const float* d_y, uint32_t flags, cudaStre
   if (p.eta <= 0) p.eta = 1.0;
   if (p.dualfb_iters <= 0) p.dualfb_iters = 1;
   if (p.check_every <= 0) p.check_every = 10;
-  if (p.gamma <= 0) GBRI_TRY(default_gamma(S, st, &p.gamma));
+  if (p.gamma <= 0)
+    GBRI_TRY(S->prec == GBRI_F64 ? default_gamma<double>(S, st, &p.gamma) : default_gamma<float>(S, st, &p.gamma));
   // x = 0, xhat = 0, duals = 0, c = 0
-  GBRI_CHECK_CUDA(cudaMemsetAsync(S->z1, 0, sizeof(float) * N * nw, st));
-  GBRI_CHECK_CUDA(cudaMemsetAsync(S->psiz, 0, sizeof(float) * N, st));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(S->z1, 0, rb * N * nw, st));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(S->psiz, 0, rb * N, st));
   GBRI_CHECK_CUDA(cudaMemsetAsync(S->sc, 0, sizeof(double) * SC_N, st));
   return GBRI_OK;
 }
@@ -424,16 +461,18 @@ void solver_add_iterations(gbri_solver* s, int n) { s->iters += n; }
 
 extern "C" {
 
-int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav, const float* d_y,
+int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav, const void* d_y,
                            const gbri_solve_params* params, uint32_t flags, void* stream) {
   GBRI_CHECK(out && plan && wav && params && (d_y || plan->M == 0), GBRI_EINVAL, "null argument");
   *out = nullptr;
   GBRI_CHECK(wav->n == plan->n_side, GBRI_EINVAL, "wavelet and plan image sizes differ");
+  GBRI_CHECK(wav->prec == plan->prec, GBRI_EINVAL, "wavelet and plan precisions differ");
   GBRI_CHECK(params->algo == GBRI_ALGO_PD || params->algo == GBRI_ALGO_ADMM, GBRI_EINVAL, "unknown algo");
   gbri_solver* S = new (std::nothrow) gbri_solver();
   GBRI_CHECK(S, GBRI_ENOMEM, "host allocation");
   S->plan = plan;
   S->wav = wav;
+  S->prec = plan->prec;
   S->p = *params;
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t r = create_solver(S, d_y, flags, st);
@@ -471,16 +510,17 @@ int32_t gbri_solver_step(gbri_solver* S, int32_t n_iter, void* stream) {
     }
   }
   for (int k = 0; k < n_iter; ++k) {
-    GBRI_TRY(S->p.algo == GBRI_ALGO_PD ? pd_iteration(S, st) : admm_iteration(S, st));
+    GBRI_TRY(iteration(S, st));
     ++S->iters;
   }
   return GBRI_OK;
 }
 
-int32_t gbri_solver_get_x(gbri_solver* S, float* d_x, void* stream) {
+int32_t gbri_solver_get_x(gbri_solver* S, void* d_x, void* stream) {
   GBRI_CHECK(S && d_x, GBRI_EINVAL, "null argument");
   const int64_t N = (int64_t)S->plan->n_side * S->plan->n_side;
-  GBRI_CHECK_CUDA(cudaMemcpyAsync(d_x, S->x, sizeof(float) * N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(d_x, S->x, real_bytes(S->prec) * N, cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream));
   return GBRI_OK;
 }
 
@@ -500,7 +540,7 @@ int32_t gbri_solver_status(gbri_solver* S, int32_t* iters, double* rel_change, v
 int32_t gbri_solver_report(gbri_solver* S, gbri_solve_report* r, void* stream) {
   GBRI_CHECK(S && r, GBRI_EINVAL, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
-  GBRI_TRY(residual(S, st));
+  GBRI_TRY(S->prec == GBRI_F64 ? residual<double>(S, st) : residual<float>(S, st));
   double sc[SC_N];
   GBRI_CHECK_CUDA(cudaMemcpyAsync(sc, S->sc, sizeof(sc), cudaMemcpyDeviceToHost, st));
   GBRI_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -514,8 +554,8 @@ int32_t gbri_solver_report(gbri_solver* S, gbri_solve_report* r, void* stream) {
   return GBRI_OK;
 }
 
-int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const float* d_y, const gbri_solve_params* params,
-                   float* d_x_out, gbri_solve_report* report, uint32_t flags, void* stream) {
+int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const void* d_y, const gbri_solve_params* params,
+                   void* d_x_out, gbri_solve_report* report, uint32_t flags, void* stream) {
   GBRI_CHECK(d_x_out, GBRI_EINVAL, "null x");
   gbri_solver* S = nullptr;
   GBRI_TRY(gbri_solver_create(&S, plan, wav, d_y, params, flags, stream));

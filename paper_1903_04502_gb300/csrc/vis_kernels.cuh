@@ -1,0 +1,259 @@
+// Degridding (G, W) and gridding (G^T, W^T) kernels of Sec. 2 / Eq. 2 over the
+// plan's tile-sorted visibilities, templated on the real type R (float: FP32 path,
+// double: FP64 path).  Included by exactly one translation unit per precision
+// (vis_f32.cu, vis_f64.cu), which instantiates every launch helper it needs.
+#pragma once
+
+#include <mutex>
+
+#include "nufft.cuh"
+
+namespace gbri {
+
+// Degridding (G then W, Sec. 2).  A block takes one chunk (one contiguous range of
+// at most kThreads * kRun visibilities of one 16 x 16 tile), copies the tile's
+// (T + J - 1)^2 grid window into shared memory when the tile changes, and gives one
+// thread per visibility with kRun visibilities in flight per thread (coalesced
+// metadata and epilogue streams):
+//   v = w * sum_{t'} wy[t'] sum_t wx[t] win[cy + t'][cx + t]
+// with the two J-tap weight rows from the shared-memory table.  The visibilities of
+// a sub-run share a cell, so neighbouring lanes often read the same window words.
+// `Epi` consumes (plan position, v).  Persistent blocks stride over the chunks.
+template <int J, class Epi>
+__global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi::real), J))
+    k_degrid(VisGeom geo, const cplx<typename Epi::real>* __restrict__ grid, Epi epi) {
+  using R = typename Epi::real;
+  using C = cplx<R>;
+  extern __shared__ float4 smem_dg[];
+  constexpr int P = kTile + J - 1;
+  R* sw = reinterpret_cast<R*>(smem_dg);
+  const int S = 1 << geo.log2S;
+  C* win = reinterpret_cast<C*>(sw + table_elems(S, J));
+  copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
+  const int K = geo.K;
+  int cur_tile = -1;
+  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
+    const int4 ch = geo.chunks[c];
+    const int2 s0 = geo.subruns[ch.y], s1 = geo.subruns[ch.y + ch.z - 1];
+    const int lo = s0.x, cnt = s1.x + s1.y - s0.x;
+    if (ch.x != cur_tile) {
+      __syncthreads();
+      const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
+      const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
+      for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int r = i / P, cc = i - r * P;
+        win[r * kWinPitch + cc] = __ldg(grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K));
+      }
+      cur_tile = ch.x;
+      __syncthreads();
+    }
+    uint2 m[kRun];
+    typename Epi::Pre pre[kRun];
+#pragma unroll
+    for (int k = 0; k < kRun; ++k) {
+      const int i = threadIdx.x + k * kThreads;
+      if (i < cnt) {
+        m[k] = geo.meta[lo + i];
+        pre[k] = epi.load(lo + i);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kRun; ++k) {
+      const int i = threadIdx.x + k * kThreads;
+      if (i >= cnt) break;
+      const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
+      R wx[J], wy[J];
+      load_taps<J>(sw, lx & (S - 1), S, wx);
+      load_taps<J>(sw, ly & (S - 1), S, wy);
+      const C* base = win + (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
+      R ar = 0, ai = 0;
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp) {
+        R rr = 0, ri = 0;
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+          const C gv = base[tp * kWinPitch + t];
+          rr = fma_r(wx[t], gv.x, rr);
+          ri = fma_r(wx[t], gv.y, ri);
+        }
+        ar = fma_r(wy[tp], rr, ar);
+        ai = fma_r(wy[tp], ri, ai);
+      }
+      const R w = (R)__uint_as_float(m[k].y);
+      epi.store(lo + i, pre[k], mkc<R>(w * ar, w * ai));
+    }
+  }
+  epi.finish();
+}
+
+// Gridding (W^T then G^T, Sec. 2).  A block takes one chunk (up to kThreads sub-run
+// slots of one tile; each round of the rank-major order starts at a warp boundary,
+// so the 32 lanes of a warp hold sub-runs of 32 distinct cells).  Thread t loads
+// its sub-run (<= kRun visibilities of one cell) at once, sums w * v * wy[t'] wx[t]
+// into a J x J register patch and adds it to its warp's private (T + J - 1)^2
+// accumulator in shared memory with plain read-modify-writes: the lanes of one
+// instruction touch distinct cells, and successive instructions of a warp are
+// ordered, so no atomics are needed.  The block then sums the warp accumulators and
+// writes the tile window to the global grid: plain stores for the cells no other
+// tile touches when the tile is a single chunk, atomics otherwise.
+// `Src` gives the visibility value at a plan position.
+template <int J, class Src>
+__global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::real), J))
+    k_grid(VisGeom geo, cplx<typename Src::real>* __restrict__ grid, Src src) {
+  using R = typename Src::real;
+  using C = cplx<R>;
+  extern __shared__ float4 smem_gr[];
+  constexpr int P = kTile + J - 1;
+  constexpr int W = kThreads / 32;
+  const int S = 1 << geo.log2S;
+  R* sw = reinterpret_cast<R*>(smem_gr);
+  C* accs = reinterpret_cast<C*>(sw + table_elems(S, J));
+  copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
+  C* acc = accs + (threadIdx.x >> 5) * (P * kAccPitch2);
+  const int K = geo.K;
+  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
+    const int4 ch = geo.chunks[c];
+    for (int i = threadIdx.x; i < W * P * kAccPitch2; i += blockDim.x) accs[i] = mkc<R>(0, 0);
+    __syncthreads();
+    {
+      const int2 sr = ((int)threadIdx.x < ch.z) ? geo.subruns[ch.y + threadIdx.x] : make_int2(0, 0);
+      const bool active = sr.y > 0;
+      uint2 m[kRun];
+      C v[kRun];
+#pragma unroll
+      for (int k = 0; k < kRun; ++k)
+        if (k < sr.y) {
+          m[k] = geo.meta[sr.x + k];
+          v[k] = src(sr.x + k);
+        }
+      C pt[J][J];
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+        for (int t = 0; t < J; ++t) pt[tp][t] = mkc<R>(0, 0);
+#pragma unroll
+      for (int k = 0; k < kRun; ++k) {
+        if (k >= sr.y) break;
+        R wx[J], wy[J];
+        load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
+        load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
+        const R w = (R)__uint_as_float(m[k].y);
+        const R vr = w * v[k].x, vi = w * v[k].y;
+#pragma unroll
+        for (int tp = 0; tp < J; ++tp) {
+          const R br = wy[tp] * vr, bi = wy[tp] * vi;
+#pragma unroll
+          for (int t = 0; t < J; ++t) {
+            pt[tp][t].x = fma_r(wx[t], br, pt[tp][t].x);
+            pt[tp][t].y = fma_r(wx[t], bi, pt[tp][t].y);
+          }
+        }
+      }
+      const int a0 = active ? ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S)
+                            : 0;
+      // all 32 lanes walk the taps in lockstep: within one tap the active lanes touch
+      // distinct cells, and the warp barrier orders one tap's stores before the next
+      // tap's loads (a neighbour cell's patch overlaps this one)
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+          if (active) {
+            C* q = acc + a0 + tp * kAccPitch2 + t;
+            const C o = *q;
+            *q = mkc<R>(o.x + pt[tp][t].x, o.y + pt[tp][t].y);
+          }
+          __syncwarp();
+        }
+    }
+    __syncthreads();
+    const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
+    const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
+    // accumulator rows / cols [lo_x, hi_x) belong to no other tile's window
+    constexpr int lo_x = J - 1, hi_x = kTile;
+    const bool single = ch.w != 0;
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+      const int r = i / P, cc = i - r * P;
+      R ax = 0, ay = 0;
+#pragma unroll
+      for (int wq = 0; wq < W; ++wq) {
+        const C b = accs[wq * (P * kAccPitch2) + r * kAccPitch2 + cc];
+        ax += b.x;
+        ay += b.y;
+      }
+      C* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      if (single && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) {
+        *dst = mkc<R>(ax, ay);
+      } else if (ax != 0 || ay != 0) {
+        if constexpr (sizeof(R) == 4) {
+          atomicAdd(dst, mkc<R>(ax, ay));  // one vector atomic
+        } else {
+          atomicAdd(&dst->x, ax);
+          atomicAdd(&dst->y, ay);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <class Epi>
+int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s) {
+  using R = typename Epi::real;
+  launch_begin(GBRI_K_DEGRID, s);
+  const cplx<R>* g = p->as<cplx<R>>(p->grid);
+  if (p->J == 4) k_degrid<4, Epi><<<p->degrid_blocks, kThreads, degrid_smem(p), s>>>(vis_geom(p), g, epi);
+  else k_degrid<6, Epi><<<p->degrid_blocks, kThreads, degrid_smem(p), s>>>(vis_geom(p), g, epi);
+  return launch_end(GBRI_K_DEGRID, s);
+}
+
+template <class Src>
+int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s) {
+  using R = typename Src::real;
+  cplx<R>* g = p->as<cplx<R>>(p->grid);
+  GBRI_CHECK_CUDA(cudaMemsetAsync(g, 0, sizeof(cplx<R>) * (size_t)p->K * p->K, s));
+  if (p->n_chunks == 0) return GBRI_OK;
+  launch_begin(GBRI_K_GRID, s);
+  if (p->J == 4) k_grid<4, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(vis_geom(p), g, src);
+  else k_grid<6, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(vis_geom(p), g, src);
+  return launch_end(GBRI_K_GRID, s);
+}
+
+// Dynamic shared memory above 48 KB needs a per-kernel attribute; it is set once
+// for every instantiation of one precision before any launch (so never inside a
+// stream capture).
+template <class R>
+int32_t prepare_visibility_kernels() {
+  static int32_t status = -100;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int lim = 220 * 1024;
+    cudaError_t e = cudaSuccess;
+#define GBRI_ATTR(kern) if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+    GBRI_ATTR((k_degrid<4, EpiStorePlan<R>>)); GBRI_ATTR((k_degrid<6, EpiStorePlan<R>>));
+    GBRI_ATTR((k_degrid<4, EpiStoreRaw<R>>)); GBRI_ATTR((k_degrid<6, EpiStoreRaw<R>>));
+    GBRI_ATTR((k_degrid<4, EpiPD1<R>>)); GBRI_ATTR((k_degrid<6, EpiPD1<R>>));
+    GBRI_ATTR((k_degrid<4, EpiADMM1<R>>)); GBRI_ATTR((k_degrid<6, EpiADMM1<R>>));
+    GBRI_ATTR((k_grid<4, SrcPlan<R>>)); GBRI_ATTR((k_grid<6, SrcPlan<R>>));
+    GBRI_ATTR((k_grid<4, SrcRaw<R>>)); GBRI_ATTR((k_grid<6, SrcRaw<R>>));
+    GBRI_ATTR((k_grid<4, SrcADMM2<R>>)); GBRI_ATTR((k_grid<6, SrcADMM2<R>>));
+#undef GBRI_ATTR
+    status = (e == cudaSuccess) ? GBRI_OK : cuda_error(e, "cudaFuncSetAttribute");
+  });
+  return status;
+}
+
+}  // namespace gbri
+
+// Instantiates every visibility launch helper of real type R (one translation unit per R).
+#define GBRI_INSTANTIATE_VIS(R)                                                              \
+  namespace gbri {                                                                           \
+  template int32_t launch_degrid<EpiStorePlan<R>>(gbri_plan*, EpiStorePlan<R>, cudaStream_t); \
+  template int32_t launch_degrid<EpiStoreRaw<R>>(gbri_plan*, EpiStoreRaw<R>, cudaStream_t);   \
+  template int32_t launch_degrid<EpiPD1<R>>(gbri_plan*, EpiPD1<R>, cudaStream_t);             \
+  template int32_t launch_degrid<EpiADMM1<R>>(gbri_plan*, EpiADMM1<R>, cudaStream_t);         \
+  template int32_t launch_grid<SrcPlan<R>>(gbri_plan*, SrcPlan<R>, cudaStream_t);             \
+  template int32_t launch_grid<SrcRaw<R>>(gbri_plan*, SrcRaw<R>, cudaStream_t);               \
+  template int32_t launch_grid<SrcADMM2<R>>(gbri_plan*, SrcADMM2<R>, cudaStream_t);           \
+  template int32_t prepare_visibility_kernels<R>();                                           \
+  }

@@ -91,17 +91,21 @@ std::vector<double> daubechies_lowpass(int N) {
 
 namespace {
 
-__device__ __forceinline__ int pmod(int v, int m) {
-  v %= m;
-  return v < 0 ? v + m : v;
-}
+template <class R>
+struct EpiR {  // DualEpi rounded to R once per thread
+  int mode;
+  R ca, cb, lim, ce;
+  __device__ __forceinline__ explicit EpiR(const DualEpi& e)
+      : mode(e.mode), ca((R)e.ca), cb((R)e.cb), lim((R)e.lim), ce((R)e.ce) {}
+};
 
-__device__ __forceinline__ void emit(float* __restrict__ out, size_t q, float v, const DualEpi& e) {
+template <class R>
+__device__ __forceinline__ void emit(R* __restrict__ out, size_t q, R v, const EpiR<R>& e) {
   if (e.mode == 0) {
     out[q] = v;
   } else {
-    const float u = fmaf(e.ca, out[q], e.cb * v);
-    out[q] = fminf(fmaxf(u, -e.lim), e.lim) * e.ce;
+    const R u = fma_r(e.ca, out[q], e.cb * v);
+    out[q] = min_r(max_r(u, -e.lim), e.lim) * e.ce;
   }
 }
 
@@ -110,26 +114,27 @@ constexpr int kATile = 2 * kAB + kMaxTaps - 2;  // input rows / cols a block rea
 constexpr int kSB = 32;                         // synthesis: output samples per block side
 constexpr int kSK = kSB / 2 + kMaxTaps / 2 - 1; // coefficient rows / cols per half a block reads
 
+template <class R>
 struct AnaSmem {
-  float tin[kATile][kATile + 1];
-  float trow[kATile][2 * kAB + 1];
+  R tin[kATile][kATile + 1];
+  R trow[kATile][2 * kAB + 1];
 };
+template <class R>
 struct SynSmem {
-  float tc[2 * kSK][2 * kSK + 1];  // [a|d rows][a|d cols]
-  float tm[kSB][2 * kSK + 1];      // after the column synthesis
+  R tc[2 * kSK][2 * kSK + 1];  // [a|d rows][a|d cols]
+  R tm[kSB][2 * kSK + 1];      // after the column synthesis
 };
 
 // One analysis level of one basis with an L-tap filter pair (unrolled), block
 // (blockIdx.x, blockIdx.y) = 16 x 16 output coefficients of each quadrant.
-template <int L>
-__device__ __forceinline__ void dwt_block(AnaSmem& sm, const float* __restrict__ src, float* __restrict__ carry,
-                                          float* __restrict__ dst, int m, int n, bool last, float scale,
-                                          const float* __restrict__ hf, const float* __restrict__ gf,
-                                          const DualEpi& e) {
+template <int L, class R>
+__device__ __forceinline__ void dwt_block(AnaSmem<R>& sm, const R* __restrict__ src, R* __restrict__ carry,
+                                          R* __restrict__ dst, int m, int n, bool last, R scale,
+                                          const R* __restrict__ hf, const R* __restrict__ gf, const EpiR<R>& e) {
   constexpr int T = 2 * kAB + L - 2;
   const int half = m >> 1;
   const int k0 = blockIdx.y * kAB, l0 = blockIdx.x * kAB;
-  float h[L], g[L];
+  R h[L], g[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) {
     h[i] = hf[i];
@@ -139,7 +144,7 @@ __device__ __forceinline__ void dwt_block(AnaSmem& sm, const float* __restrict__
   for (int rr = ty; rr < T; rr += 8) {
     int gr = 2 * k0 + rr;
     gr = gr < m ? gr : gr % m;
-    const float* row = src + (size_t)gr * n;
+    const R* row = src + (size_t)gr * n;
     for (int cc = tx; cc < T; cc += 32) {
       int gc = 2 * l0 + cc;
       gc = gc < m ? gc : gc % m;
@@ -150,12 +155,12 @@ __device__ __forceinline__ void dwt_block(AnaSmem& sm, const float* __restrict__
   {
     const int l = threadIdx.x & (kAB - 1);
     for (int rr = threadIdx.x >> 4; rr < T; rr += 256 / kAB) {
-      float a = 0.f, d = 0.f;
+      R a = 0, d = 0;
 #pragma unroll
       for (int i = 0; i < L; ++i) {
-        const float v = sm.tin[rr][2 * l + i];
-        a = fmaf(h[i], v, a);
-        d = fmaf(g[i], v, d);
+        const R v = sm.tin[rr][2 * l + i];
+        a = fma_r(h[i], v, a);
+        d = fma_r(g[i], v, d);
       }
       sm.trow[rr][l] = a;
       sm.trow[rr][kAB + l] = d;
@@ -167,12 +172,12 @@ __device__ __forceinline__ void dwt_block(AnaSmem& sm, const float* __restrict__
   for (int k = ty; k < kAB; k += 8) {
     const int kk = k0 + k;
     if (kk >= half || ll_ >= half) continue;
-    float lo = 0.f, hi = 0.f;
+    R lo = 0, hi = 0;
 #pragma unroll
     for (int i = 0; i < L; ++i) {
-      const float v = sm.trow[2 * k + i][c];
-      lo = fmaf(h[i], v, lo);
-      hi = fmaf(g[i], v, hi);
+      const R v = sm.trow[2 * k + i][c];
+      lo = fma_r(h[i], v, lo);
+      hi = fma_r(g[i], v, hi);
     }
     const int col = (c < kAB) ? ll_ : half + ll_;
     if (c < kAB && !last) carry[(size_t)kk * n + col] = lo;
@@ -186,16 +191,18 @@ __device__ __forceinline__ void dwt_block(AnaSmem& sm, const float* __restrict__
 // [a | d] halves in shared memory, then its columns, and writes a 16 x 16 block of each
 // quadrant.  The LL quadrant goes to the carry buffer unless this is the last level;
 // every other coefficient is final and goes through the epilogue.
-__global__ void __launch_bounds__(256) k_dwt_level(const float* __restrict__ in, size_t in_stride,
-                                                   float* __restrict__ ll, float* __restrict__ out, int m, int n,
-                                                   bool last, float scale, const Filters F, const DualEpi e) {
-  __shared__ AnaSmem sm;
+template <class R>
+__global__ void __launch_bounds__(256) k_dwt_level(const R* __restrict__ in, size_t in_stride, R* __restrict__ ll,
+                                                   R* __restrict__ out, int m, int n, bool last, R scale,
+                                                   const Filters<R> F, const DualEpi ep) {
+  __shared__ AnaSmem<R> sm;
+  const EpiR<R> e(ep);
   const int j = blockIdx.z;
-  const float* src = in + in_stride * j;
-  float* carry = ll + (size_t)n * n * j;
-  float* dst = out + (size_t)n * n * F.aidx[j];
+  const R* src = in + in_stride * j;
+  R* carry = ll + (size_t)n * n * j;
+  R* dst = out + (size_t)n * n * F.aidx[j];
 #define GBRI_DWT_CASE(LL) \
-  case LL: dwt_block<LL>(sm, src, carry, dst, m, n, last, scale, F.h[j], F.g[j], e); break;
+  case LL: dwt_block<LL, R>(sm, src, carry, dst, m, n, last, scale, F.h[j], F.g[j], e); break;
   switch (F.len[j]) {
     GBRI_DWT_CASE(2) GBRI_DWT_CASE(4) GBRI_DWT_CASE(6) GBRI_DWT_CASE(8) GBRI_DWT_CASE(10) GBRI_DWT_CASE(12)
     GBRI_DWT_CASE(14) GBRI_DWT_CASE(16) GBRI_DWT_CASE(18) GBRI_DWT_CASE(20)
@@ -207,15 +214,15 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float* __restrict__ in,
 // One synthesis level of one basis with an L-tap filter pair (the transpose of the
 // analysis): reconstructs a 32 x 32 window of the m x m block from the
 // 2 x (16 + L/2 - 1) coefficient rows and columns it touches (periodic).
-template <int L>
-__device__ __forceinline__ void idwt_block(SynSmem& sm, const float* __restrict__ coef, const float* __restrict__ llsrc,
-                                           float* __restrict__ dst, int m, int n, const float* __restrict__ hf,
-                                           const float* __restrict__ gf) {
+template <int L, class R>
+__device__ __forceinline__ void idwt_block(SynSmem<R>& sm, const R* __restrict__ coef, const R* __restrict__ llsrc,
+                                           R* __restrict__ dst, int m, int n, const R* __restrict__ hf,
+                                           const R* __restrict__ gf) {
   constexpr int KB = kSB / 2 + L / 2 - 1;
   const int half = m >> 1;
   const int r0 = blockIdx.y * kSB, c0 = blockIdx.x * kSB;
   const int kr_lo = r0 / 2 - L / 2 + 1, kc_lo = c0 / 2 - L / 2 + 1;
-  float h[L], g[L];
+  R h[L], g[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) {
     h[i] = hf[i];
@@ -238,7 +245,7 @@ __device__ __forceinline__ void idwt_block(SynSmem& sm, const float* __restrict_
       if (small) kc %= half;
       if (kc < 0) kc += half;
       if (kc >= half) kc -= half;
-      const float* srcp = (pr == 0 && pc == 0) ? llsrc : coef;
+      const R* srcp = (pr == 0 && pc == 0) ? llsrc : coef;
       sm.tc[sr][sc] = srcp[rowoff + pc * half + kc];
     }
   }
@@ -247,13 +254,13 @@ __device__ __forceinline__ void idwt_block(SynSmem& sm, const float* __restrict_
   // coefficient rows kq = p + L/2 - 1 - s of the a and d halves
   for (int idx = threadIdx.x; idx < (kSB / 2) * 2 * KB; idx += blockDim.x) {
     const int pr = idx / (2 * KB), sc = idx - pr * (2 * KB);
-    float ve = 0.f, vo = 0.f;
+    R ve = 0, vo = 0;
 #pragma unroll
     for (int q = 0; q < L / 2; ++q) {
       const int kq = pr + L / 2 - 1 - q;
-      const float a = sm.tc[kq][sc], d = sm.tc[KB + kq][sc];
-      ve = fmaf(h[2 * q], a, fmaf(g[2 * q], d, ve));
-      vo = fmaf(h[2 * q + 1], a, fmaf(g[2 * q + 1], d, vo));
+      const R a = sm.tc[kq][sc], d = sm.tc[KB + kq][sc];
+      ve = fma_r(h[2 * q], a, fma_r(g[2 * q], d, ve));
+      vo = fma_r(h[2 * q + 1], a, fma_r(g[2 * q + 1], d, vo));
     }
     sm.tm[2 * pr][sc] = ve;
     sm.tm[2 * pr + 1][sc] = vo;
@@ -262,18 +269,18 @@ __device__ __forceinline__ void idwt_block(SynSmem& sm, const float* __restrict_
   // row synthesis, two output columns per item
   for (int idx = threadIdx.x; idx < kSB * (kSB / 2); idx += blockDim.x) {
     const int r = idx / (kSB / 2), pc = idx - r * (kSB / 2);
-    float ve = 0.f, vo = 0.f;
+    R ve = 0, vo = 0;
 #pragma unroll
     for (int q = 0; q < L / 2; ++q) {
       const int kq = pc + L / 2 - 1 - q;
-      const float a = sm.tm[r][kq], d = sm.tm[r][KB + kq];
-      ve = fmaf(h[2 * q], a, fmaf(g[2 * q], d, ve));
-      vo = fmaf(h[2 * q + 1], a, fmaf(g[2 * q + 1], d, vo));
+      const R a = sm.tm[r][kq], d = sm.tm[r][KB + kq];
+      ve = fma_r(h[2 * q], a, fma_r(g[2 * q], d, ve));
+      vo = fma_r(h[2 * q + 1], a, fma_r(g[2 * q + 1], d, vo));
     }
-    const int R = r0 + r, C = c0 + 2 * pc;
-    if (R < m) {
-      if (C < m) dst[(size_t)R * n + C] = ve;
-      if (C + 1 < m) dst[(size_t)R * n + C + 1] = vo;
+    const int Rr = r0 + r, Cc = c0 + 2 * pc;
+    if (Rr < m) {
+      if (Cc < m) dst[(size_t)Rr * n + Cc] = ve;
+      if (Cc + 1 < m) dst[(size_t)Rr * n + Cc + 1] = vo;
     }
   }
 }
@@ -281,16 +288,17 @@ __device__ __forceinline__ void idwt_block(SynSmem& sm, const float* __restrict_
 // One synthesis level at block size m for basis blockIdx.z: writes the reconstruction
 // of the m x m block into rec_out[basis].  The LL quadrant is read from rec_in (the
 // coarser level's reconstruction, from_rec) or from the coefficients.
-__global__ void __launch_bounds__(256) k_idwt_level(const float* __restrict__ alpha, const float* __restrict__ rec_in,
-                                                    bool from_rec, float* __restrict__ rec_out, int m, int n,
-                                                    const Filters F) {
-  __shared__ SynSmem sm;
+template <class R>
+__global__ void __launch_bounds__(256) k_idwt_level(const R* __restrict__ alpha, const R* __restrict__ rec_in,
+                                                    bool from_rec, R* __restrict__ rec_out, int m, int n,
+                                                    const Filters<R> F) {
+  __shared__ SynSmem<R> sm;
   const int j = blockIdx.z;
-  const float* coef = alpha + (size_t)n * n * F.aidx[j];
-  const float* llsrc = from_rec ? rec_in + (size_t)n * n * j : coef;
-  float* dst = rec_out + (size_t)n * n * j;
+  const R* coef = alpha + (size_t)n * n * F.aidx[j];
+  const R* llsrc = from_rec ? rec_in + (size_t)n * n * j : coef;
+  R* dst = rec_out + (size_t)n * n * j;
 #define GBRI_IDWT_CASE(LL) \
-  case LL: idwt_block<LL>(sm, coef, llsrc, dst, m, n, F.h[j], F.g[j]); break;
+  case LL: idwt_block<LL, R>(sm, coef, llsrc, dst, m, n, F.h[j], F.g[j]); break;
   switch (F.len[j]) {
     GBRI_IDWT_CASE(2) GBRI_IDWT_CASE(4) GBRI_IDWT_CASE(6) GBRI_IDWT_CASE(8) GBRI_IDWT_CASE(10) GBRI_IDWT_CASE(12)
     GBRI_IDWT_CASE(14) GBRI_IDWT_CASE(16) GBRI_IDWT_CASE(18) GBRI_IDWT_CASE(20)
@@ -300,23 +308,27 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float* __restrict__ al
 }
 
 // x[q] = scale * (sum_j rec[j][q] + dirac[q])
-__global__ void k_psi_sum(const float* __restrict__ rec, int nb, const float* __restrict__ dirac,
-                          float* __restrict__ x, int64_t N, float scale) {
+template <class R>
+__global__ void k_psi_sum(const R* __restrict__ rec, int nb, const R* __restrict__ dirac, R* __restrict__ x,
+                          int64_t N, R scale) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-    float v = dirac ? dirac[q] : 0.f;
+    R v = dirac ? dirac[q] : (R)0;
     for (int j = 0; j < nb; ++j) v += rec[(size_t)N * j + q];
     x[q] = scale * v;
   }
 }
 
 // Dirac basis of the analysis: out[q] = epi(scale * x[q]).
-__global__ void k_dirac(const float* __restrict__ x, float* __restrict__ out, int64_t N, float scale, const DualEpi e) {
+template <class R>
+__global__ void k_dirac(const R* __restrict__ x, R* __restrict__ out, int64_t N, R scale, const DualEpi ep) {
+  const EpiR<R> e(ep);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
     emit(out, (size_t)q, scale * x[q], e);
 }
 
 // x[q] = scale * dirac[q] (a dictionary that holds only the Dirac basis)
-__global__ void k_scale_copy(const float* __restrict__ a, float* __restrict__ x, int64_t N, float scale) {
+template <class R>
+__global__ void k_scale_copy(const R* __restrict__ a, R* __restrict__ x, int64_t N, R scale) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
     x[q] = scale * a[q];
 }
@@ -325,58 +337,71 @@ int blocks_for(int64_t work) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), (int64_t)num_sms() * 8));
 }
 
+template <class R> const Filters<R>& filters(const gbri_wavelet* w);
+template <> const Filters<float>& filters<float>(const gbri_wavelet* w) { return w->F; }
+template <> const Filters<double>& filters<double>(const gbri_wavelet* w) { return w->Fd; }
+
 }  // namespace
 
-int32_t psi_adjoint_apply(gbri_wavelet* w, const float* x, float* out, DualEpi epi, cudaStream_t s) {
+template <class R>
+int32_t psi_adjoint_apply(gbri_wavelet* w, const R* x, R* out, DualEpi epi, cudaStream_t s) {
   const int n = w->n;
   const int64_t N = (int64_t)n * n;
+  const R scale = (R)w->scale;
   if (w->dirac_idx >= 0) {
     launch_begin(GBRI_K_PSI_ADJ, s);
-    k_dirac<<<blocks_for(N), 256, 0, s>>>(x, out + (size_t)N * w->dirac_idx, N, w->scale, epi);
+    k_dirac<R><<<blocks_for(N), 256, 0, s>>>(x, out + (size_t)N * w->dirac_idx, N, scale, epi);
     GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
   }
   if (w->nb == 0) return GBRI_OK;
   // the LL carry ping-pongs between the two buffers: a level must not overwrite the
   // window another block of the same level still has to read
-  float* carry[2] = {w->ll, w->tmp};
+  R* carry[2] = {static_cast<R*>(w->ll), static_cast<R*>(w->tmp)};
   for (int lev = 0; lev < w->levels; ++lev) {
     const int m = n >> lev;
     const int bq = (int)ceil_div(m / 2, kAB);
-    const float* in = (lev == 0) ? x : carry[(lev - 1) & 1];
+    const R* in = (lev == 0) ? x : carry[(lev - 1) & 1];
     const size_t in_stride = (lev == 0) ? 0 : (size_t)N;
     launch_begin(GBRI_K_PSI_ADJ, s);
-    k_dwt_level<<<dim3(bq, bq, w->nb), 256, 0, s>>>(in, in_stride, carry[lev & 1], out, m, n, lev == w->levels - 1,
-                                                    w->scale, w->F, epi);
+    k_dwt_level<R><<<dim3(bq, bq, w->nb), 256, 0, s>>>(in, in_stride, carry[lev & 1], out, m, n,
+                                                       lev == w->levels - 1, scale, filters<R>(w), epi);
     GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
   }
   return GBRI_OK;
 }
 
-int32_t psi_apply(gbri_wavelet* w, const float* alpha, float* x, cudaStream_t s) {
+template <class R>
+int32_t psi_apply(gbri_wavelet* w, const R* alpha, R* x, cudaStream_t s) {
   const int n = w->n;
   const int64_t N = (int64_t)n * n;
-  const float* dirac = w->dirac_idx >= 0 ? alpha + (size_t)N * w->dirac_idx : nullptr;
+  const R scale = (R)w->scale;
+  const R* dirac = w->dirac_idx >= 0 ? alpha + (size_t)N * w->dirac_idx : nullptr;
   if (w->nb == 0) {
     launch_begin(GBRI_K_PSI, s);
-    k_scale_copy<<<blocks_for(N), 256, 0, s>>>(dirac, x, N, w->scale);
+    k_scale_copy<R><<<blocks_for(N), 256, 0, s>>>(dirac, x, N, scale);
     return launch_end(GBRI_K_PSI, s);
   }
   // ping-pong reconstruction buffers: level l reads the coarser level's output
-  float* bufs[2] = {w->ll, w->tmp};
+  R* bufs[2] = {static_cast<R*>(w->ll), static_cast<R*>(w->tmp)};
   int cur = 0;
   for (int lev = w->levels - 1; lev >= 0; --lev) {
     const int m = n >> lev;
     const int bs = (int)ceil_div(m, kSB);
     launch_begin(GBRI_K_PSI, s);
-    k_idwt_level<<<dim3(bs, bs, w->nb), 256, 0, s>>>(alpha, bufs[cur ^ 1], lev != w->levels - 1, bufs[cur], m, n,
-                                                     w->F);
+    k_idwt_level<R><<<dim3(bs, bs, w->nb), 256, 0, s>>>(alpha, bufs[cur ^ 1], lev != w->levels - 1, bufs[cur], m, n,
+                                                        filters<R>(w));
     GBRI_TRY(launch_end(GBRI_K_PSI, s));
     cur ^= 1;
   }
   launch_begin(GBRI_K_PSI, s);
-  k_psi_sum<<<blocks_for(N), 256, 0, s>>>(bufs[cur ^ 1], w->nb, dirac, x, N, w->scale);
+  k_psi_sum<R><<<blocks_for(N), 256, 0, s>>>(bufs[cur ^ 1], w->nb, dirac, x, N, scale);
   return launch_end(GBRI_K_PSI, s);
 }
+
+template int32_t psi_adjoint_apply<float>(gbri_wavelet*, const float*, float*, DualEpi, cudaStream_t);
+template int32_t psi_adjoint_apply<double>(gbri_wavelet*, const double*, double*, DualEpi, cudaStream_t);
+template int32_t psi_apply<float>(gbri_wavelet*, const float*, float*, cudaStream_t);
+template int32_t psi_apply<double>(gbri_wavelet*, const double*, double*, cudaStream_t);
 
 }  // namespace gbri
 
@@ -388,7 +413,7 @@ int32_t gbri_wavelet_create(gbri_wavelet** out, int32_t n_side, int32_t levels, 
                             int32_t n_w, int32_t precision) {
   GBRI_CHECK(out && db_orders, GBRI_EINVAL, "null argument");
   *out = nullptr;
-  GBRI_CHECK(precision == GBRI_F32, GBRI_EINVAL, "only GBRI_F32 is supported");
+  GBRI_CHECK(precision == GBRI_F32 || precision == GBRI_F64, GBRI_EINVAL, "precision must be GBRI_F32 or GBRI_F64");
   GBRI_CHECK(n_w >= 1 && n_w <= kMaxBases, GBRI_EINVAL, "n_w must be in [1, 16]");
   GBRI_CHECK(levels >= 1 && levels <= 12, GBRI_EINVAL, "levels must be in [1, 12]");
   GBRI_CHECK(n_side >= 4 && n_side % (1 << levels) == 0 && (n_side >> levels) >= 2, GBRI_EINVAL,
@@ -398,7 +423,8 @@ int32_t gbri_wavelet_create(gbri_wavelet** out, int32_t n_side, int32_t levels, 
   w->n = n_side;
   w->levels = levels;
   w->nw = n_w;
-  w->scale = (float)(1.0 / std::sqrt((double)n_w));
+  w->prec = precision;
+  w->scale = 1.0 / std::sqrt((double)n_w);
   for (int b = 0; b < n_w; ++b) {
     const int N = db_orders[b];
     if (N < 0 || N > kMaxTaps / 2 || (N == 0 && w->dirac_idx >= 0)) {
@@ -414,14 +440,18 @@ int32_t gbri_wavelet_create(gbri_wavelet** out, int32_t n_side, int32_t levels, 
     const int L = (int)h.size();
     const int j = w->nb++;
     for (int i = 0; i < kMaxTaps; ++i) {
-      w->F.h[j][i] = i < L ? (float)h[i] : 0.f;
-      w->F.g[j][i] = i < L ? (float)((i % 2 ? -1.0 : 1.0) * h[L - 1 - i]) : 0.f;
+      const double hv = i < L ? h[i] : 0.0;
+      const double gv = i < L ? (i % 2 ? -1.0 : 1.0) * h[L - 1 - i] : 0.0;
+      w->F.h[j][i] = (float)hv;
+      w->F.g[j][i] = (float)gv;
+      w->Fd.h[j][i] = hv;
+      w->Fd.g[j][i] = gv;
     }
-    w->F.len[j] = L;
-    w->F.aidx[j] = b;
+    w->F.len[j] = w->Fd.len[j] = L;
+    w->F.aidx[j] = w->Fd.aidx[j] = b;
   }
-  const size_t bytes = sizeof(float) * (size_t)std::max(1, w->nb) * n_side * n_side;
-  if (cudaMalloc((void**)&w->tmp, bytes) != cudaSuccess || cudaMalloc((void**)&w->ll, bytes) != cudaSuccess) {
+  const size_t bytes = real_bytes(precision) * (size_t)std::max(1, w->nb) * n_side * n_side;
+  if (cudaMalloc(&w->tmp, bytes) != cudaSuccess || cudaMalloc(&w->ll, bytes) != cudaSuccess) {
     cudaFree(w->tmp);
     cudaFree(w->ll);
     delete w;
@@ -440,15 +470,20 @@ int32_t gbri_wavelet_destroy(gbri_wavelet* w) {
   return GBRI_OK;
 }
 
-int32_t gbri_psi(gbri_wavelet* w, const float* d_alpha, float* d_x, void* stream) {
+int32_t gbri_psi(gbri_wavelet* w, const void* d_alpha, void* d_x, void* stream) {
   GBRI_CHECK(w && d_alpha && d_x, GBRI_EINVAL, "null argument");
-  return psi_apply(w, d_alpha, d_x, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (w->prec == GBRI_F64) return psi_apply(w, static_cast<const double*>(d_alpha), static_cast<double*>(d_x), s);
+  return psi_apply(w, static_cast<const float*>(d_alpha), static_cast<float*>(d_x), s);
 }
 
-int32_t gbri_psi_adjoint(gbri_wavelet* w, const float* d_x, float* d_alpha, void* stream) {
+int32_t gbri_psi_adjoint(gbri_wavelet* w, const void* d_x, void* d_alpha, void* stream) {
   GBRI_CHECK(w && d_alpha && d_x, GBRI_EINVAL, "null argument");
-  DualEpi e{0, 0.f, 0.f, 0.f, 0.f};
-  return psi_adjoint_apply(w, d_x, d_alpha, e, (cudaStream_t)stream);
+  DualEpi e{0, 0.0, 0.0, 0.0, 0.0};
+  cudaStream_t s = (cudaStream_t)stream;
+  if (w->prec == GBRI_F64)
+    return psi_adjoint_apply(w, static_cast<const double*>(d_x), static_cast<double*>(d_alpha), e, s);
+  return psi_adjoint_apply(w, static_cast<const float*>(d_x), static_cast<float*>(d_alpha), e, s);
 }
 
 }  // extern "C"

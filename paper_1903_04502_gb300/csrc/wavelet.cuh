@@ -11,10 +11,11 @@ namespace gbri {
 constexpr int kMaxTaps = 20;   // db10
 constexpr int kMaxBases = 16;
 
-// Filter bank of the non-Dirac bases, passed to the kernels by value.
+// Filter bank of the non-Dirac bases in real type R, passed to the kernels by value.
+template <class R>
 struct Filters {
-  float h[kMaxBases][kMaxTaps];
-  float g[kMaxBases][kMaxTaps];
+  R h[kMaxBases][kMaxTaps];
+  R g[kMaxBases][kMaxTaps];
   int len[kMaxBases];
   int aidx[kMaxBases];  // position of the basis in the coefficient stack
 };
@@ -22,9 +23,10 @@ struct Filters {
 // How the analysis writes a final coefficient v (already scaled by 1/sqrt(n_w)):
 //   mode 0: out[q] = v
 //   mode 1: out[q] = clip(ca * out[q] + cb * v, [-lim, lim]) * ce   (dual updates of PD / DualFB)
+// (constants in FP64; the kernels round them once to their real type)
 struct DualEpi {
   int mode;
-  float ca, cb, lim, ce;
+  double ca, cb, lim, ce;
 };
 
 // Daubechies low-pass filter dbN (2N taps, minimum phase, sum = sqrt 2) by
@@ -36,16 +38,20 @@ std::vector<double> daubechies_lowpass(int N);
 struct gbri_wavelet {
   int n = 0, levels = 0, nw = 0, nb = 0;  // nb = number of non-Dirac bases
   int dirac_idx = -1;
-  float scale = 1.f;                       // 1 / sqrt(n_w)
+  int prec = 0;                            // GBRI_F32 or GBRI_F64: element type of every buffer
+  double scale = 1.0;                      // 1 / sqrt(n_w)
   std::vector<int> orders;
-  gbri::Filters F;
-  float* tmp = nullptr;  // [nb][n][n]
-  float* ll = nullptr;   // [nb][n][n] LL carry (analysis) / reconstruction (synthesis)
+  gbri::Filters<float> F;                  // FP32 path
+  gbri::Filters<double> Fd;                // FP64 path
+  void* tmp = nullptr;  // R [nb][n][n]
+  void* ll = nullptr;   // R [nb][n][n] LL carry (analysis) / reconstruction (synthesis)
 };
 
 namespace gbri {
 // Psi^dagger x with the epilogue applied to every final coefficient of the stack `out` [n_w][n][n].
-int32_t psi_adjoint_apply(gbri_wavelet* w, const float* x, float* out, DualEpi epi, cudaStream_t s);
+template <class R>
+int32_t psi_adjoint_apply(gbri_wavelet* w, const R* x, R* out, DualEpi epi, cudaStream_t s);
 // x = Psi alpha (overwrites x).
-int32_t psi_apply(gbri_wavelet* w, const float* alpha, float* x, cudaStream_t s);
+template <class R>
+int32_t psi_apply(gbri_wavelet* w, const R* alpha, R* x, cudaStream_t s);
 }  // namespace gbri
