@@ -33,7 +33,7 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernels at the 1024^2 / M = 1e7 workload; set to None
 # whenever a kernel changes after its capture.
-KERNEL_TRAFFIC = {"degrid": 343.66e6, "grid": 232.99e6}
+KERNEL_TRAFFIC = {"degrid": 335.63e6, "grid": 218.04e6}
 
 
 def parse():
@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=10.0, help="Poisson job arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window of the serving leg (0: skip)")
+    ap.add_argument("--batch-problems", type=int, default=64,
+                    help="independent problems of the batching leg (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=20, help="timed iterations of the batching leg")
     ap.add_argument("--fp64-steps", type=int, default=50,
                     help="timed iterations of the plain FP64 path (0: skip the precision leg)")
     ap.add_argument("--quick", action="store_true",
@@ -266,6 +269,103 @@ def serving_leg(args, dev, seed=1000):
             "budget_gb": 150, "jobs_mix": "n in {256,512,1024}, M log-uniform [1e5, 2e6], J in {4,6}"}
 
 
+def device_coverage(M, gen, dev, outlier_frac=0.2):
+    """uv coverage drawn on the device with the distribution of synth.uv_coverage: isotropic
+    Gaussian (sigma = pi / 3 per axis) truncated to |u|, |v| <= pi by rejection, a fraction
+    uniform in the disk of radius pi, weights uniform in [0.5, 1]; float32 [M, 4]."""
+    import torch
+    n_out = int(round(outlier_frac * M))
+    n_g = M - n_out
+    parts = []
+    got = 0
+    while got < n_g:
+        c = torch.randn((int((n_g - got) * 1.1) + 1024, 2), dtype=torch.float64, device=dev, generator=gen)
+        c = c * (np.pi / 3.0)
+        c = c[(c.abs() <= np.pi).all(dim=1)][: n_g - got]
+        parts.append(c)
+        got += c.shape[0]
+    r = np.pi * torch.sqrt(torch.rand(n_out, dtype=torch.float64, device=dev, generator=gen))
+    th = 2 * np.pi * torch.rand(n_out, dtype=torch.float64, device=dev, generator=gen)
+    parts.append(torch.stack([r * torch.cos(th), r * torch.sin(th)], dim=1))
+    uv = torch.cat(parts)[torch.randperm(M, device=dev, generator=gen)]
+    out = torch.zeros((M, 4), dtype=torch.float32, device=dev)
+    out[:, :2] = uv.to(torch.float32).clamp(-np.float32(np.pi), np.float32(np.pi))
+    out[:, 3] = 0.5 + 0.5 * torch.rand(M, dtype=torch.float32, device=dev, generator=gen)
+    return out
+
+
+def batch_leg(args, dev, seed=5000):
+    """Many independent problems at once: image side uniform in {256, 512, 1024, 2048}, M
+    log-uniform in [1e5, 5e7], J in {4, 6}, SARA Dirac + db1..db8 over 4 levels, FP32 with
+    FP64 norms, autotuned plans.  Times the batch (one CUDA-graph launch per iteration whose
+    branches are every problem's iteration) against the same problems stepped one after the
+    other (one graph launch per problem and iteration)."""
+    import torch
+    import paper_1903_04502_gb300 as g
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    objs, Ms, tune = [], [], {}
+    t_setup = time.perf_counter()
+    for i in range(args.batch_problems):
+        n = int(rng.choice([256, 512, 1024, 2048]))
+        M = int(np.exp(rng.uniform(np.log(1e5), np.log(5e7))))
+        J = int(rng.choice([4, 6]))
+        uvw = device_coverage(M, gen, dev)
+        plan = g.Plan(uvw, n, J=J, autotune=True)
+        del uvw
+        run, dg, gr = plan.launch_config()
+        key = "n%d_J%d" % (n, J)
+        tune.setdefault(key, []).append([M, run, dg, gr])
+        x = torch.from_numpy(synth.sky(n, 10, 4, seed=seed + i).astype(np.float32)).to(dev)
+        y0 = g.phi(plan, x)
+        sigma = 10 ** (-30 / 20) * float(torch.linalg.vector_norm(y0.to(torch.complex128))) / np.sqrt(M)
+        y = y0 + sigma * torch.randn(M, dtype=torch.complex64, device=dev, generator=gen)
+        del y0, x
+        opn, _ = g.op_norm(plan, 20, 1e-4, seed=i)
+        wav = g.Wavelet(n, 4, tuple(range(9)))
+        s = g.Solver(plan, wav, y, eps=sigma * np.sqrt(M + 2 * np.sqrt(M)), op_norm_sq=opn)
+        del y
+        objs.append((plan, wav, s))
+        Ms.append(M)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    stream = torch.cuda.current_stream()
+    batch = g.Batch()
+    for _, _, s in objs:
+        batch.add(s)
+    batch.step(3)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    batch.step(args.batch_steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(b) * 1e-3
+    for _, _, s in objs:
+        s.step(3)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _, _, s in objs:
+        s.step(args.batch_steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_seq = a.elapsed_time(b) * 1e-3
+    batch.close()
+    for plan, wav, s in objs:
+        s.close()
+        wav.close()
+        plan.close()
+    vis = float(sum(Ms)) * args.batch_steps
+    its = len(Ms) * args.batch_steps
+    return {"problems": len(Ms), "total_visibilities": int(sum(Ms)), "steps": args.batch_steps,
+            "batch_vis_per_s": vis / t_batch, "batch_iterations_per_s": its / t_batch,
+            "one_by_one_vis_per_s": vis / t_seq, "one_by_one_iterations_per_s": its / t_seq,
+            "speedup": t_seq / t_batch, "setup_s": t_setup,
+            "autotune": {k: v for k, v in sorted(tune.items())},
+            "mix": "n in {256,512,1024,2048}, M log-uniform [1e5, 5e7], J in {4,6}, uv drawn on the device"}
+
+
 def precision_leg(args, g, cfg, uvw_dev, y, eps, opn, gamma, ms_mixed, stream):
     """The plain FP64 path on the same workload: ms per primal-dual iteration (graph replays,
     CUDA events) and, after the workload's iteration count from x = 0 on both paths, the
@@ -457,6 +557,9 @@ def run_gbri(args):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(cfg, x_true, uvw, args.cpu_sample)
+    batching = None
+    if args.batch_problems > 0 and ws == 1:
+        batching = batch_leg(args, dev)
     serving = None
     if args.serve_seconds > 0 and ws == 1:
         solver.close()
@@ -472,7 +575,8 @@ def run_gbri(args):
                    % (ws_bytes / 1e9), "plan_s": t_plan, "op_norm_sq": opn, "gamma": gamma},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "profiled_region": {"steps": k_prof, "ms_per_step": ms_prof, "launch": "kernel by kernel with events"},
-        "clocks": clk, "kernels": kern, "operators": ops, "precision": precision, "serving": serving,
+        "clocks": clk, "kernels": kern, "operators": ops, "precision": precision, "batching": batching,
+        "serving": serving,
         "impl": "gbri",
     }
     print(json.dumps(line))

@@ -70,8 +70,9 @@ typedef struct {
   double kb_beta;            /* Kaiser-Bessel shape; <= 0 selects 2.34 * J */
   int64_t M;                 /* number of visibilities, >= 0 */
   int32_t precision;         /* GBRI_F32 or GBRI_F64: tables, grids and data in float or double */
-  int32_t vis_per_run;       /* visibilities of one grid cell a thread takes at once: 1..4; 0 selects 4 */
-  int32_t autotune;          /* 1: time the run lengths 1, 2, 4 and the resident blocks per SM of the
+  int32_t vis_per_run;       /* longest run of one grid cell's visibilities a gridding thread sums in
+                                registers before one shared-memory update: 1..1024; 0 selects 64 */
+  int32_t autotune;          /* 1: time the run lengths 8, 16, 64 and the resident blocks per SM of the
                                 visibility kernels at plan creation and keep the fastest (cached per
                                 problem shape for the process); 0: vis_per_run and the occupancy limit */
   int32_t reserved;          /* must be 0 */

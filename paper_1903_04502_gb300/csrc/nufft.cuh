@@ -6,13 +6,15 @@
 //                      fixed-point coordinates (cell-in-tile * S + fraction),
 //                      .y = weight bits (float).  8 bytes per visibility.
 //   perm   [M] int32   plan position -> caller's visibility index.
-//   subruns [R] int2   {first plan position, count <= kRun}: consecutive visibilities
-//                      of one cell; within a tile listed rank-major (all cells' first
-//                      sub-runs in cell order, then all second sub-runs, ...).
-//   chunks [C] int4    {tile, first sub-run, sub-runs (<= kThreads), single}; single =
-//                      the tile is one chunk.
-//   Visibilities are sorted by (tile, cell row, cell column): a cell's visibilities
-//   are contiguous.
+//   subruns [R] int2   runs {first plan position, count}: consecutive visibilities of one
+//                      cell (at most the plan's run length); within a tile listed round by
+//                      round (every cell's first run, then every second one, ...), each
+//                      round padded to a multiple of 32 with empty runs {0, 0}.
+//   gtiles [G] int4    gridding work items, one per non-empty tile: {tile, first run, runs}.
+//   chunks [C] int4    degridding work items: {tile, first plan position, visibilities
+//                      (<= kChunk), 0}: consecutive visibilities of one tile.
+//   Visibilities are stored in run order: a tile's visibilities are contiguous, and so
+//   are a run's.
 //   wtab   [S/2+1][J] R  tap weights by fractional offset f = k~ mod S: entry t is
 //                      table[|f + (J/2 - 1 - t) S|] (Sec. 8.1 zeroth-order table,
 //                      re-indexed so one visibility reads one row per axis).
@@ -33,9 +35,13 @@ namespace gbri {
 
 constexpr int kTile = 16;      // grid tile side in cells (T * S <= 65536 keeps 16-bit local coords)
 constexpr int kThreads = 256;  // threads per block of the visibility kernels
-constexpr int kRun = 4;        // consecutive visibilities a thread owns within a chunk
-constexpr int kChunk = kThreads * kRun;  // visibilities per work chunk
-constexpr int kWinPitch = 21;  // complex-element pitch of the degridding window (same bank-slot map as the gridding accumulators)
+constexpr int kRun = 4;        // visibilities a thread has in flight (degridding: per chunk; gridding: per load round)
+constexpr int kChunk = kThreads * kRun;  // visibilities per degridding chunk
+constexpr int kDefaultRun = 64;  // default longest run of one cell's visibilities a gridding thread takes
+constexpr int kMaxRun = 1024;
+// complex-element row pitch of the degridding window and of the gridding accumulators
+// (the plan's bank-slot map uses it)
+constexpr int kWinPitch = 22;
 
 // Resident blocks per SM the visibility kernels are compiled for (launch bounds) and
 // launched with at most, by element size (4: FP32 path, 8: FP64 path) and support.
@@ -51,8 +57,10 @@ struct gbri_plan {
   uint2* meta = nullptr;
   int32_t* perm = nullptr;
   int4* chunks = nullptr;
-  int2* subruns = nullptr;  // {first plan position, count <= kRun}: visibilities of one cell
+  int2* subruns = nullptr;  // runs {first plan position, count}: visibilities of one cell
+  int4* gtiles = nullptr;   // gridding work items {tile, first run, runs}
   int64_t n_chunks = 0;
+  int64_t n_gtiles = 0;
   int64_t n_tiles = 0;  // non-empty tiles
   int32_t* cell_off = nullptr;  // plan creation only
   void* wtab = nullptr;     // R
@@ -68,7 +76,7 @@ struct gbri_plan {
   int64_t device_bytes = 0;
   int64_t layout_bytes = 0;
   int degrid_blocks = 0, grid_blocks = 0;
-  int run_len = 4;  // visibilities per sub-run (<= kRun)
+  int run_len = gbri::kDefaultRun;  // longest run (visibilities of one cell a gridding thread takes)
   int autotune = 0;
   template <class T> T* as(void* q) const { return static_cast<T*>(q); }
 };
@@ -120,16 +128,18 @@ struct VisGeom {
   const uint2* __restrict__ meta;
   const int4* __restrict__ chunks;
   const int2* __restrict__ subruns;
+  const int4* __restrict__ gtiles;
   const void* __restrict__ wtab;
-  int n_chunks, K, log2S, nT;
+  int n_chunks, n_gtiles, K, log2S, nT;
 };
 
+// Degridding shared memory: the tap table, then the tile's grid window.
 inline size_t degrid_smem(const gbri_plan* p) {
   const size_t rb = real_bytes(p->prec);
   return (size_t)table_elems(p->S, p->J) * rb + (size_t)(kTile + p->J - 1) * kWinPitch * 2 * rb;
 }
 // warp-private gridding accumulators: complex cells, row pitch kAccPitch2 (>= T + J - 1)
-constexpr int kAccPitch2 = 21;
+constexpr int kAccPitch2 = kWinPitch;
 inline size_t grid_smem(const gbri_plan* p) {
   const size_t rb = real_bytes(p->prec);
   const int P = kTile + p->J - 1;
@@ -141,8 +151,10 @@ inline VisGeom vis_geom(const gbri_plan* p) {
   g.meta = p->meta;
   g.chunks = p->chunks;
   g.subruns = p->subruns;
+  g.gtiles = p->gtiles;
   g.wtab = p->wtab;
   g.n_chunks = (int)p->n_chunks;
+  g.n_gtiles = (int)p->n_gtiles;
   g.K = p->K;
   g.log2S = p->log2S;
   g.nT = p->nT;
@@ -150,25 +162,32 @@ inline VisGeom vis_geom(const gbri_plan* p) {
 }
 
 // ---- epilogues / sources ------------------------------------------------------
-// A degridding epilogue has two phases so that its global loads can be issued
-// together with the metadata loads: Pre p = load(pos); ...; store(pos, p, v).
-// Each names its real type R (the plan's precision).
+// A degridding epilogue reads kStreams per-visibility input streams of element type
+// SElem (stream(j), indexed by plan position); pre_from(st, pos) gathers element pos
+// of every stream (issued with the metadata loads), and store(pos, pre, v) consumes
+// the degridded value.  Each names its real type R (the plan's precision).
 template <class R>
 struct EpiStorePlan {  // y[pos] = v
   using real = R;
+  using SElem = cplx<R>;
+  static constexpr int kStreams = 0;
   cplx<R>* y;
   struct Pre {};
-  __device__ __forceinline__ Pre load(int) const { return Pre{}; }
+  __device__ __forceinline__ const SElem* stream(int) const { return nullptr; }
+  __device__ __forceinline__ Pre pre_from(const SElem* const*, int) const { return Pre{}; }
   __device__ __forceinline__ void store(int pos, const Pre&, cplx<R> v) { y[pos] = v; }
   __device__ __forceinline__ void finish() {}
 };
 template <class R>
 struct EpiStoreRaw {  // y[perm[pos]] = v
   using real = R;
+  using SElem = int32_t;
+  static constexpr int kStreams = 1;
   cplx<R>* y;
   const int32_t* perm;
   struct Pre { int dst; };
-  __device__ __forceinline__ Pre load(int pos) const { return Pre{perm[pos]}; }
+  __device__ __forceinline__ const SElem* stream(int) const { return perm; }
+  __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i]}; }
   __device__ __forceinline__ void store(int, const Pre& p, cplx<R> v) { y[p.dst] = v; }
   __device__ __forceinline__ void finish() {}
 };
@@ -190,6 +209,8 @@ struct SrcRaw {
 template <class R>
 struct EpiPD1 {
   using real = R;
+  using SElem = cplx<R>;
+  static constexpr int kStreams = 2;
   cplx<R>* u;
   const cplx<R>* y;
   const double* c;
@@ -197,7 +218,8 @@ struct EpiPD1 {
   R sigma2;
   acc_t<R> acc;
   struct Pre { cplx<R> u, y; };
-  __device__ __forceinline__ Pre load(int pos) const { return Pre{u[pos], y[pos]}; }
+  __device__ __forceinline__ const SElem* stream(int j) const { return j == 0 ? u : y; }
+  __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
   __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> phi) {
     const R cc = (R)*c;  // broadcast load, cached
     const cplx<R> un = mkc<R>(fma_r(cc, p.u.x, sigma2 * (phi.x - p.y.x)), fma_r(cc, p.u.y, sigma2 * (phi.y - p.y.y)));
@@ -214,13 +236,16 @@ struct EpiPD1 {
 template <class R>
 struct EpiADMM1 {  // w = Phi x + s - y, partial ||w||^2
   using real = R;
+  using SElem = cplx<R>;
+  static constexpr int kStreams = 2;
   cplx<R>* w;
   const cplx<R>* sv;
   const cplx<R>* y;
   double* partials;
   acc_t<R> acc;
   struct Pre { cplx<R> s, y; };
-  __device__ __forceinline__ Pre load(int pos) const { return Pre{sv[pos], y[pos]}; }
+  __device__ __forceinline__ const SElem* stream(int j) const { return j == 0 ? sv : y; }
+  __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
   __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> v) {
     const cplx<R> r = mkc<R>(v.x + p.s.x - p.y.x, v.y + p.s.y - p.y.y);
     w[pos] = r;

@@ -158,8 +158,8 @@ __global__ void k_scatter(const int32_t* __restrict__ key, const uint32_t* __res
   }
 }
 
-// Move every sub-run (<= kRun visibilities of one cell) from its cell-sorted place to
-// its place in the sub-run order: one thread per sub-run.
+// Move every run (consecutive visibilities of one cell) from its cell-sorted place to
+// its place in the run order: one thread per run.
 __global__ void k_relayout(const int2* __restrict__ old_sub, const int32_t* __restrict__ new_start, int64_t n_sub,
                            const uint2* __restrict__ meta_in, const int32_t* __restrict__ perm_in,
                            uint2* __restrict__ meta_out, int32_t* __restrict__ perm_out) {
@@ -246,6 +246,7 @@ void destroy_plan(gbri_plan* p) {
   cudaFree(p->perm);
   cudaFree(p->chunks);
   cudaFree(p->subruns);
+  cudaFree(p->gtiles);
   cudaFree(p->wtab);
   cudaFree(p->corr);
   cudaFree(p->padded);
@@ -257,64 +258,80 @@ void destroy_plan(gbri_plan* p) {
   delete p;
 }
 
-// Sub-runs: at most R consecutive visibilities of one cell.  Within a tile they are
-// listed rank-major (every cell's first sub-run in cell order, then every second one,
-// ...), each round padded to a multiple of 32 slots, so the lanes of a warp take
-// sub-runs of distinct cells.  A chunk is up to kThreads sub-runs of one tile (one per
-// thread), heaviest tiles first.  The visibilities are stored in sub-run order, so a
-// chunk is one contiguous range.  (Re)builds p->meta, p->perm, p->subruns, p->chunks
-// from the cell-sorted arrays.
+// Runs: at most R consecutive visibilities of one cell.  Within a tile they are listed
+// round by round (every cell's first run, then every second one, ...; one round for
+// tiles whose cells hold at most R visibilities), each round padded to a multiple of 32
+// entries so that the lanes of a warp take runs of distinct cells.  Inside a round the
+// runs go in bands of equal load rounds ceil(length / kRun), most first, so that the 32
+// runs of a warp loop equally long; inside a band they are dealt round robin over the
+// 16 eight-byte shared-memory bank slots of their cell's first accumulator / window word
+// ((row * 21 + col) mod 16; cell order inside a slot), so that the 16 lanes of a
+// half-warp hit distinct slots while enough slots are left.  Tiles are listed heaviest first.  The visibilities are
+// stored in run order.  Work items: one gridding item per tile (its runs), and
+// degridding chunks of at most kChunk consecutive visibilities of one tile.  (Re)builds
+// p->meta, p->perm, p->subruns, p->gtiles, p->chunks from the cell-sorted arrays.
 int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector<int32_t>& hst,
                const std::vector<int32_t>& order, int R, const uint2* meta_cell, const int32_t* perm_cell,
                cudaStream_t s) {
   const int64_t M = p->M;
   constexpr int NC = kTile * kTile;
-  cudaFree(p->meta); cudaFree(p->perm); cudaFree(p->subruns); cudaFree(p->chunks);
-  p->meta = nullptr; p->perm = nullptr; p->subruns = nullptr; p->chunks = nullptr;
+  cudaFree(p->meta); cudaFree(p->perm); cudaFree(p->subruns); cudaFree(p->chunks); cudaFree(p->gtiles);
+  p->meta = nullptr; p->perm = nullptr; p->subruns = nullptr; p->chunks = nullptr; p->gtiles = nullptr;
   std::vector<int2> sub;
-  sub.reserve((size_t)(M / R + order.size() * 64 + 16));
-  std::vector<int4> ch;
-  int nsub[NC];
+  sub.reserve((size_t)(M / std::max(R, 4) + order.size() * 64 + 16));
+  std::vector<int4> ch, gt;
+  int cnt[NC], nsub[NC];
+  int64_t vis_base = 0;  // first plan position of the current tile
   for (int t : order) {
     const int64_t base = (int64_t)t * NC;
     int maxsub = 0;
     for (int c = 0; c < NC; ++c) {
-      const int cnt = hoff[base + c + 1] - hoff[base + c];
-      nsub[c] = (cnt + R - 1) / R;
+      cnt[c] = hoff[base + c + 1] - hoff[base + c];
+      nsub[c] = (cnt[c] + R - 1) / R;
       maxsub = std::max(maxsub, nsub[c]);
     }
     const int64_t first = (int64_t)sub.size();
     for (int r = 0; r < maxsub; ++r) {
-      // order inside the round: round robin over the 16 eight-byte shared-memory bank
-      // slots of the cells' first accumulator / window word, so that the 16 lanes of a
-      // half-warp hit distinct slots while enough slots are left
-      int bucket[16][NC];
-      int nb[16] = {0};
-      for (int c = 0; c < NC; ++c)
-        if (nsub[c] > r) {
-          const int slot = ((c / kTile) * kAccPitch2 + (c % kTile)) & 15;
-          bucket[slot][nb[slot]++] = c;
-        }
-      int taken[16] = {0};
-      for (bool any = true; any;) {
-        any = false;
-        for (int q = 0; q < 16; ++q)
-          if (taken[q] < nb[q]) {
-            const int c = bucket[q][taken[q]++];
-            const int st0 = hoff[base + c] + r * R;
-            sub.push_back(make_int2(st0, std::min(R, hoff[base + c + 1] - st0)));
-            any = true;
+      int len[NC];
+      int maxband = 0;
+      for (int c = 0; c < NC; ++c) {
+        len[c] = nsub[c] > r ? std::min(R, cnt[c] - r * R) : 0;
+        maxband = std::max(maxband, (len[c] + kRun - 1) / kRun);
+      }
+      // bands of equal load rounds (ceil(length / kRun)), most rounds first; inside a
+      // band, round robin over the bank slots in cell order
+      for (int band = maxband; band >= 1; --band) {
+        int bucket[16][NC];
+        int nb[16] = {0};
+        for (int c = 0; c < NC; ++c)
+          if (len[c] > 0 && (len[c] + kRun - 1) / kRun == band) {
+            const int slot = ((c / kTile) * kAccPitch2 + (c % kTile)) & 15;
+            bucket[slot][nb[slot]++] = c;
           }
+        int taken[16] = {0};
+        for (bool any = true; any;) {
+          any = false;
+          for (int q = 0; q < 16; ++q)
+            if (taken[q] < nb[q]) {
+              const int c = bucket[q][taken[q]++];
+              sub.push_back(make_int2(hoff[base + c] + r * R, len[c]));
+              any = true;
+            }
+        }
       }
       while ((sub.size() - first) % 32) sub.push_back(make_int2(0, 0));
     }
     const int64_t nt = (int64_t)sub.size() - first;
-    const int single = nt <= kThreads ? 1 : 0;
-    for (int64_t k = 0; k < nt; k += kThreads)
-      ch.push_back(make_int4(t, (int)(first + k), (int)std::min<int64_t>(kThreads, nt - k), single));
+    gt.push_back(make_int4(t, (int)first, (int)nt, 0));
+    const int64_t nv = hst[t + 1] - hst[t];
+    const int64_t nch = (nv + kChunk - 1) / kChunk;
+    for (int64_t k = 0; k < nch; ++k) {
+      const int64_t a = vis_base + k * nv / nch, b = vis_base + (k + 1) * nv / nch;
+      ch.push_back(make_int4(t, (int)a, (int)(b - a), 0));
+    }
+    vis_base += nv;
   }
-  GBRI_CHECK((int64_t)sub.size() < ((int64_t)1 << 31), GBRI_EINVAL, "too many sub-runs");
-  (void)hst;
+  GBRI_CHECK((int64_t)sub.size() < ((int64_t)1 << 31), GBRI_EINVAL, "too many runs");
   std::vector<int32_t> nstart(sub.size());
   int64_t run = 0;
   for (size_t i = 0; i < sub.size(); ++i) {
@@ -322,9 +339,11 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
     run += sub[i].y;
   }
   p->n_chunks = (int64_t)ch.size();
+  p->n_gtiles = (int64_t)gt.size();
   int32_t st = GBRI_OK;
   if ((st = dmalloc(&p->meta, (size_t)M, nullptr)) || (st = dmalloc(&p->perm, (size_t)M, nullptr)) ||
-      (st = dmalloc(&p->chunks, ch.size(), nullptr)) || (st = dmalloc(&p->subruns, sub.size(), nullptr)))
+      (st = dmalloc(&p->chunks, ch.size(), nullptr)) || (st = dmalloc(&p->subruns, sub.size(), nullptr)) ||
+      (st = dmalloc(&p->gtiles, gt.size(), nullptr)))
     return st;
   if (!sub.empty()) {
     int2* dold = nullptr;
@@ -348,8 +367,10 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
   }
   if (!ch.empty())
     GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  if (!gt.empty())
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->gtiles, gt.data(), gt.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   GBRI_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
-  p->layout_bytes = (int64_t)(sub.size() * sizeof(int2) + ch.size() * sizeof(int4));
+  p->layout_bytes = (int64_t)(sub.size() * sizeof(int2) + (ch.size() + gt.size()) * sizeof(int4));
   return GBRI_OK;
 }
 
@@ -516,7 +537,7 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
 
   auto set_blocks = [&](int bpm_dg, int bpm_gr) {
     p->degrid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * bpm_dg));
-    p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * bpm_gr));
+    p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_gtiles, (int64_t)sms * bpm_gr));
   };
   int best_run = p->run_len, best_dg = lim_dg, best_gr = lim_gr;
   const TuneKey tkey{K, p->J, S, p->prec, M, p->n_tiles};
@@ -529,7 +550,7 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int runs[3] = {1, 2, 4};
+    const int runs[3] = {8, 16, 64};
     for (int R : runs) {
       st = layout(p, hoff, hst, order, R, meta_cell, perm_cell, s);
       if (st != GBRI_OK) break;
@@ -616,9 +637,9 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* 
   p->beta = d->kb_beta > 0 ? d->kb_beta : 2.34 * d->J;
   p->M = d->M;
   p->prec = d->precision;
-  GBRI_CHECK(d->vis_per_run >= 0 && d->vis_per_run <= kRun, GBRI_EINVAL, "vis_per_run must be in [0, 4]");
+  GBRI_CHECK(d->vis_per_run >= 0 && d->vis_per_run <= kMaxRun, GBRI_EINVAL, "vis_per_run must be in [0, 1024]");
   GBRI_CHECK(d->autotune == 0 || d->autotune == 1, GBRI_EINVAL, "autotune must be 0 or 1");
-  p->run_len = d->vis_per_run ? d->vis_per_run : kRun;
+  p->run_len = d->vis_per_run ? d->vis_per_run : kDefaultRun;
   p->autotune = d->autotune;
   const int32_t st = build_plan(p, d_uvw, (cudaStream_t)stream);
   if (st != GBRI_OK) {

@@ -10,20 +10,22 @@
 
 namespace gbri {
 
-// Degridding (G then W, Sec. 2).  A block takes one chunk (one contiguous range of
-// at most kThreads * kRun visibilities of one 16 x 16 tile), copies the tile's
-// (T + J - 1)^2 grid window into shared memory when the tile changes, and gives one
-// thread per visibility with kRun visibilities in flight per thread (coalesced
-// metadata and epilogue streams):
+// Degridding (G then W, Sec. 2).  Persistent blocks stride over the chunks (one
+// contiguous range of at most kChunk = kThreads * kRun visibilities of one 16 x 16
+// tile).  At the start of a chunk every thread issues the loads of its kRun
+// visibilities (metadata and the epilogue's inputs, coalesced) and only then, when the
+// tile changes, the block reloads the tile's (T + J - 1)^2 grid window into shared
+// memory, so that the two latencies overlap.  One thread per visibility:
 //   v = w * sum_{t'} wy[t'] sum_t wx[t] win[cy + t'][cx + t]
-// with the two J-tap weight rows from the shared-memory table.  The visibilities of
-// a sub-run share a cell, so neighbouring lanes often read the same window words.
-// `Epi` consumes (plan position, v).  Persistent blocks stride over the chunks.
+// with the two J-tap weight rows from the shared-memory table.  A cell's visibilities
+// are consecutive, so neighbouring lanes often read the same window words.
+// `Epi` consumes (plan position, v).
 template <int J, class Epi>
 __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi::real), J))
     k_degrid(VisGeom geo, const cplx<typename Epi::real>* __restrict__ grid, Epi epi) {
   using R = typename Epi::real;
   using C = cplx<R>;
+  using E = typename Epi::SElem;
   extern __shared__ float4 smem_dg[];
   constexpr int P = kTile + J - 1;
   R* sw = reinterpret_cast<R*>(smem_dg);
@@ -31,11 +33,21 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
   C* win = reinterpret_cast<C*>(sw + table_elems(S, J));
   copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
   const int K = geo.K;
+  const E* streams[2] = {Epi::kStreams > 0 ? epi.stream(0) : nullptr, Epi::kStreams > 1 ? epi.stream(1) : nullptr};
   int cur_tile = -1;
   for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
     const int4 ch = geo.chunks[c];
-    const int2 s0 = geo.subruns[ch.y], s1 = geo.subruns[ch.y + ch.z - 1];
-    const int lo = s0.x, cnt = s1.x + s1.y - s0.x;
+    const int lo = ch.y, cnt = ch.z;
+    uint2 m[kRun];
+    typename Epi::Pre pre[kRun];
+#pragma unroll
+    for (int k = 0; k < kRun; ++k) {
+      const int i = threadIdx.x + k * kThreads;
+      if (i < cnt) {
+        m[k] = geo.meta[lo + i];
+        pre[k] = epi.pre_from(streams, lo + i);
+      }
+    }
     if (ch.x != cur_tile) {
       __syncthreads();
       const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
@@ -46,16 +58,6 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
       }
       cur_tile = ch.x;
       __syncthreads();
-    }
-    uint2 m[kRun];
-    typename Epi::Pre pre[kRun];
-#pragma unroll
-    for (int k = 0; k < kRun; ++k) {
-      const int i = threadIdx.x + k * kThreads;
-      if (i < cnt) {
-        m[k] = geo.meta[lo + i];
-        pre[k] = epi.load(lo + i);
-      }
     }
 #pragma unroll
     for (int k = 0; k < kRun; ++k) {
@@ -86,16 +88,17 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
   epi.finish();
 }
 
-// Gridding (W^T then G^T, Sec. 2).  A block takes one chunk (up to kThreads sub-run
-// slots of one tile; each round of the rank-major order starts at a warp boundary,
-// so the 32 lanes of a warp hold sub-runs of 32 distinct cells).  Thread t loads
-// its sub-run (<= kRun visibilities of one cell) at once, sums w * v * wy[t'] wx[t]
-// into a J x J register patch and adds it to its warp's private (T + J - 1)^2
-// accumulator in shared memory with plain read-modify-writes: the lanes of one
-// instruction touch distinct cells, and successive instructions of a warp are
-// ordered, so no atomics are needed.  The block then sums the warp accumulators and
-// writes the tile window to the global grid: plain stores for the cells no other
-// tile touches when the tile is a single chunk, atomics otherwise.
+// Gridding (W^T then G^T, Sec. 2).  A block takes one tile at a time (its runs, in
+// groups of kThreads; each round of runs starts at a warp boundary, so the 32 lanes of
+// a warp hold runs of 32 distinct cells).  Thread t takes one run (consecutive
+// visibilities of one cell), loads it kRun visibilities at a time, sums
+// w * v * wy[t'] wx[t] into a J x J register patch and adds the patch to its warp's
+// private (T + J - 1)^2 accumulator in shared memory with plain read-modify-writes:
+// the lanes of one instruction touch distinct cells, and successive instructions of a
+// warp are ordered, so no atomics are needed.  After the tile the block sums the
+// accumulators of the warps it used (zeroing them for the next tile) and writes the
+// tile window to the global grid: plain stores for the cells no other tile touches,
+// atomics for the border shared with the neighbouring tiles.
 // `Src` gives the visibility value at a plan position.
 template <int J, class Src>
 __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::real), J))
@@ -109,48 +112,51 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
   R* sw = reinterpret_cast<R*>(smem_gr);
   C* accs = reinterpret_cast<C*>(sw + table_elems(S, J));
   copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
+  for (int i = threadIdx.x; i < W * P * kAccPitch2; i += blockDim.x) accs[i] = mkc<R>(0, 0);
+  __syncthreads();
   C* acc = accs + (threadIdx.x >> 5) * (P * kAccPitch2);
   const int K = geo.K;
-  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
-    const int4 ch = geo.chunks[c];
-    for (int i = threadIdx.x; i < W * P * kAccPitch2; i += blockDim.x) accs[i] = mkc<R>(0, 0);
-    __syncthreads();
-    {
-      const int2 sr = ((int)threadIdx.x < ch.z) ? geo.subruns[ch.y + threadIdx.x] : make_int2(0, 0);
+  for (int it = blockIdx.x; it < geo.n_gtiles; it += gridDim.x) {
+    const int4 gt = geo.gtiles[it];
+    for (int b0 = 0; b0 < gt.z; b0 += kThreads) {
+      const int e = b0 + (int)threadIdx.x;
+      const int2 sr = (e < gt.z) ? geo.subruns[gt.y + e] : make_int2(0, 0);
       const bool active = sr.y > 0;
-      uint2 m[kRun];
-      C v[kRun];
-#pragma unroll
-      for (int k = 0; k < kRun; ++k)
-        if (k < sr.y) {
-          m[k] = geo.meta[sr.x + k];
-          v[k] = src(sr.x + k);
-        }
       C pt[J][J];
 #pragma unroll
       for (int tp = 0; tp < J; ++tp)
 #pragma unroll
         for (int t = 0; t < J; ++t) pt[tp][t] = mkc<R>(0, 0);
+      int a0 = 0;
+      for (int k0 = 0; k0 < sr.y; k0 += kRun) {
+        uint2 m[kRun];
+        C v[kRun];
 #pragma unroll
-      for (int k = 0; k < kRun; ++k) {
-        if (k >= sr.y) break;
-        R wx[J], wy[J];
-        load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
-        load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
-        const R w = (R)__uint_as_float(m[k].y);
-        const R vr = w * v[k].x, vi = w * v[k].y;
+        for (int k = 0; k < kRun; ++k)
+          if (k0 + k < sr.y) {
+            m[k] = geo.meta[sr.x + k0 + k];
+            v[k] = src(sr.x + k0 + k);
+          }
+        if (k0 == 0) a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S);
 #pragma unroll
-        for (int tp = 0; tp < J; ++tp) {
-          const R br = wy[tp] * vr, bi = wy[tp] * vi;
+        for (int k = 0; k < kRun; ++k) {
+          if (k0 + k >= sr.y) break;
+          R wx[J], wy[J];
+          load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
+          load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
+          const R w = (R)__uint_as_float(m[k].y);
+          const R vr = w * v[k].x, vi = w * v[k].y;
 #pragma unroll
-          for (int t = 0; t < J; ++t) {
-            pt[tp][t].x = fma_r(wx[t], br, pt[tp][t].x);
-            pt[tp][t].y = fma_r(wx[t], bi, pt[tp][t].y);
+          for (int tp = 0; tp < J; ++tp) {
+            const R br = wy[tp] * vr, bi = wy[tp] * vi;
+#pragma unroll
+            for (int t = 0; t < J; ++t) {
+              pt[tp][t].x = fma_r(wx[t], br, pt[tp][t].x);
+              pt[tp][t].y = fma_r(wx[t], bi, pt[tp][t].y);
+            }
           }
         }
       }
-      const int a0 = active ? ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S)
-                            : 0;
       // all 32 lanes walk the taps in lockstep: within one tap the active lanes touch
       // distinct cells, and the warp barrier orders one tap's stores before the next
       // tap's loads (a neighbour cell's patch overlaps this one)
@@ -167,22 +173,23 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
         }
     }
     __syncthreads();
-    const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
+    const int ty = gt.x / geo.nT, tx = gt.x - ty * geo.nT;
     const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
     // accumulator rows / cols [lo_x, hi_x) belong to no other tile's window
     constexpr int lo_x = J - 1, hi_x = kTile;
-    const bool single = ch.w != 0;
+    const int used = min(W, (gt.z + 31) >> 5);  // warps that held runs of this tile
     for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
       const int r = i / P, cc = i - r * P;
       R ax = 0, ay = 0;
-#pragma unroll
-      for (int wq = 0; wq < W; ++wq) {
-        const C b = accs[wq * (P * kAccPitch2) + r * kAccPitch2 + cc];
+      for (int wq = 0; wq < used; ++wq) {
+        C* q = accs + wq * (P * kAccPitch2) + r * kAccPitch2 + cc;
+        const C b = *q;
         ax += b.x;
         ay += b.y;
+        *q = mkc<R>(0, 0);
       }
       C* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
-      if (single && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) {
+      if (r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) {
         *dst = mkc<R>(ax, ay);
       } else if (ax != 0 || ay != 0) {
         if constexpr (sizeof(R) == 4) {
@@ -202,8 +209,9 @@ int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s) {
   using R = typename Epi::real;
   launch_begin(GBRI_K_DEGRID, s);
   const cplx<R>* g = p->as<cplx<R>>(p->grid);
-  if (p->J == 4) k_degrid<4, Epi><<<p->degrid_blocks, kThreads, degrid_smem(p), s>>>(vis_geom(p), g, epi);
-  else k_degrid<6, Epi><<<p->degrid_blocks, kThreads, degrid_smem(p), s>>>(vis_geom(p), g, epi);
+  const size_t sm = degrid_smem(p);
+  if (p->J == 4) k_degrid<4, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(vis_geom(p), g, epi);
+  else k_degrid<6, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(vis_geom(p), g, epi);
   return launch_end(GBRI_K_DEGRID, s);
 }
 
@@ -212,7 +220,7 @@ int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s) {
   using R = typename Src::real;
   cplx<R>* g = p->as<cplx<R>>(p->grid);
   GBRI_CHECK_CUDA(cudaMemsetAsync(g, 0, sizeof(cplx<R>) * (size_t)p->K * p->K, s));
-  if (p->n_chunks == 0) return GBRI_OK;
+  if (p->n_gtiles == 0) return GBRI_OK;
   launch_begin(GBRI_K_GRID, s);
   if (p->J == 4) k_grid<4, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(vis_geom(p), g, src);
   else k_grid<6, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(vis_geom(p), g, src);

@@ -78,15 +78,44 @@ def test_plan_order_and_permutation(g):
     assert rel(b, a) <= 1e-6
 
 
-def test_sort_is_bit_exact_tile_major(g):
-    """The plan's visibility order follows the oracle's FP64 quantisation exactly (integer work,
-    compared exactly): non-empty 16 x 16 tiles heaviest first (ties by tile index), and inside a
-    tile the sub-runs (up to 4 visibilities of one base cell) listed rank-major: every cell's
-    first sub-run, then every second one, and so on; inside a round the cells go round robin
-    over the 16 shared-memory bank slots of their first word, in cell order within a slot."""
-    n, M, K, S, T, R = 128, 30_000, 256, 4096, 16, 4
+def expected_plan_order(tile, cell, K, T, R, load=4):
+    """(tile, cell) of every plan position under the plan's layout rule: non-empty 16 x 16
+    tiles heaviest first (ties by tile index); inside a tile the runs (up to R consecutive
+    visibilities of one cell) round by round (every cell's first run, then every second
+    one, ...); inside a round in bands of equal load rounds ceil(length / 4), most first;
+    inside a band round robin over the 16 shared-memory bank slots (row * 22 + col) mod 16
+    of the cell, in cell order within a slot."""
+    counts = np.bincount(tile, minlength=(K // T) ** 2)
+    tiles = np.nonzero(counts)[0]
+    order = tiles[np.argsort(-counts[tiles], kind="stable")]
+    exp_t, exp_c = [], []
+    for t in order:
+        cc = np.bincount(cell[tile == t], minlength=T * T)
+        for r in range(int(-(-cc.max() // R))):
+            ln = {c: min(R, cc[c] - r * R) for c in range(T * T) if cc[c] > r * R}
+            bands = {c: -(-ln[c] // load) for c in ln}
+            for b in range(max(bands.values()), 0, -1):
+                buckets = [[c for c in sorted(ln) if bands[c] == b and ((c // T) * 22 + c % T) % 16 == q]
+                           for q in range(16)]
+                while any(buckets):
+                    for q in range(16):
+                        if buckets[q]:
+                            c = buckets[q].pop(0)
+                            exp_t += [t] * ln[c]
+                            exp_c += [c] * ln[c]
+    return np.array(exp_t), np.array(exp_c), len(tiles)
+
+
+@pytest.mark.parametrize("run", [0, 2])
+def test_sort_is_bit_exact_tile_major(g, run):
+    """The plan's visibility order follows the oracle's FP64 quantisation exactly (integer
+    work, compared exactly) under the layout rule of expected_plan_order; run 0 is the
+    default run length 64, run 2 splits cells into several rounds."""
+    n, M, K, S, T = 128, 30_000, 256, 4096, 16
+    R = run or 64
     _, uvw = make(n, M)
-    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, S=S)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, S=S, vis_per_run=run)
+    assert plan.launch_config()[0] == R
     perm = plan.permutation().cpu().numpy()
     assert np.array_equal(np.sort(perm), np.arange(M))
     kx = me.quantise(uvw[:, 0], K, S)
@@ -95,26 +124,10 @@ def test_sort_is_bit_exact_tile_major(g):
     cy = np.mod(np.floor_divide(ky, S), K)
     tile = (cy // T) * (K // T) + cx // T
     cell = (cy % T) * T + (cx % T)
-    counts = np.bincount(tile, minlength=(K // T) ** 2)
-    tiles = np.nonzero(counts)[0]
-    order = tiles[np.argsort(-counts[tiles], kind="stable")]
-    expect_tiles, expect_cells = [], []
-    for t in order:
-        cc = np.bincount(cell[tile == t], minlength=T * T)
-        for r in range(int(-(-cc.max() // R))):
-            # inside a round: round robin over the 16 bank slots ((row * 21 + col) mod 16)
-            buckets = [[c for c in np.nonzero(cc > r * R)[0] if ((c // T) * 21 + c % T) % 16 == q]
-                       for q in range(16)]
-            while any(buckets):
-                for q in range(16):
-                    if buckets[q]:
-                        c = buckets[q].pop(0)
-                        k = min(R, cc[c] - r * R)
-                        expect_tiles += [t] * k
-                        expect_cells += [c] * k
-    assert np.array_equal(tile[perm], np.array(expect_tiles))
-    assert np.array_equal(cell[perm], np.array(expect_cells))
-    assert plan.n_tiles == len(tiles)
+    exp_t, exp_c, n_tiles = expected_plan_order(tile, cell, K, T, R)
+    assert np.array_equal(tile[perm], exp_t)
+    assert np.array_equal(cell[perm], exp_c)
+    assert plan.n_tiles == n_tiles
 
 
 def test_adjoint_identity_on_gpu(g):
@@ -205,7 +218,7 @@ def test_autotuned_plan_matches_oracle_and_is_cached(g):
     x, uvw = make(n, M, seed=79)
     plan = g.Plan(torch.from_numpy(uvw).cuda(), n, autotune=True)
     run, dg, gr = plan.launch_config()
-    assert run in (1, 2, 4) and dg >= 1 and gr >= 1
+    assert run in (8, 16, 64) and dg >= 1 and gr >= 1
     idx = np.arange(0, M, 97)
     geo = me.Geometry(uvw[idx], n, 2, 4, 4096)
     y = g.phi(plan, torch.from_numpy(x).cuda()).cpu().numpy()
