@@ -132,3 +132,71 @@ def test_pd_and_admm_reach_the_same_constrained_solution():
         assert np.all(x >= 0)
     # the primal-dual objective is the smaller one (both are feasible)
     assert np.abs(psit(xp)).sum() <= np.abs(psit(xa)).sum() * (1 + 1e-9)
+
+
+def test_fista_identity_operator_closed_form():
+    """Phi = I, Psi = Dirac: min 1/2 ||y - x||^2 + gamma ||x||_1, x >= 0 has x = max(y - gamma, 0);
+    with Psi = Dirac one DualFB step is the exact prox."""
+    y = synth.normal(300, seed=7) + 0.3
+    ident = lambda x: x.astype(complex)
+    ident_t = lambda z: np.real(z)
+    dirac = lambda a: a[0]
+    dirac_t = lambda x: x[None]
+    for gamma, lam in ((0.2, 1.0), (0.7, 0.4)):
+        x, info = so.fista(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                           so.FISTAParams(gamma=gamma, lam=lam, max_iter=5000, rel_tol=1e-15))
+        assert np.max(np.abs(x - np.maximum(y - gamma, 0))) < 1e-10
+        assert info["iters"] < 5000
+
+
+def _tiny_unconstrained(orders, L):
+    n, M, (phi, phit, _, _), y, _ = _tiny_problem()
+    psi = lambda a: wv.psi(a, orders, L)
+    psit = lambda x: wv.psi_adjoint(x, orders, L)
+    N = n * n
+    A = np.stack([phi(e.reshape(n, n)) for e in np.eye(N)], 1)
+    P = np.stack([psit(e.reshape(n, n)).ravel() for e in np.eye(N)], 1)
+    Ar, yr = np.vstack([A.real, A.imag]), np.concatenate([y.real, y.imag])
+    K = P.shape[0]
+    G = np.block([[P, -np.eye(K)], [-P, -np.eye(K)]])
+    gamma = 0.02 * float(np.max(np.abs(psit(phit(y)))))
+
+    def obj(z):
+        r = Ar @ z[:N] - yr
+        return 0.5 * r @ r + gamma * z[N:].sum()
+
+    def jac(z):
+        return np.r_[Ar.T @ (Ar @ z[:N] - yr), gamma * np.ones(K)]
+
+    # SLSQP on the smooth form min 1/2 ||A x - y||^2 + gamma sum t, -t <= Psi^dagger x <= t, x >= 0
+    res = minimize(obj, np.zeros(N + K), jac=jac, method="SLSQP", bounds=[(0, None)] * (N + K),
+                   constraints=[{"type": "ineq", "fun": lambda z: -(G @ z), "jac": lambda z: -G}],
+                   options={"maxiter": 3000, "ftol": 1e-15})
+    opn, _ = so.power_iteration(phi, phit, (n, n))
+    return n, (phi, phit, psi, psit), y, gamma, opn, res
+
+
+def test_fista_matches_independent_unconstrained_solver():
+    """Dirac dictionary (the DualFB prox is exact in one step): FISTA's gradient steps and
+    extrapolation reach the minimiser that SLSQP finds for the smooth reformulation."""
+    n, (phi, phit, psi, psit), y, gamma, opn, res = _tiny_unconstrained((0,), 1)
+    N = n * n
+    x, info = so.fista(y, phi, phit, psi, psit,
+                       so.FISTAParams(gamma=gamma, lam=1.0 / opn, max_iter=50000, rel_tol=1e-14))
+    assert np.max(np.abs(x.ravel() - res.x[:N])) < 1e-6
+    f = so.fista_objective(x, y, phi, psit, gamma)
+    assert f == pytest.approx(res.fun, rel=1e-10)
+    assert np.all(x >= 0)
+    x10, _ = so.fista(y, phi, phit, psi, psit, so.FISTAParams(gamma=gamma, lam=1.0 / opn, max_iter=10))
+    assert so.fista_objective(x10, y, phi, psit, gamma) > f  # descends overall
+
+
+def test_fista_with_sara_dictionary_approaches_the_minimiser():
+    """Dirac + db1 + db2 over 2 levels: with an inexact DualFB prox (30 inner iterations) the
+    objective comes within 1e-5 of the SLSQP minimum."""
+    n, (phi, phit, psi, psit), y, gamma, opn, res = _tiny_unconstrained((0, 1, 2), 2)
+    x, info = so.fista(y, phi, phit, psi, psit,
+                       so.FISTAParams(gamma=gamma, lam=1.0 / opn, dualfb_iters=30, max_iter=400))
+    f = so.fista_objective(x, y, phi, psit, gamma)
+    assert f == pytest.approx(res.fun, rel=1e-5)
+    assert np.all(x >= 0)
