@@ -179,25 +179,31 @@ int32_t gbri_proj_l2ball(const void* d_z, const void* d_center, void* d_out, int
 int32_t gbri_proj_l2ball_noalloc(const float* d_z, const float* d_center, float* d_out, int64_t M, double eps,
                                  double* d_norm_out, void* stream);
 
-/* ---- solvers (Appendix A.4 Algorithm 7; Sec. 5 Algorithm 1) --------------- */
+/* ---- solvers (Appendix A.4 Algorithm 7; Sec. 5 Algorithm 1; Algorithm 4) --- */
 #define GBRI_ALGO_PD 0
 #define GBRI_ALGO_ADMM 1
+/* FISTA (Algorithm 4) on the unconstrained analysis problem (Sec. 3.1, the MAP estimate)
+ * min_x 1/2 ||y - Phi x||^2 + gamma ||Psi^dagger x||_1, x >= 0 (the paper's 1 / (2 sigma^2)
+ * data weight folded into gamma); prox of lambda * (gamma ||Psi^dagger .||_1 + iota_{R+}) by the
+ * Dual Forward-Backward function of Algorithm 1 (eta, dualfb_iters); eps is not used. */
+#define GBRI_ALGO_FISTA 2
 
 typedef struct {
-  int32_t algo;          /* GBRI_ALGO_PD or GBRI_ALGO_ADMM */
+  int32_t algo;          /* GBRI_ALGO_PD, GBRI_ALGO_ADMM or GBRI_ALGO_FISTA */
   int32_t max_iter;      /* iterations run by gbri_solve */
   double rel_tol;        /* stop when ||x+ - x|| / ||x+|| < rel_tol (Sec. 6.6); 0 = never */
-  double eps;            /* l2-ball radius epsilon (> 0) */
-  double gamma;          /* l1 weight; <= 0 selects 1e-3 max|Psi^dagger Phi^dagger y| / ||Phi||^2 */
+  double eps;            /* l2-ball radius epsilon (> 0; PD and ADMM) */
+  double gamma;          /* l1 weight; <= 0 selects 1e-3 max|Psi^dagger Phi^dagger y| / ||Phi||^2 (PD, ADMM)
+                            or 1e-3 max|Psi^dagger Phi^dagger y| (FISTA) */
   double op_norm_sq;     /* ||Phi||^2; <= 0 runs the power method (200 iterations, tol 1e-8, seed) */
   double tau;            /* PD primal step; <= 0 selects 0.49 */
   double sigma1;         /* PD step of the l1 dual; <= 0 selects 1 */
   double sigma2;         /* PD step of the l2-ball dual; <= 0 selects 1 / ||Phi||^2 */
   double theta;          /* PD extrapolation in [0, 1]; < 0 selects 1 */
-  double rho;            /* ADMM gradient step; <= 0 selects 1 / ||Phi||^2 */
+  double rho;            /* ADMM / FISTA gradient step (FISTA: lambda); <= 0 selects 1 / ||Phi||^2 */
   double varrho;         /* ADMM multiplier step; <= 0 selects 1 */
-  double eta;            /* DualFB step; <= 0 selects 1 */
-  int32_t dualfb_iters;  /* DualFB inner iterations (>= 1; 0 selects 1) */
+  double eta;            /* DualFB step (ADMM, FISTA); <= 0 selects 1 */
+  int32_t dualfb_iters;  /* DualFB inner iterations (ADMM, FISTA; >= 1; 0 selects 1) */
   int32_t check_every;   /* host reads the convergence test every k iterations (0 selects 10) */
   uint64_t seed;         /* power-method start vector seed */
 } gbri_solve_params;

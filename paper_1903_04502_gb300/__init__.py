@@ -16,7 +16,7 @@ import ctypes as C
 import torch
 
 from . import _lib
-from ._lib import (ALGO_ADMM, ALGO_PD, F32, F64, PLAN_ORDER, GbriError, SolveParams, SolveReport,  # noqa: F401
+from ._lib import (ALGO_ADMM, ALGO_FISTA, ALGO_PD, F32, F64, PLAN_ORDER, GbriError, SolveParams, SolveReport,  # noqa: F401
                    K_NAMES)
 
 __all__ = ["Plan", "Wavelet", "Solver", "Batch", "phi", "phi_adjoint", "op_norm", "psi", "psi_adjoint", "prox_l1",

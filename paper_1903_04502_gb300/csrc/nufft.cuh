@@ -259,6 +259,30 @@ struct EpiADMM1 {  // w = Phi x + s - y, partial ||w||^2
 };
 
 template <class R>
+struct EpiResid {  // r = Phi x - y, partial ||r||^2 (FISTA's gradient residual)
+  using real = R;
+  using SElem = cplx<R>;
+  static constexpr int kStreams = 1;
+  cplx<R>* r;
+  const cplx<R>* y;
+  double* partials;
+  acc_t<R> acc;
+  struct Pre { cplx<R> y; };
+  __device__ __forceinline__ const SElem* stream(int) const { return y; }
+  __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i]}; }
+  __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> v) {
+    const cplx<R> d = mkc<R>(v.x - p.y.x, v.y - p.y.y);
+    r[pos] = d;
+    acc.add(fma_r(d.x, d.x, d.y * d.y));
+  }
+  __device__ __forceinline__ void finish() {
+    __shared__ double sh[40];
+    const double v = block_sum(acc.value(), sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+};
+
+template <class R>
 struct SrcADMM2 {  // s+ = s + varrho((1 - rho_b) w - s); source q = (1 - rho_b) w - s + s+
   using real = R;
   const cplx<R>* w;

@@ -19,6 +19,11 @@
 //   xt = x - rho Re Phi^dagger (v - r + s+),  v - r + s+ = (1 - rho_b) w - s + s+
 //   DualFB(xt): zbar = P_C(xt); repeat { d = clip(eta d + Psi^dagger zbar, gamma) / eta;
 //               zbar = P_C(xt - Psi d) }; x = zbar.
+//
+// FISTA (Algorithm 4) on the unconstrained analysis problem (Sec. 3.1):
+//   r = Phi xhat - y;  z = xhat - lambda Re Phi^dagger r;  x+ = DualFB(z, lambda gamma);
+//   theta+ = (1 + sqrt(1 + 4 theta^2)) / 2;  xhat = x+ + (theta - 1) / theta+ (x+ - x).
+// theta lives on the device (graph replays need no host work).
 // All global norms are FP64 (FP32 path: per-thread compensated FP32 partials, FP64
 // block sums).  Every kernel is templated on the real type R of the plan: float for
 // the mixed-precision path, double for the plain FP64 path.
@@ -35,7 +40,7 @@
 namespace gbri {
 namespace {
 
-enum { SC_C = 0, SC_DIST = 1, SC_REL = 2, SC_XN = 3, SC_RES = 4, SC_MAX = 5, SC_N = 16 };
+enum { SC_C = 0, SC_DIST = 1, SC_REL = 2, SC_XN = 3, SC_RES = 4, SC_MAX = 5, SC_THETA = 6, SC_ALPHA = 7, SC_N = 16 };
 
 // c = 1 - min(1, eps / (||u|| / sigma2))  (PD)   or   rho_b = min(1, eps / ||w||)  (ADMM, sigma2 = 1, want_rho)
 __global__ void k_ball_scalar(const double* __restrict__ partials, int n, double eps, double sigma2, bool want_rho,
@@ -134,6 +139,40 @@ __global__ void k_admm_zbar(const R* __restrict__ xt, const R* __restrict__ psid
   }
 }
 
+// FISTA momentum: alpha = (theta - 1) / theta+, theta <- theta+ (theta starts at 1)
+__global__ void k_fista_theta(double* __restrict__ sc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double t = sc[SC_THETA];
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    sc[SC_ALPHA] = (t - 1.0) / tn;
+    sc[SC_THETA] = tn;
+  }
+}
+
+// Last DualFB step of FISTA: x+ = max(z - Psi d, 0); xhat = x+ + alpha (x+ - x); x = x+; change partials.
+template <class R>
+__global__ void k_fista_last(const R* __restrict__ z, const R* __restrict__ psid, R* __restrict__ xhat,
+                             R* __restrict__ x, int64_t N, const double* __restrict__ sc,
+                             double* __restrict__ partials) {
+  __shared__ double sh[40];
+  const R alpha = (R)sc[SC_ALPHA];
+  acc_t<R> dd, xx;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const R xn = max_r(z[i] - psid[i], (R)0);
+    const R xo = x[i];
+    xhat[i] = fma_r(alpha, xn - xo, xn);
+    x[i] = xn;
+    dd.add((xn - xo) * (xn - xo));
+    xx.add(xn * xn);
+  }
+  const double a = block_sum(dd.value(), sh);
+  const double b = block_sum(xx.value(), sh);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+}
+
 template <class R>
 __global__ void k_absmax_partials(const R* __restrict__ a, int64_t n, double* __restrict__ partials) {
   __shared__ R sh[32];
@@ -193,6 +232,7 @@ struct gbri_solver {
   int prec = 0;  // the plan's precision: element type R of every vector below
   void *yp = nullptr, *u = nullptr, *w = nullptr;                            // complex [M], plan order
   void *x = nullptr, *xhat = nullptr, *psiz = nullptr, *z1 = nullptr, *xt = nullptr;  // real images / stacks
+  void* zb = nullptr;  // FISTA: the DualFB iterate zbar (image)
   double* partials = nullptr;
   double* sc = nullptr;
   int n_partials = 0;
@@ -214,7 +254,7 @@ void free_solver(gbri_solver* s) {
   if (s->graph) cudaGraphDestroy(s->graph);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   cudaFree(s->yp); cudaFree(s->u); cudaFree(s->w);
-  cudaFree(s->x); cudaFree(s->xhat); cudaFree(s->psiz); cudaFree(s->z1); cudaFree(s->xt);
+  cudaFree(s->x); cudaFree(s->xhat); cudaFree(s->psiz); cudaFree(s->z1); cudaFree(s->xt); cudaFree(s->zb);
   cudaFree(s->partials); cudaFree(s->sc);
   delete s;
 }
@@ -291,10 +331,55 @@ int32_t admm_iteration(gbri_solver* S, cudaStream_t st) {
   return launch_end(GBRI_K_OTHER, st);
 }
 
+template <class R>
+int32_t fista_iteration(gbri_solver* S, cudaStream_t st) {
+  gbri_plan* P = S->plan;
+  gbri_wavelet* W = S->wav;
+  const auto& p = S->p;
+  const int n = P->n_side;
+  const int64_t N = (int64_t)n * n;
+  // r = Phi xhat - y (into u)
+  GBRI_TRY(launch_pad<R>(P, vec<R>(S->xhat), nullptr, st));
+  GBRI_TRY(fft_forward(P, st));
+  GBRI_TRY(launch_degrid(P, EpiResid<R>{cvec<R>(S->u), cvec<R>(S->yp), S->partials, acc_t<R>{}}, st));
+  // z = xhat - lambda Re Phi^dagger r (into xt); zbar = P_C(z) (into zb)
+  GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st));
+  GBRI_TRY(fft_inverse(P, st));
+  const int ib = std::min(img_blocks(N), S->n_partials / 2);
+  launch_begin(GBRI_K_UPDATE, st);
+  k_admm_xt<R><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->xhat),
+                                   vec<R>(S->xt), vec<R>(S->zb), n, P->K, (R)p.rho);
+  GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
+  launch_begin(GBRI_K_OTHER, st);
+  k_fista_theta<<<1, 32, 0, st>>>(S->sc);
+  GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+  // x+ = DualFB(z, lambda gamma), d warm-started in z1; the last step also extrapolates
+  const double thr = p.rho * p.gamma;
+  for (int k = 0; k < p.dualfb_iters; ++k) {
+    GBRI_TRY(psi_adjoint_apply<R>(W, vec<R>(S->zb), vec<R>(S->z1) /* d */,
+                                  DualEpi{1, p.eta, 1.0, thr, 1.0 / p.eta}, st));
+    GBRI_TRY(psi_apply<R>(W, vec<R>(S->z1), vec<R>(S->psiz), st));
+    launch_begin(GBRI_K_UPDATE, st);
+    if (k < p.dualfb_iters - 1)
+      k_admm_zbar<R><<<ib, 256, 0, st>>>(vec<R>(S->xt), vec<R>(S->psiz), vec<R>(S->zb), vec<R>(S->x), N, false,
+                                         S->partials);
+    else
+      k_fista_last<R><<<ib, 256, 0, st>>>(vec<R>(S->xt), vec<R>(S->psiz), vec<R>(S->xhat), vec<R>(S->x), N, S->sc,
+                                          S->partials);
+    GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
+  }
+  launch_begin(GBRI_K_OTHER, st);
+  k_rel_change<<<1, 256, 0, st>>>(S->partials, ib, S->sc);
+  return launch_end(GBRI_K_OTHER, st);
+}
+
 int32_t iteration(gbri_solver* S, cudaStream_t st) {
+  const int a = S->p.algo;
   if (S->prec == GBRI_F64)
-    return S->p.algo == GBRI_ALGO_PD ? pd_iteration<double>(S, st) : admm_iteration<double>(S, st);
-  return S->p.algo == GBRI_ALGO_PD ? pd_iteration<float>(S, st) : admm_iteration<float>(S, st);
+    return a == GBRI_ALGO_PD ? pd_iteration<double>(S, st)
+                             : (a == GBRI_ALGO_ADMM ? admm_iteration<double>(S, st) : fista_iteration<double>(S, st));
+  return a == GBRI_ALGO_PD ? pd_iteration<float>(S, st)
+                           : (a == GBRI_ALGO_ADMM ? admm_iteration<float>(S, st) : fista_iteration<float>(S, st));
 }
 
 // ||y - Phi x|| into sc[SC_RES] (uses the plan's visibility scratch)
@@ -410,6 +495,7 @@ int32_t create_solver(gbri_solver* S, const void* d_y, uint32_t flags, cudaStrea
   GBRI_TRY(zalloc_bytes(&S->xhat, (size_t)N * rb, st));
   GBRI_TRY(zalloc_bytes(&S->psiz, (size_t)N * rb, st));
   GBRI_TRY(zalloc_bytes(&S->xt, (size_t)N * rb, st));
+  if (p.algo == GBRI_ALGO_FISTA) GBRI_TRY(zalloc_bytes(&S->zb, (size_t)N * rb, st));
   GBRI_TRY(zalloc_bytes(&S->z1, (size_t)(N * nw) * rb, st));
   if (M > 0) {
     if (flags & GBRI_PLAN_ORDER)
@@ -419,7 +505,7 @@ int32_t create_solver(gbri_solver* S, const void* d_y, uint32_t flags, cudaStrea
   }
   // resolve defaults
   if (p.max_iter < 0) return set_error(GBRI_EINVAL, "max_iter < 0");
-  if (!(p.eps > 0)) return set_error(GBRI_EINVAL, "eps must be > 0");
+  if (p.algo != GBRI_ALGO_FISTA && !(p.eps > 0)) return set_error(GBRI_EINVAL, "eps must be > 0");
   if (p.op_norm_sq <= 0) {
     int32_t it = 0;
     GBRI_TRY(gbri_op_norm(P, 200, 1e-8, p.seed, &p.op_norm_sq, &it, st));
@@ -433,12 +519,17 @@ int32_t create_solver(gbri_solver* S, const void* d_y, uint32_t flags, cudaStrea
   if (p.eta <= 0) p.eta = 1.0;
   if (p.dualfb_iters <= 0) p.dualfb_iters = 1;
   if (p.check_every <= 0) p.check_every = 10;
-  if (p.gamma <= 0)
+  if (p.gamma <= 0) {
     GBRI_TRY(S->prec == GBRI_F64 ? default_gamma<double>(S, st, &p.gamma) : default_gamma<float>(S, st, &p.gamma));
-  // x = 0, xhat = 0, duals = 0, c = 0
+    if (p.algo == GBRI_ALGO_FISTA) p.gamma *= p.op_norm_sq;  // 1e-3 max|Psi^dagger Phi^dagger y|
+  }
+  // x = 0, xhat = 0, duals = 0, c = 0, FISTA theta = 1
   GBRI_CHECK_CUDA(cudaMemsetAsync(S->z1, 0, rb * N * nw, st));
   GBRI_CHECK_CUDA(cudaMemsetAsync(S->psiz, 0, rb * N, st));
   GBRI_CHECK_CUDA(cudaMemsetAsync(S->sc, 0, sizeof(double) * SC_N, st));
+  const double one = 1.0;
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(S->sc + SC_THETA, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+  GBRI_CHECK_CUDA(cudaStreamSynchronize(st));  // the host scalar goes out of scope
   return GBRI_OK;
 }
 
@@ -467,7 +558,8 @@ int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav
   *out = nullptr;
   GBRI_CHECK(wav->n == plan->n_side, GBRI_EINVAL, "wavelet and plan image sizes differ");
   GBRI_CHECK(wav->prec == plan->prec, GBRI_EINVAL, "wavelet and plan precisions differ");
-  GBRI_CHECK(params->algo == GBRI_ALGO_PD || params->algo == GBRI_ALGO_ADMM, GBRI_EINVAL, "unknown algo");
+  GBRI_CHECK(params->algo == GBRI_ALGO_PD || params->algo == GBRI_ALGO_ADMM || params->algo == GBRI_ALGO_FISTA,
+             GBRI_EINVAL, "unknown algo");
   gbri_solver* S = new (std::nothrow) gbri_solver();
   GBRI_CHECK(S, GBRI_ENOMEM, "host allocation");
   S->plan = plan;

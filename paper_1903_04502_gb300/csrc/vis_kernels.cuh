@@ -242,6 +242,7 @@ int32_t prepare_visibility_kernels() {
     GBRI_ATTR((k_degrid<4, EpiStoreRaw<R>>)); GBRI_ATTR((k_degrid<6, EpiStoreRaw<R>>));
     GBRI_ATTR((k_degrid<4, EpiPD1<R>>)); GBRI_ATTR((k_degrid<6, EpiPD1<R>>));
     GBRI_ATTR((k_degrid<4, EpiADMM1<R>>)); GBRI_ATTR((k_degrid<6, EpiADMM1<R>>));
+    GBRI_ATTR((k_degrid<4, EpiResid<R>>)); GBRI_ATTR((k_degrid<6, EpiResid<R>>));
     GBRI_ATTR((k_grid<4, SrcPlan<R>>)); GBRI_ATTR((k_grid<6, SrcPlan<R>>));
     GBRI_ATTR((k_grid<4, SrcRaw<R>>)); GBRI_ATTR((k_grid<6, SrcRaw<R>>));
     GBRI_ATTR((k_grid<4, SrcADMM2<R>>)); GBRI_ATTR((k_grid<6, SrcADMM2<R>>));
@@ -260,6 +261,7 @@ int32_t prepare_visibility_kernels() {
   template int32_t launch_degrid<EpiStoreRaw<R>>(gbri_plan*, EpiStoreRaw<R>, cudaStream_t);   \
   template int32_t launch_degrid<EpiPD1<R>>(gbri_plan*, EpiPD1<R>, cudaStream_t);             \
   template int32_t launch_degrid<EpiADMM1<R>>(gbri_plan*, EpiADMM1<R>, cudaStream_t);         \
+  template int32_t launch_degrid<EpiResid<R>>(gbri_plan*, EpiResid<R>, cudaStream_t);         \
   template int32_t launch_grid<SrcPlan<R>>(gbri_plan*, SrcPlan<R>, cudaStream_t);             \
   template int32_t launch_grid<SrcRaw<R>>(gbri_plan*, SrcRaw<R>, cudaStream_t);               \
   template int32_t launch_grid<SrcADMM2<R>>(gbri_plan*, SrcADMM2<R>, cudaStream_t);           \

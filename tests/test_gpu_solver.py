@@ -114,3 +114,44 @@ def test_dictionary_of_the_fp32_workload_short_run(g):
     s = g.Solver(plan, wav, torch.from_numpy(y).cuda(), eps=eps, gamma=gamma, op_norm_sq=opn)
     s.step(20)
     assert rel(s.x().cpu().numpy(), x_ref) <= 1e-4
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-4), ("f64", 1e-9)])
+def test_fista_matches_oracle(g, prec, tol):
+    """FISTA (Algorithm 4) on the unconstrained analysis problem, 128^2 sky, M = 2e4, Dirac +
+    db1..db4, 3 levels, 100 iterations with 2 DualFB inner steps: the image against the oracle
+    run with the same gamma, step and starting point."""
+    n, M, orders, L = 128, 20_000, (0, 1, 2, 3, 4), 3
+    uvw, geo, ops, y, eps = problem(n, M, orders, L)
+    yd = y.astype(np.complex128)
+    opn, _ = so.power_iteration(ops[0], ops[1], (n, n))
+    gamma = 1e-3 * float(np.max(np.abs(ops[3](ops[1](yd)))))
+    iters = 100
+    x_ref, info = so.fista(yd, *ops, so.FISTAParams(gamma=gamma, lam=1.0 / opn, dualfb_iters=2, max_iter=iters))
+    F = g.F64 if prec == "f64" else g.F32
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, precision=F)
+    wav = g.Wavelet(n, L, orders, precision=F)
+    ydev = torch.from_numpy(yd if prec == "f64" else y).cuda()
+    s = g.Solver(plan, wav, ydev, algo=g.ALGO_FISTA, gamma=gamma, op_norm_sq=opn, rho=1.0 / opn, dualfb_iters=2)
+    s.step(iters)
+    x = s.x().cpu().numpy().astype(np.float64)
+    assert rel(x, x_ref) <= tol, rel(x, x_ref)
+    r = s.report()
+    assert r["rel_change"] == pytest.approx(info["rel_change"], rel=1e-2 if prec == "f32" else 1e-6)
+    assert r["residual_norm"] == pytest.approx(info["residual_norm"], rel=1e-4 if prec == "f32" else 1e-9)
+
+
+def test_fista_default_gamma_and_solve(g):
+    n, M, orders, L = 64, 8000, (0, 1, 2), 2
+    uvw, geo, ops, y, eps = problem(n, M, orders, L, seed=13)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    wav = g.Wavelet(n, L, orders)
+    s = g.Solver(plan, wav, torch.from_numpy(y).cuda(), algo=g.ALGO_FISTA, seed=0)
+    r = s.report()
+    opn, _ = so.power_iteration(ops[0], ops[1], (n, n), seed=0)
+    gam = 1e-3 * float(np.max(np.abs(ops[3](ops[1](y.astype(np.complex128))))))
+    assert r["gamma"] == pytest.approx(gam, rel=1e-5)
+    x, rep = g.solve(plan, wav, torch.from_numpy(y).cuda(), algo=g.ALGO_FISTA, max_iter=2000, rel_tol=1e-3,
+                     check_every=20)
+    assert rep["status"] == 0 and rep["iters"] < 2000 and rep["rel_change"] < 1e-3
+    assert float(x.min()) >= 0.0
