@@ -24,6 +24,12 @@ Problem (Sec. 3.1, analysis form; Sec. 5):
   Forward-Backward function of Algorithm 1 with threshold lambda * gamma (reading
   R11: the paper's 1 / (2 sigma^2) data weight is folded into gamma).
 
+Local fidelity constraints (Sec. 6.8, local l2 balls): with ``balls`` = [(idx_j, eps_j)]
+(a partition of the visibilities) the single constraint ||y - Phi x|| <= eps becomes
+||y_j - Phi_j x|| <= eps_j for every block j, and every projection onto the l2 ball is
+the product of the per-block projections (``proj_balls``).  ``balls`` = None is the
+global ball.
+
 Convergence (Sec. 6.6): relative iterate change ||x+ - x|| / ||x+|| < delta.
 Every norm is FP64.
 """
@@ -77,6 +83,17 @@ def power_iteration(phi, phi_adj, shape, seed=0, max_iter=200, tol=1e-8, b0=None
     return val, it
 
 
+def proj_balls(z, y, eps, balls):
+    """Projection onto the global l2 ball of radius eps around y (balls None) or onto the
+    product of the local balls {||z_j - y_j|| <= eps_j} (Sec. 6.8)."""
+    if balls is None:
+        return prox.proj_l2ball(z, y, eps)[0]
+    out = np.array(z, dtype=np.complex128, copy=True)
+    for idx, e in balls:
+        out[idx] = prox.proj_l2ball(z[idx], y[idx], e)[0]
+    return out
+
+
 @dataclass
 class PDParams:
     """Primal-dual parameters (reading R8): sigma1 = 1, sigma2 = 1/||Phi||^2, tau = 0.49, theta = 1."""
@@ -89,6 +106,7 @@ class PDParams:
     sigma1: float = 1.0
     sigma2: float = 0.0  # <= 0 means 1 / op_norm_sq
     theta: float = 1.0
+    balls: object = None  # local l2 balls [(idx_j, eps_j)]; None: the global ball
 
 
 def primal_dual(y, phi, phi_adj, psi, psi_adj, p, x0=None):
@@ -107,7 +125,7 @@ def primal_dual(y, phi, phi_adj, psi, psi_adj, p, x0=None):
     for it in range(1, p.max_iter + 1):
         z1 = prox.clip_linf(z1 + p.sigma1 * psi_adj(xhat), p.gamma)
         t = z2 + sigma2 * phi(xhat)
-        proj, _ = prox.proj_l2ball(t / sigma2, y, p.eps)
+        proj = proj_balls(t / sigma2, y, p.eps, p.balls)
         z2 = t - sigma2 * proj
         x_new = prox.proj_positive(x - p.tau * (psi(z1) + np.real(phi_adj(z2))))
         xhat = x_new + p.theta * (x_new - x)
@@ -133,6 +151,7 @@ class ADMMParams:
     dualfb_iters: int = 1
     max_iter: int = 200
     rel_tol: float = 0.0
+    balls: object = None  # local l2 balls [(idx_j, eps_j)]; None: the global ball
 
 
 def admm(y, phi, phi_adj, psi, psi_adj, p, x0=None):
@@ -148,7 +167,7 @@ def admm(y, phi, phi_adj, psi, psi_adj, p, x0=None):
     it = 0
     for it in range(1, p.max_iter + 1):
         v = phi(x)
-        r, _ = prox.proj_l2ball(v + s, y, p.eps)
+        r = proj_balls(v + s, y, p.eps, p.balls)
         s = s + p.varrho * (v - r)
         xt = x - p.rho * np.real(phi_adj(v - r + s))
         zbar = prox.proj_positive(xt)

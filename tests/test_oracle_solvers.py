@@ -200,3 +200,60 @@ def test_fista_with_sara_dictionary_approaches_the_minimiser():
     f = so.fista_objective(x, y, phi, psit, gamma)
     assert f == pytest.approx(res.fun, rel=1e-5)
     assert np.all(x >= 0)
+
+
+def test_local_balls_identity_operator_closed_form_and_global_feasibility():
+    """Phi = I, Psi = Dirac, the visibilities split into blocks: the problem separates, each block
+    has the closed form max(y_j - lam_j, 0) for its own radius eps_j; the local solution also lies
+    in the global ball of radius sqrt(sum eps_j^2) (Sec. 6.8).  One block is the global ball."""
+    y = np.abs(synth.normal(240, seed=11)) + 0.1  # positive data: every block's constraint is feasible
+    idx = np.array_split(np.random.default_rng(3).permutation(240), 4)
+    eps_j = [0.5 * np.linalg.norm(y[i]) for i in idx]
+    xs = np.zeros_like(y)
+    for i, e in zip(idx, eps_j):
+        xs[i] = _closed_form(y[i], e)
+    ident = lambda x: x.astype(complex)
+    ident_t = lambda z: np.real(z)
+    dirac = lambda a: a[0]
+    dirac_t = lambda x: x[None]
+    balls = list(zip(idx, eps_j))
+    eps = float(np.sqrt(np.sum(np.square(eps_j))))
+    for gamma in (0.05, 0.5):
+        x, _ = so.primal_dual(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                              so.PDParams(gamma=gamma, op_norm_sq=1.0, eps=eps, max_iter=20000, rel_tol=1e-14,
+                                          balls=balls))
+        assert np.max(np.abs(x - xs)) < 1e-8
+        xa, _ = so.admm(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                        so.ADMMParams(gamma=gamma, eps=eps, rho=1.0, max_iter=20000, rel_tol=1e-14, balls=balls))
+        assert np.max(np.abs(xa - xs)) < 1e-8
+    assert np.linalg.norm(y - x) <= eps * (1 + 1e-9)       # inside the global ball
+    for i, e in balls:
+        assert np.linalg.norm(y[i] - x[i]) <= e * (1 + 1e-9)
+    # a single block with the whole index set is the global ball
+    xg, _ = so.primal_dual(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                           so.PDParams(gamma=0.2, op_norm_sq=1.0, eps=eps, max_iter=300))
+    x1, _ = so.primal_dual(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                           so.PDParams(gamma=0.2, op_norm_sq=1.0, eps=eps, max_iter=300,
+                                       balls=[(np.arange(240), eps)]))
+    assert np.array_equal(xg, x1)
+
+
+def test_product_of_balls_projection_is_the_blockwise_projection():
+    """proj_balls onto {||z_j - y_j|| <= eps_j}: every block is inside its ball, blocks inside
+    their ball are unchanged, and the variational inequality <z - p, q - p> <= 0 holds for
+    random feasible q (p is the nearest feasible point)."""
+    rng = np.random.default_rng(5)
+    z = synth.complex_normal(90, seed=8) * 3
+    y = synth.complex_normal(90, seed=9)
+    idx = np.array_split(rng.permutation(90), 3)
+    eps_j = [1.0, 50.0, 2.0]
+    p = so.proj_balls(z, y, None, list(zip(idx, eps_j)))
+    for i, e in zip(idx, eps_j):
+        assert np.linalg.norm(p[i] - y[i]) <= e * (1 + 1e-12)
+    assert np.array_equal(p[idx[1]], z[idx[1]])
+    for _ in range(200):
+        q = y.copy()
+        for i, e in zip(idx, eps_j):
+            d = rng.normal(size=len(i)) + 1j * rng.normal(size=len(i))
+            q[i] = y[i] + d / np.linalg.norm(d) * e * rng.uniform() ** 0.5
+        assert np.real(np.vdot(z - p, q - p)) <= 1e-9
