@@ -206,6 +206,15 @@ typedef struct {
   int32_t dualfb_iters;  /* DualFB inner iterations (ADMM, FISTA; >= 1; 0 selects 1) */
   int32_t check_every;   /* host reads the convergence test every k iterations (0 selects 10) */
   uint64_t seed;         /* power-method start vector seed */
+  int32_t n_balls;       /* PD / ADMM fidelity constraint: 0 or 1 = the global l2 ball of radius eps;
+                            2..64 = local l2 balls (Sec. 6.8): the plan order is cut at tile boundaries
+                            into n_balls consecutive ranges -- walking the non-empty tiles in plan order
+                            with cumulative visibility count C, ball j (< n_balls - 1) ends after the
+                            first tile at which C * n_balls >= (j + 1) * M (at most one ball ends per
+                            tile) -- and ball j constrains ||y_j - Phi_j x|| <= eps * sqrt(M_j / M), so
+                            that the radii add up to eps in quadrature.  EINVAL if fewer non-empty balls
+                            result. */
+  int32_t reserved;      /* must be 0 */
 } gbri_solve_params;
 
 typedef struct {

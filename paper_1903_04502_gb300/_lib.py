@@ -33,7 +33,7 @@ class SolveParams(C.Structure):
                 ("gamma", C.c_double), ("op_norm_sq", C.c_double), ("tau", C.c_double), ("sigma1", C.c_double),
                 ("sigma2", C.c_double), ("theta", C.c_double), ("rho", C.c_double), ("varrho", C.c_double),
                 ("eta", C.c_double), ("dualfb_iters", C.c_int32), ("check_every", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("n_balls", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SolveReport(C.Structure):

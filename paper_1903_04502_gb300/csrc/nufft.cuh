@@ -174,6 +174,8 @@ struct EpiStorePlan {  // y[pos] = v
   cplx<R>* y;
   struct Pre {};
   __device__ __forceinline__ const SElem* stream(int) const { return nullptr; }
+  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const*, int) const { return Pre{}; }
   __device__ __forceinline__ void store(int pos, const Pre&, cplx<R> v) { y[pos] = v; }
   __device__ __forceinline__ void finish() {}
@@ -187,22 +189,31 @@ struct EpiStoreRaw {  // y[perm[pos]] = v
   const int32_t* perm;
   struct Pre { int dst; };
   __device__ __forceinline__ const SElem* stream(int) const { return perm; }
+  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i]}; }
   __device__ __forceinline__ void store(int, const Pre& p, cplx<R> v) { y[p.dst] = v; }
   __device__ __forceinline__ void finish() {}
 };
+// A gridding source gives the value at a plan position; ctx(pos) is evaluated once per
+// tile (any position of the tile) and passed to every call of that tile.
+struct NoCtx {};
 template <class R>
 struct SrcPlan {
   using real = R;
+  using Ctx = NoCtx;
   const cplx<R>* y;
-  __device__ __forceinline__ cplx<R> operator()(int pos) const { return y[pos]; }
+  __device__ __forceinline__ Ctx ctx(int) const { return Ctx{}; }
+  __device__ __forceinline__ cplx<R> operator()(int pos, const Ctx&) const { return y[pos]; }
 };
 template <class R>
 struct SrcRaw {
   using real = R;
+  using Ctx = NoCtx;
   const cplx<R>* y;
   const int32_t* perm;
-  __device__ __forceinline__ cplx<R> operator()(int pos) const { return y[perm[pos]]; }
+  __device__ __forceinline__ Ctx ctx(int) const { return Ctx{}; }
+  __device__ __forceinline__ cplx<R> operator()(int pos, const Ctx&) const { return y[perm[pos]]; }
 };
 
 // Solver epilogues (fused dual updates; see solver.cu for the algebra).
@@ -219,6 +230,8 @@ struct EpiPD1 {
   acc_t<R> acc;
   struct Pre { cplx<R> u, y; };
   __device__ __forceinline__ const SElem* stream(int j) const { return j == 0 ? u : y; }
+  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
   __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> phi) {
     const R cc = (R)*c;  // broadcast load, cached
@@ -245,6 +258,8 @@ struct EpiADMM1 {  // w = Phi x + s - y, partial ||w||^2
   acc_t<R> acc;
   struct Pre { cplx<R> s, y; };
   __device__ __forceinline__ const SElem* stream(int j) const { return j == 0 ? sv : y; }
+  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
   __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> v) {
     const cplx<R> r = mkc<R>(v.x + p.s.x - p.y.x, v.y + p.s.y - p.y.y);
@@ -269,6 +284,8 @@ struct EpiResid {  // r = Phi x - y, partial ||r||^2 (FISTA's gradient residual)
   acc_t<R> acc;
   struct Pre { cplx<R> y; };
   __device__ __forceinline__ const SElem* stream(int) const { return y; }
+  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i]}; }
   __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> v) {
     const cplx<R> d = mkc<R>(v.x - p.y.x, v.y - p.y.y);
@@ -285,14 +302,159 @@ struct EpiResid {  // r = Phi x - y, partial ||r||^2 (FISTA's gradient residual)
 template <class R>
 struct SrcADMM2 {  // s+ = s + varrho((1 - rho_b) w - s); source q = (1 - rho_b) w - s + s+
   using real = R;
+  using Ctx = NoCtx;
   const cplx<R>* w;
   cplx<R>* sv;
   const double* rho_b;
   R varrho;
-  __device__ __forceinline__ cplx<R> operator()(int pos) const {
+  __device__ __forceinline__ Ctx ctx(int) const { return Ctx{}; }
+  __device__ __forceinline__ cplx<R> operator()(int pos, const Ctx&) const {
     const R one_m = (R)(1.0 - *rho_b);
     const cplx<R> ww = w[pos], so = sv[pos];
     const cplx<R> pw = mkc<R>(one_m * ww.x, one_m * ww.y);
+    const cplx<R> sn = mkc<R>(fma_r(varrho, pw.x - so.x, so.x), fma_r(varrho, pw.y - so.y, so.y));
+    sv[pos] = sn;
+    return mkc<R>(pw.x - so.x + sn.x, pw.y - so.y + sn.y);
+  }
+};
+
+// ---- local l2 balls (Sec. 6.8) ----------------------------------------------------
+// Ball j holds the plan positions [bstart[j], bstart[j + 1]) (whole tiles, so that a
+// degridding chunk and a gridding tile lie in one ball).
+constexpr int kMaxBalls = 64;
+__device__ __forceinline__ int ball_of(const int32_t* bstart, int nb, int pos) {
+  int lo = 0, hi = nb;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (bstart[mid] <= pos) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ double* ball_sums_smem() {
+  __shared__ double b[kMaxBalls];
+  return b;
+}
+__device__ __forceinline__ double* ball_red_smem() {
+  __shared__ double b[40];
+  return b;
+}
+
+// Per-ball sums of squares of one degridding launch: each thread accumulates into the
+// current ball (compensated FP32 / FP64); when a block's chunk enters another ball the
+// block sum goes into the block's per-ball shared sums; at the end every block writes
+// partials[j * gridDim.x + blockIdx.x] for every ball j (fixed-order reduction later).
+template <class R>
+struct BallAcc {
+  const int32_t* bstart;
+  int nb;
+  double* partials;
+  acc_t<R> acc;
+  int cur;
+  __device__ __forceinline__ void init() {
+    double* b = ball_sums_smem();
+    for (int j = threadIdx.x; j < kMaxBalls; j += blockDim.x) b[j] = 0.0;
+    acc = acc_t<R>{};
+    cur = -1;
+    __syncthreads();
+  }
+  __device__ __forceinline__ void flush() {  // block-uniform
+    if (cur < 0) return;
+    const double v = block_sum(acc.value(), ball_red_smem());
+    if (threadIdx.x == 0) ball_sums_smem()[cur] += v;
+    acc = acc_t<R>{};
+  }
+  __device__ __forceinline__ int enter(int lo) {  // block-uniform
+    const int b = ball_of(bstart, nb, lo);
+    if (b != cur) {
+      flush();
+      cur = b;
+    }
+    return b;
+  }
+  __device__ __forceinline__ void finish() {
+    flush();
+    __syncthreads();
+    const double* b = ball_sums_smem();
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) partials[(size_t)j * gridDim.x + blockIdx.x] = b[j];
+  }
+};
+
+template <class R>
+struct EpiPD1L {  // EpiPD1 with one scale c_j per ball: u <- c_j u + sigma2 (Phi xhat - y)
+  using real = R;
+  using SElem = cplx<R>;
+  static constexpr int kStreams = 2;
+  cplx<R>* u;
+  const cplx<R>* y;
+  const double* cb;
+  R sigma2;
+  BallAcc<R> ba;
+  R c;
+  struct Pre { cplx<R> u, y; };
+  __device__ __forceinline__ const SElem* stream(int j) const { return j == 0 ? u : y; }
+  __device__ __forceinline__ void init() { ba.init(); }
+  __device__ __forceinline__ void begin_chunk(int lo) { c = (R)cb[ba.enter(lo)]; }
+  __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
+  __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> phi) {
+    const cplx<R> un = mkc<R>(fma_r(c, p.u.x, sigma2 * (phi.x - p.y.x)), fma_r(c, p.u.y, sigma2 * (phi.y - p.y.y)));
+    u[pos] = un;
+    ba.acc.add(fma_r(un.x, un.x, un.y * un.y));
+  }
+  __device__ __forceinline__ void finish() { ba.finish(); }
+};
+
+template <class R>
+struct EpiADMM1L {  // EpiADMM1 with per-ball sums of ||w_j||^2
+  using real = R;
+  using SElem = cplx<R>;
+  static constexpr int kStreams = 2;
+  cplx<R>* w;
+  const cplx<R>* sv;
+  const cplx<R>* y;
+  BallAcc<R> ba;
+  struct Pre { cplx<R> s, y; };
+  __device__ __forceinline__ const SElem* stream(int j) const { return j == 0 ? sv : y; }
+  __device__ __forceinline__ void init() { ba.init(); }
+  __device__ __forceinline__ void begin_chunk(int lo) { ba.enter(lo); }
+  __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
+  __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> v) {
+    const cplx<R> r = mkc<R>(v.x + p.s.x - p.y.x, v.y + p.s.y - p.y.y);
+    w[pos] = r;
+    ba.acc.add(fma_r(r.x, r.x, r.y * r.y));
+  }
+  __device__ __forceinline__ void finish() { ba.finish(); }
+};
+
+template <class R>
+struct SrcScaledL {  // z2 = c_j u (the PD dual with local balls)
+  using real = R;
+  struct Ctx { R c; };
+  const cplx<R>* u;
+  const double* cb;
+  const int32_t* bstart;
+  int nb;
+  __device__ __forceinline__ Ctx ctx(int pos) const { return Ctx{(R)cb[ball_of(bstart, nb, pos)]}; }
+  __device__ __forceinline__ cplx<R> operator()(int pos, const Ctx& x) const {
+    const cplx<R> v = u[pos];
+    return mkc<R>(x.c * v.x, x.c * v.y);
+  }
+};
+
+template <class R>
+struct SrcADMM2L {  // SrcADMM2 with one rho_j per ball
+  using real = R;
+  struct Ctx { R one_m; };
+  const cplx<R>* w;
+  cplx<R>* sv;
+  const double* rho_b;
+  const int32_t* bstart;
+  int nb;
+  R varrho;
+  __device__ __forceinline__ Ctx ctx(int pos) const { return Ctx{(R)(1.0 - rho_b[ball_of(bstart, nb, pos)])}; }
+  __device__ __forceinline__ cplx<R> operator()(int pos, const Ctx& x) const {
+    const cplx<R> ww = w[pos], so = sv[pos];
+    const cplx<R> pw = mkc<R>(x.one_m * ww.x, x.one_m * ww.y);
     const cplx<R> sn = mkc<R>(fma_r(varrho, pw.x - so.x, so.x), fma_r(varrho, pw.y - so.y, so.y));
     sv[pos] = sn;
     return mkc<R>(pw.x - so.x + sn.x, pw.y - so.y + sn.y);

@@ -31,6 +31,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <new>
+#include <vector>
 
 #include "nufft.cuh"
 #include "prox.cuh"
@@ -40,7 +41,10 @@
 namespace gbri {
 namespace {
 
-enum { SC_C = 0, SC_DIST = 1, SC_REL = 2, SC_XN = 3, SC_RES = 4, SC_MAX = 5, SC_THETA = 6, SC_ALPHA = 7, SC_N = 16 };
+enum {
+  SC_C = 0, SC_DIST = 1, SC_REL = 2, SC_XN = 3, SC_RES = 4, SC_MAX = 5, SC_THETA = 6, SC_ALPHA = 7, SC_ONE = 8,
+  SC_N = 16
+};
 
 // c = 1 - min(1, eps / (||u|| / sigma2))  (PD)   or   rho_b = min(1, eps / ||w||)  (ADMM, sigma2 = 1, want_rho)
 __global__ void k_ball_scalar(const double* __restrict__ partials, int n, double eps, double sigma2, bool want_rho,
@@ -51,6 +55,19 @@ __global__ void k_ball_scalar(const double* __restrict__ partials, int n, double
     const double rho = dist > eps ? eps / dist : 1.0;
     sc[SC_C] = want_rho ? rho : 1.0 - rho;
     sc[SC_DIST] = dist;
+  }
+}
+
+// Local balls: block j of the grid reduces ball j's partials in a fixed order;
+// rho_j = min(1, eps_j / dist_j), dist_j = sqrt(sum) / sigma2; out[j] = rho_j or 1 - rho_j.
+__global__ void k_ball_scalar_local(const double* __restrict__ partials, int n, const double* __restrict__ eps,
+                                    double sigma2, bool want_rho, double* __restrict__ out) {
+  __shared__ double sh[40];
+  const int j = blockIdx.x;
+  const double dist = sqrt(reduce_partials(partials + (size_t)j * n, n, sh)) / sigma2;
+  if (threadIdx.x == 0) {
+    const double rho = dist > eps[j] ? eps[j] / dist : 1.0;
+    out[j] = want_rho ? rho : 1.0 - rho;
   }
 }
 
@@ -233,6 +250,11 @@ struct gbri_solver {
   void *yp = nullptr, *u = nullptr, *w = nullptr;                            // complex [M], plan order
   void *x = nullptr, *xhat = nullptr, *psiz = nullptr, *z1 = nullptr, *xt = nullptr;  // real images / stacks
   void* zb = nullptr;  // FISTA: the DualFB iterate zbar (image)
+  // local l2 balls (n_balls >= 2): plan-position starts [nb + 1], radii [nb], per-ball
+  // scalars [nb] (PD: c_j = 1 - rho_j; ADMM: rho_j), per-ball block partials [nb][degrid blocks]
+  int nb = 0;
+  int32_t* bstart = nullptr;
+  double *beps = nullptr, *bsc = nullptr, *bpart = nullptr;
   double* partials = nullptr;
   double* sc = nullptr;
   int n_partials = 0;
@@ -256,6 +278,7 @@ void free_solver(gbri_solver* s) {
   cudaFree(s->yp); cudaFree(s->u); cudaFree(s->w);
   cudaFree(s->x); cudaFree(s->xhat); cudaFree(s->psiz); cudaFree(s->z1); cudaFree(s->xt); cudaFree(s->zb);
   cudaFree(s->partials); cudaFree(s->sc);
+  cudaFree(s->bstart); cudaFree(s->beps); cudaFree(s->bsc); cudaFree(s->bpart);
   delete s;
 }
 
@@ -274,21 +297,31 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   // u <- c u + sigma2 (Phi xhat - y), ||u||^2
   GBRI_TRY(launch_pad<R>(P, vec<R>(S->xhat), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
-  EpiPD1<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->sc + SC_C, S->partials, (R)p.sigma2, acc_t<R>{}};
-  GBRI_TRY(launch_degrid(P, e1, st));
-  launch_begin(GBRI_K_OTHER, st);
-  k_ball_scalar<<<1, 256, 0, st>>>(S->partials, P->degrid_blocks, p.eps, p.sigma2, false, S->sc);
-  GBRI_TRY(launch_end(GBRI_K_OTHER, st));
-  // Phi^dagger u (scaled by c in the update)
-  GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st));
+  if (S->nb == 0) {
+    EpiPD1<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->sc + SC_C, S->partials, (R)p.sigma2, acc_t<R>{}};
+    GBRI_TRY(launch_degrid(P, e1, st));
+    launch_begin(GBRI_K_OTHER, st);
+    k_ball_scalar<<<1, 256, 0, st>>>(S->partials, P->degrid_blocks, p.eps, p.sigma2, false, S->sc);
+    GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+    // Phi^dagger u (scaled by c in the update)
+    GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st));
+  } else {  // local balls: c_j per ball, applied inside the gridding source
+    EpiPD1L<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->bsc, (R)p.sigma2,
+                  BallAcc<R>{S->bstart, S->nb, S->bpart, acc_t<R>{}, -1}, (R)0};
+    GBRI_TRY(launch_degrid(P, e1, st));
+    launch_begin(GBRI_K_OTHER, st);
+    k_ball_scalar_local<<<S->nb, 256, 0, st>>>(S->bpart, P->degrid_blocks, S->beps, p.sigma2, false, S->bsc);
+    GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+    GBRI_TRY(launch_grid(P, SrcScaledL<R>{cvec<R>(S->u), S->bsc, S->bstart, S->nb}, st));
+  }
   GBRI_TRY(fft_inverse(P, st));
   // Psi z1
   GBRI_TRY(psi_apply<R>(W, vec<R>(S->z1), vec<R>(S->psiz), st));
   const int ib = std::min(img_blocks(N), S->n_partials / 2);
   launch_begin(GBRI_K_UPDATE, st);
   k_pd_update<R><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz),
-                                     vec<R>(S->x), vec<R>(S->xhat), n, P->K, (R)p.tau, (R)p.theta, S->sc,
-                                     S->partials);
+                                     vec<R>(S->x), vec<R>(S->xhat), n, P->K, (R)p.tau, (R)p.theta,
+                                     S->nb ? S->sc + SC_ONE : S->sc + SC_C, S->partials);
   GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
   launch_begin(GBRI_K_OTHER, st);
   k_rel_change<<<1, 256, 0, st>>>(S->partials, ib, S->sc);
@@ -304,12 +337,22 @@ int32_t admm_iteration(gbri_solver* S, cudaStream_t st) {
   const int64_t N = (int64_t)n * n;
   GBRI_TRY(launch_pad<R>(P, vec<R>(S->x), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
-  EpiADMM1<R> e1{cvec<R>(S->w), cvec<R>(S->u), cvec<R>(S->yp), S->partials, acc_t<R>{}};
-  GBRI_TRY(launch_degrid(P, e1, st));
-  launch_begin(GBRI_K_OTHER, st);
-  k_ball_scalar<<<1, 256, 0, st>>>(S->partials, P->degrid_blocks, p.eps, 1.0, true, S->sc);
-  GBRI_TRY(launch_end(GBRI_K_OTHER, st));
-  GBRI_TRY(launch_grid(P, SrcADMM2<R>{cvec<R>(S->w), cvec<R>(S->u), S->sc + SC_C, (R)p.varrho}, st));
+  if (S->nb == 0) {
+    EpiADMM1<R> e1{cvec<R>(S->w), cvec<R>(S->u), cvec<R>(S->yp), S->partials, acc_t<R>{}};
+    GBRI_TRY(launch_degrid(P, e1, st));
+    launch_begin(GBRI_K_OTHER, st);
+    k_ball_scalar<<<1, 256, 0, st>>>(S->partials, P->degrid_blocks, p.eps, 1.0, true, S->sc);
+    GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+    GBRI_TRY(launch_grid(P, SrcADMM2<R>{cvec<R>(S->w), cvec<R>(S->u), S->sc + SC_C, (R)p.varrho}, st));
+  } else {  // local balls: rho_j per ball
+    EpiADMM1L<R> e1{cvec<R>(S->w), cvec<R>(S->u), cvec<R>(S->yp), BallAcc<R>{S->bstart, S->nb, S->bpart, acc_t<R>{}, -1}};
+    GBRI_TRY(launch_degrid(P, e1, st));
+    launch_begin(GBRI_K_OTHER, st);
+    k_ball_scalar_local<<<S->nb, 256, 0, st>>>(S->bpart, P->degrid_blocks, S->beps, 1.0, true, S->bsc);
+    GBRI_TRY(launch_end(GBRI_K_OTHER, st));
+    GBRI_TRY(launch_grid(P, SrcADMM2L<R>{cvec<R>(S->w), cvec<R>(S->u), S->bsc, S->bstart, S->nb, (R)p.varrho},
+                         st));
+  }
   GBRI_TRY(fft_inverse(P, st));
   const int ib = std::min(img_blocks(N), S->n_partials / 2);
   launch_begin(GBRI_K_UPDATE, st);
@@ -478,6 +521,44 @@ int32_t zalloc_bytes(void** p, size_t bytes, cudaStream_t s) {
   return GBRI_OK;
 }
 
+// Local l2 balls: cut the plan order at tile boundaries (the plan's degridding chunks are
+// tile-contiguous and ascending) into S->nb ranges; ball j < nb - 1 ends after the first
+// tile at which C * nb >= (j + 1) * M (C = cumulative count), at most one ball per tile;
+// radius eps_j = eps sqrt(M_j / M).
+int32_t setup_balls(gbri_solver* S, cudaStream_t st) {
+  gbri_plan* P = S->plan;
+  const int nb = S->nb;
+  const int64_t M = P->M;
+  std::vector<int4> ch((size_t)P->n_chunks);
+  if (!ch.empty()) {
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(ch.data(), P->chunks, ch.size() * sizeof(int4), cudaMemcpyDeviceToHost, st));
+    GBRI_CHECK_CUDA(cudaStreamSynchronize(st));
+  }
+  std::vector<int32_t> start(1, 0);
+  int64_t cum = 0;
+  for (size_t k = 0; k < ch.size(); ++k) {
+    cum += ch[k].z;
+    const bool tile_end = (k + 1 == ch.size()) || ch[k + 1].x != ch[k].x;
+    const int j = (int)start.size() - 1;
+    if (tile_end && j < nb - 1 && cum * nb >= (int64_t)(j + 1) * M) start.push_back((int32_t)cum);
+  }
+  start.push_back((int32_t)M);
+  GBRI_CHECK((int)start.size() == nb + 1, GBRI_EINVAL, "too few tiles for the requested number of l2 balls");
+  std::vector<double> eps(nb);
+  for (int j = 0; j < nb; ++j) {
+    GBRI_CHECK(start[j + 1] > start[j], GBRI_EINVAL, "empty l2 ball");
+    eps[j] = S->p.eps * std::sqrt((double)(start[j + 1] - start[j]) / (double)M);
+  }
+  GBRI_TRY(zalloc(&S->bstart, (size_t)nb + 1, st));
+  GBRI_TRY(zalloc(&S->beps, (size_t)nb, st));
+  GBRI_TRY(zalloc(&S->bsc, (size_t)nb, st));
+  GBRI_TRY(zalloc(&S->bpart, (size_t)nb * P->degrid_blocks, st));
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(S->bstart, start.data(), start.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(S->beps, eps.data(), eps.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  GBRI_CHECK_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
+  return GBRI_OK;
+}
+
 int32_t create_solver(gbri_solver* S, const void* d_y, uint32_t flags, cudaStream_t st) {
   gbri_plan* P = S->plan;
   const int64_t N = (int64_t)P->n_side * P->n_side;
@@ -505,6 +586,12 @@ int32_t create_solver(gbri_solver* S, const void* d_y, uint32_t flags, cudaStrea
   }
   // resolve defaults
   if (p.max_iter < 0) return set_error(GBRI_EINVAL, "max_iter < 0");
+  if (p.reserved != 0) return set_error(GBRI_EINVAL, "reserved must be 0");
+  if (p.n_balls < 0 || p.n_balls > kMaxBalls) return set_error(GBRI_EINVAL, "n_balls must be in [0, 64]");
+  if (p.n_balls >= 2 && p.algo != GBRI_ALGO_FISTA && M > 0) {
+    S->nb = p.n_balls;
+    GBRI_TRY(setup_balls(S, st));
+  }
   if (p.algo != GBRI_ALGO_FISTA && !(p.eps > 0)) return set_error(GBRI_EINVAL, "eps must be > 0");
   if (p.op_norm_sq <= 0) {
     int32_t it = 0;
@@ -529,6 +616,8 @@ int32_t create_solver(gbri_solver* S, const void* d_y, uint32_t flags, cudaStrea
   GBRI_CHECK_CUDA(cudaMemsetAsync(S->sc, 0, sizeof(double) * SC_N, st));
   const double one = 1.0;
   GBRI_CHECK_CUDA(cudaMemcpyAsync(S->sc + SC_THETA, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(S->sc + SC_ONE, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+  if (S->nb) GBRI_CHECK_CUDA(cudaMemsetAsync(S->bsc, 0, sizeof(double) * S->nb, st));  // c_j = 0 before the first step
   GBRI_CHECK_CUDA(cudaStreamSynchronize(st));  // the host scalar goes out of scope
   return GBRI_OK;
 }

@@ -34,10 +34,12 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
   copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
   const int K = geo.K;
   const E* streams[2] = {Epi::kStreams > 0 ? epi.stream(0) : nullptr, Epi::kStreams > 1 ? epi.stream(1) : nullptr};
+  epi.init();
   int cur_tile = -1;
   for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
     const int4 ch = geo.chunks[c];
     const int lo = ch.y, cnt = ch.z;
+    epi.begin_chunk(lo);  // block-uniform
     uint2 m[kRun];
     typename Epi::Pre pre[kRun];
 #pragma unroll
@@ -118,6 +120,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
   const int K = geo.K;
   for (int it = blockIdx.x; it < geo.n_gtiles; it += gridDim.x) {
     const int4 gt = geo.gtiles[it];
+    const typename Src::Ctx sctx = src.ctx(geo.subruns[gt.y].x);  // a tile's first run is never padding
     for (int b0 = 0; b0 < gt.z; b0 += kThreads) {
       const int e = b0 + (int)threadIdx.x;
       const int2 sr = (e < gt.z) ? geo.subruns[gt.y + e] : make_int2(0, 0);
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
         for (int k = 0; k < kRun; ++k)
           if (k0 + k < sr.y) {
             m[k] = geo.meta[sr.x + k0 + k];
-            v[k] = src(sr.x + k0 + k);
+            v[k] = src(sr.x + k0 + k, sctx);
           }
         if (k0 == 0) a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S);
 #pragma unroll
@@ -243,6 +246,10 @@ int32_t prepare_visibility_kernels() {
     GBRI_ATTR((k_degrid<4, EpiPD1<R>>)); GBRI_ATTR((k_degrid<6, EpiPD1<R>>));
     GBRI_ATTR((k_degrid<4, EpiADMM1<R>>)); GBRI_ATTR((k_degrid<6, EpiADMM1<R>>));
     GBRI_ATTR((k_degrid<4, EpiResid<R>>)); GBRI_ATTR((k_degrid<6, EpiResid<R>>));
+    GBRI_ATTR((k_degrid<4, EpiPD1L<R>>)); GBRI_ATTR((k_degrid<6, EpiPD1L<R>>));
+    GBRI_ATTR((k_degrid<4, EpiADMM1L<R>>)); GBRI_ATTR((k_degrid<6, EpiADMM1L<R>>));
+    GBRI_ATTR((k_grid<4, SrcScaledL<R>>)); GBRI_ATTR((k_grid<6, SrcScaledL<R>>));
+    GBRI_ATTR((k_grid<4, SrcADMM2L<R>>)); GBRI_ATTR((k_grid<6, SrcADMM2L<R>>));
     GBRI_ATTR((k_grid<4, SrcPlan<R>>)); GBRI_ATTR((k_grid<6, SrcPlan<R>>));
     GBRI_ATTR((k_grid<4, SrcRaw<R>>)); GBRI_ATTR((k_grid<6, SrcRaw<R>>));
     GBRI_ATTR((k_grid<4, SrcADMM2<R>>)); GBRI_ATTR((k_grid<6, SrcADMM2<R>>));
@@ -262,6 +269,10 @@ int32_t prepare_visibility_kernels() {
   template int32_t launch_degrid<EpiPD1<R>>(gbri_plan*, EpiPD1<R>, cudaStream_t);             \
   template int32_t launch_degrid<EpiADMM1<R>>(gbri_plan*, EpiADMM1<R>, cudaStream_t);         \
   template int32_t launch_degrid<EpiResid<R>>(gbri_plan*, EpiResid<R>, cudaStream_t);         \
+  template int32_t launch_degrid<EpiPD1L<R>>(gbri_plan*, EpiPD1L<R>, cudaStream_t);           \
+  template int32_t launch_degrid<EpiADMM1L<R>>(gbri_plan*, EpiADMM1L<R>, cudaStream_t);       \
+  template int32_t launch_grid<SrcScaledL<R>>(gbri_plan*, SrcScaledL<R>, cudaStream_t);       \
+  template int32_t launch_grid<SrcADMM2L<R>>(gbri_plan*, SrcADMM2L<R>, cudaStream_t);         \
   template int32_t launch_grid<SrcPlan<R>>(gbri_plan*, SrcPlan<R>, cudaStream_t);             \
   template int32_t launch_grid<SrcRaw<R>>(gbri_plan*, SrcRaw<R>, cudaStream_t);               \
   template int32_t launch_grid<SrcADMM2<R>>(gbri_plan*, SrcADMM2<R>, cudaStream_t);           \
