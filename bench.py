@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=10.0, help="Poisson job arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window of the serving leg (0: skip)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the Phi / Phi^dagger sweep over image sizes")
     ap.add_argument("--batch-problems", type=int, default=64,
                     help="independent problems of the batching leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=20, help="timed iterations of the batching leg")
@@ -291,6 +292,39 @@ def device_coverage(M, gen, dev, outlier_frac=0.2):
     out = torch.zeros((M, 4), dtype=torch.float32, device=dev)
     out[:, :2] = uv.to(torch.float32).clamp(-np.float32(np.pi), np.float32(np.pi))
     out[:, 3] = 0.5 + 0.5 * torch.rand(M, dtype=torch.float32, device=dev, generator=gen)
+    return out
+
+
+def sweep_leg(dev, seed=7000, M=5_000_000, reps=20):
+    """The shape of the paper's CPU/GPU operator benchmark: M = 5e6 visibilities, J = 4, image
+    side 256 ... 2048 (grid 512^2 ... 4096^2).  ms per application of Phi and Phi^dagger (plan
+    order, with pad / crop and the FFTs), CUDA events on the launching stream, inputs resident."""
+    import torch
+    import paper_1903_04502_gb300 as g
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    stream = torch.cuda.current_stream()
+    out = []
+    for n in (256, 512, 1024, 2048):
+        plan = g.Plan(device_coverage(M, gen, dev), n, J=4)
+        x = torch.rand((n, n), device=dev, generator=gen)
+        y = torch.empty(M, dtype=torch.complex64, device=dev)
+        xo = torch.empty_like(x)
+        for _ in range(3):
+            g.phi(plan, x, y, plan_order=True)
+            g.phi_adjoint(plan, y, xo, plan_order=True)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        for _ in range(reps):
+            g.phi(plan, x, y, plan_order=True)
+        b.record(stream)
+        for _ in range(reps):
+            g.phi_adjoint(plan, y, xo, plan_order=True)
+        c.record(stream)
+        torch.cuda.synchronize()
+        out.append({"n_side": n, "grid": 2 * n, "M": M, "phi_ms": a.elapsed_time(b) / reps,
+                    "phi_adjoint_ms": b.elapsed_time(c) / reps})
+        plan.close()
     return out
 
 
@@ -557,6 +591,9 @@ def run_gbri(args):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(cfg, x_true, uvw, args.cpu_sample)
+    sweep = None
+    if not args.no_sweep and ws == 1:
+        sweep = sweep_leg(dev)
     batching = None
     if args.batch_problems > 0 and ws == 1:
         batching = batch_leg(args, dev)
@@ -575,7 +612,8 @@ def run_gbri(args):
                    % (ws_bytes / 1e9), "plan_s": t_plan, "op_norm_sq": opn, "gamma": gamma},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "profiled_region": {"steps": k_prof, "ms_per_step": ms_prof, "launch": "kernel by kernel with events"},
-        "clocks": clk, "kernels": kern, "operators": ops, "precision": precision, "batching": batching,
+        "clocks": clk, "kernels": kern, "operators": ops, "operator_sweep": sweep, "precision": precision,
+        "batching": batching,
         "serving": serving,
         "impl": "gbri",
     }
