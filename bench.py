@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gbri", choices=["gbri", "reference"])
-    ap.add_argument("--config", default="large", choices=["large", "small"])
+    ap.add_argument("--config", default="large", choices=["large", "small", "huge"],
+                    help="huge: the precision study (4096^2, J = 6, M = 2e9), mixed vs FP64 paths")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -179,6 +180,9 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if args.config == "huge":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle is not run at the precision-study size"}))
+        return 0
     cfg, seed, x_true, uvw = workload(args.config, 0)
     steps, warm = max(1, args.steps), max(0, args.warmup)
     # each step: one oracle primal-dual iteration on the bounded sample; keep the run to minutes
@@ -270,31 +274,6 @@ def serving_leg(args, dev, seed=1000):
             "budget_gb": 150, "jobs_mix": "n in {256,512,1024}, M log-uniform [1e5, 2e6], J in {4,6}"}
 
 
-def device_coverage(M, gen, dev, outlier_frac=0.2):
-    """uv coverage drawn on the device with the distribution of synth.uv_coverage: isotropic
-    Gaussian (sigma = pi / 3 per axis) truncated to |u|, |v| <= pi by rejection, a fraction
-    uniform in the disk of radius pi, weights uniform in [0.5, 1]; float32 [M, 4]."""
-    import torch
-    n_out = int(round(outlier_frac * M))
-    n_g = M - n_out
-    parts = []
-    got = 0
-    while got < n_g:
-        c = torch.randn((int((n_g - got) * 1.1) + 1024, 2), dtype=torch.float64, device=dev, generator=gen)
-        c = c * (np.pi / 3.0)
-        c = c[(c.abs() <= np.pi).all(dim=1)][: n_g - got]
-        parts.append(c)
-        got += c.shape[0]
-    r = np.pi * torch.sqrt(torch.rand(n_out, dtype=torch.float64, device=dev, generator=gen))
-    th = 2 * np.pi * torch.rand(n_out, dtype=torch.float64, device=dev, generator=gen)
-    parts.append(torch.stack([r * torch.cos(th), r * torch.sin(th)], dim=1))
-    uv = torch.cat(parts)[torch.randperm(M, device=dev, generator=gen)]
-    out = torch.zeros((M, 4), dtype=torch.float32, device=dev)
-    out[:, :2] = uv.to(torch.float32).clamp(-np.float32(np.pi), np.float32(np.pi))
-    out[:, 3] = 0.5 + 0.5 * torch.rand(M, dtype=torch.float32, device=dev, generator=gen)
-    return out
-
-
 def sweep_leg(dev, seed=7000, M=5_000_000, reps=20):
     """The shape of the paper's CPU/GPU operator benchmark: M = 5e6 visibilities, J = 4, image
     side 256 ... 2048 (grid 512^2 ... 4096^2).  ms per application of Phi and Phi^dagger (plan
@@ -306,7 +285,7 @@ def sweep_leg(dev, seed=7000, M=5_000_000, reps=20):
     stream = torch.cuda.current_stream()
     out = []
     for n in (256, 512, 1024, 2048):
-        plan = g.Plan(device_coverage(M, gen, dev), n, J=4)
+        plan = g.Plan(synth.uv_coverage_device(M, seed + n, dev), n, J=4)
         x = torch.rand((n, n), device=dev, generator=gen)
         y = torch.empty(M, dtype=torch.complex64, device=dev)
         xo = torch.empty_like(x)
@@ -345,7 +324,7 @@ def batch_leg(args, dev, seed=5000):
         n = int(rng.choice([256, 512, 1024, 2048]))
         M = int(np.exp(rng.uniform(np.log(1e5), np.log(5e7))))
         J = int(rng.choice([4, 6]))
-        uvw = device_coverage(M, gen, dev)
+        uvw = synth.uv_coverage_device(M, seed + 100 + i, dev)
         plan = g.Plan(uvw, n, J=J, autotune=True)
         del uvw
         run, dg, gr = plan.launch_config()
@@ -448,6 +427,77 @@ def precision_leg(args, g, cfg, uvw_dev, y, eps, opn, gamma, ms_mixed, stream):
             "speedup_mixed_over_fp64": ms64 / ms_mixed, "iterations_compared": iters,
             "final_image_rel_err_mixed_vs_fp64": err, "fp64_steps": args.fp64_steps, "fp64_kernels": kern64,
             "note": "both paths from x = 0 with the same data, ||Phi||^2, gamma and eps; CUDA-graph replays"}
+
+
+def run_huge(args):
+    """Precision study at full size (4096^2 image, 8192^2 grid, J = 6, M = 2e9, uv drawn on
+    the device): primal-dual iterations of the mixed-precision path and of the plain FP64
+    path (CUDA-graph replays, CUDA events), and the relative L2 distance of the two images
+    after the same number of iterations from x = 0 with the same data and parameters."""
+    import torch
+    import paper_1903_04502_gb300 as g
+    cfg = dict(synth.CONFIGS["huge"])
+    n, M, J = cfg["n_side"], cfg["M"], cfg["J"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    iters = args.steps
+    x_true = torch.from_numpy(synth.sky(n, cfg["n_points"], cfg["n_blobs"], seed=cfg["seed"]).astype(np.float32)).to(dev)
+
+    def timed(solver, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        solver.step(k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    out = {}
+    t0 = time.perf_counter()
+    plan = g.Plan(synth.uv_coverage_device(M, cfg["seed"] + 1, dev), n, J=J, S=cfg["S"])
+    torch.cuda.synchronize()
+    out["plan_s"] = time.perf_counter() - t0
+    y = g.phi(plan, x_true)
+    sigma = 10 ** (-cfg["snr_db"] / 20) * float(torch.linalg.vector_norm(y)) / np.sqrt(M)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(cfg["seed"] + 3)
+    for a in range(0, M, 1 << 27):
+        k = min(1 << 27, M - a)
+        y[a:a + k] += sigma * torch.randn(k, dtype=torch.complex64, device=dev, generator=gen)
+    eps = sigma * np.sqrt(M + 2 * np.sqrt(M))
+    opn, _ = g.op_norm(plan, 20, 1e-4, seed=cfg["seed"])
+    wav = g.Wavelet(n, cfg["levels"], cfg["db_orders"])
+    s = g.Solver(plan, wav, y, eps=eps, op_norm_sq=opn)
+    gamma = s.report()["gamma"]
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    ms32 = timed(s, iters)
+    x32 = s.x().cpu()
+    y_host = y.cpu()
+    s.close(); wav.close(); plan.close()
+    del y
+    torch.cuda.empty_cache()
+    # plain FP64 path on the same data (the coverage is drawn again from the same seed)
+    p64 = g.Plan(synth.uv_coverage_device(M, cfg["seed"] + 1, dev), n, J=J, S=cfg["S"], precision=g.F64)
+    w64 = g.Wavelet(n, cfg["levels"], cfg["db_orders"], precision=g.F64)
+    y64 = torch.empty(M, dtype=torch.complex128, device=dev)
+    for a in range(0, M, 1 << 27):
+        y64[a:a + (1 << 27)] = y_host[a:a + (1 << 27)].to(dev).to(torch.complex128)
+    s64 = g.Solver(p64, w64, y64, eps=eps, op_norm_sq=opn, gamma=gamma)
+    del y64
+    s64.step(args.warmup)  # both paths: warmup + steps iterations from x = 0
+    ms64 = timed(s64, iters)
+    x64 = s64.x().cpu()
+    s64.close(); w64.close(); p64.close()
+    err = float(torch.linalg.vector_norm(x32.double() - x64) / torch.linalg.vector_norm(x64))
+    line = {"metric": "Phi+Phi-dagger visibilities/s per primal-dual iteration (precision study)",
+            "value": M / (ms32 * 1e-3), "unit": "vis/s", "n_gpus": 1, "steps": iters, "warmup": args.warmup,
+            "ms_per_step": ms32, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "precision study: 4096^2 sky, 8192^2 grid, J = 6, M = 2e9, uv drawn on the device",
+                       "n_side": n, "M": M, "J": J, "op_norm_sq": opn, "gamma": gamma, "plan_s": out["plan_s"]},
+            "fp64_ms_per_step": ms64, "fp64_value": M / (ms64 * 1e-3), "speedup_mixed_over_fp64": ms64 / ms32,
+            "final_image_rel_err_mixed_vs_fp64": err, "impl": "gbri"}
+    print(json.dumps(line))
+    return 0
 
 
 def run_gbri(args):
@@ -627,6 +677,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "huge":
+        return run_huge(args)
     return run_gbri(args)
 
 

@@ -95,6 +95,40 @@ def normal(n, seed=0, stream=_AUX):
     return _rng(seed, stream).normal(0.0, 1.0, size=n)
 
 
+def uv_coverage_device(M, seed, device, outlier_frac=0.2):
+    """uv coverage drawn on a torch device (for visibility counts too large for the host
+    generator), with the distribution of ``uv_coverage`` (weights "uniform"): isotropic
+    Gaussian, sigma = pi / 3 per axis, truncated to |u|, |v| <= pi by rejection; a fraction
+    uniform in the disk of radius pi; weights uniform in [0.5, 1]; float32 [M, 4] on the
+    device, w = 0.  Seeded by a torch generator on that device (its own random stream, not
+    the numpy one)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    n_out = int(round(outlier_frac * M))
+    n_g = M - n_out
+    out = torch.zeros((M, 4), dtype=torch.float32, device=device)
+    got = 0
+    while got < n_g:  # rejection in bounded batches (float64 draws, float32 storage)
+        want = min(n_g - got, 1 << 27)
+        c = torch.randn((int(want * 1.05) + 1024, 2), dtype=torch.float64, device=device, generator=gen)
+        c = c * (np.pi / 3.0)
+        c = c[(c.abs() <= np.pi).all(dim=1)][:want]
+        out[got:got + c.shape[0], :2] = c.to(torch.float32)
+        got += c.shape[0]
+    for a in range(0, n_out, 1 << 27):
+        k = min(1 << 27, n_out - a)
+        r = np.pi * torch.sqrt(torch.rand(k, dtype=torch.float64, device=device, generator=gen))
+        th = 2 * np.pi * torch.rand(k, dtype=torch.float64, device=device, generator=gen)
+        out[n_g + a:n_g + a + k, 0] = (r * torch.cos(th)).to(torch.float32)
+        out[n_g + a:n_g + a + k, 1] = (r * torch.sin(th)).to(torch.float32)
+    out[:, :2].clamp_(-np.float32(np.pi), np.float32(np.pi))
+    for a in range(0, M, 1 << 27):
+        k = min(1 << 27, M - a)
+        out[a:a + k, 3] = 0.5 + 0.5 * torch.rand(k, dtype=torch.float32, device=device, generator=gen)
+    return out
+
+
 # Workload shapes of the paper-shaped problems (sizes only).
 CONFIGS = {
     # plain method, FP64: 128^2 sky, 5 points + 3 blobs, K = 256, J = 4, S = 2^12, M = 2e4,
