@@ -228,13 +228,13 @@ struct EpiPD1 {
   double* partials;
   R sigma2;
   acc_t<R> acc;
+  R cc;  // *c rounded to R once per thread (a per-visibility conversion would run on the FP64 pipe)
   struct Pre { cplx<R> u, y; };
   __device__ __forceinline__ const SElem* stream(int j) const { return j == 0 ? u : y; }
-  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void init() { cc = (R)*c; }
   __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
   __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> phi) {
-    const R cc = (R)*c;  // broadcast load, cached
     const cplx<R> un = mkc<R>(fma_r(cc, p.u.x, sigma2 * (phi.x - p.y.x)), fma_r(cc, p.u.y, sigma2 * (phi.y - p.y.y)));
     u[pos] = un;
     acc.add(fma_r(un.x, un.x, un.y * un.y));
@@ -302,14 +302,14 @@ struct EpiResid {  // r = Phi x - y, partial ||r||^2 (FISTA's gradient residual)
 template <class R>
 struct SrcADMM2 {  // s+ = s + varrho((1 - rho_b) w - s); source q = (1 - rho_b) w - s + s+
   using real = R;
-  using Ctx = NoCtx;
+  struct Ctx { R one_m; };  // 1 - rho_b rounded once per tile
   const cplx<R>* w;
   cplx<R>* sv;
   const double* rho_b;
   R varrho;
-  __device__ __forceinline__ Ctx ctx(int) const { return Ctx{}; }
-  __device__ __forceinline__ cplx<R> operator()(int pos, const Ctx&) const {
-    const R one_m = (R)(1.0 - *rho_b);
+  __device__ __forceinline__ Ctx ctx(int) const { return Ctx{(R)(1.0 - *rho_b)}; }
+  __device__ __forceinline__ cplx<R> operator()(int pos, const Ctx& x) const {
+    const R one_m = x.one_m;
     const cplx<R> ww = w[pos], so = sv[pos];
     const cplx<R> pw = mkc<R>(one_m * ww.x, one_m * ww.y);
     const cplx<R> sn = mkc<R>(fma_r(varrho, pw.x - so.x, so.x), fma_r(varrho, pw.y - so.y, so.y));

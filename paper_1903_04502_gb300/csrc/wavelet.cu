@@ -92,14 +92,6 @@ std::vector<double> daubechies_lowpass(int N) {
 namespace {
 
 template <class R>
-struct EpiR {  // DualEpi rounded to R once per thread
-  int mode;
-  R ca, cb, lim, ce;
-  __device__ __forceinline__ explicit EpiR(const DualEpi& e)
-      : mode(e.mode), ca((R)e.ca), cb((R)e.cb), lim((R)e.lim), ce((R)e.ce) {}
-};
-
-template <class R>
 __device__ __forceinline__ void emit(R* __restrict__ out, size_t q, R v, const EpiR<R>& e) {
   if (e.mode == 0) {
     out[q] = v;
@@ -194,9 +186,8 @@ __device__ __forceinline__ void dwt_block(AnaSmem<R>& sm, const R* __restrict__ 
 template <class R>
 __global__ void __launch_bounds__(256) k_dwt_level(const R* __restrict__ in, size_t in_stride, R* __restrict__ ll,
                                                    R* __restrict__ out, int m, int n, bool last, R scale,
-                                                   const Filters<R> F, const DualEpi ep) {
+                                                   const Filters<R> F, const EpiR<R> e) {
   __shared__ AnaSmem<R> sm;
-  const EpiR<R> e(ep);
   const int j = blockIdx.z;
   const R* src = in + in_stride * j;
   R* carry = ll + (size_t)n * n * j;
@@ -320,8 +311,7 @@ __global__ void k_psi_sum(const R* __restrict__ rec, int nb, const R* __restrict
 
 // Dirac basis of the analysis: out[q] = epi(scale * x[q]).
 template <class R>
-__global__ void k_dirac(const R* __restrict__ x, R* __restrict__ out, int64_t N, R scale, const DualEpi ep) {
-  const EpiR<R> e(ep);
+__global__ void k_dirac(const R* __restrict__ x, R* __restrict__ out, int64_t N, R scale, const EpiR<R> e) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
     emit(out, (size_t)q, scale * x[q], e);
 }
@@ -350,7 +340,7 @@ int32_t psi_adjoint_apply(gbri_wavelet* w, const R* x, R* out, DualEpi epi, cuda
   const R scale = (R)w->scale;
   if (w->dirac_idx >= 0) {
     launch_begin(GBRI_K_PSI_ADJ, s);
-    k_dirac<R><<<blocks_for(N), 256, 0, s>>>(x, out + (size_t)N * w->dirac_idx, N, scale, epi);
+    k_dirac<R><<<blocks_for(N), 256, 0, s>>>(x, out + (size_t)N * w->dirac_idx, N, scale, EpiR<R>(epi));
     GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
   }
   if (w->nb == 0) return GBRI_OK;
@@ -364,7 +354,7 @@ int32_t psi_adjoint_apply(gbri_wavelet* w, const R* x, R* out, DualEpi epi, cuda
     const size_t in_stride = (lev == 0) ? 0 : (size_t)N;
     launch_begin(GBRI_K_PSI_ADJ, s);
     k_dwt_level<R><<<dim3(bq, bq, w->nb), 256, 0, s>>>(in, in_stride, carry[lev & 1], out, m, n,
-                                                       lev == w->levels - 1, scale, filters<R>(w), epi);
+                                                       lev == w->levels - 1, scale, filters<R>(w), EpiR<R>(epi));
     GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
   }
   return GBRI_OK;

@@ -29,6 +29,16 @@ struct DualEpi {
   double ca, cb, lim, ce;
 };
 
+// DualEpi rounded to the kernels' real type once, on the host (a per-thread conversion
+// from double would run on the FP64 pipe).
+template <class R>
+struct EpiR {
+  int mode;
+  R ca, cb, lim, ce;
+  __host__ __device__ explicit EpiR(const DualEpi& e)
+      : mode(e.mode), ca((R)e.ca), cb((R)e.cb), lim((R)e.lim), ce((R)e.ce) {}
+};
+
 // Daubechies low-pass filter dbN (2N taps, minimum phase, sum = sqrt 2) by
 // spectral factorisation of the Daubechies polynomial (host, long double).
 std::vector<double> daubechies_lowpass(int N);
