@@ -133,14 +133,22 @@ __device__ __forceinline__ void dwt_block(AnaSmem<R>& sm, const R* __restrict__ 
     g[i] = gf[i];
   }
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int rr = ty; rr < T; rr += 8) {
-    int gr = 2 * k0 + rr;
-    gr = gr < m ? gr : gr % m;
-    const R* row = src + (size_t)gr * n;
-    for (int cc = tx; cc < T; cc += 32) {
-      int gc = 2 * l0 + cc;
-      gc = gc < m ? gc : gc % m;
-      sm.tin[rr][cc] = row[gc];
+  if (2 * k0 + T <= m && 2 * l0 + T <= m) {  // interior window: no periodic wrap
+    const R* base = src + (size_t)(2 * k0) * n + 2 * l0;
+    for (int rr = ty; rr < T; rr += 8) {
+      const R* row = base + (size_t)rr * n;
+      for (int cc = tx; cc < T; cc += 32) sm.tin[rr][cc] = row[cc];
+    }
+  } else {
+    for (int rr = ty; rr < T; rr += 8) {
+      int gr = 2 * k0 + rr;
+      gr = gr < m ? gr : gr % m;
+      const R* row = src + (size_t)gr * n;
+      for (int cc = tx; cc < T; cc += 32) {
+        int gc = 2 * l0 + cc;
+        gc = gc < m ? gc : gc % m;
+        sm.tin[rr][cc] = row[gc];
+      }
     }
   }
   __syncthreads();
@@ -223,6 +231,18 @@ __device__ __forceinline__ void idwt_block(SynSmem<R>& sm, const R* __restrict__
   // coefficient indexes stay within [-half, 2 half) once half >= 16 and half >= L: one
   // conditional wrap instead of an integer modulo per element
   const bool small = half < 16 || half < L;
+  if (kr_lo >= 0 && kr_lo + KB <= half && kc_lo >= 0 && kc_lo + KB <= half) {
+    // interior: each quadrant's KB x KB coefficients are one rectangle, no wrap
+#pragma unroll
+    for (int qd = 0; qd < 4; ++qd) {
+      const int pr = qd >> 1, pc = qd & 1;
+      const R* base = ((pr == 0 && pc == 0) ? llsrc : coef) + (size_t)(pr * half + kr_lo) * n + pc * half + kc_lo;
+      for (int sr = ty; sr < KB; sr += 8) {
+        const R* row = base + (size_t)sr * n;
+        for (int sc = tx; sc < KB; sc += 32) sm.tc[pr * KB + sr][pc * KB + sc] = row[sc];
+      }
+    }
+  } else
   for (int sr = ty; sr < 2 * KB; sr += 8) {
     const int pr = sr >= KB ? 1 : 0;
     int kr = kr_lo + sr - pr * KB;
