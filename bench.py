@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=10.0, help="Poisson job arrivals per second")
+    ap.add_argument("--serve-rates", default="",
+                    help="comma-separated arrival rates for several serving runs (overrides --serve-rate)")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0, help="HBM admission budget of the serving leg")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window of the serving leg (0: skip)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the Phi / Phi^dagger sweep over image sizes")
     ap.add_argument("--batch-problems", type=int, default=64,
@@ -218,7 +221,7 @@ def run_reference(args):
     return 0
 
 
-def serving_leg(args, dev, seed=1000):
+def serving_leg(args, dev, seed=1000, rate=None, budget_gb=None):
     """Request loop under Poisson arrivals: jobs of mixed size (image side in {256, 512, 1024},
     M log-uniform in [1e5, 2e6], J in {4, 6}, SARA Dirac + db1..db8 over 4 levels, at most 300
     primal-dual iterations or relative change < 1e-3), 150 GB admission budget.  Reports job
@@ -227,8 +230,10 @@ def serving_leg(args, dev, seed=1000):
     import paper_1903_04502_gb300 as g
     from paper_1903_04502_gb300 import serve
     rng = np.random.default_rng(seed)
-    n_jobs = max(1, int(round(args.serve_rate * args.serve_seconds)))
-    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n_jobs))
+    rate = args.serve_rate if rate is None else rate
+    budget_gb = args.serve_budget_gb if budget_gb is None else budget_gb
+    n_jobs = max(1, int(round(rate * args.serve_seconds)))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
     jobs = []
     for i in range(n_jobs):
         n = int(rng.choice([256, 512, 1024]))
@@ -247,7 +252,7 @@ def serving_leg(args, dev, seed=1000):
                               db_orders=tuple(range(9)), levels=4, max_iter=300, rel_tol=1e-3,
                               arrival=float(arrivals[i])))
     torch.cuda.synchronize()
-    srv = serve.Server(serve.GpuEngine(dev.index or 0), hbm_budget=150e9, check_every=10)
+    srv = serve.Server(serve.GpuEngine(dev.index or 0), hbm_budget=budget_gb * 1e9, check_every=10)
     t0 = time.perf_counter()
     srv.run(jobs)
     torch.cuda.synchronize()
@@ -259,7 +264,8 @@ def serving_leg(args, dev, seed=1000):
     for j in jobs:
         plan = g.Plan(torch.from_numpy(j.uvw).to(dev), j.n_side, J=j.J)
         wav = g.Wavelet(j.n_side, j.levels, j.db_orders)
-        s = g.Solver(plan, wav, torch.from_numpy(j.y).to(dev), eps=j.eps)
+        opn, _ = g.op_norm(plan, 50, 1e-4, seed=j.job_id)  # as the request loop does
+        s = g.Solver(plan, wav, torch.from_numpy(j.y).to(dev), eps=j.eps, op_norm_sq=opn)
         s.step(j.iters)
         s.x().cpu()
         seq_vis += j.iters * j.M
@@ -267,11 +273,11 @@ def serving_leg(args, dev, seed=1000):
     torch.cuda.synchronize()
     seq = time.perf_counter() - t1
     busy = max(1e-9, max(j.done_at for j in srv.done) - min(j.admitted_at for j in srv.done))
-    return {"rate_jobs_per_s": args.serve_rate, "jobs": st["jobs"], "failed": st["failed"],
+    return {"rate_jobs_per_s": rate, "jobs": st["jobs"], "failed": st["failed"],
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_resident": st["max_resident"],
             "iterations_per_s": srv.iterations / busy, "vis_per_s": srv.vis_iterations / busy,
             "wall_s": wall, "one_at_a_time_vis_per_s": seq_vis / seq, "one_at_a_time_s": seq,
-            "budget_gb": 150, "jobs_mix": "n in {256,512,1024}, M log-uniform [1e5, 2e6], J in {4,6}"}
+            "budget_gb": budget_gb, "jobs_mix": "n in {256,512,1024}, M log-uniform [1e5, 2e6], J in {4,6}"}
 
 
 def sweep_leg(dev, seed=7000, M=5_000_000, reps=20):
@@ -650,7 +656,11 @@ def run_gbri(args):
     serving = None
     if args.serve_seconds > 0 and ws == 1:
         solver.close()
-        serving = serving_leg(args, dev)
+        if args.serve_rates:
+            serving = [serving_leg(args, dev, seed=1000 + 17 * i, rate=float(r))
+                       for i, r in enumerate(args.serve_rates.split(","))]
+        else:
+            serving = serving_leg(args, dev)
     ws_bytes = plan.device_bytes + 2 * M * 8 + cfg["n_side"] ** 2 * 4 * (len(cfg["db_orders"]) + 8)
     line = {
         "metric": "Phi+Phi-dagger visibilities/s per primal-dual iteration", "value": value, "unit": "vis/s",

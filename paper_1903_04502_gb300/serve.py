@@ -85,7 +85,12 @@ class GpuEngine:
         del uvw
         wav = g.Wavelet(job.n_side, job.levels, job.db_orders)
         y = torch.from_numpy(np.ascontiguousarray(job.y, dtype=np.complex64)).to(self.device)
-        s = g.Solver(plan, wav, y, eps=job.eps, op_norm_sq=job.op_norm_sq, gamma=job.gamma, max_iter=job.max_iter,
+        opn = job.op_norm_sq
+        if opn <= 0:
+            # step sizes need ||Phi||^2 to a few digits: the power method approaches it from below,
+            # and stopping at 1e-4 relative change keeps tau (sigma1 + sigma2 ||Phi||^2) < 1
+            opn, _ = g.op_norm(plan, 50, 1e-4, seed=job.job_id)
+        s = g.Solver(plan, wav, y, eps=job.eps, op_norm_sq=opn, gamma=job.gamma, max_iter=job.max_iter,
                      rel_tol=job.rel_tol)
         self.batch.add(s)
         self.state[job.job_id] = (plan, wav, s)
