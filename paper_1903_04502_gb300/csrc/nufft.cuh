@@ -133,10 +133,9 @@ struct VisGeom {
   int n_chunks, n_gtiles, K, log2S, nT;
 };
 
-// Degridding shared memory: the tap table, then the tile's grid window.
-inline size_t degrid_smem(const gbri_plan* p) {
+inline size_t degrid_smem(const gbri_plan* p) {  // the tap table and one window per warp
   const size_t rb = real_bytes(p->prec);
-  return (size_t)table_elems(p->S, p->J) * rb + (size_t)(kTile + p->J - 1) * kWinPitch * 2 * rb;
+  return (size_t)table_elems(p->S, p->J) * rb + (size_t)(kThreads / 32) * (kTile + p->J - 1) * kWinPitch * 2 * rb;
 }
 // warp-private gridding accumulators: complex cells, row pitch kAccPitch2 (>= T + J - 1)
 constexpr int kAccPitch2 = kWinPitch;
@@ -174,7 +173,7 @@ struct EpiStorePlan {  // y[pos] = v
   cplx<R>* y;
   struct Pre {};
   __device__ __forceinline__ const SElem* stream(int) const { return nullptr; }
-  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void init() { __syncthreads(); }
   __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const*, int) const { return Pre{}; }
   __device__ __forceinline__ void store(int pos, const Pre&, cplx<R> v) { y[pos] = v; }
@@ -189,7 +188,7 @@ struct EpiStoreRaw {  // y[perm[pos]] = v
   const int32_t* perm;
   struct Pre { int dst; };
   __device__ __forceinline__ const SElem* stream(int) const { return perm; }
-  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void init() { __syncthreads(); }
   __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i]}; }
   __device__ __forceinline__ void store(int, const Pre& p, cplx<R> v) { y[p.dst] = v; }
@@ -231,7 +230,10 @@ struct EpiPD1 {
   R cc;  // *c rounded to R once per thread (a per-visibility conversion would run on the FP64 pipe)
   struct Pre { cplx<R> u, y; };
   __device__ __forceinline__ const SElem* stream(int j) const { return j == 0 ? u : y; }
-  __device__ __forceinline__ void init() { cc = (R)*c; }
+  __device__ __forceinline__ void init() {
+    cc = (R)*c;
+    __syncthreads();
+  }
   __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
   __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> phi) {
@@ -258,7 +260,7 @@ struct EpiADMM1 {  // w = Phi x + s - y, partial ||w||^2
   acc_t<R> acc;
   struct Pre { cplx<R> s, y; };
   __device__ __forceinline__ const SElem* stream(int j) const { return j == 0 ? sv : y; }
-  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void init() { __syncthreads(); }
   __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
   __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> v) {
@@ -284,7 +286,7 @@ struct EpiResid {  // r = Phi x - y, partial ||r||^2 (FISTA's gradient residual)
   acc_t<R> acc;
   struct Pre { cplx<R> y; };
   __device__ __forceinline__ const SElem* stream(int) const { return y; }
-  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void init() { __syncthreads(); }
   __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i]}; }
   __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> v) {
@@ -341,8 +343,8 @@ __device__ __forceinline__ double* ball_red_smem() {
 }
 
 // Per-ball sums of squares of one degridding launch: each thread accumulates into the
-// current ball (compensated FP32 / FP64); when a block's chunk enters another ball the
-// block sum goes into the block's per-ball shared sums; at the end every block writes
+// current ball (compensated FP32 / FP64); when a warp's chunk enters another ball the warp
+// sum is added to the block's per-ball shared sums; at the end every block writes
 // partials[j * gridDim.x + blockIdx.x] for every ball j (fixed-order reduction later).
 template <class R>
 struct BallAcc {
@@ -351,20 +353,20 @@ struct BallAcc {
   double* partials;
   acc_t<R> acc;
   int cur;
-  __device__ __forceinline__ void init() {
+  __device__ __forceinline__ void init() {  // block-wide
     double* b = ball_sums_smem();
     for (int j = threadIdx.x; j < kMaxBalls; j += blockDim.x) b[j] = 0.0;
     acc = acc_t<R>{};
     cur = -1;
     __syncthreads();
   }
-  __device__ __forceinline__ void flush() {  // block-uniform
+  __device__ __forceinline__ void flush() {  // warp-uniform
     if (cur < 0) return;
-    const double v = block_sum(acc.value(), ball_red_smem());
-    if (threadIdx.x == 0) ball_sums_smem()[cur] += v;
+    const double v = warp_sum(acc.value());
+    if ((threadIdx.x & 31) == 0) atomicAdd(ball_sums_smem() + cur, v);
     acc = acc_t<R>{};
   }
-  __device__ __forceinline__ int enter(int lo) {  // block-uniform
+  __device__ __forceinline__ int enter(int lo) {  // warp-uniform
     const int b = ball_of(bstart, nb, lo);
     if (b != cur) {
       flush();
@@ -372,7 +374,7 @@ struct BallAcc {
     }
     return b;
   }
-  __device__ __forceinline__ void finish() {
+  __device__ __forceinline__ void finish() {  // block-wide
     flush();
     __syncthreads();
     const double* b = ball_sums_smem();

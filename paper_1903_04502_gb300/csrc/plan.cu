@@ -536,8 +536,12 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   p->fft_ok = true;
 
   auto set_blocks = [&](int bpm_dg, int bpm_gr) {
-    p->degrid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_chunks, (int64_t)sms * bpm_dg));
-    p->grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_gtiles, (int64_t)sms * bpm_gr));
+    // one degridding chunk per warp
+    p->degrid_blocks =
+        (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(p->n_chunks, kThreads / 32), (int64_t)sms * bpm_dg));
+    // one gridding work item per warp
+    p->grid_blocks =
+        (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(p->n_gtiles, kThreads / 32), (int64_t)sms * bpm_gr));
   };
   int best_run = p->run_len, best_dg = lim_dg, best_gr = lim_gr;
   const TuneKey tkey{K, p->J, S, p->prec, M, p->n_tiles};

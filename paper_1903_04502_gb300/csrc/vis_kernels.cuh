@@ -10,16 +10,16 @@
 
 namespace gbri {
 
-// Degridding (G then W, Sec. 2).  Persistent blocks stride over the chunks (one
-// contiguous range of at most kChunk = kThreads * kRun visibilities of one 16 x 16
-// tile).  At the start of a chunk every thread issues the loads of its kRun
-// visibilities (metadata and the epilogue's inputs, coalesced) and only then, when the
-// tile changes, the block reloads the tile's (T + J - 1)^2 grid window into shared
-// memory, so that the two latencies overlap.  One thread per visibility:
+// Degridding (G then W, Sec. 2).  Every warp works alone: it takes whole chunks (one
+// contiguous range of at most kChunk visibilities of one 16 x 16 tile; warps stride
+// over the chunk list) and copies the chunk's tile window ((T + J - 1)^2 grid values)
+// into its private shared-memory window when the tile changes.  The warp walks the
+// chunk 32 * kRun visibilities at a time, one per lane and kRun in flight per lane
+// (metadata and epilogue loads issued before the window reload, coalesced):
 //   v = w * sum_{t'} wy[t'] sum_t wx[t] win[cy + t'][cx + t]
-// with the two J-tap weight rows from the shared-memory table.  A cell's visibilities
-// are consecutive, so neighbouring lanes often read the same window words.
-// `Epi` consumes (plan position, v).
+// with the two J-tap weight rows from the block's shared table.  A cell's visibilities
+// are consecutive, so neighbouring lanes often read the same window words.  No block-wide
+// barrier after the table load.  `Epi` consumes (plan position, v).
 template <int J, class Epi>
 __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi::real), J))
     k_degrid(VisGeom geo, const cplx<typename Epi::real>* __restrict__ grid, Epi epi) {
@@ -28,79 +28,83 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
   using E = typename Epi::SElem;
   extern __shared__ float4 smem_dg[];
   constexpr int P = kTile + J - 1;
+  constexpr int W = kThreads / 32;
   R* sw = reinterpret_cast<R*>(smem_dg);
   const int S = 1 << geo.log2S;
-  C* win = reinterpret_cast<C*>(sw + table_elems(S, J));
+  const int lane = threadIdx.x & 31;
+  C* win = reinterpret_cast<C*>(sw + table_elems(S, J)) + (threadIdx.x >> 5) * (P * kWinPitch);
   copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
   const int K = geo.K;
   const E* streams[2] = {Epi::kStreams > 0 ? epi.stream(0) : nullptr, Epi::kStreams > 1 ? epi.stream(1) : nullptr};
-  epi.init();
+  epi.init();  // includes a block barrier: the table is in place after it
   int cur_tile = -1;
-  for (int c = blockIdx.x; c < geo.n_chunks; c += gridDim.x) {
+  for (int c = blockIdx.x * W + (threadIdx.x >> 5); c < geo.n_chunks; c += gridDim.x * W) {
     const int4 ch = geo.chunks[c];
     const int lo = ch.y, cnt = ch.z;
-    epi.begin_chunk(lo);  // block-uniform
-    uint2 m[kRun];
-    typename Epi::Pre pre[kRun];
+    epi.begin_chunk(lo);  // warp-uniform
+    for (int b0 = 0; b0 < cnt; b0 += 32 * kRun) {
+      uint2 m[kRun];
+      typename Epi::Pre pre[kRun];
 #pragma unroll
-    for (int k = 0; k < kRun; ++k) {
-      const int i = threadIdx.x + k * kThreads;
-      if (i < cnt) {
-        m[k] = geo.meta[lo + i];
-        pre[k] = epi.pre_from(streams, lo + i);
-      }
-    }
-    if (ch.x != cur_tile) {
-      __syncthreads();
-      const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
-      const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
-      for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
-        const int r = i / P, cc = i - r * P;
-        win[r * kWinPitch + cc] = __ldg(grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K));
-      }
-      cur_tile = ch.x;
-      __syncthreads();
-    }
-#pragma unroll
-    for (int k = 0; k < kRun; ++k) {
-      const int i = threadIdx.x + k * kThreads;
-      if (i >= cnt) break;
-      const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
-      R wx[J], wy[J];
-      load_taps<J>(sw, lx & (S - 1), S, wx);
-      load_taps<J>(sw, ly & (S - 1), S, wy);
-      const C* base = win + (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
-      R ar = 0, ai = 0;
-#pragma unroll
-      for (int tp = 0; tp < J; ++tp) {
-        R rr = 0, ri = 0;
-#pragma unroll
-        for (int t = 0; t < J; ++t) {
-          const C gv = base[tp * kWinPitch + t];
-          rr = fma_r(wx[t], gv.x, rr);
-          ri = fma_r(wx[t], gv.y, ri);
+      for (int k = 0; k < kRun; ++k) {
+        const int i = b0 + lane + 32 * k;
+        if (i < cnt) {
+          m[k] = geo.meta[lo + i];
+          pre[k] = epi.pre_from(streams, lo + i);
         }
-        ar = fma_r(wy[tp], rr, ar);
-        ai = fma_r(wy[tp], ri, ai);
       }
-      const R w = (R)__uint_as_float(m[k].y);
-      epi.store(lo + i, pre[k], mkc<R>(w * ar, w * ai));
+      if (ch.x != cur_tile) {  // warp-uniform
+        __syncwarp();
+        const int ty = ch.x / geo.nT, tx = ch.x - ty * geo.nT;
+        const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
+        for (int i = lane; i < P * P; i += 32) {
+          const int r = i / P, cc = i - r * P;
+          win[r * kWinPitch + cc] = __ldg(grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K));
+        }
+        cur_tile = ch.x;
+        __syncwarp();
+      }
+#pragma unroll
+      for (int k = 0; k < kRun; ++k) {
+        const int i = b0 + lane + 32 * k;
+        if (i >= cnt) break;
+        const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
+        R wx[J], wy[J];
+        load_taps<J>(sw, lx & (S - 1), S, wx);
+        load_taps<J>(sw, ly & (S - 1), S, wy);
+        const C* base = win + (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
+        R ar = 0, ai = 0;
+#pragma unroll
+        for (int tp = 0; tp < J; ++tp) {
+          R rr = 0, ri = 0;
+#pragma unroll
+          for (int t = 0; t < J; ++t) {
+            const C gv = base[tp * kWinPitch + t];
+            rr = fma_r(wx[t], gv.x, rr);
+            ri = fma_r(wx[t], gv.y, ri);
+          }
+          ar = fma_r(wy[tp], rr, ar);
+          ai = fma_r(wy[tp], ri, ai);
+        }
+        const R w = (R)__uint_as_float(m[k].y);
+        epi.store(lo + i, pre[k], mkc<R>(w * ar, w * ai));
+      }
     }
   }
   epi.finish();
 }
 
-// Gridding (W^T then G^T, Sec. 2).  A block takes one tile at a time (its runs, in
-// groups of kThreads; each round of runs starts at a warp boundary, so the 32 lanes of
-// a warp hold runs of 32 distinct cells).  Thread t takes one run (consecutive
-// visibilities of one cell), loads it kRun visibilities at a time, sums
-// w * v * wy[t'] wx[t] into a J x J register patch and adds the patch to its warp's
-// private (T + J - 1)^2 accumulator in shared memory with plain read-modify-writes:
-// the lanes of one instruction touch distinct cells, and successive instructions of a
-// warp are ordered, so no atomics are needed.  After the tile the block sums the
-// accumulators of the warps it used (zeroing them for the next tile) and writes the
-// tile window to the global grid: plain stores for the cells no other tile touches,
-// atomics for the border shared with the neighbouring tiles.
+// Gridding (W^T then G^T, Sec. 2).  Every warp works alone: it takes whole tiles
+// (heaviest first, warps striding over the tile list) and walks the tile's runs 32 at a
+// time (each round of runs starts at a warp boundary, so the 32 lanes hold runs of 32
+// distinct cells).  A lane takes one run (consecutive visibilities of one cell), loads it
+// kRun visibilities at a time, sums w * v * wy[t'] wx[t] into a J x J register patch and
+// adds the patch to the warp's private (T + J - 1)^2 accumulator in shared memory with
+// plain read-modify-writes: the lanes of one instruction touch distinct cells and the
+// warp's instructions are ordered, so no atomics are needed.  After the tile the warp
+// writes its accumulator to the global grid (zeroing it for the next tile): plain stores
+// for the cells no other tile touches, atomics for the border shared with the
+// neighbouring tiles.  No block-wide barrier after the table load.
 // `Src` gives the visibility value at a plan position.
 template <int J, class Src>
 __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::real), J))
@@ -116,14 +120,16 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
   copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
   for (int i = threadIdx.x; i < W * P * kAccPitch2; i += blockDim.x) accs[i] = mkc<R>(0, 0);
   __syncthreads();
+  const int lane = threadIdx.x & 31;
   C* acc = accs + (threadIdx.x >> 5) * (P * kAccPitch2);
   const int K = geo.K;
-  for (int it = blockIdx.x; it < geo.n_gtiles; it += gridDim.x) {
+  // accumulator rows / cols [lo_x, hi_x) belong to no other tile's window
+  constexpr int lo_x = J - 1, hi_x = kTile;
+  for (int it = blockIdx.x * W + (threadIdx.x >> 5); it < geo.n_gtiles; it += gridDim.x * W) {
     const int4 gt = geo.gtiles[it];
     const typename Src::Ctx sctx = src.ctx(geo.subruns[gt.y].x);  // a tile's first run is never padding
-    for (int b0 = 0; b0 < gt.z; b0 += kThreads) {
-      const int e = b0 + (int)threadIdx.x;
-      const int2 sr = (e < gt.z) ? geo.subruns[gt.y + e] : make_int2(0, 0);
+    for (int b0 = 0; b0 < gt.z; b0 += 32) {
+      const int2 sr = geo.subruns[gt.y + b0 + lane];  // gt.z is a multiple of 32
       const bool active = sr.y > 0;
       C pt[J][J];
 #pragma unroll
@@ -175,35 +181,26 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
           __syncwarp();
         }
     }
-    __syncthreads();
     const int ty = gt.x / geo.nT, tx = gt.x - ty * geo.nT;
     const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
-    // accumulator rows / cols [lo_x, hi_x) belong to no other tile's window
-    constexpr int lo_x = J - 1, hi_x = kTile;
-    const int used = min(W, (gt.z + 31) >> 5);  // warps that held runs of this tile
-    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+    for (int i = lane; i < P * P; i += 32) {
       const int r = i / P, cc = i - r * P;
-      R ax = 0, ay = 0;
-      for (int wq = 0; wq < used; ++wq) {
-        C* q = accs + wq * (P * kAccPitch2) + r * kAccPitch2 + cc;
-        const C b = *q;
-        ax += b.x;
-        ay += b.y;
-        *q = mkc<R>(0, 0);
-      }
+      C* q = acc + r * kAccPitch2 + cc;
+      const C a = *q;
+      *q = mkc<R>(0, 0);
       C* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
       if (r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) {
-        *dst = mkc<R>(ax, ay);
-      } else if (ax != 0 || ay != 0) {
+        *dst = a;
+      } else if (a.x != 0 || a.y != 0) {
         if constexpr (sizeof(R) == 4) {
-          atomicAdd(dst, mkc<R>(ax, ay));  // one vector atomic
+          atomicAdd(dst, a);  // one vector atomic
         } else {
-          atomicAdd(&dst->x, ax);
-          atomicAdd(&dst->y, ay);
+          atomicAdd(&dst->x, a.x);
+          atomicAdd(&dst->y, a.y);
         }
       }
     }
-    __syncthreads();
+    __syncwarp();  // the zeroed accumulator is visible to every lane before the next tile
   }
 }
 
