@@ -30,6 +30,11 @@ Local fidelity constraints (Sec. 6.8, local l2 balls): with ``balls`` = [(idx_j,
 the product of the per-block projections (``proj_balls``).  ``balls`` = None is the
 global ball.
 
+Weighted l1 (the reweighted analysis of SARA, Sec. 3.1; reading R12): with ``weights``
+w (one per coefficient of Psi^dagger x) the prior is gamma sum_i w_i |(Psi^dagger x)_i|,
+so every l1 bound gamma becomes gamma w_i.  ``sara_weights`` gives the reweighting
+w_i = delta / (delta + |(Psi^dagger x)_i|) for a caller-chosen delta.
+
 Convergence (Sec. 6.6): relative iterate change ||x+ - x|| / ||x+|| < delta.
 Every norm is FP64.
 """
@@ -107,6 +112,16 @@ class PDParams:
     sigma2: float = 0.0  # <= 0 means 1 / op_norm_sq
     theta: float = 1.0
     balls: object = None  # local l2 balls [(idx_j, eps_j)]; None: the global ball
+    weights: object = None  # per-coefficient l1 weights (shape of Psi^dagger x); None: all 1
+
+
+def _bound(gamma, weights):
+    return gamma if weights is None else gamma * np.asarray(weights)
+
+
+def sara_weights(x, psi_adj, delta):
+    """w_i = delta / (delta + |(Psi^dagger x)_i|) (reading R12)."""
+    return delta / (delta + np.abs(psi_adj(x)))
 
 
 def primal_dual(y, phi, phi_adj, psi, psi_adj, p, x0=None):
@@ -123,7 +138,7 @@ def primal_dual(y, phi, phi_adj, psi, psi_adj, p, x0=None):
     hist = []
     it = 0
     for it in range(1, p.max_iter + 1):
-        z1 = prox.clip_linf(z1 + p.sigma1 * psi_adj(xhat), p.gamma)
+        z1 = prox.clip_linf(z1 + p.sigma1 * psi_adj(xhat), _bound(p.gamma, p.weights))
         t = z2 + sigma2 * phi(xhat)
         proj = proj_balls(t / sigma2, y, p.eps, p.balls)
         z2 = t - sigma2 * proj
@@ -152,6 +167,7 @@ class ADMMParams:
     max_iter: int = 200
     rel_tol: float = 0.0
     balls: object = None  # local l2 balls [(idx_j, eps_j)]; None: the global ball
+    weights: object = None  # per-coefficient l1 weights; None: all 1
 
 
 def admm(y, phi, phi_adj, psi, psi_adj, p, x0=None):
@@ -172,7 +188,7 @@ def admm(y, phi, phi_adj, psi, psi_adj, p, x0=None):
         xt = x - p.rho * np.real(phi_adj(v - r + s))
         zbar = prox.proj_positive(xt)
         for _ in range(p.dualfb_iters):
-            d = (1.0 / p.eta) * prox.clip_linf(p.eta * d + psi_adj(zbar), p.gamma)
+            d = (1.0 / p.eta) * prox.clip_linf(p.eta * d + psi_adj(zbar), _bound(p.gamma, p.weights))
             zbar = prox.proj_positive(xt - psi(d))
         dn = float(np.sqrt(np.sum((zbar - x) ** 2)))
         xn = float(np.sqrt(np.sum(zbar ** 2)))
@@ -195,6 +211,7 @@ class FISTAParams:
     dualfb_iters: int = 1
     max_iter: int = 200
     rel_tol: float = 0.0
+    weights: object = None  # per-coefficient l1 weights; None: all 1
 
 
 def dual_fb(z, thr, d, psi, psi_adj, eta, iters):
@@ -222,7 +239,7 @@ def fista(y, phi, phi_adj, psi, psi_adj, p, x0=None):
     it = 0
     for it in range(1, p.max_iter + 1):
         z = xhat - p.lam * np.real(phi_adj(phi(xhat) - y))
-        xn, d = dual_fb(z, p.lam * p.gamma, d, psi, psi_adj, p.eta, p.dualfb_iters)
+        xn, d = dual_fb(z, p.lam * _bound(p.gamma, p.weights), d, psi, psi_adj, p.eta, p.dualfb_iters)
         theta_n = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * theta * theta))
         xhat = xn + ((theta - 1.0) / theta_n) * (xn - x)
         dn = float(np.sqrt(np.sum((xn - x) ** 2)))

@@ -257,3 +257,46 @@ def test_product_of_balls_projection_is_the_blockwise_projection():
             d = rng.normal(size=len(i)) + 1j * rng.normal(size=len(i))
             q[i] = y[i] + d / np.linalg.norm(d) * e * rng.uniform() ** 0.5
         assert np.real(np.vdot(z - p, q - p)) <= 1e-9
+
+
+def test_weighted_l1_closed_form_and_unit_weights():
+    """Phi = I, Psi = Dirac, weights w: min sum w_i x_i s.t. ||y - x|| <= eps, x >= 0 has
+    x_i = max(y_i - lam w_i, 0) with lam by bisection; unit weights give the unweighted run."""
+    y = np.abs(synth.normal(200, seed=21)) + 0.1
+    w = 0.2 + synth.uniform(200, seed=22)
+    eps = 0.5 * np.linalg.norm(y)
+    lo, hi = 0.0, float(np.max(y / w))
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.linalg.norm(y - np.maximum(y - mid * w, 0)) < eps:
+            lo = mid
+        else:
+            hi = mid
+    xs = np.maximum(y - lo * w, 0)
+    ident = lambda x: x.astype(complex)
+    ident_t = lambda z: np.real(z)
+    dirac = lambda a: a[0]
+    dirac_t = lambda x: x[None]
+    x, _ = so.primal_dual(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                          so.PDParams(gamma=0.05, op_norm_sq=1.0, eps=eps, max_iter=30000, rel_tol=1e-14,
+                                      weights=w[None]))
+    assert np.max(np.abs(x - xs)) < 1e-8
+    xa, _ = so.admm(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                    so.ADMMParams(gamma=0.05, eps=eps, rho=1.0, max_iter=30000, rel_tol=1e-14, weights=w[None]))
+    assert np.max(np.abs(xa - xs)) < 1e-8
+    x1, _ = so.primal_dual(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                           so.PDParams(gamma=0.05, op_norm_sq=1.0, eps=eps, max_iter=200, weights=np.ones((1, 200))))
+    x0, _ = so.primal_dual(y.astype(complex), ident, ident_t, dirac, dirac_t,
+                           so.PDParams(gamma=0.05, op_norm_sq=1.0, eps=eps, max_iter=200))
+    assert np.array_equal(x1, x0)
+
+
+def test_sara_weights():
+    x = synth.normal(64, seed=3).reshape(8, 8)
+    psit = lambda v: wv.psi_adjoint(v, (0, 1), 2)
+    w = so.sara_weights(x, psit, 0.1)
+    a = np.abs(psit(x))
+    assert w.shape == a.shape and np.all((w > 0) & (w <= 1))
+    assert np.allclose(w, 0.1 / (0.1 + a), rtol=0, atol=0)
+    assert np.all(np.diff(w.ravel()[np.argsort(a.ravel())]) <= 0)  # larger coefficients, smaller weights
+    assert np.all(so.sara_weights(np.zeros((8, 8)), psit, 0.1) == 1.0)
