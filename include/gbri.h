@@ -236,6 +236,14 @@ int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav
 int32_t gbri_solver_destroy(gbri_solver* s);
 /* Run n_iter iterations without any host synchronisation. */
 int32_t gbri_solver_step(gbri_solver* s, int32_t n_iter, void* stream);
+/* Reweighted l1 (SARA's reweighting, Sec. 3.1; the weights' formula follows the SARA
+ * paper the text cites): sets per-coefficient weights w_i = delta / (delta + |(Psi^dagger x)_i|)
+ * from the current iterate x; from then on the l1 prior is gamma sum_i w_i |(Psi^dagger x)_i|
+ * (every l1 bound gamma becomes gamma w_i: the PD dual clip, the DualFB step of ADMM and
+ * FISTA).  The dual variables are kept.  delta > 0.  The first call allocates the weights
+ * and drops the solver's captured iteration (captured again at the next step; a batch
+ * holding the solver rebuilds its graph).  No host synchronisation. */
+int32_t gbri_solver_reweight(gbri_solver* s, double delta, void* stream);
 /* Copy the current iterate x to d_x (image). */
 int32_t gbri_solver_get_x(gbri_solver* s, void* d_x, void* stream);
 /* Iterations run and the last FP64 relative change ||x+ - x|| / ||x+|| (host; INFINITY before the

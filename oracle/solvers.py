@@ -39,7 +39,7 @@ Convergence (Sec. 6.6): relative iterate change ||x+ - x|| / ||x+|| < delta.
 Every norm is FP64.
 """
 
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 
@@ -113,6 +113,7 @@ class PDParams:
     theta: float = 1.0
     balls: object = None  # local l2 balls [(idx_j, eps_j)]; None: the global ball
     weights: object = None  # per-coefficient l1 weights (shape of Psi^dagger x); None: all 1
+    reweight: object = None  # (k, delta): after iteration k, weights <- sara_weights(x, delta); duals kept
 
 
 def _bound(gamma, weights):
@@ -144,6 +145,8 @@ def primal_dual(y, phi, phi_adj, psi, psi_adj, p, x0=None):
         z2 = t - sigma2 * proj
         x_new = prox.proj_positive(x - p.tau * (psi(z1) + np.real(phi_adj(z2))))
         xhat = x_new + p.theta * (x_new - x)
+        if p.reweight is not None and it == p.reweight[0]:
+            p = replace(p, weights=sara_weights(x_new, psi_adj, p.reweight[1]))
         dn = float(np.sqrt(np.sum((x_new - x) ** 2)))
         xn = float(np.sqrt(np.sum(x_new ** 2)))
         rel = dn / xn if xn > 0 else (0.0 if dn == 0 else np.inf)
@@ -168,6 +171,7 @@ class ADMMParams:
     rel_tol: float = 0.0
     balls: object = None  # local l2 balls [(idx_j, eps_j)]; None: the global ball
     weights: object = None  # per-coefficient l1 weights; None: all 1
+    reweight: object = None  # (k, delta): after iteration k, weights <- sara_weights(x, delta)
 
 
 def admm(y, phi, phi_adj, psi, psi_adj, p, x0=None):
@@ -190,6 +194,8 @@ def admm(y, phi, phi_adj, psi, psi_adj, p, x0=None):
         for _ in range(p.dualfb_iters):
             d = (1.0 / p.eta) * prox.clip_linf(p.eta * d + psi_adj(zbar), _bound(p.gamma, p.weights))
             zbar = prox.proj_positive(xt - psi(d))
+        if p.reweight is not None and it == p.reweight[0]:
+            p = replace(p, weights=sara_weights(zbar, psi_adj, p.reweight[1]))
         dn = float(np.sqrt(np.sum((zbar - x) ** 2)))
         xn = float(np.sqrt(np.sum(zbar ** 2)))
         rel = dn / xn if xn > 0 else (0.0 if dn == 0 else np.inf)
@@ -212,6 +218,7 @@ class FISTAParams:
     max_iter: int = 200
     rel_tol: float = 0.0
     weights: object = None  # per-coefficient l1 weights; None: all 1
+    reweight: object = None  # (k, delta): after iteration k, weights <- sara_weights(x, delta)
 
 
 def dual_fb(z, thr, d, psi, psi_adj, eta, iters):
@@ -242,6 +249,8 @@ def fista(y, phi, phi_adj, psi, psi_adj, p, x0=None):
         xn, d = dual_fb(z, p.lam * _bound(p.gamma, p.weights), d, psi, psi_adj, p.eta, p.dualfb_iters)
         theta_n = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * theta * theta))
         xhat = xn + ((theta - 1.0) / theta_n) * (xn - x)
+        if p.reweight is not None and it == p.reweight[0]:
+            p = replace(p, weights=sara_weights(xn, psi_adj, p.reweight[1]))
         dn = float(np.sqrt(np.sum((xn - x) ** 2)))
         nn = float(np.sqrt(np.sum(xn ** 2)))
         rel = dn / nn if nn > 0 else (0.0 if dn == 0 else np.inf)

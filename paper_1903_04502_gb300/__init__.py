@@ -280,6 +280,11 @@ class Solver:
     def step(self, n_iter=1, stream=None):
         _lib.check(_lib.load().gbri_solver_step(self._h, int(n_iter), _stream(stream)))
 
+    def reweight(self, delta, stream=None):
+        """Reweighted l1: w_i = delta / (delta + |(Psi^dagger x)_i|) from the current iterate
+        (gbri_solver_reweight)."""
+        _lib.check(_lib.load().gbri_solver_reweight(self._h, float(delta), _stream(stream)))
+
     def x(self, out=None, stream=None):
         if out is None:
             out = torch.empty((self.plan.n_side, self.plan.n_side), dtype=self.plan.real_dtype,

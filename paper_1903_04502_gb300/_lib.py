@@ -66,6 +66,7 @@ SIGNATURES = {
     "gbri_solver_create": (I32, [C.POINTER(P), P, P, P, C.POINTER(SolveParams), U32, P]),
     "gbri_solver_destroy": (I32, [P]),
     "gbri_solver_step": (I32, [P, I32, P]),
+    "gbri_solver_reweight": (I32, [P, D, P]),
     "gbri_solver_get_x": (I32, [P, P, P]),
     "gbri_solver_status": (I32, [P, C.POINTER(I32), C.POINTER(D), P]),
     "gbri_solver_report": (I32, [P, C.POINTER(SolveReport), P]),

@@ -11,6 +11,7 @@
 
 struct gbri_batch {
   std::vector<gbri_solver*> members;
+  std::vector<int64_t> versions;  // members' graph versions at the last rebuild
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool dirty = true;
@@ -45,6 +46,8 @@ int32_t rebuild(gbri_batch* b) {
     return gbri::cuda_error(e, "cudaGraphInstantiate(batch)");
   }
   b->launches_per_iter = launches;
+  b->versions.clear();
+  for (gbri_solver* s : b->members) b->versions.push_back(gbri::solver_graph_version(s));
   b->dirty = false;
   return GBRI_OK;
 }
@@ -96,6 +99,8 @@ int32_t gbri_batch_size(const gbri_batch* b) { return b ? (int32_t)b->members.si
 int32_t gbri_batch_step(gbri_batch* b, int32_t n_iter, void* stream) {
   GBRI_CHECK(b && n_iter >= 0, GBRI_EINVAL, "bad argument");
   if (b->members.empty() || n_iter == 0) return GBRI_OK;
+  for (size_t i = 0; !b->dirty && i < b->members.size(); ++i)
+    if (i >= b->versions.size() || b->versions[i] != solver_graph_version(b->members[i])) b->dirty = true;
   if (b->dirty) GBRI_TRY(rebuild(b));
   cudaStream_t st = (cudaStream_t)stream;
   for (int k = 0; k < n_iter; ++k) GBRI_CHECK_CUDA(cudaGraphLaunch(b->exec, st));

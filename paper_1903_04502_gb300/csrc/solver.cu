@@ -206,6 +206,13 @@ __global__ void k_absmax_partials(const R* __restrict__ a, int64_t n, double* __
   }
 }
 
+// SARA weights in place: w = delta / (delta + |w|) (w holds Psi^dagger x on entry)
+template <class R>
+__global__ void k_sara_weights(R* __restrict__ w, int64_t n, R delta) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = delta / (delta + abs_r(w[i]));
+}
+
 __global__ void k_max_finish(const double* __restrict__ partials, int n, double* __restrict__ out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double m = 0.0;
@@ -250,6 +257,8 @@ struct gbri_solver {
   void *yp = nullptr, *u = nullptr, *w = nullptr;                            // complex [M], plan order
   void *x = nullptr, *xhat = nullptr, *psiz = nullptr, *z1 = nullptr, *xt = nullptr;  // real images / stacks
   void* zb = nullptr;  // FISTA: the DualFB iterate zbar (image)
+  void* wts = nullptr;  // per-coefficient l1 weights [n_w][n][n] (after gbri_solver_reweight), or null
+  int64_t graph_version = 0;
   // local l2 balls (n_balls >= 2): plan-position starts [nb + 1], radii [nb], per-ball
   // scalars [nb] (PD: c_j = 1 - rho_j; ADMM: rho_j), per-ball block partials [nb][degrid blocks]
   int nb = 0;
@@ -277,6 +286,7 @@ void free_solver(gbri_solver* s) {
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   cudaFree(s->yp); cudaFree(s->u); cudaFree(s->w);
   cudaFree(s->x); cudaFree(s->xhat); cudaFree(s->psiz); cudaFree(s->z1); cudaFree(s->xt); cudaFree(s->zb);
+  cudaFree(s->wts);
   cudaFree(s->partials); cudaFree(s->sc);
   cudaFree(s->bstart); cudaFree(s->beps); cudaFree(s->bsc); cudaFree(s->bpart);
   delete s;
@@ -293,7 +303,8 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   const int n = P->n_side;
   const int64_t N = (int64_t)n * n;
   // z1 <- clip(z1 + sigma1 Psi^dagger xhat, gamma)
-  GBRI_TRY(psi_adjoint_apply<R>(W, vec<R>(S->xhat), vec<R>(S->z1), DualEpi{1, 1.0, p.sigma1, p.gamma, 1.0}, st));
+  GBRI_TRY(psi_adjoint_apply<R>(W, vec<R>(S->xhat), vec<R>(S->z1), DualEpi{1, 1.0, p.sigma1, p.gamma, 1.0, S->wts},
+                                st));
   // u <- c u + sigma2 (Phi xhat - y), ||u||^2
   GBRI_TRY(launch_pad<R>(P, vec<R>(S->xhat), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
@@ -361,7 +372,7 @@ int32_t admm_iteration(gbri_solver* S, cudaStream_t st) {
   GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
   for (int k = 0; k < p.dualfb_iters; ++k) {
     GBRI_TRY(psi_adjoint_apply<R>(W, vec<R>(S->xhat), vec<R>(S->z1) /* d */,
-                                  DualEpi{1, p.eta, 1.0, p.gamma, 1.0 / p.eta}, st));
+                                  DualEpi{1, p.eta, 1.0, p.gamma, 1.0 / p.eta, S->wts}, st));
     GBRI_TRY(psi_apply<R>(W, vec<R>(S->z1), vec<R>(S->psiz), st));
     const bool last = (k == p.dualfb_iters - 1);
     launch_begin(GBRI_K_UPDATE, st);
@@ -400,7 +411,7 @@ int32_t fista_iteration(gbri_solver* S, cudaStream_t st) {
   const double thr = p.rho * p.gamma;
   for (int k = 0; k < p.dualfb_iters; ++k) {
     GBRI_TRY(psi_adjoint_apply<R>(W, vec<R>(S->zb), vec<R>(S->z1) /* d */,
-                                  DualEpi{1, p.eta, 1.0, thr, 1.0 / p.eta}, st));
+                                  DualEpi{1, p.eta, 1.0, thr, 1.0 / p.eta, S->wts}, st));
     GBRI_TRY(psi_apply<R>(W, vec<R>(S->z1), vec<R>(S->psiz), st));
     launch_begin(GBRI_K_UPDATE, st);
     if (k < p.dualfb_iters - 1)
@@ -632,6 +643,7 @@ int32_t solver_iteration_graph(gbri_solver* s) {
   return capture_iteration(s);
 }
 cudaGraph_t solver_graph(gbri_solver* s) { return s->graph; }
+int64_t solver_graph_version(const gbri_solver* s) { return s->graph_version; }
 int64_t solver_launches_per_iteration(gbri_solver* s) { return s->launches_per_iter; }
 const gbri_plan* solver_plan(const gbri_solver* s) { return s->plan; }
 const gbri_wavelet* solver_wavelet(const gbri_solver* s) { return s->wav; }
@@ -695,6 +707,35 @@ int32_t gbri_solver_step(gbri_solver* S, int32_t n_iter, void* stream) {
     ++S->iters;
   }
   return GBRI_OK;
+}
+
+int32_t gbri_solver_reweight(gbri_solver* S, double delta, void* stream) {
+  GBRI_CHECK(S && delta > 0, GBRI_EINVAL, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t N = (int64_t)S->plan->n_side * S->plan->n_side;
+  const int64_t tot = N * S->wav->nw;
+  if (!S->wts) {
+    GBRI_TRY(zalloc_bytes(&S->wts, (size_t)tot * real_bytes(S->prec), st));
+    // the captured iteration holds the (null) weights pointer: capture again on the next step
+    if (S->graph_exec) cudaGraphExecDestroy(S->graph_exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    S->graph_exec = nullptr;
+    S->graph = nullptr;
+    ++S->graph_version;
+  }
+  const int b = img_blocks(tot);
+  if (S->prec == GBRI_F64) {
+    GBRI_TRY(psi_adjoint_apply<double>(S->wav, vec<double>(S->x), vec<double>(S->wts), DualEpi{0, 0.0, 0.0, 0.0, 0.0},
+                                       st));
+    launch_begin(GBRI_K_OTHER, st);
+    k_sara_weights<double><<<b, 256, 0, st>>>(vec<double>(S->wts), tot, delta);
+  } else {
+    GBRI_TRY(psi_adjoint_apply<float>(S->wav, vec<float>(S->x), vec<float>(S->wts), DualEpi{0, 0.0, 0.0, 0.0, 0.0},
+                                      st));
+    launch_begin(GBRI_K_OTHER, st);
+    k_sara_weights<float><<<b, 256, 0, st>>>(vec<float>(S->wts), tot, (float)delta);
+  }
+  return launch_end(GBRI_K_OTHER, st);
 }
 
 int32_t gbri_solver_get_x(gbri_solver* S, void* d_x, void* stream) {

@@ -97,7 +97,8 @@ __device__ __forceinline__ void emit(R* __restrict__ out, size_t q, R v, const E
     out[q] = v;
   } else {
     const R u = fma_r(e.ca, out[q], e.cb * v);
-    out[q] = min_r(max_r(u, -e.lim), e.lim) * e.ce;
+    const R lim = e.w ? e.lim * e.w[q] : e.lim;
+    out[q] = min_r(max_r(u, -lim), lim) * e.ce;
   }
 }
 
@@ -200,8 +201,10 @@ __global__ void __launch_bounds__(256) k_dwt_level(const R* __restrict__ in, siz
   const R* src = in + in_stride * j;
   R* carry = ll + (size_t)n * n * j;
   R* dst = out + (size_t)n * n * F.aidx[j];
+  EpiR<R> ej = e;  // the weights plane of this basis
+  if (ej.w) ej.w += (size_t)n * n * F.aidx[j];
 #define GBRI_DWT_CASE(LL) \
-  case LL: dwt_block<LL, R>(sm, src, carry, dst, m, n, last, scale, F.h[j], F.g[j], e); break;
+  case LL: dwt_block<LL, R>(sm, src, carry, dst, m, n, last, scale, F.h[j], F.g[j], ej); break;
   switch (F.len[j]) {
     GBRI_DWT_CASE(2) GBRI_DWT_CASE(4) GBRI_DWT_CASE(6) GBRI_DWT_CASE(8) GBRI_DWT_CASE(10) GBRI_DWT_CASE(12)
     GBRI_DWT_CASE(14) GBRI_DWT_CASE(16) GBRI_DWT_CASE(18) GBRI_DWT_CASE(20)
@@ -360,7 +363,9 @@ int32_t psi_adjoint_apply(gbri_wavelet* w, const R* x, R* out, DualEpi epi, cuda
   const R scale = (R)w->scale;
   if (w->dirac_idx >= 0) {
     launch_begin(GBRI_K_PSI_ADJ, s);
-    k_dirac<R><<<blocks_for(N), 256, 0, s>>>(x, out + (size_t)N * w->dirac_idx, N, scale, EpiR<R>(epi));
+    EpiR<R> ed(epi);
+    if (ed.w) ed.w += (size_t)N * w->dirac_idx;
+    k_dirac<R><<<blocks_for(N), 256, 0, s>>>(x, out + (size_t)N * w->dirac_idx, N, scale, ed);
     GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
   }
   if (w->nb == 0) return GBRI_OK;

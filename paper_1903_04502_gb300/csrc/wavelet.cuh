@@ -22,11 +22,14 @@ struct Filters {
 
 // How the analysis writes a final coefficient v (already scaled by 1/sqrt(n_w)):
 //   mode 0: out[q] = v
-//   mode 1: out[q] = clip(ca * out[q] + cb * v, [-lim, lim]) * ce   (dual updates of PD / DualFB)
-// (constants in FP64; the kernels round them once to their real type)
+//   mode 1: out[q] = clip(ca * out[q] + cb * v, [-lim w_q, lim w_q]) * ce   (dual updates of
+//           PD / DualFB; w = per-coefficient l1 weights of the stack layout, real type of the
+//           kernels, or null for w = 1)
+// (constants in FP64; rounded once to the kernels' real type)
 struct DualEpi {
   int mode;
   double ca, cb, lim, ce;
+  const void* w = nullptr;
 };
 
 // DualEpi rounded to the kernels' real type once, on the host (a per-thread conversion
@@ -35,8 +38,9 @@ template <class R>
 struct EpiR {
   int mode;
   R ca, cb, lim, ce;
+  const R* w;  // weights of the plane written (offset like the output), or null
   __host__ __device__ explicit EpiR(const DualEpi& e)
-      : mode(e.mode), ca((R)e.ca), cb((R)e.cb), lim((R)e.lim), ce((R)e.ce) {}
+      : mode(e.mode), ca((R)e.ca), cb((R)e.cb), lim((R)e.lim), ce((R)e.ce), w(static_cast<const R*>(e.w)) {}
 };
 
 // Daubechies low-pass filter dbN (2N taps, minimum phase, sum = sqrt 2) by
