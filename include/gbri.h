@@ -151,6 +151,12 @@ int32_t gbri_psi_adjoint(gbri_wavelet* wav, const void* d_x, void* d_alpha, void
 int32_t gbri_prox_l1(const void* d_in, void* d_out, int64_t n, double lambda, int32_t is_complex,
                      int32_t precision, void* stream);
 
+/* Weighted soft thresholding (the reweighted l1 prox): threshold lambda * w_i per element.
+ * d_w: n non-negative real weights of the same precision (real even for complex input).
+ * d_in == d_out allowed. */
+int32_t gbri_prox_l1_weighted(const void* d_in, const void* d_w, void* d_out, int64_t n, double lambda,
+                              int32_t is_complex, int32_t precision, void* stream);
+
 /* Projection onto the l2 ball of radius eps centred at d_center (Sec. 4.2 and the
  * global constraint of Sec. 6.8): out = z if ||z - c|| <= eps, else c + eps (z - c) / ||z - c||.
  * Complex vectors of length M in the given precision; the norm is accumulated in

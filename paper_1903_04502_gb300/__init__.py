@@ -219,6 +219,24 @@ def prox_l1(x, lam, out=None, stream=None):
     return out
 
 
+def prox_l1_weighted(x, w, lam, out=None, stream=None):
+    """Weighted soft thresholding (gbri_prox_l1_weighted): threshold lam * w elementwise.
+    w: real CUDA tensor of x's real precision and x's number of elements."""
+    if x.dtype not in (torch.float32, torch.float64, torch.complex64, torch.complex128):
+        raise ValueError("prox_l1_weighted takes float32, float64, complex64 or complex128")
+    prec = _precision(x.dtype)
+    _need(x, x.dtype, name="x")
+    _need(w, _REAL[prec], name="w")
+    if w.numel() != x.numel():
+        raise ValueError("w must have one weight per element of x")
+    if out is None:
+        out = torch.empty_like(x)
+    _need(out, x.dtype, tuple(x.shape), "out")
+    _lib.check(_lib.load().gbri_prox_l1_weighted(_ptr(x), _ptr(w), _ptr(out), x.numel(), float(lam),
+                                                 1 if x.is_complex() else 0, prec, _stream(stream)))
+    return out
+
+
 def proj_l2ball(z, center, eps, out=None, norm_out=None, stream=None):
     """Projection of complex64 / complex128 z onto the l2 ball of radius eps around center
     (gbri_proj_l2ball).  norm_out: optional float64 CUDA tensor of one element receiving ||z - center||."""

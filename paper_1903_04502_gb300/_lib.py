@@ -61,6 +61,7 @@ SIGNATURES = {
     "gbri_psi": (I32, [P, P, P, P]),
     "gbri_psi_adjoint": (I32, [P, P, P, P]),
     "gbri_prox_l1": (I32, [P, P, I64, D, I32, I32, P]),
+    "gbri_prox_l1_weighted": (I32, [P, P, P, I64, D, I32, I32, P]),
     "gbri_proj_l2ball": (I32, [P, P, P, I64, D, P, I32, P]),
     "gbri_proj_l2ball_noalloc": (I32, [P, P, P, I64, D, P, P]),
     "gbri_solver_create": (I32, [C.POINTER(P), P, P, P, C.POINTER(SolveParams), U32, P]),

@@ -9,21 +9,25 @@ namespace gbri {
 
 namespace {
 
+// soft thresholding with threshold lam (w null) or lam * w[i]
 template <class R>
-__global__ void k_soft_real(const R* __restrict__ in, R* __restrict__ out, int64_t n, R lam) {
+__global__ void k_soft_real(const R* __restrict__ in, const R* __restrict__ w, R* __restrict__ out, int64_t n,
+                            R lam) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const R v = in[i];
-    const R a = abs_r(v) - lam;
+    const R a = abs_r(v) - (w ? lam * w[i] : lam);
     out[i] = a > 0 ? copysign_r(a, v) : (R)0;
   }
 }
 
 template <class R>
-__global__ void k_soft_complex(const cplx<R>* __restrict__ in, cplx<R>* __restrict__ out, int64_t n, R lam) {
+__global__ void k_soft_complex(const cplx<R>* __restrict__ in, const R* __restrict__ w, cplx<R>* __restrict__ out,
+                               int64_t n, R lam) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const cplx<R> v = in[i];
+    const R t = w ? lam * w[i] : lam;
     const R mag = hypot_r(v.x, v.y);
-    const R s = mag > lam ? (mag - lam) / mag : (R)0;
+    const R s = mag > t ? (mag - t) / mag : (R)0;
     out[i] = mkc<R>(v.x * s, v.y * s);
   }
 }
@@ -58,14 +62,16 @@ __global__ void k_l2ball_apply(const cplx<R>* __restrict__ z, const cplx<R>* __r
 }
 
 template <class R>
-int32_t prox_l1(const void* d_in, void* d_out, int64_t n, double lambda, int32_t is_complex, cudaStream_t s) {
+int32_t prox_l1(const void* d_in, const void* d_w, void* d_out, int64_t n, double lambda, int32_t is_complex,
+                cudaStream_t s) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8));
   launch_begin(GBRI_K_OTHER, s);
   if (is_complex)
-    k_soft_complex<R><<<blocks, 256, 0, s>>>(static_cast<const cplx<R>*>(d_in), static_cast<cplx<R>*>(d_out), n,
-                                             (R)lambda);
+    k_soft_complex<R><<<blocks, 256, 0, s>>>(static_cast<const cplx<R>*>(d_in), static_cast<const R*>(d_w),
+                                             static_cast<cplx<R>*>(d_out), n, (R)lambda);
   else
-    k_soft_real<R><<<blocks, 256, 0, s>>>(static_cast<const R*>(d_in), static_cast<R*>(d_out), n, (R)lambda);
+    k_soft_real<R><<<blocks, 256, 0, s>>>(static_cast<const R*>(d_in), static_cast<const R*>(d_w),
+                                          static_cast<R*>(d_out), n, (R)lambda);
   return launch_end(GBRI_K_OTHER, s);
 }
 
@@ -119,8 +125,19 @@ int32_t gbri_prox_l1(const void* d_in, void* d_out, int64_t n, double lambda, in
   if (n == 0) return GBRI_OK;
   GBRI_CHECK(d_in && d_out, GBRI_EINVAL, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
-  return precision == GBRI_F64 ? prox_l1<double>(d_in, d_out, n, lambda, is_complex, s)
-                               : prox_l1<float>(d_in, d_out, n, lambda, is_complex, s);
+  return precision == GBRI_F64 ? prox_l1<double>(d_in, nullptr, d_out, n, lambda, is_complex, s)
+                               : prox_l1<float>(d_in, nullptr, d_out, n, lambda, is_complex, s);
+}
+
+int32_t gbri_prox_l1_weighted(const void* d_in, const void* d_w, void* d_out, int64_t n, double lambda,
+                              int32_t is_complex, int32_t precision, void* stream) {
+  GBRI_CHECK(precision == GBRI_F32 || precision == GBRI_F64, GBRI_EINVAL, "precision must be GBRI_F32 or GBRI_F64");
+  GBRI_CHECK(n >= 0 && lambda >= 0, GBRI_EINVAL, "bad size or lambda");
+  if (n == 0) return GBRI_OK;
+  GBRI_CHECK(d_in && d_out && d_w, GBRI_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  return precision == GBRI_F64 ? prox_l1<double>(d_in, d_w, d_out, n, lambda, is_complex, s)
+                               : prox_l1<float>(d_in, d_w, d_out, n, lambda, is_complex, s);
 }
 
 int32_t gbri_proj_l2ball(const void* d_z, const void* d_center, void* d_out, int64_t M, double eps,

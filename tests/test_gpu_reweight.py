@@ -89,3 +89,20 @@ def test_reweight_inside_a_batch(g):
     xa, xr = a.x().cpu().numpy(), ref.x().cpu().numpy()
     assert rel(xa, xr) <= 1e-6
     assert rel(b.x().cpu().numpy(), xr) > 1e-6  # the other member was not reweighted
+
+
+@pytest.mark.parametrize("dtype", ["float32", "complex64", "float64", "complex128"])
+def test_weighted_prox_l1_matches_oracle(g, dtype):
+    from oracle import prox
+    n = 50_001
+    x = synth.normal(n, seed=4) * 2
+    if dtype.startswith("complex"):
+        x = x + 1j * synth.normal(n, seed=5)
+    x = x.astype(dtype)
+    w = (0.1 + synth.uniform(n, seed=6)).astype("float64" if dtype in ("float64", "complex128") else "float32")
+    out = g.prox_l1_weighted(torch.from_numpy(x).cuda(), torch.from_numpy(w).cuda(), 0.7).cpu().numpy()
+    ref = prox.soft_threshold(x.astype(np.complex128 if x.dtype.kind == "c" else np.float64), 0.7 * w.astype(np.float64))
+    tol = 1e-6 if dtype in ("float32", "complex64") else 1e-14
+    assert rel(out, ref) <= tol
+    if tol < 1e-10:  # FP64: the same entries are thresholded away (FP32 may differ at |x| = lam w)
+        assert np.array_equal(np.abs(out) == 0, np.abs(ref) == 0)
