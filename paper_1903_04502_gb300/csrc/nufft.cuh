@@ -44,8 +44,11 @@ constexpr int kMaxRun = 1024;
 constexpr int kWinPitch = 22;
 
 // Resident blocks per SM the visibility kernels are compiled for (launch bounds) and
-// launched with at most, by element size (4: FP32 path, 8: FP64 path) and support.
-constexpr int degrid_occupancy(int rb, int J) { return rb == 4 ? (J == 4 ? 4 : 3) : 2; }
+// launched with at most, by element size (4: FP32 path, 8: FP64 path) and support.  An FP32
+// degridding block (kernel table + eight windows) takes about 60 KB of shared memory at
+// J = 4, so three fit an SM; bounds of three leave 80 registers a thread, which measured
+// faster than bounds of four (64 registers).
+constexpr int degrid_occupancy(int rb, int J) { return rb == 4 ? 3 : 2; }
 constexpr int grid_occupancy(int rb, int J) { return rb == 4 ? (J == 4 ? 3 : 2) : 1; }
 
 }  // namespace gbri
