@@ -269,6 +269,10 @@ struct gbri_solver {
   int n_partials = 0;
   int iters = 0;
   double ms_total = 0.0;
+  // primal-dual: the wavelet branch of an iteration runs on aux_stream, forked from and
+  // joined back to the iteration's stream by the two events
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // one iteration captured as a CUDA graph and replayed (no host work per kernel)
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -284,6 +288,9 @@ void free_solver(gbri_solver* s) {
   if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
   if (s->graph) cudaGraphDestroy(s->graph);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->aux_stream) cudaStreamDestroy(s->aux_stream);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
   cudaFree(s->yp); cudaFree(s->u); cudaFree(s->w);
   cudaFree(s->x); cudaFree(s->xhat); cudaFree(s->psiz); cudaFree(s->z1); cudaFree(s->xt); cudaFree(s->zb);
   cudaFree(s->wts);
@@ -302,9 +309,25 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   const auto& p = S->p;
   const int n = P->n_side;
   const int64_t N = (int64_t)n * n;
+  // The wavelet branch (the dual update of z1, then Psi z1) and the measurement branch
+  // (the dual update of u, then Phi^dagger u) of Algorithm 7 read only xhat and their own
+  // dual variable until the primal update joins them: the wavelet branch runs on the
+  // auxiliary stream, so its small coarse-level launches fill the SMs the visibility
+  // kernels and the FFT leave idle.  (Captured, the fork and join are graph edges.)  With
+  // kernel-by-kernel profiling on, both branches run on the one stream, so that the events
+  // around each kernel time that kernel alone.
+  const bool fork = !profiling_enabled();
+  cudaStream_t sw = fork ? S->aux_stream : st;
+  if (fork) {
+    GBRI_CHECK_CUDA(cudaEventRecord(S->ev_fork, st));
+    GBRI_CHECK_CUDA(cudaStreamWaitEvent(sw, S->ev_fork, 0));
+  }
   // z1 <- clip(z1 + sigma1 Psi^dagger xhat, gamma)
   GBRI_TRY(psi_adjoint_apply<R>(W, vec<R>(S->xhat), vec<R>(S->z1), DualEpi{1, 1.0, p.sigma1, p.gamma, 1.0, S->wts},
-                                st));
+                                sw));
+  // Psi z1
+  GBRI_TRY(psi_apply<R>(W, vec<R>(S->z1), vec<R>(S->psiz), sw));
+  if (fork) GBRI_CHECK_CUDA(cudaEventRecord(S->ev_join, sw));
   // u <- c u + sigma2 (Phi xhat - y), ||u||^2
   GBRI_TRY(launch_pad<R>(P, vec<R>(S->xhat), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
@@ -326,8 +349,7 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
     GBRI_TRY(launch_grid(P, SrcScaledL<R>{cvec<R>(S->u), S->bsc, S->bstart, S->nb}, st));
   }
   GBRI_TRY(fft_inverse(P, st));
-  // Psi z1
-  GBRI_TRY(psi_apply<R>(W, vec<R>(S->z1), vec<R>(S->psiz), st));
+  if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_join, 0));
   const int ib = std::min(img_blocks(N), S->n_partials / 2);
   launch_begin(GBRI_K_UPDATE, st);
   k_pd_update<R><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz),
@@ -578,6 +600,14 @@ int32_t create_solver(gbri_solver* S, const void* d_y, uint32_t flags, cudaStrea
   const size_t rb = real_bytes(S->prec);
   auto& p = S->p;
   S->n_partials = std::max(std::max(P->degrid_blocks, 2 * img_blocks(N * nw)), 2048);
+  {  // the wavelet branch at the highest stream priority: its blocks are dispatched first
+     // as visibility-kernel blocks retire, so the shorter branch does not trail the longer
+    int least = 0, greatest = 0;
+    GBRI_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    GBRI_CHECK_CUDA(cudaStreamCreateWithPriority(&S->aux_stream, cudaStreamNonBlocking, greatest));
+  }
+  GBRI_CHECK_CUDA(cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming));
+  GBRI_CHECK_CUDA(cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming));
   GBRI_TRY(zalloc(&S->partials, (size_t)S->n_partials * 2, st));
   GBRI_TRY(zalloc(&S->sc, SC_N, st));
   GBRI_TRY(zalloc_bytes(&S->yp, (size_t)M * 2 * rb, st));

@@ -87,6 +87,39 @@ def test_default_gamma_and_op_norm_inside_solver(g):
     assert r["gamma"] == pytest.approx(gam, rel=1e-5)
 
 
+@pytest.mark.parametrize("n_balls", [0, 4])
+def test_pd_forked_branches_match_serial(g, monkeypatch, n_balls):
+    """A primal-dual iteration runs its wavelet branch on a second stream (graph replay and
+    direct launches) and both branches on one stream while kernels are profiled.  The three
+    run the same kernels on the same data; only the order of the float atomics on gridding
+    tile borders differs from run to run, so the images agree to rounding (1e-5 after 40
+    iterations), while a branch that read a stale iterate would be an iteration behind (the
+    39-iteration image is checked to lie outside 1e-4)."""
+    n, M, orders, L = 128, 20_000, (0, 1, 2, 3, 4), 3
+    uvw, geo, ops, y, eps = problem(n, M, orders, L, seed=21)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    wav = g.Wavelet(n, L, orders)
+    yd = torch.from_numpy(y).cuda()
+    kw = dict(eps=eps, gamma=1e-3, op_norm_sq=float(g.op_norm(plan, 50, 1e-6, seed=0)[0]), n_balls=n_balls)
+    xs = []
+    for mode in ("graph", "direct", "profiled", "short"):
+        if mode == "direct":
+            monkeypatch.setenv("GBRI_GRAPHS", "0")
+        s = g.Solver(plan, wav, yd, **kw)
+        if mode == "profiled":
+            g.profile_enable(2000)
+        try:
+            s.step(39 if mode == "short" else 40)
+            xs.append(s.x().double().cpu().numpy())
+        finally:
+            if mode == "profiled":
+                g.profile_enable(0)
+            monkeypatch.delenv("GBRI_GRAPHS", raising=False)
+        s.close()
+    assert rel(xs[1], xs[0]) <= 1e-5 and rel(xs[2], xs[0]) <= 1e-5, (rel(xs[1], xs[0]), rel(xs[2], xs[0]))
+    assert rel(xs[3], xs[0]) > 1e-4  # the FP64 oracle: 6.6e-4 between iterations 39 and 40
+
+
 def test_solve_converges_and_is_feasible(g):
     n, M, orders, L = 64, 8000, (0, 1, 2, 3), 3
     uvw, geo, ops, y, eps = problem(n, M, orders, L, seed=11)
