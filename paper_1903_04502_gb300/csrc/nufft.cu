@@ -10,9 +10,10 @@ namespace gbri {
 
 namespace {
 
-// Z S: padded[(q - n/2) mod K][(p - n/2) mod K] = corr[p] corr[q] x[q][p] / *d_norm
+// Z S: padded[(q - n/2) mod K][(p - n/2) mod K] = corr[p] corr[q] x[q][p] / *d_norm (real;
+// the other cells stay zero from plan creation)
 template <class R>
-__global__ void k_pad(const R* __restrict__ x, const R* __restrict__ corr, cplx<R>* __restrict__ padded, int n,
+__global__ void k_pad(const R* __restrict__ x, const R* __restrict__ corr, R* __restrict__ padded, int n,
                       int K, const double* __restrict__ d_norm) {
   const R s = d_norm ? (R)(1.0 / *d_norm) : (R)1;
   const int total = n * n;
@@ -20,7 +21,7 @@ __global__ void k_pad(const R* __restrict__ x, const R* __restrict__ corr, cplx<
     const int q = i / n, p = i - q * n;
     int r = q - n / 2; if (r < 0) r += K;
     int c = p - n / 2; if (c < 0) c += K;
-    padded[(size_t)r * K + c] = mkc<R>(x[i] * corr[p] * corr[q] * s, 0);
+    padded[(size_t)r * K + c] = x[i] * corr[p] * corr[q] * s;
   }
 }
 
@@ -90,7 +91,7 @@ template <class R>
 int32_t launch_pad(gbri_plan* p, const R* x, const double* d_norm, cudaStream_t s) {
   launch_begin(GBRI_K_PAD, s);
   k_pad<R><<<grid_blocks_for((int64_t)p->n_side * p->n_side), 256, 0, s>>>(
-      x, p->as<const R>(p->corr), p->as<cplx<R>>(p->padded), p->n_side, p->K, d_norm);
+      x, p->as<const R>(p->corr), p->as<R>(p->padded), p->n_side, p->K, d_norm);
   return launch_end(GBRI_K_PAD, s);
 }
 
@@ -107,14 +108,15 @@ template int32_t launch_pad<double>(gbri_plan*, const double*, const double*, cu
 template int32_t launch_crop<float>(gbri_plan*, float*, cudaStream_t);
 template int32_t launch_crop<double>(gbri_plan*, double*, cudaStream_t);
 
+// F Z S x: real-to-complex, padded -> spec (the half kx = 0 .. K/2; degridding reads
+// kx > K/2 as conj(spec[-ky][K - kx]))
 int32_t fft_forward(gbri_plan* p, cudaStream_t s) {
-  if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cufftSetStream");
+  if (cufftSetStream(p->fft_r2c, s) != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cufftSetStream");
   launch_begin(GBRI_K_FFT_FWD, s, false);
   const cufftResult r =
       p->prec == GBRI_F64
-          ? cufftExecZ2Z(p->fft, p->as<cufftDoubleComplex>(p->padded), p->as<cufftDoubleComplex>(p->grid),
-                         CUFFT_FORWARD)
-          : cufftExecC2C(p->fft, p->as<cufftComplex>(p->padded), p->as<cufftComplex>(p->grid), CUFFT_FORWARD);
+          ? cufftExecD2Z(p->fft_r2c, p->as<cufftDoubleReal>(p->padded), p->as<cufftDoubleComplex>(p->spec))
+          : cufftExecR2C(p->fft_r2c, p->as<cufftReal>(p->padded), p->as<cufftComplex>(p->spec));
   const int32_t st = launch_end(GBRI_K_FFT_FWD, s);
   if (r != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cuFFT forward");
   return st;

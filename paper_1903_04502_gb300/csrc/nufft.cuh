@@ -68,14 +68,16 @@ struct gbri_plan {
   int32_t* cell_off = nullptr;  // plan creation only
   void* wtab = nullptr;     // R
   void* corr = nullptr;     // R
-  void* padded = nullptr;   // C
-  void* grid = nullptr;     // C
+  void* padded = nullptr;   // R [K][K]: Z S x (zero outside the image)
+  void* spec = nullptr;     // C [K][K/2 + 1]: its real-to-complex FFT (half spectrum; Phi)
+  void* grid = nullptr;     // C [K][K]: the gridded visibilities and their inverse FFT (Phi^dagger)
   void* vis_tmp = nullptr;  // C [M] plan-order scratch
   double* partials = nullptr;  // reduction partials
   double* scalars = nullptr;   // small device scalars
   int n_partials = 0;
-  cufftHandle fft = 0;
-  bool fft_ok = false;
+  cufftHandle fft = 0;      // C2C / Z2Z, inverse (in place on grid)
+  cufftHandle fft_r2c = 0;  // R2C / D2Z, forward (padded -> spec)
+  bool fft_ok = false, fft_r2c_ok = false;
   int64_t device_bytes = 0;
   int64_t layout_bytes = 0;
   int degrid_blocks = 0, grid_blocks = 0;

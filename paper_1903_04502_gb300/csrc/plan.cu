@@ -250,11 +250,13 @@ void destroy_plan(gbri_plan* p) {
   cudaFree(p->wtab);
   cudaFree(p->corr);
   cudaFree(p->padded);
+  cudaFree(p->spec);
   cudaFree(p->grid);
   cudaFree(p->vis_tmp);
   cudaFree(p->partials);
   cudaFree(p->scalars);
   if (p->fft_ok) cufftDestroy(p->fft);
+  if (p->fft_r2c_ok) cufftDestroy(p->fft_r2c);
   delete p;
 }
 
@@ -439,9 +441,10 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   GBRI_TRY(dmalloc(&p->meta, (size_t)M, &p->device_bytes));
   GBRI_TRY(dmalloc(&p->perm, (size_t)M, &p->device_bytes));
   GBRI_TRY(bmalloc(&p->vis_tmp, (size_t)M * 2 * rb, &p->device_bytes));
-  GBRI_TRY(bmalloc(&p->padded, (size_t)cells * 2 * rb, &p->device_bytes));
+  GBRI_TRY(bmalloc(&p->padded, (size_t)cells * rb, &p->device_bytes));
+  GBRI_TRY(bmalloc(&p->spec, (size_t)K * (K / 2 + 1) * 2 * rb, &p->device_bytes));
   GBRI_TRY(bmalloc(&p->grid, (size_t)cells * 2 * rb, &p->device_bytes));
-  GBRI_CHECK_CUDA(cudaMemsetAsync(p->padded, 0, (size_t)cells * 2 * rb, s));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(p->padded, 0, (size_t)cells * rb, s));
 
   // work arrays for the sort
   int32_t *key = nullptr, *counts = nullptr, *err = nullptr, *starts = nullptr;
@@ -534,6 +537,18 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     return set_error(GBRI_ECUFFT, "cufftPlan2d failed");
   }
   p->fft_ok = true;
+  // the padded image is real: the forward transform is real-to-complex (half the work of
+  // C2C); degridding reads the other half through G[-k] = conj(G[k])
+  if (cufftPlan2d(&p->fft_r2c, K, K, p->prec == GBRI_F64 ? CUFFT_D2Z : CUFFT_R2C) != CUFFT_SUCCESS) {
+    cudaFree(meta_cell); cudaFree(perm_cell);
+    return set_error(GBRI_ECUFFT, "cufftPlan2d (real-to-complex) failed");
+  }
+  p->fft_r2c_ok = true;
+  {
+    size_t ws1 = 0, ws2 = 0;
+    if (cufftGetSize(p->fft, &ws1) == CUFFT_SUCCESS && cufftGetSize(p->fft_r2c, &ws2) == CUFFT_SUCCESS)
+      p->device_bytes += (int64_t)(ws1 + ws2);
+  }
 
   auto set_blocks = [&](int bpm_dg, int bpm_gr) {
     // one degridding chunk per warp

@@ -13,7 +13,9 @@ namespace gbri {
 // Degridding (G then W, Sec. 2).  Every warp works alone: it takes whole chunks (one
 // contiguous range of at most kChunk visibilities of one 16 x 16 tile; warps stride
 // over the chunk list) and copies the chunk's tile window ((T + J - 1)^2 grid values)
-// into its private shared-memory window when the tile changes.  The warp walks the
+// into its private shared-memory window when the tile changes.  The grid is the FFT of a
+// real image, held as its half spectrum spec[ky][kx], kx = 0 .. K/2 (row pitch K/2 + 1):
+// a cell with kx > K/2 is read as conj(spec[(K - ky) mod K][K - kx]).  The warp walks the
 // chunk 32 * kRun visibilities at a time, one per lane and kRun in flight per lane
 // (metadata and epilogue loads issued before the window reload, coalesced):
 //   v = w * sum_{t'} wy[t'] sum_t wx[t] win[cy + t'][cx + t]
@@ -22,7 +24,7 @@ namespace gbri {
 // barrier after the table load.  `Epi` consumes (plan position, v).
 template <int J, class Epi>
 __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi::real), J))
-    k_degrid(VisGeom geo, const cplx<typename Epi::real>* __restrict__ grid, Epi epi) {
+    k_degrid(VisGeom geo, const cplx<typename Epi::real>* __restrict__ spec, Epi epi) {
   using R = typename Epi::real;
   using C = cplx<R>;
   using E = typename Epi::SElem;
@@ -34,7 +36,7 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
   const int lane = threadIdx.x & 31;
   C* win = reinterpret_cast<C*>(sw + table_elems(S, J)) + (threadIdx.x >> 5) * (P * kWinPitch);
   copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
-  const int K = geo.K;
+  const int K = geo.K, H = (K >> 1) + 1;
   const E* streams[2] = {Epi::kStreams > 0 ? epi.stream(0) : nullptr, Epi::kStreams > 1 ? epi.stream(1) : nullptr};
   epi.init();  // includes a block barrier: the table is in place after it
   int cur_tile = -1;
@@ -59,7 +61,12 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
         const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
         for (int i = lane; i < P * P; i += 32) {
           const int r = i / P, cc = i - r * P;
-          win[r * kWinPitch + cc] = __ldg(grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K));
+          const int ky = wrapK(oy + r, K), kx = wrapK(ox + cc, K);
+          const bool mirror = kx > (K >> 1);
+          const int sy = mirror ? (ky == 0 ? 0 : K - ky) : ky, sx = mirror ? K - kx : kx;
+          C v = __ldg(spec + (size_t)sy * H + sx);
+          if (mirror) v.y = -v.y;
+          win[r * kWinPitch + cc] = v;
         }
         cur_tile = ch.x;
         __syncwarp();
@@ -208,7 +215,7 @@ template <class Epi>
 int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s) {
   using R = typename Epi::real;
   launch_begin(GBRI_K_DEGRID, s);
-  const cplx<R>* g = p->as<cplx<R>>(p->grid);
+  const cplx<R>* g = p->as<cplx<R>>(p->spec);
   const size_t sm = degrid_smem(p);
   if (p->J == 4) k_degrid<4, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(vis_geom(p), g, epi);
   else k_degrid<6, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(vis_geom(p), g, epi);

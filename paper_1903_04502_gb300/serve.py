@@ -60,7 +60,10 @@ def device_footprint(n_side, M, J=4, n_w=9, oversample=2):
     """Upper estimate of the device bytes a resident job holds (plan, wavelets, solver state)."""
     K = oversample * n_side
     N = n_side * n_side
-    plan = M * (8 + 4 + 8) + M // 2 * 8 + 2 * 8 * K * K + (8 * K * K // 64) + (1 << 20)
+    # padded image 4 K^2, half spectrum 8 K (K/2 + 1), grid 8 K^2, the two cuFFT work areas
+    # (bounded by 16 K^2 together: a plan at K = 4096, M = 2e6, J = 6 measured 534 MB in all
+    # against this formula's 654 MB), tile tables, scalars
+    plan = M * (8 + 4 + 8) + M // 2 * 8 + 20 * K * K + 8 * K + 16 * K * K + (8 * K * K // 64) + (1 << 20)
     plan_build = M * (16 + 4 + 4 + 4 + 8 + 4) + 8 * K * K  # transient during plan creation
     wav = 2 * max(1, n_w - 1) * 4 * N
     solver = M * 8 * 2 + N * 4 * (5 + n_w) + (1 << 20)

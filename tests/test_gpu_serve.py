@@ -50,3 +50,16 @@ def test_served_jobs_match_alone(g):
         xa = s.x().cpu().numpy()
         assert np.linalg.norm(j.result - xa) <= 1e-5 * np.linalg.norm(xa)
         assert j.iters == 60 or j.rel_change < 2e-3
+
+
+@pytest.mark.parametrize("n,M,J", [(256, 100_000, 4), (1024, 1_000_000, 4), (2048, 2_000_000, 6)])
+def test_footprint_estimate_bounds_the_plan(g, n, M, J):
+    """The admission estimate bounds what a plan really holds (its buffers, tile tables and
+    both cuFFT work areas, as the library counts them)."""
+    from paper_1903_04502_gb300 import serve
+    uvw = torch.from_numpy(synth.uv_coverage(M, seed=1, outlier_frac=0.2, weights="uniform")).cuda()
+    plan = g.Plan(uvw, n, J=J)
+    try:
+        assert 0 < plan.device_bytes <= serve.device_footprint(n, M, J, 1)
+    finally:
+        plan.close()
