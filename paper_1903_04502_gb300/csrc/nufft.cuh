@@ -246,10 +246,41 @@ struct EpiPD1 {
     u[pos] = un;
     acc.add(fma_r(un.x, un.x, un.y * un.y));
   }
+  // The l2-ball scalar of the next update, fused: the last block to finish (device-wide
+  // counter, reset by that block) reduces the block partials in block order and stores
+  // c = 1 - min(1, eps / dist), dist = sqrt(sum) / sigma2.  Every block has read the old c
+  // (init) before it counts itself, so the store cannot race with a reader.  Without a
+  // counter (done null) only the partials are written.
+  double* c_out = nullptr;
+  double* dist_out = nullptr;
+  unsigned int* done = nullptr;
+  double eps = 0.0, sigma2d = 1.0;
   __device__ __forceinline__ void finish() {
     __shared__ double sh[40];
+    __shared__ bool last;
     const double v = block_sum(acc.value(), sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    if (done == nullptr) {
+      if (threadIdx.x == 0) partials[blockIdx.x] = v;
+      return;
+    }
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = v;
+      __threadfence();
+      last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double sum = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) sum += __ldcg(partials + i);
+    sum = block_sum(sum, sh);
+    if (threadIdx.x == 0) {
+      const double dist = sqrt(sum) / sigma2d;
+      const double rho = dist > eps ? eps / dist : 1.0;
+      *c_out = 1.0 - rho;
+      *dist_out = dist;
+      *done = 0u;
+    }
   }
 };
 
@@ -471,12 +502,14 @@ struct SrcADMM2L {  // SrcADMM2 with one rho_j per ball
 // ---- launch helpers (defined in the visibility translation units, vis_f32.cu and
 // vis_f64.cu, with explicit instantiations, so that each kernel template is
 // instantiated in exactly one translation unit) --------------------------------
-// Degrids the plan's grid (p->grid) into the epilogue.
+// Degrids the forward FFT (the half spectrum p->spec) into the epilogue.
 template <class Epi>
 int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s);
-// Zeroes p->grid, then grids every visibility into it.
+// Zeroes p->grid (unless the caller has, zeroed = true), then grids every visibility into it.
 template <class Src>
-int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s);
+int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s, bool zeroed = false);
+// Bytes of p->grid.
+inline size_t grid_bytes(const gbri_plan* p) { return (size_t)p->K * p->K * 2 * real_bytes(p->prec); }
 
 // Sets the shared-memory attributes of every visibility kernel of one precision
 // (once per process).

@@ -71,13 +71,19 @@ __global__ void k_ball_scalar_local(const double* __restrict__ partials, int n, 
   }
 }
 
-// PD primal update fused with S^T Z^T Re(.) of the gridded dual.
+// PD primal update fused with S^T Z^T Re(.) of the gridded dual (scaled by *cp, the
+// l2-ball scalar c; 1 with local balls, whose scalars the gridding source applied) and the
+// relative-change reduction: each block writes its FP64 sums of (x+ - x)^2 and x+^2; the
+// last block to finish (device-wide counter, reset by that block) reduces them in block
+// order into sc[SC_REL] = ||x+ - x|| / ||x+|| and sc[SC_XN] = ||x+||.
 template <class R>
 __global__ void k_pd_update(const cplx<R>* __restrict__ grid, const R* __restrict__ corr, const R* __restrict__ psiz,
                             R* __restrict__ x, R* __restrict__ xhat, int n, int K, R tau, R theta,
-                            const double* __restrict__ sc, double* __restrict__ partials) {
+                            const double* __restrict__ cp, double* __restrict__ sc, double* __restrict__ partials,
+                            unsigned int* __restrict__ done) {
   __shared__ double sh[40];
-  const R c = (R)sc[SC_C];
+  __shared__ bool last;
+  const R c = (R)*cp;
   acc_t<R> dd, xx;
   const int total = n * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -97,6 +103,24 @@ __global__ void k_pd_update(const cplx<R>* __restrict__ grid, const R* __restric
   if (threadIdx.x == 0) {
     partials[2 * blockIdx.x] = a;
     partials[2 * blockIdx.x + 1] = b;
+    __threadfence();  // the partials are visible device-wide before the count says so
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sa = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sa += __ldcg(partials + 2 * i);
+    sb += __ldcg(partials + 2 * i + 1);
+  }
+  sa = block_sum(sa, sh);
+  sb = block_sum(sb, sh);
+  if (threadIdx.x == 0) {
+    const double dn = sqrt(sa), xn = sqrt(sb);
+    sc[SC_REL] = xn > 0 ? dn / xn : (dn == 0 ? 0.0 : INFINITY);
+    sc[SC_XN] = xn;
+    *done = 0u;
   }
 }
 
@@ -272,7 +296,8 @@ struct gbri_solver {
   // primal-dual: the wavelet branch of an iteration runs on aux_stream, forked from and
   // joined back to the iteration's stream by the two events
   cudaStream_t aux_stream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_zero = nullptr;
+  unsigned int* done = nullptr;  // last-block counters: [0] degridding (ball scalar), [1] primal-dual update
   // one iteration captured as a CUDA graph and replayed (no host work per kernel)
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -291,10 +316,11 @@ void free_solver(gbri_solver* s) {
   if (s->aux_stream) cudaStreamDestroy(s->aux_stream);
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->ev_zero) cudaEventDestroy(s->ev_zero);
   cudaFree(s->yp); cudaFree(s->u); cudaFree(s->w);
   cudaFree(s->x); cudaFree(s->xhat); cudaFree(s->psiz); cudaFree(s->z1); cudaFree(s->xt); cudaFree(s->zb);
   cudaFree(s->wts);
-  cudaFree(s->partials); cudaFree(s->sc);
+  cudaFree(s->partials); cudaFree(s->sc); cudaFree(s->done);
   cudaFree(s->bstart); cudaFree(s->beps); cudaFree(s->bsc); cudaFree(s->bpart);
   delete s;
 }
@@ -321,6 +347,10 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   if (fork) {
     GBRI_CHECK_CUDA(cudaEventRecord(S->ev_fork, st));
     GBRI_CHECK_CUDA(cudaStreamWaitEvent(sw, S->ev_fork, 0));
+    // the gridding target is free once the previous update has read it: zero it here, off
+    // the measurement branch (which reads the separate half spectrum until the gridding)
+    GBRI_CHECK_CUDA(cudaMemsetAsync(P->grid, 0, grid_bytes(P), sw));
+    GBRI_CHECK_CUDA(cudaEventRecord(S->ev_zero, sw));
   }
   // z1 <- clip(z1 + sigma1 Psi^dagger xhat, gamma)
   GBRI_TRY(psi_adjoint_apply<R>(W, vec<R>(S->xhat), vec<R>(S->z1), DualEpi{1, 1.0, p.sigma1, p.gamma, 1.0, S->wts},
@@ -332,13 +362,13 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   GBRI_TRY(launch_pad<R>(P, vec<R>(S->xhat), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
   if (S->nb == 0) {
-    EpiPD1<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->sc + SC_C, S->partials, (R)p.sigma2, acc_t<R>{}};
+    // (the degridding's last block also stores the ball scalar c of this iteration)
+    EpiPD1<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->sc + SC_C, S->partials, (R)p.sigma2, acc_t<R>{}, (R)0,
+                 S->sc + SC_C, S->sc + SC_DIST, S->done, p.eps, p.sigma2};
     GBRI_TRY(launch_degrid(P, e1, st));
-    launch_begin(GBRI_K_OTHER, st);
-    k_ball_scalar<<<1, 256, 0, st>>>(S->partials, P->degrid_blocks, p.eps, p.sigma2, false, S->sc);
-    GBRI_TRY(launch_end(GBRI_K_OTHER, st));
     // Phi^dagger u (scaled by c in the update)
-    GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st));
+    if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_zero, 0));
+    GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st, fork));
   } else {  // local balls: c_j per ball, applied inside the gridding source
     EpiPD1L<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->bsc, (R)p.sigma2,
                   BallAcc<R>{S->bstart, S->nb, S->bpart, acc_t<R>{}, -1}, (R)0};
@@ -346,7 +376,8 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
     launch_begin(GBRI_K_OTHER, st);
     k_ball_scalar_local<<<S->nb, 256, 0, st>>>(S->bpart, P->degrid_blocks, S->beps, p.sigma2, false, S->bsc);
     GBRI_TRY(launch_end(GBRI_K_OTHER, st));
-    GBRI_TRY(launch_grid(P, SrcScaledL<R>{cvec<R>(S->u), S->bsc, S->bstart, S->nb}, st));
+    if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_zero, 0));
+    GBRI_TRY(launch_grid(P, SrcScaledL<R>{cvec<R>(S->u), S->bsc, S->bstart, S->nb}, st, fork));
   }
   GBRI_TRY(fft_inverse(P, st));
   if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_join, 0));
@@ -354,11 +385,9 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   launch_begin(GBRI_K_UPDATE, st);
   k_pd_update<R><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz),
                                      vec<R>(S->x), vec<R>(S->xhat), n, P->K, (R)p.tau, (R)p.theta,
-                                     S->nb ? S->sc + SC_ONE : S->sc + SC_C, S->partials);
-  GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
-  launch_begin(GBRI_K_OTHER, st);
-  k_rel_change<<<1, 256, 0, st>>>(S->partials, ib, S->sc);
-  return launch_end(GBRI_K_OTHER, st);
+                                     S->nb ? S->sc + SC_ONE : S->sc + SC_C, S->sc, S->partials + S->n_partials,
+                                     S->done + 1);
+  return launch_end(GBRI_K_UPDATE, st);
 }
 
 template <class R>
@@ -608,7 +637,9 @@ int32_t create_solver(gbri_solver* S, const void* d_y, uint32_t flags, cudaStrea
   }
   GBRI_CHECK_CUDA(cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming));
   GBRI_CHECK_CUDA(cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming));
+  GBRI_CHECK_CUDA(cudaEventCreateWithFlags(&S->ev_zero, cudaEventDisableTiming));
   GBRI_TRY(zalloc(&S->partials, (size_t)S->n_partials * 2, st));
+  GBRI_TRY(zalloc(&S->done, 2, st));
   GBRI_TRY(zalloc(&S->sc, SC_N, st));
   GBRI_TRY(zalloc_bytes(&S->yp, (size_t)M * 2 * rb, st));
   GBRI_TRY(zalloc_bytes(&S->u, (size_t)M * 2 * rb, st));

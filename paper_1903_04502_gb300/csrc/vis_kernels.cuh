@@ -223,10 +223,10 @@ int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s) {
 }
 
 template <class Src>
-int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s) {
+int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s, bool zeroed) {
   using R = typename Src::real;
   cplx<R>* g = p->as<cplx<R>>(p->grid);
-  GBRI_CHECK_CUDA(cudaMemsetAsync(g, 0, sizeof(cplx<R>) * (size_t)p->K * p->K, s));
+  if (!zeroed) GBRI_CHECK_CUDA(cudaMemsetAsync(g, 0, sizeof(cplx<R>) * (size_t)p->K * p->K, s));
   if (p->n_gtiles == 0) return GBRI_OK;
   launch_begin(GBRI_K_GRID, s);
   if (p->J == 4) k_grid<4, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(vis_geom(p), g, src);
@@ -275,10 +275,10 @@ int32_t prepare_visibility_kernels() {
   template int32_t launch_degrid<EpiResid<R>>(gbri_plan*, EpiResid<R>, cudaStream_t);         \
   template int32_t launch_degrid<EpiPD1L<R>>(gbri_plan*, EpiPD1L<R>, cudaStream_t);           \
   template int32_t launch_degrid<EpiADMM1L<R>>(gbri_plan*, EpiADMM1L<R>, cudaStream_t);       \
-  template int32_t launch_grid<SrcScaledL<R>>(gbri_plan*, SrcScaledL<R>, cudaStream_t);       \
-  template int32_t launch_grid<SrcADMM2L<R>>(gbri_plan*, SrcADMM2L<R>, cudaStream_t);         \
-  template int32_t launch_grid<SrcPlan<R>>(gbri_plan*, SrcPlan<R>, cudaStream_t);             \
-  template int32_t launch_grid<SrcRaw<R>>(gbri_plan*, SrcRaw<R>, cudaStream_t);               \
-  template int32_t launch_grid<SrcADMM2<R>>(gbri_plan*, SrcADMM2<R>, cudaStream_t);           \
+  template int32_t launch_grid<SrcScaledL<R>>(gbri_plan*, SrcScaledL<R>, cudaStream_t, bool); \
+  template int32_t launch_grid<SrcADMM2L<R>>(gbri_plan*, SrcADMM2L<R>, cudaStream_t, bool);   \
+  template int32_t launch_grid<SrcPlan<R>>(gbri_plan*, SrcPlan<R>, cudaStream_t, bool);       \
+  template int32_t launch_grid<SrcRaw<R>>(gbri_plan*, SrcRaw<R>, cudaStream_t, bool);         \
+  template int32_t launch_grid<SrcADMM2<R>>(gbri_plan*, SrcADMM2<R>, cudaStream_t, bool);     \
   template int32_t prepare_visibility_kernels<R>();                                           \
   }
