@@ -2,6 +2,7 @@
 // Phi^dagger = crop_correct(F^H(grid(y))), visibility reordering and the power
 // method for ||Phi||^2 (Sec. 6.3.1).
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "nufft.cuh"
@@ -11,17 +12,29 @@ namespace gbri {
 namespace {
 
 // Z S: padded[(q - n/2) mod K][(p - n/2) mod K] = corr[p] corr[q] x[q][p] / *d_norm (real;
-// the other cells stay zero from plan creation)
-template <class R>
+// the other cells stay zero from plan creation).  A thread takes V consecutive pixels of
+// one row: V = 4 on the FP32 path when n % 8 == 0 (no group straddles the wrap at column
+// n/2; all vector accesses 16-byte aligned), else V = 1.
+template <class R, int V>
 __global__ void k_pad(const R* __restrict__ x, const R* __restrict__ corr, R* __restrict__ padded, int n,
                       int K, const double* __restrict__ d_norm) {
+  static_assert(V == 1 || (V == 4 && sizeof(R) == 4), "vector path is FP32 only");
   const R s = d_norm ? (R)(1.0 / *d_norm) : (R)1;
-  const int total = n * n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+  const int groups = n * n / V;
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < groups; gi += gridDim.x * blockDim.x) {
+    const int i = gi * V;
     const int q = i / n, p = i - q * n;
     int r = q - n / 2; if (r < 0) r += K;
     int c = p - n / 2; if (c < 0) c += K;
-    padded[(size_t)r * K + c] = x[i] * corr[p] * corr[q] * s;
+    const R cq = corr[q];
+    if constexpr (V == 4) {
+      const float4 x4 = *reinterpret_cast<const float4*>(x + i);
+      const float4 c4 = *reinterpret_cast<const float4*>(corr + p);
+      *reinterpret_cast<float4*>(padded + (size_t)r * K + c) =
+          make_float4(x4.x * c4.x * cq * s, x4.y * c4.y * cq * s, x4.z * c4.z * cq * s, x4.w * c4.w * cq * s);
+    } else {
+      padded[(size_t)r * K + c] = x[i] * corr[p] * cq * s;
+    }
   }
 }
 
@@ -89,9 +102,16 @@ int grid_blocks_for(int64_t n, int threads = 256) {
 
 template <class R>
 int32_t launch_pad(gbri_plan* p, const R* x, const double* d_norm, cudaStream_t s) {
+  const int64_t N = (int64_t)p->n_side * p->n_side;
+  // the vector path also needs x 16-byte aligned (a caller's image may be an offset view)
+  const bool v4 = sizeof(R) == 4 && p->n_side % 8 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
   launch_begin(GBRI_K_PAD, s);
-  k_pad<R><<<grid_blocks_for((int64_t)p->n_side * p->n_side), 256, 0, s>>>(
-      x, p->as<const R>(p->corr), p->as<R>(p->padded), p->n_side, p->K, d_norm);
+  if (v4)
+    k_pad<R, (sizeof(R) == 4 ? 4 : 1)><<<grid_blocks_for(N / 4), 256, 0, s>>>(
+        x, p->as<const R>(p->corr), p->as<R>(p->padded), p->n_side, p->K, d_norm);
+  else
+    k_pad<R, 1><<<grid_blocks_for(N), 256, 0, s>>>(x, p->as<const R>(p->corr), p->as<R>(p->padded), p->n_side,
+                                                   p->K, d_norm);
   return launch_end(GBRI_K_PAD, s);
 }
 

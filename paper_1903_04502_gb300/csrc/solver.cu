@@ -76,27 +76,59 @@ __global__ void k_ball_scalar_local(const double* __restrict__ partials, int n, 
 // relative-change reduction: each block writes its FP64 sums of (x+ - x)^2 and x+^2; the
 // last block to finish (device-wide counter, reset by that block) reduces them in block
 // order into sc[SC_REL] = ||x+ - x|| / ||x+|| and sc[SC_XN] = ||x+||.
-template <class R>
+// A thread takes V consecutive pixels of one row: V = 4 on the FP32 path when n % 8 == 0
+// (a group never straddles the periodic wrap at column n/2, and every vector access is
+// 16-byte aligned), else V = 1.
+template <class R, int V>
 __global__ void k_pd_update(const cplx<R>* __restrict__ grid, const R* __restrict__ corr, const R* __restrict__ psiz,
                             R* __restrict__ x, R* __restrict__ xhat, int n, int K, R tau, R theta,
                             const double* __restrict__ cp, double* __restrict__ sc, double* __restrict__ partials,
                             unsigned int* __restrict__ done) {
+  static_assert(V == 1 || (V == 4 && sizeof(R) == 4), "vector path is FP32 only");
   __shared__ double sh[40];
   __shared__ bool last;
   const R c = (R)*cp;
   acc_t<R> dd, xx;
-  const int total = n * n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+  const int groups = n * n / V;
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < groups; gi += gridDim.x * blockDim.x) {
+    const int i = gi * V;
     const int q = i / n, p = i - q * n;
     int r = q - n / 2; if (r < 0) r += K;
     int cc = p - n / 2; if (cc < 0) cc += K;
-    const R phit = c * corr[p] * corr[q] * grid[(size_t)r * K + cc].x;
-    const R xo = x[i];
-    const R xn = max_r(xo - tau * (psiz[i] + phit), (R)0);
-    xhat[i] = fma_r(theta, xn - xo, xn);
-    x[i] = xn;
-    dd.add((xn - xo) * (xn - xo));
-    xx.add(xn * xn);
+    R gr[V], cr[V], ps[V], xo[V];
+    if constexpr (V == 4) {
+      const float4 g01 = *reinterpret_cast<const float4*>(grid + (size_t)r * K + cc);
+      const float4 g23 = *reinterpret_cast<const float4*>(grid + (size_t)r * K + cc + 2);
+      gr[0] = g01.x; gr[1] = g01.z; gr[2] = g23.x; gr[3] = g23.z;
+      const float4 c4 = *reinterpret_cast<const float4*>(corr + p);
+      cr[0] = c4.x; cr[1] = c4.y; cr[2] = c4.z; cr[3] = c4.w;
+      const float4 p4 = *reinterpret_cast<const float4*>(psiz + i);
+      ps[0] = p4.x; ps[1] = p4.y; ps[2] = p4.z; ps[3] = p4.w;
+      const float4 x4 = *reinterpret_cast<const float4*>(x + i);
+      xo[0] = x4.x; xo[1] = x4.y; xo[2] = x4.z; xo[3] = x4.w;
+    } else {
+      gr[0] = grid[(size_t)r * K + cc].x;
+      cr[0] = corr[p];
+      ps[0] = psiz[i];
+      xo[0] = x[i];
+    }
+    const R cq = corr[q];
+    R xn[V], xh[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const R phit = c * cr[j] * cq * gr[j];
+      xn[j] = max_r(xo[j] - tau * (ps[j] + phit), (R)0);
+      xh[j] = fma_r(theta, xn[j] - xo[j], xn[j]);
+      dd.add((xn[j] - xo[j]) * (xn[j] - xo[j]));
+      xx.add(xn[j] * xn[j]);
+    }
+    if constexpr (V == 4) {
+      *reinterpret_cast<float4*>(xhat + i) = make_float4(xh[0], xh[1], xh[2], xh[3]);
+      *reinterpret_cast<float4*>(x + i) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+    } else {
+      xhat[i] = xh[0];
+      x[i] = xn[0];
+    }
   }
   const double a = block_sum(dd.value(), sh);
   const double b = block_sum(xx.value(), sh);
@@ -381,12 +413,18 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   }
   GBRI_TRY(fft_inverse(P, st));
   if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_join, 0));
-  const int ib = std::min(img_blocks(N), S->n_partials / 2);
+  const bool v4 = sizeof(R) == 4 && n % 8 == 0;
+  const int ib = std::min(img_blocks(v4 ? N / 4 : N), S->n_partials / 2);
+  const double* cp = S->nb ? S->sc + SC_ONE : S->sc + SC_C;
   launch_begin(GBRI_K_UPDATE, st);
-  k_pd_update<R><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz),
-                                     vec<R>(S->x), vec<R>(S->xhat), n, P->K, (R)p.tau, (R)p.theta,
-                                     S->nb ? S->sc + SC_ONE : S->sc + SC_C, S->sc, S->partials + S->n_partials,
-                                     S->done + 1);
+  if (v4)
+    k_pd_update<R, (sizeof(R) == 4 ? 4 : 1)><<<ib, 256, 0, st>>>(
+        P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz), vec<R>(S->x), vec<R>(S->xhat), n,
+        P->K, (R)p.tau, (R)p.theta, cp, S->sc, S->partials + S->n_partials, S->done + 1);
+  else
+    k_pd_update<R, 1><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz),
+                                          vec<R>(S->x), vec<R>(S->xhat), n, P->K, (R)p.tau, (R)p.theta, cp, S->sc,
+                                          S->partials + S->n_partials, S->done + 1);
   return launch_end(GBRI_K_UPDATE, st);
 }
 
