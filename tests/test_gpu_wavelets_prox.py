@@ -29,6 +29,10 @@ def rel(a, b):
     (32, 2, (8, 3, 0)),          # order of the stack is the caller's; filters longer than coarse blocks wrap
     (16, 3, (8,)),
     (256, 4, (1, 8)),
+    (48, 1, (0, 2, 5)),          # one level: the first-level kernels alone; partial 32 x 32 blocks
+    (96, 2, (3, 0, 1)),          # side not a multiple of 32, Dirac in the middle of the stack
+    (40, 3, (0, 4)),
+    (64, 2, (0,)),               # Dirac only
 ])
 def test_psi_adjoint_and_psi_match_oracle(g, n, levels, orders):
     x = synth.normal(n * n, seed=n).reshape(n, n).astype(np.float32)
