@@ -112,10 +112,13 @@ struct AnaSmem {
   R tin[kATile][kATile + 1];
   R trow[kATile][2 * kAB + 1];
 };
+// Row pitch of the column-synthesis output: 16 (mod 32) words, so that the two rows a
+// warp reads in the row synthesis (16 lanes each) fall on disjoint banks.
+constexpr int kTmPitch = 2 * kSK <= 48 ? 48 : 80;
 template <class R>
 struct SynSmem {
   R tc[2 * kSK][2 * kSK + 1];  // [a|d rows][a|d cols]
-  R tm[kSB][2 * kSK + 1];      // after the column synthesis
+  R tm[kSB][kTmPitch];         // after the column synthesis
 };
 
 // One analysis level of one basis with an L-tap filter pair (unrolled), block
@@ -265,19 +268,23 @@ __device__ __forceinline__ void idwt_block(SynSmem<R>& sm, const R* __restrict__
   }
   __syncthreads();
   // column synthesis, two output rows (2p, 2p + 1) per item: both read the same L/2
-  // coefficient rows kq = p + L/2 - 1 - s of the a and d halves
-  for (int idx = threadIdx.x; idx < (kSB / 2) * 2 * KB; idx += blockDim.x) {
-    const int pr = idx / (2 * KB), sc = idx - pr * (2 * KB);
-    R ve = 0, vo = 0;
+  // coefficient rows kq = p + L/2 - 1 - s of the a and d halves.  A warp takes one row
+  // pair p, its lanes consecutive columns (no row straddles a warp).
 #pragma unroll
-    for (int q = 0; q < L / 2; ++q) {
-      const int kq = pr + L / 2 - 1 - q;
-      const R a = sm.tc[kq][sc], d = sm.tc[KB + kq][sc];
-      ve = fma_r(h[2 * q], a, fma_r(g[2 * q], d, ve));
-      vo = fma_r(h[2 * q + 1], a, fma_r(g[2 * q + 1], d, vo));
+  for (int pr = ty; pr < kSB / 2; pr += 8) {
+#pragma unroll
+    for (int sc = tx; sc < 2 * KB; sc += 32) {
+      R ve = 0, vo = 0;
+#pragma unroll
+      for (int q = 0; q < L / 2; ++q) {
+        const int kq = pr + L / 2 - 1 - q;
+        const R a = sm.tc[kq][sc], d = sm.tc[KB + kq][sc];
+        ve = fma_r(h[2 * q], a, fma_r(g[2 * q], d, ve));
+        vo = fma_r(h[2 * q + 1], a, fma_r(g[2 * q + 1], d, vo));
+      }
+      sm.tm[2 * pr][sc] = ve;
+      sm.tm[2 * pr + 1][sc] = vo;
     }
-    sm.tm[2 * pr][sc] = ve;
-    sm.tm[2 * pr + 1][sc] = vo;
   }
   __syncthreads();
   // row synthesis, two output columns per item
