@@ -33,7 +33,7 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernels at the 1024^2 / M = 1e7 workload; set to None
 # whenever a kernel changes after its capture.
-KERNEL_TRAFFIC = {"degrid": 334.73e6, "grid": 217.68e6}
+KERNEL_TRAFFIC = {"degrid": 313.67e6, "grid": 218.20e6}
 
 
 def parse():
@@ -580,7 +580,7 @@ def run_gbri(args):
 
     # roofline of the dominant visibility kernel (algorithmic bytes per launch)
     K = plan.K
-    alg = {"degrid": 32 * M + 8 * K * K,  # meta 8 + u 8 + y 8 read, u 8 written; grid read once
+    alg = {"degrid": 32 * M + 8 * K * (K // 2 + 1),  # meta 8 + u 8 + y 8 read, u 8 written; half spectrum once
            "grid": 16 * M + 8 * K * K}    # meta 8 + u 8 read; grid written once
     dom = max(("degrid", "grid"), key=lambda k: kern.get(k, {}).get("ms_total", 0.0))
     peak, peak_kind = measured_peak()
