@@ -414,7 +414,9 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   GBRI_TRY(fft_inverse(P, st));
   if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_join, 0));
   const bool v4 = sizeof(R) == 4 && n % 8 == 0;
-  const int ib = std::min(img_blocks(v4 ? N / 4 : N), S->n_partials / 2);
+  // two blocks per SM looping over the image: fewer block reductions and counter atomics
+  // than one group per thread (16.5 against 21.2 us per update at 1024^2)
+  const int ib = std::min(std::min(img_blocks(v4 ? N / 4 : N), num_sms() * 2), S->n_partials / 2);
   const double* cp = S->nb ? S->sc + SC_ONE : S->sc + SC_C;
   launch_begin(GBRI_K_UPDATE, st);
   if (v4)
