@@ -59,6 +59,27 @@ def test_phi_and_adjoint_match_oracle(g, n, M, J):
     assert rel(xa, xa_ref) <= TOL
 
 
+@pytest.mark.parametrize("n,os,J,M,prec", [
+    (48, 3, 4, 9_000, "f32"),     # K = 144: not a power of two (half spectrum, mirrored window)
+    (80, 3, 6, 12_001, "f32"),
+    (20, 4, 4, 3_001, "f32"),     # n % 8 == 4: the one-pixel-per-thread pad
+    (36, 4, 6, 5_000, "f64"),
+])
+def test_oversampling_factors_match_oracle(g, n, os, J, M, prec):
+    x, uvw = make(n, M, J, seed=n * os + M)
+    geo = me.Geometry(uvw, n, os, J, 4096)
+    F = g.F64 if prec == "f64" else g.F32
+    tol = 1e-11 if prec == "f64" else TOL
+    dt, ct = (np.float64, np.complex128) if prec == "f64" else (np.float32, np.complex64)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, oversample=os, J=J, S=4096, precision=F)
+    assert plan.K == os * n
+    y = g.phi(plan, torch.from_numpy(x.astype(dt)).cuda()).cpu().numpy()
+    assert rel(y, me.phi(x.astype(np.float64), geo)) <= tol
+    yin = synth.complex_normal(M, seed=5).astype(ct)
+    xa = g.phi_adjoint(plan, torch.from_numpy(yin).cuda()).cpu().numpy()
+    assert rel(xa, me.phi_adjoint(yin.astype(np.complex128), geo)) <= tol
+
+
 def test_plan_order_and_permutation(g):
     n, M = 128, 12_345
     x, uvw = make(n, M)
