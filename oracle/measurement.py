@@ -23,6 +23,12 @@ Readings (the paper is silent on these details):
   Grid cell j lives at column (or row) j mod K.
 * R5 weights: W is a real diagonal; x is real (Sec. 2) so the real adjoint takes
   Re(.) after S^dagger Z^dagger F^dagger.
+* R13 first-order table mode ("linear"; Sec. 8.1 names zeroth- and first-order
+  interpolation of the pre-sampled kernel and uses zeroth order): the coordinate is
+  quantised F times finer than the table step, q = round_half_away(u K S F / 2 pi)
+  (FP64, as in R4 with S F in place of S); the taps are the J cells around
+  floor(q / (S F)), and a tap at table position d = |q - j S F| / F takes
+  table[floor d] + frac(d) (table[floor d + 1] - table[floor d]) (0 beyond the support).
 """
 
 import os
@@ -62,6 +68,22 @@ def tap_weights_table(u, K, J, S, tab):
     return np.mod(cells, K), w
 
 
+def tap_weights_linear(u, K, J, S, tab, F):
+    """Cells and weights of G along one axis, first-order table mode (reading R13)."""
+    SF = int(S) * int(F)
+    kq = quantise(u, K, SF)
+    base = np.floor_divide(kq, SF)
+    t = np.arange(J, dtype=np.int64)
+    cells = base[:, None] - (J // 2) + 1 + t[None, :]
+    dist = np.abs(kq[:, None] - cells * SF)  # table position times F
+    i = dist // F
+    phi = (dist - i * F) / float(F)
+    n = len(tab)
+    t0 = np.where(i < n, tab[np.minimum(i, n - 1)], 0.0)
+    t1 = np.where(i + 1 < n, tab[np.minimum(i + 1, n - 1)], 0.0)
+    return np.mod(cells, K), t0 + phi * (t1 - t0)
+
+
 def tap_weights_exact(u, K, J, beta):
     """Cells and weights of G along one axis with the kernel evaluated exactly (no table)."""
     k = np.asarray(u, dtype=np.float64) * K / (2.0 * np.pi)
@@ -75,7 +97,7 @@ def tap_weights_exact(u, K, J, beta):
 class Geometry:
     """Everything Phi needs besides the image: grid size, kernel, coordinates, weights."""
 
-    def __init__(self, uvw, n_side, oversample=2, J=4, S=4096, beta=None, mode="table"):
+    def __init__(self, uvw, n_side, oversample=2, J=4, S=4096, beta=None, mode="table", F=256):
         uvw = np.asarray(uvw)
         self.n_side = int(n_side)
         self.K = int(oversample) * self.n_side
@@ -92,6 +114,10 @@ class Geometry:
             tab = kb.table(self.J, self.S, self.beta)
             self.cols, self.gx = tap_weights_table(self.u, self.K, self.J, self.S, tab)
             self.rows, self.gy = tap_weights_table(self.v, self.K, self.J, self.S, tab)
+        elif mode == "linear":
+            tab = kb.table(self.J, self.S, self.beta)
+            self.cols, self.gx = tap_weights_linear(self.u, self.K, self.J, self.S, tab, F)
+            self.rows, self.gy = tap_weights_linear(self.v, self.K, self.J, self.S, tab, F)
         elif mode == "exact":
             self.cols, self.gx = tap_weights_exact(self.u, self.K, self.J, self.beta)
             self.rows, self.gy = tap_weights_exact(self.v, self.K, self.J, self.beta)

@@ -48,7 +48,63 @@ def test_table_mode_within_table_step_of_exact(J):
     assert _rel(tb, me.nudft(x, uvw)) <= BAND[J] + 5e-4
 
 
-@pytest.mark.parametrize("mode", ["table", "exact"])
+@pytest.mark.parametrize("J", [4, 6])
+def test_linear_mode_weights_within_interpolation_bound(J):
+    """First-order table (reading R13) against the kernel at the unquantised position.  Away
+    from the support's last table step the error is at most max|g''| / (8 S^2) (linear
+    interpolation) + max|g'| / (2 S F) (coordinate quantised to 1 / (S F) of a cell); in the
+    last step at most the jump of the open support, g(J/2 -) = 1 / I0(beta)."""
+    from oracle import kb
+    K, S, F = 64, 4096, 256
+    beta = kb.default_beta(J)
+    tab = kb.table(J, S, beta)
+    u = np.random.default_rng(1).uniform(-np.pi, np.pi, 100_000)
+    cells, w = me.tap_weights_linear(u, K, J, S, tab, F)
+    k = u * K / (2 * np.pi)
+    ex_cells = np.floor(k).astype(np.int64)[:, None] - J // 2 + 1 + np.arange(J)[None, :]
+    same = (np.mod(ex_cells, K) == cells).all(axis=1)
+    assert same.mean() > 0.999
+    d = np.abs(k[:, None] - ex_cells)[same]
+    err = np.abs(w[same] - kb.kernel(d, J, beta))
+    t = np.linspace(0.0, J / 2 - 1.0 / S, 400_001)
+    g = kb.kernel(t, J, beta)
+    g1 = np.abs(np.diff(g) / np.diff(t)).max()
+    g2 = np.abs(np.diff(g, 2) / np.diff(t)[:-1] ** 2).max()
+    inner = d < J / 2 - 1.0 / S
+    assert err[inner].max() <= 1.01 * (g2 / (8 * S * S) + g1 / (2 * S * F))
+    assert err[~inner].max() <= 1.0 / np.i0(beta) * 1.001
+    # a wrong interpolation direction would miss by about max|g'| / S
+    assert err[inner].max() < 0.01 * g1 / S
+
+
+def test_linear_mode_equals_table_mode_on_samples():
+    """Coordinates on table samples (k S an integer): first order reduces to zeroth order."""
+    from oracle import kb
+    K, S, J = 64, 4096, 4
+    tab = kb.table(J, S, kb.default_beta(J))
+    m = np.random.default_rng(2).integers(-K * S // 2, K * S // 2, 5000)
+    u = m * (2 * np.pi / (K * S))
+    c1, w1 = me.tap_weights_linear(u, K, J, S, tab, 256)
+    c0, w0 = me.tap_weights_table(u, K, J, S, tab)
+    assert (c1 == c0).all()
+    assert np.abs(w1 - w0).max() <= 1e-15
+
+
+@pytest.mark.parametrize("J", [4, 6])
+def test_linear_mode_phi_closer_to_exact_than_table(J):
+    """Phi's error against the exact kernel is dominated by the coordinate quantisation
+    (a shift of at most half a quantisation step): 1 / (2 S) of a cell in table mode,
+    1 / (2 S F) in first-order mode, so the first-order operator is about F times closer."""
+    n = 32
+    x, uvw = _case(n, 400, seed=3)
+    ex = me.phi(x, me.Geometry(uvw, n, 2, J, 4096, mode="exact"))
+    tb = me.phi(x, me.Geometry(uvw, n, 2, J, 4096, mode="table"))
+    ln = me.phi(x, me.Geometry(uvw, n, 2, J, 4096, mode="linear"))
+    assert _rel(ln, ex) <= 1e-6
+    assert _rel(tb, ex) >= 100 * _rel(ln, ex)
+
+
+@pytest.mark.parametrize("mode", ["table", "exact", "linear"])
 @pytest.mark.parametrize("n,J", [(16, 4), (32, 6), (24, 4)])
 def test_adjoint_identity(mode, n, J):
     x, uvw = _case(n, 700, seed=7)
