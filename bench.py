@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=20, help="timed iterations of the batching leg")
     ap.add_argument("--fp64-steps", type=int, default=50,
                     help="timed iterations of the plain FP64 path (0: skip the precision leg)")
+    ap.add_argument("--interp-steps", type=int, default=200,
+                    help="timed iterations of the first-order interpolation leg (0: skip)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: short power method, no end-to-end, operator or CPU legs")
     return ap.parse_args()
@@ -435,6 +437,41 @@ def precision_leg(args, g, cfg, uvw_dev, y, eps, opn, gamma, ms_mixed, stream):
             "note": "both paths from x = 0 with the same data, ||Phi||^2, gamma and eps; CUDA-graph replays"}
 
 
+def interp_leg(args, g, cfg, uvw_dev, y, eps, opn, gamma, ms_zeroth, stream):
+    """The same workload on a first-order plan (kernel taps interpolated linearly between
+    table samples, coordinates quantised 256 times finer): ms per primal-dual iteration
+    (graph replays, CUDA events) and its visibility kernels kernel by kernel."""
+    import torch
+    from paper_1903_04502_gb300 import _lib
+    n, M = cfg["n_side"], cfg["M"]
+    p1 = g.Plan(uvw_dev, n, oversample=cfg["oversample"], J=cfg["J"], S=cfg["S"], interp_order=1)
+    w1 = g.Wavelet(n, cfg["levels"], cfg["db_orders"])
+    s1 = g.Solver(p1, w1, y, eps=eps, op_norm_sq=opn, gamma=gamma)
+    s1.step(3)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s1.step(args.interp_steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms1 = a.elapsed_time(b) / args.interp_steps
+    k = min(args.interp_steps, 50)
+    g.profile_enable(k + 8)
+    s1.step(k)
+    torch.cuda.synchronize()
+    kern = {}
+    for i, name in enumerate(_lib.K_NAMES):
+        tot, cnt = g.profile_read(i)
+        if cnt and name in ("degrid", "grid"):
+            kern[name] = {"ms_avg": tot / cnt, "launches": cnt}
+    g.profile_enable(0)
+    for o in (s1, w1, p1):
+        o.close()
+    return {"first_order_ms_per_step": ms1, "first_order_value": M / (ms1 * 1e-3), "zeroth_order_ms_per_step": ms_zeroth,
+            "first_order_kernels": kern, "steps": args.interp_steps,
+            "note": "same data, ||Phi||^2, gamma and eps; FP32 path; CUDA-graph replays"}
+
+
 def run_huge(args):
     """Precision study at full size (4096^2 image, 8192^2 grid, J = 6, M = 2e9, uv drawn on
     the device): primal-dual iterations of the mixed-precision path and of the plain FP64
@@ -639,6 +676,9 @@ def run_gbri(args):
     precision = None
     if args.fp64_steps > 0:
         precision = precision_leg(args, g, cfg, torch.from_numpy(uvw).to(dev), y, eps, opn, gamma, ms_per, stream)
+    interpolation = None
+    if args.interp_steps > 0:
+        interpolation = interp_leg(args, g, cfg, torch.from_numpy(uvw).to(dev), y, eps, opn, gamma, ms_per, stream)
 
     if ws > 1:
         torch.distributed.barrier()
@@ -673,6 +713,7 @@ def run_gbri(args):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "profiled_region": {"steps": k_prof, "ms_per_step": ms_prof, "launch": "kernel by kernel with events"},
         "clocks": clk, "kernels": kern, "operators": ops, "operator_sweep": sweep, "precision": precision,
+        "interpolation": interpolation,
         "batching": batching,
         "serving": serving,
         "impl": "gbri",

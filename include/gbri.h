@@ -64,7 +64,7 @@ typedef struct gbri_solver gbri_solver;
 /* ---- measurement operator plan (Sec. 2, Eq. 2; Sec. 8.1) ------------------ */
 typedef struct {
   int32_t n_side;            /* image side N_side (image is N_side x N_side); even, >= 16 */
-  int32_t oversample;        /* grid oversampling alpha per axis; K = alpha * N_side (only 2 is tested) */
+  int32_t oversample;        /* grid oversampling alpha per axis, 2..4; K = alpha * N_side must be a multiple of 16 */
   int32_t J;                 /* kernel support in grid cells: 4 or 6 */
   int32_t samples_per_unit;  /* table samples per grid cell S: power of two, 16 <= S <= 4096 */
   double kb_beta;            /* Kaiser-Bessel shape; <= 0 selects 2.34 * J */
@@ -75,6 +75,11 @@ typedef struct {
   int32_t autotune;          /* 1: time the run lengths 8, 16, 64 and the resident blocks per SM of the
                                 visibility kernels at plan creation and keep the fastest (cached per
                                 problem shape for the process); 0: vis_per_run and the occupancy limit */
+  int32_t interp_order;      /* kernel-table interpolation (Sec. 8.1 names zeroth and first order):
+                                0: zeroth order, k~ = round(k S), each tap takes the nearest table
+                                sample; 1: first order, k is quantised 256 S steps per cell and each
+                                tap interpolates linearly between its two table samples (8 bits of
+                                fraction per axis kept beside the metadata: 2 more bytes per visibility) */
   int32_t reserved;          /* must be 0 */
 } gbri_plan_desc;
 

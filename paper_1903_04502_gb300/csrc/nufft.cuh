@@ -42,6 +42,10 @@ constexpr int kMaxRun = 1024;
 // complex-element row pitch of the degridding window and of the gridding accumulators
 // (the plan's bank-slot map uses it)
 constexpr int kWinPitch = 22;
+// First-order interpolation: coordinates are quantised kFracSteps times finer than the
+// table step; the fraction between two table samples is kept in 8 bits per axis.
+constexpr int kLog2FracSteps = 8;
+constexpr int kFracSteps = 1 << kLog2FracSteps;
 
 // Resident blocks per SM the visibility kernels are compiled for (launch bounds) and
 // launched with at most, by element size (4: FP32 path, 8: FP64 path) and support.  An FP32
@@ -82,6 +86,11 @@ struct gbri_plan {
   int64_t layout_bytes = 0;
   int degrid_blocks = 0, grid_blocks = 0;
   int run_len = gbri::kDefaultRun;  // longest run (visibilities of one cell a gridding thread takes)
+  // first-order table interpolation: per visibility the sub-sample fractions of the two
+  // coordinates in 1/kFracSteps of a table step, (fx | fy << 8), plan order; null for zeroth order
+  uint16_t* frac = nullptr;
+  uint16_t* frac_in = nullptr;  // plan creation only: the fractions in the caller's order
+  int interp = 0;               // 0: zeroth-order table, 1: first order
   int autotune = 0;
   template <class T> T* as(void* q) const { return static_cast<T*>(q); }
 };
@@ -118,6 +127,19 @@ __device__ __forceinline__ void load_taps(const R* sw, int f, int S, R (&w)[J]) 
   for (int t = 0; t < J; ++t) w[t] = rev ? v[J - 1 - t] : v[t];
 }
 
+// First-order taps (Sec. 8.1 pre-sampling, first-order interpolation): the position lies
+// phi / kFracSteps of a table step past sample f, so each tap interpolates linearly
+// between rows f and f + 1 (0 <= f < S; row S is row 0 reversed, the next cell's row 0).
+template <int J, class R>
+__device__ __forceinline__ void load_taps_fo(const R* sw, int f, int phi, int S, R (&w)[J]) {
+  R a[J], b[J];
+  load_taps<J>(sw, f, S, a);
+  load_taps<J>(sw, f + 1, S, b);
+  const R t = (R)phi * ((R)1 / (R)kFracSteps);
+#pragma unroll
+  for (int j = 0; j < J; ++j) w[j] = fma_r(t, b[j] - a[j], a[j]);
+}
+
 // elements of the stored tap table (rows 0 .. S/2), rounded up to a multiple of 4
 __host__ __device__ inline int table_elems(int S, int J) { return (((S / 2 + 1) * J) + 3) & ~3; }
 
@@ -135,6 +157,7 @@ struct VisGeom {
   const int2* __restrict__ subruns;
   const int4* __restrict__ gtiles;
   const void* __restrict__ wtab;
+  const uint16_t* __restrict__ frac;  // first-order fractions (null: zeroth order)
   int n_chunks, n_gtiles, K, log2S, nT;
 };
 
@@ -157,6 +180,7 @@ inline VisGeom vis_geom(const gbri_plan* p) {
   g.subruns = p->subruns;
   g.gtiles = p->gtiles;
   g.wtab = p->wtab;
+  g.frac = p->frac;
   g.n_chunks = (int)p->n_chunks;
   g.n_gtiles = (int)p->n_gtiles;
   g.K = p->K;

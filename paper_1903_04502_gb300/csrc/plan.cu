@@ -37,9 +37,13 @@ double kb_ghat(double nu, int J, double beta) {
 
 // Per-visibility quantisation (Sec. 8.1, zeroth order): k~ = round_half_away(u * K S / (2 pi))
 // in FP64, tile-major cell key, tile-local packed coordinates.
-__global__ void k_quantise(const float4* __restrict__ uvw, int64_t M, double scale, int K, int log2S, int nT,
-                           int32_t* __restrict__ key, uint32_t* __restrict__ packed, float* __restrict__ wt,
-                           int32_t* __restrict__ counts, int32_t* __restrict__ err) {
+// lf = 0: zeroth order, q = k~ = round(k S); lf = kLog2FracSteps: first order, q = round(k S F)
+// with F = 2^lf, the table sample floor(q / F) mod S packed like k~ and the fraction q mod F
+// written to frac (caller's order).
+__global__ void k_quantise(const float4* __restrict__ uvw, int64_t M, double scale, int K, int log2S, int lf,
+                           int nT, int32_t* __restrict__ key, uint32_t* __restrict__ packed,
+                           float* __restrict__ wt, uint16_t* __restrict__ frac, int32_t* __restrict__ counts,
+                           int32_t* __restrict__ err) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int S = 1 << log2S;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
@@ -47,24 +51,28 @@ __global__ void k_quantise(const float4* __restrict__ uvw, int64_t M, double sca
     if (!isfinite(r.x) || !isfinite(r.y) || !isfinite(r.w)) {
       atomicOr(err, 1);
       key[i] = 0; packed[i] = 0; wt[i] = 0.f;
+      if (frac) frac[i] = 0;
       continue;
     }
     if (fabsf(r.x) > 50.2654825f || fabsf(r.y) > 50.2654825f) {  // 16 pi
       atomicOr(err, 2);
       key[i] = 0; packed[i] = 0; wt[i] = 0.f;
+      if (frac) frac[i] = 0;
       continue;
     }
-    int q[2];
+    long long q[2];
     const float uv[2] = {r.x, r.y};
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
       const double prod = __dmul_rn((double)uv[a], scale);
       const double rnd = floor(__dadd_rn(fabs(prod), 0.5));
-      q[a] = (int)(prod < 0.0 ? -rnd : rnd);
+      q[a] = (long long)(prod < 0.0 ? -rnd : rnd);
     }
-    // base cells floor(k~ / S) (arithmetic shift = floor for negatives), fraction k~ mod S
-    const int bx = q[0] >> log2S, by = q[1] >> log2S;
-    const int fx = q[0] & (S - 1), fy = q[1] & (S - 1);
+    // base cells floor(q / (S F)) (arithmetic shift = floor for negatives), table sample
+    // floor(q / F) mod S, fraction q mod F
+    const int bx = (int)(q[0] >> (log2S + lf)), by = (int)(q[1] >> (log2S + lf));
+    const int fx = (int)((q[0] >> lf) & (S - 1)), fy = (int)((q[1] >> lf) & (S - 1));
+    if (frac) frac[i] = (uint16_t)((q[0] & ((1 << lf) - 1)) | ((q[1] & ((1 << lf) - 1)) << 8));
     int cx = bx % K; if (cx < 0) cx += K;
     int cy = by % K; if (cy < 0) cy += K;
     const int tx = cx / kTile, ty = cy / kTile;
@@ -158,6 +166,13 @@ __global__ void k_scatter(const int32_t* __restrict__ key, const uint32_t* __res
   }
 }
 
+// out[pos] = in[perm[pos]]
+__global__ void k_gather_u16(const uint16_t* __restrict__ in, const int32_t* __restrict__ perm,
+                             uint16_t* __restrict__ out, int64_t M) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[perm[i]];
+}
+
 // Move every run (consecutive visibilities of one cell) from its cell-sorted place to
 // its place in the run order: one thread per run.
 __global__ void k_relayout(const int2* __restrict__ old_sub, const int32_t* __restrict__ new_start, int64_t n_sub,
@@ -244,6 +259,8 @@ void destroy_plan(gbri_plan* p) {
   if (!p) return;
   cudaFree(p->meta);
   cudaFree(p->perm);
+  cudaFree(p->frac);
+  cudaFree(p->frac_in);
   cudaFree(p->chunks);
   cudaFree(p->subruns);
   cudaFree(p->gtiles);
@@ -379,10 +396,10 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
 // Autotuner results per problem shape (grid size, support, table density, visibility
 // count, non-empty tiles): run length and resident blocks per SM of both kernels.
 struct TuneKey {
-  int K, J, S, prec;
+  int K, J, S, prec, interp;
   int64_t M, tiles;
   bool operator<(const TuneKey& o) const {
-    return std::tie(K, J, S, prec, M, tiles) < std::tie(o.K, o.J, o.S, o.prec, o.M, o.tiles);
+    return std::tie(K, J, S, prec, interp, M, tiles) < std::tie(o.K, o.J, o.S, o.prec, o.interp, o.M, o.tiles);
   }
 };
 std::mutex g_tune_mu;
@@ -456,6 +473,10 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     cudaFree(key); cudaFree(counts); cudaFree(err); cudaFree(packed); cudaFree(wt);
     cudaFree(starts);
   };
+  if (p->interp) {  // caller-order fractions, gathered into plan order after the layout
+    GBRI_TRY(dmalloc(&p->frac_in, (size_t)M, nullptr));
+  }
+  uint16_t* frac_in = p->frac_in;
   if ((st = dmalloc(&key, (size_t)M, nullptr)) || (st = dmalloc(&packed, (size_t)M, nullptr)) ||
       (st = dmalloc(&wt, (size_t)M, nullptr)) || (st = dmalloc(&counts, (size_t)cells, nullptr)) ||
       (st = dmalloc(&offsets, (size_t)cells + 1, &p->device_bytes)) || (st = dmalloc(&err, 1, nullptr)) ||
@@ -465,11 +486,12 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   }
   cudaMemsetAsync(counts, 0, sizeof(int32_t) * cells, s);
   cudaMemsetAsync(err, 0, sizeof(int32_t), s);
-  const double scale = (double)((int64_t)K * S) / (2.0 * M_PI);
+  const int lf = p->interp ? kLog2FracSteps : 0;
+  const double scale = (double)((int64_t)K * S << lf) / (2.0 * M_PI);
   const int vb = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(M, 256), 1), (int64_t)num_sms() * 16);
   launch_begin(GBRI_K_OTHER, s);
-  k_quantise<<<vb, 256, 0, s>>>(reinterpret_cast<const float4*>(d_uvw), M, scale, K, p->log2S, p->nT, key,
-                                packed, wt, counts, err);
+  k_quantise<<<vb, 256, 0, s>>>(reinterpret_cast<const float4*>(d_uvw), M, scale, K, p->log2S, lf, p->nT, key,
+                                packed, wt, frac_in, counts, err);
   st = launch_end(GBRI_K_OTHER, s);
   if (st == GBRI_OK) st = scan_counts(counts, cells, offsets, s);
   int32_t herr = 0;
@@ -559,7 +581,7 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
         (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(p->n_gtiles, kThreads / 32), (int64_t)sms * bpm_gr));
   };
   int best_run = p->run_len, best_dg = lim_dg, best_gr = lim_gr;
-  const TuneKey tkey{K, p->J, S, p->prec, M, p->n_tiles};
+  const TuneKey tkey{K, p->J, S, p->prec, p->interp, M, p->n_tiles};
   bool cached = false;
   if (p->autotune) cached = tune_cache_get(tkey, &best_run, &best_dg, &best_gr);
   if (p->autotune && !cached && M > 0) {
@@ -612,6 +634,18 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   cudaStreamSynchronize(s);
   cudaFree(meta_cell);
   cudaFree(perm_cell);
+  if (st == GBRI_OK && p->interp) {  // first-order fractions into plan order
+    st = dmalloc(&p->frac, (size_t)M, &p->device_bytes);
+    if (st == GBRI_OK && M > 0) {
+      launch_begin(GBRI_K_OTHER, s);
+      k_gather_u16<<<(unsigned)std::min<int64_t>(ceil_div(M, 256), (int64_t)num_sms() * 16), 256, 0, s>>>(
+          p->frac_in, p->perm, p->frac, M);
+      st = launch_end(GBRI_K_OTHER, s);
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(p->frac_in);
+    p->frac_in = nullptr;
+  }
   if (st != GBRI_OK) return st;
   p->run_len = best_run;
   set_blocks(best_dg, best_gr);
@@ -644,6 +678,9 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* 
   const int64_t K = (int64_t)d->oversample * d->n_side;
   GBRI_CHECK(K % kTile == 0, GBRI_EINVAL, "oversample * n_side must be a multiple of 16");
   GBRI_CHECK(K <= 16384, GBRI_EINVAL, "grid larger than 16384^2 is not supported");
+  GBRI_CHECK(d->vis_per_run >= 0 && d->vis_per_run <= kMaxRun, GBRI_EINVAL, "vis_per_run must be in [0, 1024]");
+  GBRI_CHECK(d->autotune == 0 || d->autotune == 1, GBRI_EINVAL, "autotune must be 0 or 1");
+  GBRI_CHECK(d->interp_order == 0 || d->interp_order == 1, GBRI_EINVAL, "interp_order must be 0 or 1");
   gbri_plan* p = new (std::nothrow) gbri_plan();
   GBRI_CHECK(p, GBRI_ENOMEM, "host allocation");
   p->n_side = d->n_side;
@@ -656,9 +693,8 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* 
   p->beta = d->kb_beta > 0 ? d->kb_beta : 2.34 * d->J;
   p->M = d->M;
   p->prec = d->precision;
-  GBRI_CHECK(d->vis_per_run >= 0 && d->vis_per_run <= kMaxRun, GBRI_EINVAL, "vis_per_run must be in [0, 1024]");
-  GBRI_CHECK(d->autotune == 0 || d->autotune == 1, GBRI_EINVAL, "autotune must be 0 or 1");
   p->run_len = d->vis_per_run ? d->vis_per_run : kDefaultRun;
+  p->interp = d->interp_order;
   p->autotune = d->autotune;
   const int32_t st = build_plan(p, d_uvw, (cudaStream_t)stream);
   if (st != GBRI_OK) {

@@ -22,7 +22,7 @@ namespace gbri {
 // with the two J-tap weight rows from the block's shared table.  A cell's visibilities
 // are consecutive, so neighbouring lanes often read the same window words.  No block-wide
 // barrier after the table load.  `Epi` consumes (plan position, v).
-template <int J, class Epi>
+template <int J, bool FO, class Epi>
 __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi::real), J))
     k_degrid(VisGeom geo, const cplx<typename Epi::real>* __restrict__ spec, Epi epi) {
   using R = typename Epi::real;
@@ -46,12 +46,14 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
     epi.begin_chunk(lo);  // warp-uniform
     for (int b0 = 0; b0 < cnt; b0 += 32 * kRun) {
       uint2 m[kRun];
+      uint32_t fr[kRun];
       typename Epi::Pre pre[kRun];
 #pragma unroll
       for (int k = 0; k < kRun; ++k) {
         const int i = b0 + lane + 32 * k;
         if (i < cnt) {
           m[k] = geo.meta[lo + i];
+          if constexpr (FO) fr[k] = geo.frac[lo + i];
           pre[k] = epi.pre_from(streams, lo + i);
         }
       }
@@ -77,8 +79,13 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
         if (i >= cnt) break;
         const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
         R wx[J], wy[J];
-        load_taps<J>(sw, lx & (S - 1), S, wx);
-        load_taps<J>(sw, ly & (S - 1), S, wy);
+        if constexpr (FO) {
+          load_taps_fo<J>(sw, lx & (S - 1), fr[k] & 0xff, S, wx);
+          load_taps_fo<J>(sw, ly & (S - 1), fr[k] >> 8, S, wy);
+        } else {
+          load_taps<J>(sw, lx & (S - 1), S, wx);
+          load_taps<J>(sw, ly & (S - 1), S, wy);
+        }
         const C* base = win + (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
         R ar = 0, ai = 0;
 #pragma unroll
@@ -113,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
 // for the cells no other tile touches, atomics for the border shared with the
 // neighbouring tiles.  No block-wide barrier after the table load.
 // `Src` gives the visibility value at a plan position.
-template <int J, class Src>
+template <int J, bool FO, class Src>
 __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::real), J))
     k_grid(VisGeom geo, cplx<typename Src::real>* __restrict__ grid, Src src) {
   using R = typename Src::real;
@@ -146,11 +153,13 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
       int a0 = 0;
       for (int k0 = 0; k0 < sr.y; k0 += kRun) {
         uint2 m[kRun];
+        uint32_t fr[kRun];
         C v[kRun];
 #pragma unroll
         for (int k = 0; k < kRun; ++k)
           if (k0 + k < sr.y) {
             m[k] = geo.meta[sr.x + k0 + k];
+            if constexpr (FO) fr[k] = geo.frac[sr.x + k0 + k];
             v[k] = src(sr.x + k0 + k, sctx);
           }
         if (k0 == 0) a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S);
@@ -158,8 +167,13 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
         for (int k = 0; k < kRun; ++k) {
           if (k0 + k >= sr.y) break;
           R wx[J], wy[J];
-          load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
-          load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
+          if constexpr (FO) {
+            load_taps_fo<J>(sw, (m[k].x & 0xffff) & (S - 1), fr[k] & 0xff, S, wx);
+            load_taps_fo<J>(sw, (m[k].x >> 16) & (S - 1), fr[k] >> 8, S, wy);
+          } else {
+            load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
+            load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
+          }
           const R w = (R)__uint_as_float(m[k].y);
           const R vr = w * v[k].x, vi = w * v[k].y;
 #pragma unroll
@@ -217,8 +231,14 @@ int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s) {
   launch_begin(GBRI_K_DEGRID, s);
   const cplx<R>* g = p->as<cplx<R>>(p->spec);
   const size_t sm = degrid_smem(p);
-  if (p->J == 4) k_degrid<4, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(vis_geom(p), g, epi);
-  else k_degrid<6, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(vis_geom(p), g, epi);
+  const VisGeom geo = vis_geom(p);
+  if (p->frac) {
+    if (p->J == 4) k_degrid<4, true, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
+    else k_degrid<6, true, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
+  } else {
+    if (p->J == 4) k_degrid<4, false, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
+    else k_degrid<6, false, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
+  }
   return launch_end(GBRI_K_DEGRID, s);
 }
 
@@ -229,8 +249,14 @@ int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s, bool zeroed) {
   if (!zeroed) GBRI_CHECK_CUDA(cudaMemsetAsync(g, 0, sizeof(cplx<R>) * (size_t)p->K * p->K, s));
   if (p->n_gtiles == 0) return GBRI_OK;
   launch_begin(GBRI_K_GRID, s);
-  if (p->J == 4) k_grid<4, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(vis_geom(p), g, src);
-  else k_grid<6, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(vis_geom(p), g, src);
+  const VisGeom geo = vis_geom(p);
+  if (p->frac) {
+    if (p->J == 4) k_grid<4, true, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
+    else k_grid<6, true, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
+  } else {
+    if (p->J == 4) k_grid<4, false, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
+    else k_grid<6, false, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
+  }
   return launch_end(GBRI_K_GRID, s);
 }
 
@@ -245,18 +271,14 @@ int32_t prepare_visibility_kernels() {
     const int lim = 220 * 1024;
     cudaError_t e = cudaSuccess;
 #define GBRI_ATTR(kern) if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-    GBRI_ATTR((k_degrid<4, EpiStorePlan<R>>)); GBRI_ATTR((k_degrid<6, EpiStorePlan<R>>));
-    GBRI_ATTR((k_degrid<4, EpiStoreRaw<R>>)); GBRI_ATTR((k_degrid<6, EpiStoreRaw<R>>));
-    GBRI_ATTR((k_degrid<4, EpiPD1<R>>)); GBRI_ATTR((k_degrid<6, EpiPD1<R>>));
-    GBRI_ATTR((k_degrid<4, EpiADMM1<R>>)); GBRI_ATTR((k_degrid<6, EpiADMM1<R>>));
-    GBRI_ATTR((k_degrid<4, EpiResid<R>>)); GBRI_ATTR((k_degrid<6, EpiResid<R>>));
-    GBRI_ATTR((k_degrid<4, EpiPD1L<R>>)); GBRI_ATTR((k_degrid<6, EpiPD1L<R>>));
-    GBRI_ATTR((k_degrid<4, EpiADMM1L<R>>)); GBRI_ATTR((k_degrid<6, EpiADMM1L<R>>));
-    GBRI_ATTR((k_grid<4, SrcScaledL<R>>)); GBRI_ATTR((k_grid<6, SrcScaledL<R>>));
-    GBRI_ATTR((k_grid<4, SrcADMM2L<R>>)); GBRI_ATTR((k_grid<6, SrcADMM2L<R>>));
-    GBRI_ATTR((k_grid<4, SrcPlan<R>>)); GBRI_ATTR((k_grid<6, SrcPlan<R>>));
-    GBRI_ATTR((k_grid<4, SrcRaw<R>>)); GBRI_ATTR((k_grid<6, SrcRaw<R>>));
-    GBRI_ATTR((k_grid<4, SrcADMM2<R>>)); GBRI_ATTR((k_grid<6, SrcADMM2<R>>));
+#define GBRI_ATTR4(K, T) GBRI_ATTR((K<4, false, T<R>>)); GBRI_ATTR((K<6, false, T<R>>)); \
+                         GBRI_ATTR((K<4, true, T<R>>)); GBRI_ATTR((K<6, true, T<R>>))
+    GBRI_ATTR4(k_degrid, EpiStorePlan); GBRI_ATTR4(k_degrid, EpiStoreRaw); GBRI_ATTR4(k_degrid, EpiPD1);
+    GBRI_ATTR4(k_degrid, EpiADMM1); GBRI_ATTR4(k_degrid, EpiResid); GBRI_ATTR4(k_degrid, EpiPD1L);
+    GBRI_ATTR4(k_degrid, EpiADMM1L);
+    GBRI_ATTR4(k_grid, SrcScaledL); GBRI_ATTR4(k_grid, SrcADMM2L); GBRI_ATTR4(k_grid, SrcPlan);
+    GBRI_ATTR4(k_grid, SrcRaw); GBRI_ATTR4(k_grid, SrcADMM2);
+#undef GBRI_ATTR4
 #undef GBRI_ATTR
     status = (e == cudaSuccess) ? GBRI_OK : cuda_error(e, "cudaFuncSetAttribute");
   });
