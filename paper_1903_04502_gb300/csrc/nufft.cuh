@@ -18,9 +18,12 @@
 //   wtab   [S/2+1][J] R  tap weights by fractional offset f = k~ mod S: entry t is
 //                      table[|f + (J/2 - 1 - t) S|] (Sec. 8.1 zeroth-order table,
 //                      re-indexed so one visibility reads one row per axis).
+//   frac   [M] uint16  first-order plans only: sub-sample fractions (fx | fy << 8) in
+//                      1/256 of a table step, plan order.
 //   corr   [n] R       1 / ghat(p'/K) (the S factor along one axis).
-//   padded [K][K] C    FFT input; zero outside the n x n image block (kept zero).
-//   grid   [K][K] C    FFT output / gridding accumulator.
+//   padded [K][K] R    real FFT input; zero outside the n x n image block (kept zero).
+//   spec   [K][K/2+1] C  its real-to-complex FFT (half spectrum), read by degridding.
+//   grid   [K][K] C    gridding accumulator, inverse FFT in place.
 // R is the plan's real type (float for GBRI_F32, double for GBRI_F64) and C the
 // interleaved complex of R; the visibility order and metadata do not depend on it.
 #pragma once

@@ -8,10 +8,12 @@
 // u = t - sigma2 y, the projection gives z2 = (1 - rho) u with
 // rho = min(1, eps / ||u / sigma2||), so the device keeps u and the scalar
 // c = 1 - rho instead of z2:
-//   degrid epilogue:  u <- c u + sigma2 (Phi xhat - y), partial ||u||^2  (FP64 block sums)
-//   scalar kernel:    c <- 1 - min(1, eps sigma2 / ||u||)
+//   degrid epilogue:  u <- c u + sigma2 (Phi xhat - y), partial ||u||^2  (FP64 block sums);
+//                     its last block: c <- 1 - min(1, eps sigma2 / ||u||)
 //   gridding source:  u (Phi^dagger is linear; c scales the image)
-//   image epilogue:   x+ = max(x - tau (Psi z1 + c Re Phi^dagger u), 0), xhat = x+ + theta (x+ - x)
+//   image epilogue:   x+ = max(x - tau (Psi z1 + c Re Phi^dagger u), 0), xhat = x+ + theta (x+ - x);
+//                     its last block: ||x+ - x|| / ||x+||
+// The wavelet half (z1 and Psi z1) runs on a second stream beside the measurement half.
 //
 // Dual Forward-Backward ADMM (Sec. 5, Algorithm 1), with w = v + s - y, v = Phi x:
 //   r = y + rho_b w, rho_b = min(1, eps / ||w||)  (projection onto the ball around y)
