@@ -250,7 +250,8 @@ int32_t scan_counts(const int32_t* counts, int64_t n, int32_t* offsets, cudaStre
     k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, s>>>(counts, n, sums, offsets);
     st = launch_end(GBRI_K_OTHER, s);
   }
-  cudaStreamSynchronize(s);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (st == GBRI_OK && e != cudaSuccess) st = cuda_error(e, "cudaStreamSynchronize (scan)");
   cudaFree(sums);
   return st;
 }
@@ -371,13 +372,20 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
       cudaFree(dold);
       return st;
     }
-    cudaMemcpyAsync(dold, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(dnew, nstart.data(), nstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    launch_begin(GBRI_K_OTHER, s);
-    k_relayout<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)sub.size(), 256), (int64_t)num_sms() * 16), 256, 0, s>>>(
-        dold, dnew, (int64_t)sub.size(), meta_cell, perm_cell, p->meta, p->perm);
-    st = launch_end(GBRI_K_OTHER, s);
-    cudaStreamSynchronize(s);
+    cudaError_t e = cudaMemcpyAsync(dold, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dnew, nstart.data(), nstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      st = cuda_error(e, "cudaMemcpyAsync (run layout)");
+    } else {
+      launch_begin(GBRI_K_OTHER, s);
+      k_relayout<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)sub.size(), 256), (int64_t)num_sms() * 16), 256, 0,
+                   s>>>(dold, dnew, (int64_t)sub.size(), meta_cell, perm_cell, p->meta, p->perm);
+      st = launch_end(GBRI_K_OTHER, s);
+    }
+    // the host vectors are read by the copies: wait for them before anything goes out of scope
+    e = cudaStreamSynchronize(s);
+    if (st == GBRI_OK && e != cudaSuccess) st = cuda_error(e, "cudaStreamSynchronize (run layout)");
     cudaFree(dold);
     cudaFree(dnew);
     if (st != GBRI_OK) return st;
@@ -484,8 +492,14 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     cleanup();
     return st;
   }
-  cudaMemsetAsync(counts, 0, sizeof(int32_t) * cells, s);
-  cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+  {
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * cells, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_error(e, "cudaMemsetAsync (plan counts)");
+    }
+  }
   const int lf = p->interp ? kLog2FracSteps : 0;
   const double scale = (double)((int64_t)K * S << lf) / (2.0 * M_PI);
   const int vb = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(M, 256), 1), (int64_t)num_sms() * 16);
@@ -504,10 +518,14 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   }
   if (st == GBRI_OK) {
     // cursor = offsets (reuse counts as the cursor array)
-    cudaMemcpyAsync(counts, offsets, sizeof(int32_t) * cells, cudaMemcpyDeviceToDevice, s);
-    launch_begin(GBRI_K_OTHER, s);
-    k_scatter<<<vb, 256, 0, s>>>(key, packed, wt, M, counts, p->meta, p->perm);
-    st = launch_end(GBRI_K_OTHER, s);
+    const cudaError_t e = cudaMemcpyAsync(counts, offsets, sizeof(int32_t) * cells, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+      st = cuda_error(e, "cudaMemcpyAsync (sort cursor)");
+    } else {
+      launch_begin(GBRI_K_OTHER, s);
+      k_scatter<<<vb, 256, 0, s>>>(key, packed, wt, M, counts, p->meta, p->perm);
+      st = launch_end(GBRI_K_OTHER, s);
+    }
   }
   std::vector<int32_t> hst(n_tiles + 1);
   if (st == GBRI_OK) {
@@ -588,30 +606,32 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     // time the plain degridding and gridding kernels for every run length and
     // persistent-grid size, keep the pair with the smallest summed time
     float best = 1e30f;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      st = set_error(GBRI_ECUDA, "cudaEventCreate (autotune)");
     const int runs[3] = {8, 16, 64};
     for (int R : runs) {
+      if (st != GBRI_OK) break;
       st = layout(p, hoff, hst, order, R, meta_cell, perm_cell, s);
       if (st != GBRI_OK) break;
       float tdg[8] = {0}, tgr[8] = {0};
       for (int b = 1; b <= std::max(lim_dg, lim_gr); ++b) {
         set_blocks(std::min(b, lim_dg), std::min(b, lim_gr));
         for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up
+          float ms = 0.f;
           cudaEventRecord(e0, s);
           if (b <= lim_dg) plain_degrid(p, s);
           cudaEventRecord(e1, s);
-          cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
+          cudaError_t e = cudaEventSynchronize(e1);
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
           if (rep) tdg[b] += ms;
           cudaEventRecord(e0, s);
           if (b <= lim_gr) plain_grid(p, s);
           cudaEventRecord(e1, s);
-          cudaEventSynchronize(e1);
-          cudaEventElapsedTime(&ms, e0, e1);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
           if (rep) tgr[b] += ms;
+          if (e != cudaSuccess && st == GBRI_OK) st = cuda_error(e, "autotune timing");
         }
       }
       int bd = 1, bg = 1;
@@ -626,12 +646,15 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
         best_gr = bg;
       }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     if (st == GBRI_OK) tune_cache_put(tkey, best_run, best_dg, best_gr);
   }
   if (st == GBRI_OK) st = layout(p, hoff, hst, order, best_run, meta_cell, perm_cell, s);
-  cudaStreamSynchronize(s);
+  {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (st == GBRI_OK && e != cudaSuccess) st = cuda_error(e, "cudaStreamSynchronize (plan layout)");
+  }
   cudaFree(meta_cell);
   cudaFree(perm_cell);
   if (st == GBRI_OK && p->interp) {  // first-order fractions into plan order
@@ -642,7 +665,8 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
           p->frac_in, p->perm, p->frac, M);
       st = launch_end(GBRI_K_OTHER, s);
     }
-    cudaStreamSynchronize(s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (st == GBRI_OK && e != cudaSuccess) st = cuda_error(e, "cudaStreamSynchronize (fractions)");
     cudaFree(p->frac_in);
     p->frac_in = nullptr;
   }

@@ -885,10 +885,10 @@ int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const void* d_y, const gb
   gbri_solver* S = nullptr;
   GBRI_TRY(gbri_solver_create(&S, plan, wav, d_y, params, flags, stream));
   cudaStream_t st = (cudaStream_t)stream;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, st);
+  // wall time of the solve for the report (best effort: without events it reads 0)
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool timed = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  if (timed) cudaEventRecord(e0, st);
   int32_t rc = GBRI_OK;
   bool converged = false;
   const int every = S->p.check_every;
@@ -909,12 +909,12 @@ int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const void* d_y, const gb
       }
     }
   }
-  cudaEventRecord(e1, st);
+  if (timed) cudaEventRecord(e1, st);
   if (rc == GBRI_OK) rc = gbri_solver_get_x(S, d_x_out, stream);
   if (rc == GBRI_OK) {
-    cudaEventSynchronize(e1);
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    if (timed && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      ms = 0.f;
     S->ms_total = ms;
     gbri_solve_report r{};
     rc = gbri_solver_report(S, &r, stream);
@@ -924,8 +924,8 @@ int32_t gbri_solve(gbri_plan* plan, gbri_wavelet* wav, const void* d_y, const gb
       rc = r.status;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   gbri_solver_destroy(S);
   return rc;
 }
