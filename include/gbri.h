@@ -245,7 +245,12 @@ typedef struct {
 int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav, const void* d_y,
                            const gbri_solve_params* params, uint32_t flags, void* stream);
 int32_t gbri_solver_destroy(gbri_solver* s);
-/* Run n_iter iterations without any host synchronisation. */
+/* Run n_iter iterations without any host synchronisation.  All work is ordered on
+ * `stream`: a primal-dual iteration forks its wavelet half (Psi^dagger with the dual update,
+ * then Psi) onto a solver-owned stream after the previous iteration and joins it back
+ * before the primal update (a graph edge when the iteration is a captured CUDA graph), so
+ * the call returns with every iteration enqueued behind `stream`'s earlier work and ahead
+ * of its later work.  A solver is stepped by one host thread at a time. */
 int32_t gbri_solver_step(gbri_solver* s, int32_t n_iter, void* stream);
 /* Reweighted l1 (SARA's reweighting, Sec. 3.1; the weights' formula follows the SARA
  * paper the text cites): sets per-coefficient weights w_i = delta / (delta + |(Psi^dagger x)_i|)
