@@ -10,7 +10,9 @@
 //                      cell (at most the plan's run length); within a tile listed round by
 //                      round (every cell's first run, then every second one, ...), each
 //                      round padded to a multiple of 32 with empty runs {0, 0}.
-//   gtiles [G] int4    gridding work items, one per non-empty tile: {tile, first run, runs}.
+//   gtiles [G] int4    gridding work items: {tile, first run, runs, split}; one per non-empty
+//                      tile, or several (split = 1) for a tile heavier than twice a warp's
+//                      share of the visibilities.
 //   chunks [C] int4    degridding work items: {tile, first plan position, visibilities
 //                      (<= kChunk), 0}: consecutive visibilities of one tile.
 //   Visibilities are stored in run order: a tile's visibilities are contiguous, and so

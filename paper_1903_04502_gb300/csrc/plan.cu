@@ -302,6 +302,12 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
   std::vector<int4> ch, gt;
   int cnt[NC], nsub[NC];
   int64_t vis_base = 0;  // first plan position of the current tile
+  // A gridding work item is one warp's: a tile heavier than twice a warp's share of the
+  // visibilities (at full occupancy) is cut into items of whole 32-run groups of at most
+  // that weight, which then flush with atomics on every cell (.w = 1); lighter tiles are one
+  // item that writes its interior with plain stores.
+  const int64_t warps = (int64_t)num_sms() * grid_occupancy((int)real_bytes(p->prec), p->J) * (kThreads / 32);
+  const int64_t item_cap = std::max<int64_t>(1024, 2 * ((M + warps - 1) / warps));
   for (int t : order) {
     const int64_t base = (int64_t)t * NC;
     int maxsub = 0;
@@ -342,7 +348,23 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
       while ((sub.size() - first) % 32) sub.push_back(make_int2(0, 0));
     }
     const int64_t nt = (int64_t)sub.size() - first;
-    gt.push_back(make_int4(t, (int)first, (int)nt, 0));
+    const int64_t nv_tile = hst[t + 1] - hst[t];
+    if (nv_tile <= item_cap) {
+      gt.push_back(make_int4(t, (int)first, (int)nt, 0));
+    } else {
+      int64_t g0 = first, w = 0;
+      for (int64_t g = first; g < first + nt; g += 32) {
+        int64_t wg = 0;
+        for (int i = 0; i < 32; ++i) wg += sub[g + i].y;
+        if (w > 0 && w + wg > item_cap) {
+          gt.push_back(make_int4(t, (int)g0, (int)(g - g0), 1));
+          g0 = g;
+          w = 0;
+        }
+        w += wg;
+      }
+      gt.push_back(make_int4(t, (int)g0, (int)(first + nt - g0), 1));
+    }
     const int64_t nv = hst[t + 1] - hst[t];
     const int64_t nch = (nv + kChunk - 1) / kChunk;
     for (int64_t k = 0; k < nch; ++k) {

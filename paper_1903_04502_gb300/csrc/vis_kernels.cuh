@@ -118,7 +118,9 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
 // warp's instructions are ordered, so no atomics are needed.  After the tile the warp
 // writes its accumulator to the global grid (zeroing it for the next tile): plain stores
 // for the cells no other tile touches, atomics for the border shared with the
-// neighbouring tiles.  No block-wide barrier after the table load.
+// neighbouring tiles.  A heavy tile is cut into several items (whole 32-run groups, flag
+// gt.w = 1), whose warps flush every cell with atomics.  No block-wide barrier after the
+// table load.
 // `Src` gives the visibility value at a plan position.
 template <int J, bool FO, class Src>
 __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::real), J))
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
       const C a = *q;
       *q = mkc<R>(0, 0);
       C* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
-      if (r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) {
+      if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) {
         *dst = a;
       } else if (a.x != 0 || a.y != 0) {
         if constexpr (sizeof(R) == 4) {

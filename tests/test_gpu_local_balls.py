@@ -98,6 +98,25 @@ def test_local_balls_match_oracle(g, algo, iters, prec, tol):
     assert rel(s2.x().cpu().numpy().astype(np.float64), x) > 10 * tol
 
 
+def test_local_balls_with_split_tiles(g):
+    """Dense small grid (heavy tiles cut into several gridding items): the per-ball scale in
+    the gridding source is taken per item; PD with 4 balls against the oracle."""
+    nb = 4
+    n, M, orders, L, uvw, ops, y, eps = workload(n=64, M=150_000, orders=(0, 1, 2), L=2, seed=13)
+    idx = ball_partition(uvw, n, nb)
+    balls = [(i, eps * np.sqrt(len(i) / M)) for i in idx]
+    opn, _ = so.power_iteration(ops[0], ops[1], (n, n), max_iter=30)  # passed to both sides
+    gamma = so.default_gamma(y, ops[1], ops[3], opn)
+    y = y.astype(np.complex64).astype(np.complex128)
+    x_ref, _ = so.primal_dual(y, *ops, so.PDParams(gamma=gamma, op_norm_sq=opn, eps=eps, max_iter=30, balls=balls))
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n)
+    wav = g.Wavelet(n, L, orders)
+    s = g.Solver(plan, wav, torch.from_numpy(y.astype(np.complex64)).cuda(), eps=eps, gamma=gamma,
+                 op_norm_sq=opn, n_balls=nb)
+    s.step(30)
+    assert rel(s.x().cpu().numpy().astype(np.float64), x_ref) <= 1e-4
+
+
 def test_local_balls_reach_local_feasibility(g):
     """Converged PD with 8 local balls: every block inside its ball, hence the data inside the
     global ball of radius sqrt(sum eps_j^2) = eps (Sec. 6.8)."""
