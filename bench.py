@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=20, help="timed iterations of the batching leg")
     ap.add_argument("--fp64-steps", type=int, default=50,
                     help="timed iterations of the plain FP64 path (0: skip the precision leg)")
+    ap.add_argument("--algo-steps", type=int, default=100,
+                    help="timed iterations per solver of the algorithms leg (0: skip)")
     ap.add_argument("--interp-steps", type=int, default=200,
                     help="timed iterations of the first-order interpolation leg (0: skip)")
     ap.add_argument("--quick", action="store_true",
@@ -472,6 +474,61 @@ def interp_leg(args, g, cfg, uvw_dev, y, eps, opn, gamma, ms_zeroth, stream):
             "note": "same data, ||Phi||^2, gamma and eps; FP32 path; CUDA-graph replays"}
 
 
+def algorithms_leg(args, g, plan, wav, y, eps, opn, gamma, stream, nw):
+    """The other solvers and options on the same plan and data (graph replays, CUDA events):
+    ms per iteration of Dual-FB ADMM, FISTA (default gamma), primal-dual with 8 local l2
+    balls and primal-dual after one reweighting; and the proximal operators on the
+    workload's vectors (the coefficient stack and the visibilities), us per call."""
+    import torch
+    n, M = plan.n_side, plan.M
+    steps = args.algo_steps
+
+    def per_iter(s):
+        s.step(3)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.step(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    out = {"steps": steps}
+    for name, kw in (("admm", dict(algo=g.ALGO_ADMM, gamma=gamma)), ("fista", dict(algo=g.ALGO_FISTA)),
+                     ("pd_local_balls_8", dict(gamma=gamma, n_balls=8)), ("pd_reweighted", dict(gamma=gamma))):
+        s = g.Solver(plan, wav, y, eps=eps, op_norm_sq=opn, **kw)
+        if name == "pd_reweighted":
+            s.step(10)
+            s.reweight(1e-3)
+        out[name + "_ms_per_iter"] = per_iter(s)
+        s.close()
+
+    def per_call(fn, reps=200):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps * 1e3
+
+    gen = torch.Generator(device=y.device)
+    gen.manual_seed(3)
+    z = torch.randn(nw * n * n, device=y.device, generator=gen)
+    w = torch.rand(nw * n * n, device=y.device, generator=gen)
+    zo = torch.empty_like(z)
+    yo = torch.empty_like(y)
+    c0 = torch.zeros_like(y)
+    out["prox_l1_us"] = per_call(lambda: g.prox_l1(z, 0.1, out=zo))
+    out["prox_l1_weighted_us"] = per_call(lambda: g.prox_l1_weighted(z, w, 0.1, out=zo))
+    out["proj_l2ball_us"] = per_call(lambda: g.proj_l2ball(y, c0, eps, out=yo))
+    out["sizes"] = {"coefficients": nw * n * n, "visibilities": M}
+    return out
+
+
 def run_huge(args):
     """Precision study at full size (4096^2 image, 8192^2 grid, J = 6, M = 2e9, uv drawn on
     the device): primal-dual iterations of the mixed-precision path and of the plain FP64
@@ -676,6 +733,9 @@ def run_gbri(args):
     precision = None
     if args.fp64_steps > 0:
         precision = precision_leg(args, g, cfg, torch.from_numpy(uvw).to(dev), y, eps, opn, gamma, ms_per, stream)
+    algorithms = None
+    if args.algo_steps > 0:
+        algorithms = algorithms_leg(args, g, plan, wav, y, eps, opn, gamma, stream, len(cfg["db_orders"]))
     interpolation = None
     if args.interp_steps > 0:
         interpolation = interp_leg(args, g, cfg, torch.from_numpy(uvw).to(dev), y, eps, opn, gamma, ms_per, stream)
@@ -713,7 +773,7 @@ def run_gbri(args):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "profiled_region": {"steps": k_prof, "ms_per_step": ms_prof, "launch": "kernel by kernel with events"},
         "clocks": clk, "kernels": kern, "operators": ops, "operator_sweep": sweep, "precision": precision,
-        "interpolation": interpolation,
+        "interpolation": interpolation, "algorithms": algorithms,
         "batching": batching,
         "serving": serving,
         "impl": "gbri",
