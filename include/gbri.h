@@ -306,7 +306,8 @@ int32_t gbri_batch_step(gbri_batch* b, int32_t n_iter, void* stream);
 #define GBRI_K_PSI 7
 #define GBRI_K_UPDATE 8
 #define GBRI_K_OTHER 9
-#define GBRI_K_COUNT 10
+#define GBRI_K_DEGRID_GRID 10   /* degridding fused with the gridding of its output */
+#define GBRI_K_COUNT 11
 int32_t gbri_profile_enable(int32_t capacity);
 /* Sum of recorded durations (ms) and number of launches of one kind. Synchronises the device. */
 int32_t gbri_profile_read(int32_t kind, double* total_ms, int64_t* launches);

@@ -18,7 +18,8 @@ F32, F64 = 0, 1
 PLAN_ORDER = 1
 ALGO_PD, ALGO_ADMM, ALGO_FISTA = 0, 1, 2
 K_PAD, K_FFT_FWD, K_DEGRID, K_GRID, K_FFT_INV, K_CROP, K_PSI_ADJ, K_PSI, K_UPDATE, K_OTHER = range(10)
-K_NAMES = ["pad", "fft_fwd", "degrid", "grid", "fft_inv", "crop", "psi_adjoint", "psi", "update", "other"]
+K_NAMES = ["pad", "fft_fwd", "degrid", "grid", "fft_inv", "crop", "psi_adjoint", "psi", "update", "other",
+           "degrid_grid"]
 
 
 class PlanDesc(C.Structure):

@@ -270,11 +270,14 @@ struct EpiPD1 {
   }
   __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i], st[1][i]}; }
-  __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> phi) {
+  // u <- c u + sigma2 (phi - y), stored and returned (the fused degrid + grid pass grids it)
+  __device__ __forceinline__ cplx<R> update(int pos, const Pre& p, cplx<R> phi) {
     const cplx<R> un = mkc<R>(fma_r(cc, p.u.x, sigma2 * (phi.x - p.y.x)), fma_r(cc, p.u.y, sigma2 * (phi.y - p.y.y)));
     u[pos] = un;
     acc.add(fma_r(un.x, un.x, un.y * un.y));
+    return un;
   }
+  __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> phi) { update(pos, p, phi); }
   // The l2-ball scalar of the next update, fused: the last block to finish (device-wide
   // counter, reset by that block) reduces the block partials in block order and stores
   // c = 1 - min(1, eps / dist), dist = sqrt(sum) / sigma2.  Every block has read the old c
@@ -537,6 +540,13 @@ int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s);
 // Zeroes p->grid (unless the caller has, zeroed = true), then grids every visibility into it.
 template <class Src>
 int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s, bool zeroed = false);
+// Degridding with the PD dual update fused with the gridding of the updated u (global
+// ball; J = 4, FP32, zeroth-order plans): zeroes p->grid first unless zeroed.
+int32_t launch_degrid_grid_pd(gbri_plan* p, EpiPD1<float> epi, cudaStream_t s, bool zeroed);
+// Whether launch_degrid_grid_pd applies to the plan.
+inline bool fused_pd_applies(const gbri_plan* p) {
+  return p->J == 4 && p->prec == GBRI_F32 && p->frac == nullptr && p->n_gtiles > 0;
+}
 // Bytes of p->grid.
 inline size_t grid_bytes(const gbri_plan* p) { return (size_t)p->K * p->K * 2 * real_bytes(p->prec); }
 

@@ -399,10 +399,20 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
     // (the degridding's last block also stores the ball scalar c of this iteration)
     EpiPD1<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->sc + SC_C, S->partials, (R)p.sigma2, acc_t<R>{}, (R)0,
                  S->sc + SC_C, S->sc + SC_DIST, S->done, p.eps, p.sigma2};
-    GBRI_TRY(launch_degrid(P, e1, st));
-    // Phi^dagger u (scaled by c in the update)
-    if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_zero, 0));
-    GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st, fork));
+    bool fused = false;
+    if constexpr (sizeof(R) == 4) {
+      if (fused_pd_applies(P)) {  // degridding + gridding of the updated u in one pass
+        if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_zero, 0));
+        GBRI_TRY(launch_degrid_grid_pd(P, e1, st, fork));
+        fused = true;
+      }
+    }
+    if (!fused) {
+      GBRI_TRY(launch_degrid(P, e1, st));
+      // Phi^dagger u (scaled by c in the update)
+      if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_zero, 0));
+      GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st, fork));
+    }
   } else {  // local balls: c_j per ball, applied inside the gridding source
     EpiPD1L<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->bsc, (R)p.sigma2,
                   BallAcc<R>{S->bstart, S->nb, S->bpart, acc_t<R>{}, -1}, (R)0};

@@ -227,6 +227,141 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
   }
 }
 
+// Degridding fused with the gridding of the updated dual (primal-dual iteration, global
+// ball, J = 4, FP32, zeroth order).  One warp per gridding work item (a tile, or a piece of
+// a heavy tile), one lane per run (consecutive visibilities of one cell), as in k_grid.  A
+// lane reads its cell's J x J window block from the warp's window once, then per
+// visibility: the two tap rows (once, for both directions), v = w sum wy sum wx block,
+// u <- c u + sigma2 (v - y) (stored; FP64 partials of ||u||^2), and the gridding patch
+// += w u wy wx.  After the run the patch is added to the warp's accumulator; after the
+// item the accumulator is flushed as in k_grid.  Gridding u as soon as it is updated is
+// valid because Phi^dagger is applied to u itself (c scales the image later), so no global
+// reduction separates the two passes.
+template <int J>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_degrid_grid_pd(VisGeom geo, const float2* __restrict__ spec, float2* __restrict__ grid, EpiPD1<float> epi) {
+  using R = float;
+  using C = float2;
+  using E = EpiPD1<float>::SElem;
+  extern __shared__ float4 smem_dgg[];
+  constexpr int P = kTile + J - 1;
+  constexpr int W = kThreads / 32;
+  R* sw = reinterpret_cast<R*>(smem_dgg);
+  const int S = 1 << geo.log2S;
+  const int lane = threadIdx.x & 31;
+  C* wins = reinterpret_cast<C*>(sw + table_elems(S, J));
+  C* win = wins + (threadIdx.x >> 5) * (P * kWinPitch);
+  C* acc = wins + W * (P * kWinPitch) + (threadIdx.x >> 5) * (P * kAccPitch2);
+  copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
+  for (int i = threadIdx.x; i < W * P * kAccPitch2; i += blockDim.x) wins[W * P * kWinPitch + i] = mkc<R>(0, 0);
+  const int K = geo.K, H = (K >> 1) + 1;
+  const E* streams[2] = {epi.stream(0), epi.stream(1)};
+  epi.init();  // includes a block barrier: table and zeroed accumulators in place
+  constexpr int lo_x = J - 1, hi_x = kTile;
+  for (int it = blockIdx.x * W + (threadIdx.x >> 5); it < geo.n_gtiles; it += gridDim.x * W) {
+    const int4 gt = geo.gtiles[it];
+    const int ty = gt.x / geo.nT, tx = gt.x - ty * geo.nT;
+    const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
+    for (int i = lane; i < P * P; i += 32) {  // the tile's window of the half spectrum
+      const int r = i / P, cc = i - r * P;
+      const int ky = wrapK(oy + r, K), kx = wrapK(ox + cc, K);
+      const bool mirror = kx > (K >> 1);
+      const int sy = mirror ? (ky == 0 ? 0 : K - ky) : ky, sx = mirror ? K - kx : kx;
+      C v = __ldg(spec + (size_t)sy * H + sx);
+      if (mirror) v.y = -v.y;
+      win[r * kWinPitch + cc] = v;
+    }
+    __syncwarp();
+    for (int b0 = 0; b0 < gt.z; b0 += 32) {
+      const int2 sr = geo.subruns[gt.y + b0 + lane];  // gt.z is a multiple of 32
+      const bool active = sr.y > 0;
+      C pt[J][J];
+      C blk[J][J];
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+        for (int t = 0; t < J; ++t) pt[tp][t] = mkc<R>(0, 0);
+      int a0 = 0;
+      for (int k0 = 0; k0 < sr.y; k0 += kRun) {
+        uint2 m[kRun];
+        EpiPD1<float>::Pre pre[kRun];
+#pragma unroll
+        for (int k = 0; k < kRun; ++k)
+          if (k0 + k < sr.y) {
+            m[k] = geo.meta[sr.x + k0 + k];
+            pre[k] = epi.pre_from(streams, sr.x + k0 + k);
+          }
+        if (k0 == 0) {  // the run's cell: its J x J block of the window
+          a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kWinPitch + ((int)(m[0].x & 0xffff) >> geo.log2S);
+#pragma unroll
+          for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+            for (int t = 0; t < J; ++t) blk[tp][t] = win[a0 + tp * kWinPitch + t];
+        }
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) {
+          if (k0 + k >= sr.y) break;
+          R wx[J], wy[J];
+          load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
+          load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
+          R ar = 0, ai = 0;
+#pragma unroll
+          for (int tp = 0; tp < J; ++tp) {
+            R rr = 0, ri = 0;
+#pragma unroll
+            for (int t = 0; t < J; ++t) {
+              rr = fma_r(wx[t], blk[tp][t].x, rr);
+              ri = fma_r(wx[t], blk[tp][t].y, ri);
+            }
+            ar = fma_r(wy[tp], rr, ar);
+            ai = fma_r(wy[tp], ri, ai);
+          }
+          const R w = __uint_as_float(m[k].y);
+          const C un = epi.update(sr.x + k0 + k, pre[k], mkc<R>(w * ar, w * ai));
+          const R vr = w * un.x, vi = w * un.y;
+#pragma unroll
+          for (int tp = 0; tp < J; ++tp) {
+            const R br = wy[tp] * vr, bi = wy[tp] * vi;
+#pragma unroll
+            for (int t = 0; t < J; ++t) {
+              pt[tp][t].x = fma_r(wx[t], br, pt[tp][t].x);
+              pt[tp][t].y = fma_r(wx[t], bi, pt[tp][t].y);
+            }
+          }
+        }
+      }
+      // lanes hold distinct cells within one tap; the warp barrier orders neighbouring patches
+#pragma unroll
+      for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+          if (active) {
+            C* q = acc + a0 + tp * kAccPitch2 + t;
+            const C o = *q;
+            *q = mkc<R>(o.x + pt[tp][t].x, o.y + pt[tp][t].y);
+          }
+          __syncwarp();
+        }
+    }
+    for (int i = lane; i < P * P; i += 32) {
+      const int r = i / P, cc = i - r * P;
+      C* q = acc + r * kAccPitch2 + cc;
+      const C a = *q;
+      *q = mkc<R>(0, 0);
+      C* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) *dst = a;
+      else if (a.x != 0 || a.y != 0) atomicAdd(dst, a);
+    }
+    __syncwarp();  // window and zeroed accumulator visible to every lane before the next item
+  }
+  epi.finish();
+}
+
+inline size_t degrid_grid_smem(const gbri_plan* p) {
+  return (size_t)table_elems(p->S, p->J) * sizeof(float) +
+         (size_t)(kThreads / 32) * (kTile + p->J - 1) * (kWinPitch + kAccPitch2) * sizeof(float2);
+}
+
 template <class Epi>
 int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s) {
   using R = typename Epi::real;
@@ -281,6 +416,7 @@ int32_t prepare_visibility_kernels() {
     GBRI_ATTR4(k_grid, SrcScaledL); GBRI_ATTR4(k_grid, SrcADMM2L); GBRI_ATTR4(k_grid, SrcPlan);
     GBRI_ATTR4(k_grid, SrcRaw); GBRI_ATTR4(k_grid, SrcADMM2);
 #undef GBRI_ATTR4
+    if constexpr (sizeof(R) == 4) GBRI_ATTR((k_degrid_grid_pd<4>));
 #undef GBRI_ATTR
     status = (e == cudaSuccess) ? GBRI_OK : cuda_error(e, "cudaFuncSetAttribute");
   });
