@@ -357,11 +357,14 @@ struct EpiResid {  // r = Phi x - y, partial ||r||^2 (FISTA's gradient residual)
   __device__ __forceinline__ void init() { __syncthreads(); }
   __device__ __forceinline__ void begin_chunk(int) {}
   __device__ __forceinline__ Pre pre_from(const SElem* const* st, int i) const { return Pre{st[0][i]}; }
-  __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> v) {
+  // r = v - y, stored and returned (the fused degrid + grid pass grids it)
+  __device__ __forceinline__ cplx<R> update(int pos, const Pre& p, cplx<R> v) {
     const cplx<R> d = mkc<R>(v.x - p.y.x, v.y - p.y.y);
     r[pos] = d;
     acc.add(fma_r(d.x, d.x, d.y * d.y));
+    return d;
   }
+  __device__ __forceinline__ void store(int pos, const Pre& p, cplx<R> v) { update(pos, p, v); }
   __device__ __forceinline__ void finish() {
     __shared__ double sh[40];
     const double v = block_sum(acc.value(), sh);
@@ -540,10 +543,12 @@ int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s);
 // Zeroes p->grid (unless the caller has, zeroed = true), then grids every visibility into it.
 template <class Src>
 int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s, bool zeroed = false);
-// Degridding with the PD dual update fused with the gridding of the updated u (global
-// ball; J = 4, FP32, zeroth-order plans): zeroes p->grid first unless zeroed.
-int32_t launch_degrid_grid_pd(gbri_plan* p, EpiPD1<float> epi, cudaStream_t s, bool zeroed);
-// Whether launch_degrid_grid_pd applies to the plan.
+// Degridding into an epilogue with an `update` (EpiPD1: the PD dual update; EpiResid: the
+// FISTA residual) fused with the gridding of the values it returns (J = 4, FP32,
+// zeroth-order plans): zeroes p->grid first unless zeroed.
+int32_t launch_degrid_grid(gbri_plan* p, EpiPD1<float> epi, cudaStream_t s, bool zeroed);
+int32_t launch_degrid_grid(gbri_plan* p, EpiResid<float> epi, cudaStream_t s, bool zeroed);
+// Whether launch_degrid_grid applies to the plan.
 inline bool fused_pd_applies(const gbri_plan* p) {
   return p->J == 4 && p->prec == GBRI_F32 && p->frac == nullptr && p->n_gtiles > 0;
 }

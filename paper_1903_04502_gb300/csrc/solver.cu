@@ -403,7 +403,7 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
       if (fused_pd_applies(P)) {  // degridding + gridding of the updated u in one pass
         if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_zero, 0));
-        GBRI_TRY(launch_degrid_grid_pd(P, e1, st, fork));
+        GBRI_TRY(launch_degrid_grid(P, e1, st, fork));
         fused = true;
       }
     }
@@ -498,9 +498,19 @@ int32_t fista_iteration(gbri_solver* S, cudaStream_t st) {
   // r = Phi xhat - y (into u)
   GBRI_TRY(launch_pad<R>(P, vec<R>(S->xhat), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
-  GBRI_TRY(launch_degrid(P, EpiResid<R>{cvec<R>(S->u), cvec<R>(S->yp), S->partials, acc_t<R>{}}, st));
-  // z = xhat - lambda Re Phi^dagger r (into xt); zbar = P_C(z) (into zb)
-  GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st));
+  const EpiResid<R> er{cvec<R>(S->u), cvec<R>(S->yp), S->partials, acc_t<R>{}};
+  bool fused = false;
+  if constexpr (sizeof(R) == 4) {
+    if (fused_pd_applies(P)) {  // degridding + gridding of the residual in one pass
+      GBRI_TRY(launch_degrid_grid(P, er, st, false));
+      fused = true;
+    }
+  }
+  if (!fused) {
+    GBRI_TRY(launch_degrid(P, er, st));
+    // z = xhat - lambda Re Phi^dagger r (into xt); zbar = P_C(z) (into zb)
+    GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st));
+  }
   GBRI_TRY(fft_inverse(P, st));
   const int ib = std::min(img_blocks(N), S->n_partials / 2);
   launch_begin(GBRI_K_UPDATE, st);

@@ -237,12 +237,13 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
 // item the accumulator is flushed as in k_grid.  Gridding u as soon as it is updated is
 // valid because Phi^dagger is applied to u itself (c scales the image later), so no global
 // reduction separates the two passes.
-template <int J>
+template <int J, class Epi>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_degrid_grid_pd(VisGeom geo, const float2* __restrict__ spec, float2* __restrict__ grid, EpiPD1<float> epi) {
+    k_degrid_grid(VisGeom geo, const float2* __restrict__ spec, float2* __restrict__ grid, Epi epi) {
+  static_assert(sizeof(typename Epi::real) == 4, "FP32 path only");
   using R = float;
   using C = float2;
-  using E = EpiPD1<float>::SElem;
+  using E = typename Epi::SElem;
   extern __shared__ float4 smem_dgg[];
   constexpr int P = kTile + J - 1;
   constexpr int W = kThreads / 32;
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   copy_table_to_smem(sw, static_cast<const R*>(geo.wtab), table_elems(S, J));
   for (int i = threadIdx.x; i < W * P * kAccPitch2; i += blockDim.x) wins[W * P * kWinPitch + i] = mkc<R>(0, 0);
   const int K = geo.K, H = (K >> 1) + 1;
-  const E* streams[2] = {epi.stream(0), epi.stream(1)};
+  const E* streams[2] = {Epi::kStreams > 0 ? epi.stream(0) : nullptr, Epi::kStreams > 1 ? epi.stream(1) : nullptr};
   epi.init();  // includes a block barrier: table and zeroed accumulators in place
   constexpr int lo_x = J - 1, hi_x = kTile;
   for (int it = blockIdx.x * W + (threadIdx.x >> 5); it < geo.n_gtiles; it += gridDim.x * W) {
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       int a0 = 0;
       for (int k0 = 0; k0 < sr.y; k0 += kRun) {
         uint2 m[kRun];
-        EpiPD1<float>::Pre pre[kRun];
+        typename Epi::Pre pre[kRun];
 #pragma unroll
         for (int k = 0; k < kRun; ++k)
           if (k0 + k < sr.y) {
@@ -416,7 +417,10 @@ int32_t prepare_visibility_kernels() {
     GBRI_ATTR4(k_grid, SrcScaledL); GBRI_ATTR4(k_grid, SrcADMM2L); GBRI_ATTR4(k_grid, SrcPlan);
     GBRI_ATTR4(k_grid, SrcRaw); GBRI_ATTR4(k_grid, SrcADMM2);
 #undef GBRI_ATTR4
-    if constexpr (sizeof(R) == 4) GBRI_ATTR((k_degrid_grid_pd<4>));
+    if constexpr (sizeof(R) == 4) {
+      GBRI_ATTR((k_degrid_grid<4, EpiPD1<float>>));
+      GBRI_ATTR((k_degrid_grid<4, EpiResid<float>>));
+    }
 #undef GBRI_ATTR
     status = (e == cudaSuccess) ? GBRI_OK : cuda_error(e, "cudaFuncSetAttribute");
   });
