@@ -464,7 +464,7 @@ def interp_leg(args, g, cfg, uvw_dev, y, eps, opn, gamma, ms_zeroth, stream):
     kern = {}
     for i, name in enumerate(_lib.K_NAMES):
         tot, cnt = g.profile_read(i)
-        if cnt and name in ("degrid", "grid"):
+        if cnt and name in ("degrid", "grid", "degrid_grid"):
             kern[name] = {"ms_avg": tot / cnt, "launches": cnt}
     g.profile_enable(0)
     for o in (s1, w1, p1):

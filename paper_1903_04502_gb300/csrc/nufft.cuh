@@ -544,13 +544,13 @@ int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s);
 template <class Src>
 int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s, bool zeroed = false);
 // Degridding into an epilogue with an `update` (EpiPD1: the PD dual update; EpiResid: the
-// FISTA residual) fused with the gridding of the values it returns (J = 4, FP32,
-// zeroth-order plans): zeroes p->grid first unless zeroed.
+// FISTA residual) fused with the gridding of the values it returns (J = 4, FP32 plans of
+// either table order): zeroes p->grid first unless zeroed.
 int32_t launch_degrid_grid(gbri_plan* p, EpiPD1<float> epi, cudaStream_t s, bool zeroed);
 int32_t launch_degrid_grid(gbri_plan* p, EpiResid<float> epi, cudaStream_t s, bool zeroed);
 // Whether launch_degrid_grid applies to the plan.
 inline bool fused_pd_applies(const gbri_plan* p) {
-  return p->J == 4 && p->prec == GBRI_F32 && p->frac == nullptr && p->n_gtiles > 0;
+  return p->J == 4 && p->prec == GBRI_F32 && p->n_gtiles > 0;
 }
 // Bytes of p->grid.
 inline size_t grid_bytes(const gbri_plan* p) { return (size_t)p->K * p->K * 2 * real_bytes(p->prec); }

@@ -14,8 +14,12 @@ int32_t degrid_grid(gbri_plan* p, Epi epi, cudaStream_t s, bool zeroed) {
   const int blocks = (int)std::max<int64_t>(
       1, std::min<int64_t>(ceil_div(p->n_gtiles, kThreads / 32), (int64_t)num_sms() * 2));
   launch_begin(GBRI_K_DEGRID_GRID, s);
-  k_degrid_grid<4, Epi><<<blocks, kThreads, degrid_grid_smem(p), s>>>(vis_geom(p), p->as<const float2>(p->spec), g,
-                                                                       epi);
+  if (p->frac)
+    k_degrid_grid<4, true, Epi><<<blocks, kThreads, degrid_grid_smem(p), s>>>(vis_geom(p), p->as<const float2>(p->spec),
+                                                                             g, epi);
+  else
+    k_degrid_grid<4, false, Epi><<<blocks, kThreads, degrid_grid_smem(p), s>>>(vis_geom(p),
+                                                                              p->as<const float2>(p->spec), g, epi);
   return launch_end(GBRI_K_DEGRID_GRID, s);
 }
 

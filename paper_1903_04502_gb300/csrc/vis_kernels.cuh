@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
 }
 
 // Degridding fused with the gridding of the updated dual (primal-dual iteration, global
-// ball, J = 4, FP32, zeroth order).  One warp per gridding work item (a tile, or a piece of
+// ball; FISTA's residual; J = 4, FP32; FO: first-order table).  One warp per gridding work item (a tile, or a piece of
 // a heavy tile), one lane per run (consecutive visibilities of one cell), as in k_grid.  A
 // lane reads its cell's J x J window block from the warp's window once, then per
 // visibility: the two tap rows (once, for both directions), v = w sum wy sum wx block,
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
 // item the accumulator is flushed as in k_grid.  Gridding u as soon as it is updated is
 // valid because Phi^dagger is applied to u itself (c scales the image later), so no global
 // reduction separates the two passes.
-template <int J, class Epi>
+template <int J, bool FO, class Epi>
 __global__ void __launch_bounds__(kThreads, 2)
     k_degrid_grid(VisGeom geo, const float2* __restrict__ spec, float2* __restrict__ grid, Epi epi) {
   static_assert(sizeof(typename Epi::real) == 4, "FP32 path only");
@@ -285,11 +285,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       int a0 = 0;
       for (int k0 = 0; k0 < sr.y; k0 += kRun) {
         uint2 m[kRun];
+        uint32_t fr[kRun];
         typename Epi::Pre pre[kRun];
 #pragma unroll
         for (int k = 0; k < kRun; ++k)
           if (k0 + k < sr.y) {
             m[k] = geo.meta[sr.x + k0 + k];
+            if constexpr (FO) fr[k] = geo.frac[sr.x + k0 + k];
             pre[k] = epi.pre_from(streams, sr.x + k0 + k);
           }
         if (k0 == 0) {  // the run's cell: its J x J block of the window
@@ -303,8 +305,13 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int k = 0; k < kRun; ++k) {
           if (k0 + k >= sr.y) break;
           R wx[J], wy[J];
-          load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
-          load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
+          if constexpr (FO) {
+            load_taps_fo<J>(sw, (m[k].x & 0xffff) & (S - 1), fr[k] & 0xff, S, wx);
+            load_taps_fo<J>(sw, (m[k].x >> 16) & (S - 1), fr[k] >> 8, S, wy);
+          } else {
+            load_taps<J>(sw, (m[k].x & 0xffff) & (S - 1), S, wx);
+            load_taps<J>(sw, (m[k].x >> 16) & (S - 1), S, wy);
+          }
           R ar = 0, ai = 0;
 #pragma unroll
           for (int tp = 0; tp < J; ++tp) {
@@ -418,8 +425,10 @@ int32_t prepare_visibility_kernels() {
     GBRI_ATTR4(k_grid, SrcRaw); GBRI_ATTR4(k_grid, SrcADMM2);
 #undef GBRI_ATTR4
     if constexpr (sizeof(R) == 4) {
-      GBRI_ATTR((k_degrid_grid<4, EpiPD1<float>>));
-      GBRI_ATTR((k_degrid_grid<4, EpiResid<float>>));
+      GBRI_ATTR((k_degrid_grid<4, false, EpiPD1<float>>));
+      GBRI_ATTR((k_degrid_grid<4, false, EpiResid<float>>));
+      GBRI_ATTR((k_degrid_grid<4, true, EpiPD1<float>>));
+      GBRI_ATTR((k_degrid_grid<4, true, EpiResid<float>>));
     }
 #undef GBRI_ATTR
     status = (e == cudaSuccess) ? GBRI_OK : cuda_error(e, "cudaFuncSetAttribute");
