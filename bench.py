@@ -733,6 +733,27 @@ def run_gbri(args):
     torch.cuda.synchronize()
     ops = {"phi_vis_per_s": M * reps / (a.elapsed_time(b) * 1e-3),
            "phi_adjoint_vis_per_s": M * reps / (b.elapsed_time(c) * 1e-3)}
+    # the standalone degridding and gridding kernels (Phi, Phi^dagger, the power method and
+    # the solvers the fused pass does not cover), kernel by kernel with events; in Phi the
+    # degridding reads the metadata and writes y (16 B per visibility), in Phi^dagger the
+    # gridding reads the metadata and y (16 B)
+    alg_ops = {"degrid": 16 * M + 8 * K * (K // 2 + 1), "grid": 16 * M + 8 * K * K}
+    g.profile_enable(reps + 8)
+    for _ in range(reps):
+        g.phi(plan, xd, yd, plan_order=True)
+        g.phi_adjoint(plan, yd, xo, plan_order=True)
+    torch.cuda.synchronize()
+    standalone = {}
+    for i, name in enumerate(_lib.K_NAMES):
+        if name in ("degrid", "grid"):
+            tot, cnt = g.profile_read(i)
+            if cnt:
+                t = tot / cnt
+                a2 = alg_ops[name] / (t * 1e-3) / 1e9
+                standalone[name] = {"call": "phi" if name == "degrid" else "phi_adjoint", "us": t * 1e3,
+                                    "achieved": a2, "frac": a2 / peak, "algorithmic_bytes": alg_ops[name]}
+    g.profile_enable(0)
+    roof["standalone"] = standalone
     precision = None
     if args.fp64_steps > 0:
         precision = precision_leg(args, g, cfg, torch.from_numpy(uvw).to(dev), y, eps, opn, gamma, ms_per, stream)
