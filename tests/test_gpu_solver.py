@@ -246,6 +246,38 @@ def test_fista_matches_oracle(g, prec, tol):
     assert r["residual_norm"] == pytest.approx(info["residual_norm"], rel=1e-4 if prec == "f32" else 1e-9)
 
 
+@pytest.mark.parametrize("algo", ["fista", "admm"])
+def test_first_order_plan_fista_and_admm_match_oracle(g, algo):
+    """First-order table (reading R13) under the other solvers: FISTA runs the fused degrid +
+    grid pass with its residual epilogue, ADMM the separate kernels with its epilogues; both
+    against the oracle's linear mode."""
+    n, M, orders, L = 64, 8000, (0, 1, 2, 3), 2
+    x_true = synth.sky(n, 4, 2, seed=18)
+    uvw = synth.uv_coverage(M, seed=19, outlier_frac=0.2, weights="uniform")
+    geo = me.Geometry(uvw, n, 2, 4, 4096, mode="linear")
+    ops = (lambda v: me.phi(v, geo), lambda v: me.phi_adjoint(v, geo),
+           lambda a: wv.psi(a, orders, L), lambda v: wv.psi_adjoint(v, orders, L))
+    y0 = ops[0](x_true)
+    sigma = 10 ** (-30 / 20) * np.linalg.norm(y0) / np.sqrt(M)
+    y = (y0 + sigma * synth.complex_normal(M, seed=20)).astype(np.complex64)
+    yd = y.astype(np.complex128)
+    eps = so.epsilon_from_sigma(sigma, M)
+    opn, _ = so.power_iteration(ops[0], ops[1], (n, n))
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, interp_order=1)
+    wav = g.Wavelet(n, L, orders)
+    if algo == "fista":
+        gamma = 1e-3 * float(np.max(np.abs(ops[3](ops[1](yd)))))
+        x_ref, _ = so.fista(yd, *ops, so.FISTAParams(gamma=gamma, lam=1.0 / opn, dualfb_iters=2, max_iter=60))
+        s = g.Solver(plan, wav, torch.from_numpy(y).cuda(), algo=g.ALGO_FISTA, gamma=gamma, op_norm_sq=opn,
+                     rho=1.0 / opn, dualfb_iters=2)
+    else:
+        gamma = so.default_gamma(yd, ops[1], ops[3], opn)
+        x_ref, _ = so.admm(yd, *ops, so.ADMMParams(gamma=gamma, eps=eps, rho=1.0 / opn, max_iter=60))
+        s = g.Solver(plan, wav, torch.from_numpy(y).cuda(), algo=g.ALGO_ADMM, eps=eps, gamma=gamma, op_norm_sq=opn)
+    s.step(60)
+    assert rel(s.x().cpu().numpy().astype(np.float64), x_ref) <= 1e-4
+
+
 def test_fista_default_gamma_and_solve(g):
     n, M, orders, L = 64, 8000, (0, 1, 2), 2
     uvw, geo, ops, y, eps = problem(n, M, orders, L, seed=13)
