@@ -300,3 +300,76 @@ def test_sara_weights():
     assert np.allclose(w, 0.1 / (0.1 + a), rtol=0, atol=0)
     assert np.all(np.diff(w.ravel()[np.argsort(a.ravel())]) <= 0)  # larger coefficients, smaller weights
     assert np.all(so.sara_weights(np.zeros((8, 8)), psit, 0.1) == 1.0)
+
+
+# ---- pins of the parameter rules (gamma, eps, SARA weights) against hand-computed values ----
+
+def test_default_gamma_hand_computed():
+    """gamma = 1e-3 max|Psi^dagger Phi^dagger y| / ||Phi||^2 (reading R8) on cases worked by hand."""
+    # Phi = I (adjoint takes the real part), Psi = Dirac: max|Re y| = 2, ||Phi||^2 = 4
+    y = np.array([0.5, -2.0 + 0.3j, 1.0])
+    ident_t = lambda z: np.real(z)
+    dirac_t = lambda x: x[None]
+    assert so.default_gamma(y, ident_t, dirac_t, 4.0) == pytest.approx(5e-4, rel=1e-15)
+    assert so.default_gamma(y, ident_t, dirac_t, 4.0, factor=0.1) == pytest.approx(0.05, rel=1e-15)
+    # 2 x 2 image, Dirac + Haar (db1) over one level, stack scaled by 1/sqrt(2): the Haar LL
+    # coefficient of [[1, 2], [3, 4]] is (1 + 2 + 3 + 4) / 2 = 5, so max = 5 / sqrt(2);
+    # with ||Phi||^2 = 2: gamma = 1e-3 * 5 / (2 sqrt(2))
+    y4 = np.array([1.0, 2.0, 3.0, 4.0], dtype=complex)
+    g = so.default_gamma(y4, lambda z: np.real(z).reshape(2, 2), lambda v: wv.psi_adjoint(v, (0, 1), 1), 2.0)
+    assert g == pytest.approx(0.0017677669529663686, rel=1e-14)
+
+
+def test_default_gamma_with_brute_force_adjoint():
+    """The dirty image inside gamma is Phi^dagger y: the oracle's gridding adjoint (J = 6) and the
+    adjoint of the brute-force measurement equation (Eq. 1, conjugate exponentials) give the
+    same gamma to the gridding error."""
+    n, M = 16, 300
+    uvw = synth.uv_coverage(M, seed=11, weights="uniform")
+    geo = me.Geometry(uvw, n, 2, 6, 4096)
+    y = synth.complex_normal(M, seed=12)
+    c = np.arange(n, dtype=np.float64) - n // 2
+    u, v, w = (np.asarray(uvw[:, k], dtype=np.float64) for k in (0, 1, 3))
+
+    def brute_adj(z):  # x[q, p] = Re sum_i w_i z_i exp(+i (u_i p' + v_i q'))
+        return np.real(np.einsum("m,mq,mp->qp", w * z, np.exp(1j * v[:, None] * c[None, :]),
+                                 np.exp(1j * u[:, None] * c[None, :])))
+
+    psit = lambda x: wv.psi_adjoint(x, (0, 1, 2), 2)
+    g_grid = so.default_gamma(y, lambda z: me.phi_adjoint(z, geo), psit, 3.0)
+    g_brute = so.default_gamma(y, brute_adj, psit, 3.0)
+    assert g_grid == pytest.approx(g_brute, rel=1e-3)
+
+
+def test_epsilon_from_sigma_chi_square_rule():
+    """eps^2 / sigma^2 = mean + 2 std of ||n||^2 / sigma^2 for n_i ~ CN(0, sigma^2): that ratio is
+    chi^2 with 2M degrees of freedom halved (scipy's moments); a hand value; and a Monte-Carlo
+    draw of the synthetic noise covers eps with the chi-square probability."""
+    from scipy.stats import chi2
+    for M in (1, 100, 20_000, 10_000_000):
+        d = chi2(2 * M)
+        ref = 0.7 * np.sqrt(d.mean() / 2 + 2 * d.std() / 2)
+        assert so.epsilon_from_sigma(0.7, M) == pytest.approx(ref, rel=1e-13)
+    assert so.epsilon_from_sigma(0.5, 100) == pytest.approx(0.5 * np.sqrt(120.0), rel=1e-15)  # 5.4772...
+    M, draws, sigma = 400, 4000, 0.3
+    n = sigma * synth.complex_normal(M * draws, seed=9).reshape(draws, M)
+    sq = np.sum(np.abs(n) ** 2, axis=1)
+    assert np.mean(sq) == pytest.approx(M * sigma ** 2, rel=0.01)
+    assert np.std(sq) == pytest.approx(np.sqrt(M) * sigma ** 2, rel=0.05)
+    covered = np.mean(np.sqrt(sq) <= so.epsilon_from_sigma(sigma, M))
+    p = chi2.cdf(2 * M + 4 * np.sqrt(M), 2 * M)  # about 0.977
+    assert abs(covered - p) < 0.012  # 5 binomial standard deviations
+
+
+def test_sara_weights_hand_computed():
+    """w = delta / (delta + |Psi^dagger x|) on [[1, 2], [3, 4]] with Dirac + Haar over one level
+    (stack scaled by 1/sqrt(2)), delta = 1/2.  Coefficients: Dirac x / sqrt(2); Haar LL 5, HL -1,
+    LH -2, HH 0, over sqrt(2).  So the weights are 1 / (1 + sqrt(2) |c sqrt(2)|) by hand."""
+    x = np.array([[1.0, 2.0], [3.0, 4.0]])
+    w = so.sara_weights(x, lambda v: wv.psi_adjoint(v, (0, 1), 1), 0.5)
+    r2 = np.sqrt(2.0)
+    expect = np.array([[[r2 - 1, 1 / (1 + 2 * r2)], [1 / (1 + 3 * r2), 1 / (1 + 4 * r2)]],
+                       [[1 / (1 + 5 * r2), r2 - 1], [1 / (1 + 2 * r2), 1.0]]])
+    assert np.allclose(w, expect, rtol=1e-13, atol=1e-15)
+    assert expect[0, 0, 0] == pytest.approx(0.4142135623730951, rel=1e-15)
+    assert expect[1, 0, 0] == pytest.approx(0.12389934309929541, rel=1e-15)
