@@ -180,8 +180,11 @@ int32_t gbri_proj_l2ball(const void* d_z, const void* d_center, void* d_out, int
  * handler, a loop that must not synchronise).  No cudaMalloc or cudaFree is made.
  *  - The array lives on every GPU that loads the library until the process exits.
  *  - The first call on a device resolves the array's device address for that device
- *    (cudaGetSymbolAddress, with the device current); make that first call before
- *    any stream capture.
+ *    (cudaGetSymbolAddress, with the device current) and caches it; make that first
+ *    call before any stream capture.  The cached address belongs to the device's
+ *    primary context: after cudaDeviceReset on that device it is stale, so do not
+ *    call this entry point on that device again in the same process.
+ *  - The number of reduction blocks follows the SM count of the current device.
  *  - Every call shares the one array: calls that overlap on the GPU (different
  *    streams, or devices sharing nothing but the same call in flight) race.  Each
  *    call writes every scratch entry it reads, so nothing needs clearing.
@@ -218,7 +221,7 @@ typedef struct {
   int32_t check_every;   /* host reads the convergence test every k iterations (0 selects 10) */
   uint64_t seed;         /* power-method start vector seed */
   int32_t n_balls;       /* PD / ADMM fidelity constraint: 0 or 1 = the global l2 ball of radius eps;
-                            2..64 = local l2 balls (Sec. 6.8): the plan order is cut at tile boundaries
+                            2..64 = local l2 balls (Sec. 6.9): the plan order is cut at tile boundaries
                             into n_balls consecutive ranges -- walking the non-empty tiles in plan order
                             with cumulative visibility count C, ball j (< n_balls - 1) ends after the
                             first tile at which C * n_balls >= (j + 1) * M (at most one ball ends per

@@ -24,7 +24,7 @@ Problem (Sec. 3.1, analysis form; Sec. 5):
   Forward-Backward function of Algorithm 1 with threshold lambda * gamma (reading
   R11: the paper's 1 / (2 sigma^2) data weight is folded into gamma).
 
-Local fidelity constraints (Sec. 6.8, local l2 balls): with ``balls`` = [(idx_j, eps_j)]
+Local fidelity constraints (Sec. 6.9, local l2 balls): with ``balls`` = [(idx_j, eps_j)]
 (a partition of the visibilities) the single constraint ||y - Phi x|| <= eps becomes
 ||y_j - Phi_j x|| <= eps_j for every block j, and every projection onto the l2 ball is
 the product of the per-block projections (``proj_balls``).  ``balls`` = None is the
@@ -90,7 +90,7 @@ def power_iteration(phi, phi_adj, shape, seed=0, max_iter=200, tol=1e-8, b0=None
 
 def proj_balls(z, y, eps, balls):
     """Projection onto the global l2 ball of radius eps around y (balls None) or onto the
-    product of the local balls {||z_j - y_j|| <= eps_j} (Sec. 6.8)."""
+    product of the local balls {||z_j - y_j|| <= eps_j} (Sec. 6.9)."""
     if balls is None:
         return prox.proj_l2ball(z, y, eps)[0]
     out = np.array(z, dtype=np.complex128, copy=True)

@@ -257,14 +257,14 @@ def proj_l2ball(z, center, eps, out=None, norm_out=None, stream=None):
     return out
 
 
-def proj_l2ball_noalloc(z, center, eps, out=None, norm_out=None, stream=None):
+def proj_l2ball_noalloc(z, center, eps, out, norm_out=None, stream=None):
     """Allocation-free projection onto the l2 ball (gbri_proj_l2ball_noalloc): same result as
     ``proj_l2ball``, with the reduction scratch in a fixed device array inside the library, for
-    callers that cannot allocate device memory at that point.  Concurrent calls race."""
+    callers that cannot allocate device memory at that point.  ``out`` is required (it may be
+    ``z`` itself): this wrapper allocates nothing, so the caller provides every buffer.
+    Concurrent calls race."""
     _need(z, torch.complex64, name="z")
     _need(center, torch.complex64, tuple(z.shape), "center")
-    if out is None:
-        out = torch.empty_like(z)
     _need(out, torch.complex64, tuple(z.shape), "out")
     if norm_out is not None:
         _need(norm_out, torch.float64, (1,), "norm_out")

@@ -46,8 +46,10 @@ __global__ void k_l2dist_partials(const cplx<R>* __restrict__ z, const cplx<R>* 
   if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
+// z and out may be the same vector (in-place projection): neither is declared __restrict__;
+// each thread reads element i of z and c before it writes element i of out.
 template <class R>
-__global__ void k_l2ball_apply(const cplx<R>* __restrict__ z, const cplx<R>* __restrict__ c, cplx<R>* __restrict__ out,
+__global__ void k_l2ball_apply(const cplx<R>* z, const cplx<R>* __restrict__ c, cplx<R>* out,
                                int64_t M, double eps, const double* __restrict__ partials, int n_partials,
                                double* __restrict__ norm_out) {
   __shared__ double sh[40];

@@ -1,5 +1,6 @@
 // Library runtime: thread-local error messages, the launch counter and the
 // optional per-kernel-kind CUDA-event timing used by the benchmark.
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -82,12 +83,21 @@ int64_t launch_counter() {
 }
 
 int num_sms() {
-  static int n = 0;
+  // cached per device ordinal: a host may hold GPUs with different SM counts
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  if (dev >= kMaxDev) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }
+  int n = cache[dev].load(std::memory_order_relaxed);
   if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (n <= 0) n = 1;
+    cache[dev].store(n, std::memory_order_relaxed);
   }
   return n;
 }

@@ -1,4 +1,4 @@
-"""Local l2-ball constraints (Sec. 6.8) on the GPU against the oracle.
+"""Local l2-ball constraints (Sec. 6.9) on the GPU against the oracle.
 
 The library cuts its plan order at tile boundaries into n_balls ranges (rule in
 include/gbri.h); the test derives the same partition independently from the oracle's
@@ -119,7 +119,7 @@ def test_local_balls_with_split_tiles(g):
 
 def test_local_balls_reach_local_feasibility(g):
     """Converged PD with 8 local balls: every block inside its ball, hence the data inside the
-    global ball of radius sqrt(sum eps_j^2) = eps (Sec. 6.8)."""
+    global ball of radius sqrt(sum eps_j^2) = eps (Sec. 6.9)."""
     nb = 8
     n, M, orders, L, uvw, ops, y, eps = workload(n=64, M=8000, orders=(0, 1, 2), L=2, seed=5)
     idx = ball_partition(uvw, n, nb)

@@ -205,7 +205,7 @@ def test_fista_with_sara_dictionary_approaches_the_minimiser():
 def test_local_balls_identity_operator_closed_form_and_global_feasibility():
     """Phi = I, Psi = Dirac, the visibilities split into blocks: the problem separates, each block
     has the closed form max(y_j - lam_j, 0) for its own radius eps_j; the local solution also lies
-    in the global ball of radius sqrt(sum eps_j^2) (Sec. 6.8).  One block is the global ball."""
+    in the global ball of radius sqrt(sum eps_j^2) (Sec. 6.9).  One block is the global ball."""
     y = np.abs(synth.normal(240, seed=11)) + 0.1  # positive data: every block's constraint is feasible
     idx = np.array_split(np.random.default_rng(3).permutation(240), 4)
     eps_j = [0.5 * np.linalg.norm(y[i]) for i in idx]
