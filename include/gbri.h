@@ -102,6 +102,15 @@ int32_t gbri_plan_destroy(gbri_plan* plan);
 int32_t gbri_plan_launch_config(const gbri_plan* plan, int32_t* vis_per_run, int32_t* degrid_blocks,
                                 int32_t* grid_blocks);
 
+/* How the plan's visibility kernels get the Kaiser-Bessel tap weights (Sec. 8.1):
+ * 0 = the zeroth-order pre-sampled table in shared memory; 1 = first-order interpolation
+ * between table samples (interp_order = 1); 2 = FP32 zeroth-order plans: a polynomial fit of
+ * the kernel on each unit segment of its support, evaluated at the same quantised positions
+ * the table is sampled at (the table's weights to within 3e-7; chosen when the fit reaches
+ * that bound, which it does for J = 4 and 6 with the default beta; the environment variable
+ * GBRI_TAP_TABLE=1 at plan creation keeps the table instead).  Errors: EINVAL (null). */
+int32_t gbri_plan_tap_mode(const gbri_plan* plan, int32_t* mode);
+
 /* Plan facts: K, M, number of non-empty 16 x 16 grid tiles, device bytes held. Any pointer may be NULL. */
 int32_t gbri_plan_info(const gbri_plan* plan, int64_t* K, int64_t* M, int64_t* n_tiles,
                        int64_t* device_bytes);

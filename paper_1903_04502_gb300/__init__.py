@@ -103,6 +103,12 @@ class Plan:
         _lib.check(_lib.load().gbri_plan_launch_config(self._h, C.byref(r), C.byref(d), C.byref(g_)))
         return r.value, d.value, g_.value
 
+    def tap_mode(self):
+        """0: shared-memory table, 1: first-order table, 2: polynomial taps (gbri_plan_tap_mode)."""
+        m = C.c_int32()
+        _lib.check(_lib.load().gbri_plan_tap_mode(self._h, C.byref(m)))
+        return m.value
+
     def permutation(self, stream=None):
         out = torch.empty(self.M, dtype=torch.int32, device=self.device)
         _lib.check(_lib.load().gbri_plan_permutation(self._h, _ptr(out), _stream(stream)))

@@ -52,6 +52,25 @@ constexpr int kWinPitch = 22;
 constexpr int kLog2FracSteps = 8;
 constexpr int kFracSteps = 1 << kLog2FracSteps;
 
+// How a visibility kernel gets its tap weights:
+//   kTapTable: zeroth-order pre-sampled table in shared memory (Sec. 8.1);
+//   kTapFO:    first-order interpolation between two table rows (Sec. 8.1, reading R13);
+//   kTapPoly:  the kernel g on each unit segment [k, k + 1] of its support as a polynomial
+//              fitted at plan time (FP32 plans, zeroth-order positions), evaluated in
+//              registers at the same quantised positions the table is sampled at, so the
+//              weights equal the table's to FP32 rounding.  It replaces the table's random
+//              shared-memory rows (the pipe the visibility kernels are bound by) with FMAs.
+enum TapMode { kTapTable = 0, kTapFO = 1, kTapPoly = 2 };
+
+// Polynomial taps: on segment k (distance s in [k, k + 1] from the tap's cell) and with
+// z = 2 (s - k) - 1 in [-1, 1], g = P_k(z) = E_k(z^2) + z O_k(z^2), E_k and O_k of degree
+// kPolyHalf - 1 (P_k of degree 2 kPolyHalf - 1).
+constexpr int kPolyHalf = 5;
+struct PolyTaps {
+  float e[3][kPolyHalf];  // even part of segment k, coefficient of (z^2)^i
+  float o[3][kPolyHalf];  // odd part
+};
+
 // Resident blocks per SM the visibility kernels are compiled for (launch bounds) and
 // launched with at most, by element size (4: FP32 path, 8: FP64 path) and support.  An FP32
 // degridding block (kernel table + eight windows) takes about 60 KB of shared memory at
@@ -96,6 +115,11 @@ struct gbri_plan {
   uint16_t* frac = nullptr;
   uint16_t* frac_in = nullptr;  // plan creation only: the fractions in the caller's order
   int interp = 0;               // 0: zeroth-order table, 1: first order
+  int tap_mode = gbri::kTapTable;  // how the visibility kernels get their tap weights
+  gbri::PolyTaps poly{};        // kTapPoly coefficients
+  // work counters of the kTapPoly kernels, a pair {next item, finished blocks} per kernel
+  // (degridding, gridding, fused); zero between launches
+  unsigned int* work = nullptr;
   int autotune = 0;
   template <class T> T* as(void* q) const { return static_cast<T*>(q); }
 };
@@ -164,18 +188,22 @@ struct VisGeom {
   const void* __restrict__ wtab;
   const uint16_t* __restrict__ frac;  // first-order fractions (null: zeroth order)
   int n_chunks, n_gtiles, K, log2S, nT;
+  PolyTaps poly;                       // kTapPoly coefficients (kernel parameter space)
 };
 
+// shared-memory elements of the tap table a kernel of tap mode tm holds (none for kTapPoly)
+inline int smem_table_elems(int tm, int S, int J) { return tm == kTapPoly ? 0 : table_elems(S, J); }
 inline size_t degrid_smem(const gbri_plan* p) {  // the tap table and one window per warp
   const size_t rb = real_bytes(p->prec);
-  return (size_t)table_elems(p->S, p->J) * rb + (size_t)(kThreads / 32) * (kTile + p->J - 1) * kWinPitch * 2 * rb;
+  return (size_t)smem_table_elems(p->tap_mode, p->S, p->J) * rb +
+         (size_t)(kThreads / 32) * (kTile + p->J - 1) * kWinPitch * 2 * rb;
 }
 // warp-private gridding accumulators: complex cells, row pitch kAccPitch2 (>= T + J - 1)
 constexpr int kAccPitch2 = kWinPitch;
 inline size_t grid_smem(const gbri_plan* p) {
   const size_t rb = real_bytes(p->prec);
   const int P = kTile + p->J - 1;
-  return (size_t)table_elems(p->S, p->J) * rb + (size_t)(kThreads / 32) * P * kAccPitch2 * 2 * rb;
+  return (size_t)smem_table_elems(p->tap_mode, p->S, p->J) * rb + (size_t)(kThreads / 32) * P * kAccPitch2 * 2 * rb;
 }
 
 inline VisGeom vis_geom(const gbri_plan* p) {
@@ -191,6 +219,7 @@ inline VisGeom vis_geom(const gbri_plan* p) {
   g.K = p->K;
   g.log2S = p->log2S;
   g.nT = p->nT;
+  g.poly = p->poly;
   return g;
 }
 
@@ -391,7 +420,7 @@ struct SrcADMM2 {  // s+ = s + varrho((1 - rho_b) w - s); source q = (1 - rho_b)
   }
 };
 
-// ---- local l2 balls (Sec. 6.8) ----------------------------------------------------
+// ---- local l2 balls (Sec. 6.9) ----------------------------------------------------
 // Ball j holds the plan positions [bstart[j], bstart[j + 1]) (whole tiles, so that a
 // degridding chunk and a gridding tile lie in one ball).
 constexpr int kMaxBalls = 64;
@@ -543,6 +572,12 @@ int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s);
 // Zeroes p->grid (unless the caller has, zeroed = true), then grids every visibility into it.
 template <class Src>
 int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s, bool zeroed = false);
+// The FP32 kernels with polynomial taps (plans with tap_mode == kTapPoly; defined in the FP32
+// visibility translation unit); launch_degrid / launch_grid dispatch to them.
+template <class Epi>
+int32_t launch_degrid_fast(gbri_plan* p, Epi epi, cudaStream_t s);
+template <class Src>
+int32_t launch_grid_fast(gbri_plan* p, Src src, cudaStream_t s);
 // Degridding into an epilogue with an `update` (EpiPD1: the PD dual update; EpiResid: the
 // FISTA residual) fused with the gridding of the values it returns (J = 4, FP32 plans of
 // either table order): zeroes p->grid first unless zeroed.

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <new>
@@ -33,6 +34,72 @@ double kb_ghat(double nu, int J, double beta) {
   double ratio = 1.0;
   if (a > 0.0) ratio = (s > 0.0) ? std::sinh(a) / a : std::sin(a) / a;
   return J * ratio / std::cyl_bessel_i(0.0, beta);
+}
+
+// Polynomial taps (kTapPoly): on each unit segment [k, k + 1] of the support, g(k + (z + 1) / 2)
+// is interpolated at 32 Chebyshev nodes in z, truncated to degree 2 kPolyHalf - 1 and written
+// in the monomial basis, split into its even and odd parts in z (FP64 on the host).  The fit is
+// accepted when, with its coefficients rounded to FP32, it reproduces every sample of the
+// zeroth-order table (the positions the kernels evaluate it at) to kPolyTol; otherwise the
+// plan keeps the table.  g is an entire function of t (a power series in 1 - (2t/J)^2), so
+// the Chebyshev coefficients fall off fast: degree 9 reaches ~5e-9 for J = 4 and 6 with
+// beta = 2.34 J.  kPolyTol is near the FP32 table's own rounding (6e-8 of g(0) = 1).
+constexpr double kPolyTol = 3e-7;
+
+bool fit_poly_taps(gbri_plan* p) {
+  if (p->prec != GBRI_F32 || p->interp != 0 || p->J / 2 > 3) return false;
+  const int J = p->J, S = p->S;
+  constexpr int N = 32, D = 2 * kPolyHalf - 1;
+  PolyTaps pt{};
+  for (int k = 0; k < J / 2; ++k) {
+    double c[D + 1] = {};
+    for (int m = 0; m <= D; ++m) {
+      double acc = 0.0;
+      for (int j = 0; j < N; ++j) {
+        const double th = M_PI * (j + 0.5) / N;
+        acc += kb_g(k + 0.5 * (std::cos(th) + 1.0), J, p->beta) * std::cos(m * th);
+      }
+      c[m] = acc * 2.0 / N;
+    }
+    c[0] *= 0.5;
+    // monomial coefficients of sum_m c[m] T_m(z)
+    double mono[D + 1] = {}, tprev[D + 1] = {}, tcur[D + 1] = {}, tnext[D + 1] = {};
+    tprev[0] = 1.0;  // T_0
+    tcur[1] = 1.0;   // T_1
+    mono[0] += c[0];
+    mono[1] += c[1];
+    for (int m = 2; m <= D; ++m) {
+      for (int i = 0; i <= D; ++i) tnext[i] = (i > 0 ? 2.0 * tcur[i - 1] : 0.0) - tprev[i];
+      for (int i = 0; i <= D; ++i) {
+        mono[i] += c[m] * tnext[i];
+        tprev[i] = tcur[i];
+        tcur[i] = tnext[i];
+      }
+    }
+    for (int i = 0; i < kPolyHalf; ++i) {
+      pt.e[k][i] = (float)mono[2 * i];
+      pt.o[k][i] = (float)mono[2 * i + 1];
+    }
+  }
+  // every table sample, from the FP32 coefficients (both taps of every segment)
+  double worst = 0.0;
+  for (int f = 0; f < S; ++f) {
+    const double z = 2.0 * f / S - 1.0, u = z * z;
+    for (int k = 0; k < J / 2; ++k) {
+      double e = pt.e[k][kPolyHalf - 1], o = pt.o[k][kPolyHalf - 1];
+      for (int i = kPolyHalf - 2; i >= 0; --i) {
+        e = e * u + pt.e[k][i];
+        o = o * u + pt.o[k][i];
+      }
+      const double lo = e + z * o, hi = e - z * o;  // distances k + f / S and k + 1 - f / S
+      worst = std::max(worst, std::fabs(lo - kb_g(k + (double)f / S, J, p->beta)));
+      if (!(k == J / 2 - 1 && f == 0))  // the edge tap at distance J / 2 is set to 0 explicitly
+        worst = std::max(worst, std::fabs(hi - kb_g(k + 1 - (double)f / S, J, p->beta)));
+    }
+  }
+  if (!(worst <= kPolyTol)) return false;
+  p->poly = pt;
+  return true;
 }
 
 // Per-visibility quantisation (Sec. 8.1, zeroth order): k~ = round_half_away(u * K S / (2 pi))
@@ -273,6 +340,7 @@ void destroy_plan(gbri_plan* p) {
   cudaFree(p->vis_tmp);
   cudaFree(p->partials);
   cudaFree(p->scalars);
+  cudaFree(p->work);
   if (p->fft_ok) cufftDestroy(p->fft);
   if (p->fft_r2c_ok) cufftDestroy(p->fft_r2c);
   delete p;
@@ -483,6 +551,11 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     for (int i = 0; i < p->n_side; ++i) corr[i] = 1.0 / kb_ghat((double)(i - p->n_side / 2) / K, p->J, p->beta);
     GBRI_TRY(upload_real(&p->wtab, w, p->prec, &p->device_bytes, s));
     GBRI_TRY(upload_real(&p->corr, corr, p->prec, &p->device_bytes, s));
+    // FP32 zeroth-order plans evaluate the kernel from its polynomial fit unless
+    // GBRI_TAP_TABLE=1 asks for the shared-memory table (both give the table's weights)
+    const char* force_table = std::getenv("GBRI_TAP_TABLE");
+    const bool table_only = force_table && force_table[0] == '1';
+    p->tap_mode = p->interp ? kTapFO : (!table_only && fit_poly_taps(p)) ? kTapPoly : kTapTable;
   }
 
   GBRI_TRY(dmalloc(&p->meta, (size_t)M, &p->device_bytes));
@@ -588,12 +661,16 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   const int sms = num_sms();
   const int lim_dg =
       std::min(std::max(1, (int)((227 * 1024) / (degrid_smem(p) + 1024))), degrid_occupancy((int)rb, p->J));
-  const int lim_gr =
-      std::min(std::max(1, (int)((227 * 1024) / (grid_smem(p) + 1024))), grid_occupancy((int)rb, p->J));
+  // the pipelined FP32 polynomial-tap gridding kernel is compiled for two blocks per SM
+  const int lim_gr = std::min(std::min(std::max(1, (int)((227 * 1024) / (grid_smem(p) + 1024))),
+                                       grid_occupancy((int)rb, p->J)),
+                              p->tap_mode == kTapPoly ? 2 : 1 << 20);
   p->n_partials = std::max(sms * 8, 1024);
   GBRI_TRY(dmalloc(&p->partials, (size_t)p->n_partials * 4, &p->device_bytes));
   GBRI_TRY(dmalloc(&p->scalars, 64, &p->device_bytes));
   GBRI_CHECK_CUDA(cudaMemsetAsync(p->scalars, 0, 64 * sizeof(double), s));
+  GBRI_TRY(dmalloc(&p->work, 16, &p->device_bytes));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(p->work, 0, 16 * sizeof(unsigned int), s));
   if (cufftPlan2d(&p->fft, K, K, p->prec == GBRI_F64 ? CUFFT_Z2Z : CUFFT_C2C) != CUFFT_SUCCESS) {
     cudaFree(meta_cell); cudaFree(perm_cell);
     return set_error(GBRI_ECUFFT, "cufftPlan2d failed");
@@ -762,6 +839,12 @@ int32_t gbri_plan_launch_config(const gbri_plan* p, int32_t* run, int32_t* dg, i
   if (run) *run = p->run_len;
   if (dg) *dg = p->degrid_blocks;
   if (gr) *gr = p->grid_blocks;
+  return GBRI_OK;
+}
+
+int32_t gbri_plan_tap_mode(const gbri_plan* p, int32_t* mode) {
+  GBRI_CHECK(p && mode, GBRI_EINVAL, "null argument");
+  *mode = p->tap_mode;
   return GBRI_OK;
 }
 

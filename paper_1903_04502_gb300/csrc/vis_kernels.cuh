@@ -22,7 +22,7 @@ namespace gbri {
 // with the two J-tap weight rows from the block's shared table.  A cell's visibilities
 // are consecutive, so neighbouring lanes often read the same window words.  No block-wide
 // barrier after the table load.  `Epi` consumes (plan position, v).
-template <int J, bool FO, class Epi>
+template <int J, int TM, class Epi>
 __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi::real), J))
     k_degrid(VisGeom geo, const cplx<typename Epi::real>* __restrict__ spec, Epi epi) {
   using R = typename Epi::real;
@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
   extern __shared__ float4 smem_dg[];
   constexpr int P = kTile + J - 1;
   constexpr int W = kThreads / 32;
+  static_assert(TM == kTapTable || TM == kTapFO, "table kernels (polynomial taps: k_degrid_fast)");
   R* sw = reinterpret_cast<R*>(smem_dg);
   const int S = 1 << geo.log2S;
   const int lane = threadIdx.x & 31;
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
         const int i = b0 + lane + 32 * k;
         if (i < cnt) {
           m[k] = geo.meta[lo + i];
-          if constexpr (FO) fr[k] = geo.frac[lo + i];
+          if constexpr (TM == kTapFO) fr[k] = geo.frac[lo + i];
           pre[k] = epi.pre_from(streams, lo + i);
         }
       }
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
         if (i >= cnt) break;
         const int lx = m[k].x & 0xffff, ly = m[k].x >> 16;
         R wx[J], wy[J];
-        if constexpr (FO) {
+        if constexpr (TM == kTapFO) {
           load_taps_fo<J>(sw, lx & (S - 1), fr[k] & 0xff, S, wx);
           load_taps_fo<J>(sw, ly & (S - 1), fr[k] >> 8, S, wy);
         } else {
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
 // gt.w = 1), whose warps flush every cell with atomics.  No block-wide barrier after the
 // table load.
 // `Src` gives the visibility value at a plan position.
-template <int J, bool FO, class Src>
+template <int J, int TM, class Src>
 __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::real), J))
     k_grid(VisGeom geo, cplx<typename Src::real>* __restrict__ grid, Src src) {
   using R = typename Src::real;
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
   extern __shared__ float4 smem_gr[];
   constexpr int P = kTile + J - 1;
   constexpr int W = kThreads / 32;
+  static_assert(TM == kTapTable || TM == kTapFO, "table kernels (polynomial taps: k_grid_fast)");
   const int S = 1 << geo.log2S;
   R* sw = reinterpret_cast<R*>(smem_gr);
   C* accs = reinterpret_cast<C*>(sw + table_elems(S, J));
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
         for (int k = 0; k < kRun; ++k)
           if (k0 + k < sr.y) {
             m[k] = geo.meta[sr.x + k0 + k];
-            if constexpr (FO) fr[k] = geo.frac[sr.x + k0 + k];
+            if constexpr (TM == kTapFO) fr[k] = geo.frac[sr.x + k0 + k];
             v[k] = src(sr.x + k0 + k, sctx);
           }
         if (k0 == 0) a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S);
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
         for (int k = 0; k < kRun; ++k) {
           if (k0 + k >= sr.y) break;
           R wx[J], wy[J];
-          if constexpr (FO) {
+          if constexpr (TM == kTapFO) {
             load_taps_fo<J>(sw, (m[k].x & 0xffff) & (S - 1), fr[k] & 0xff, S, wx);
             load_taps_fo<J>(sw, (m[k].x >> 16) & (S - 1), fr[k] >> 8, S, wy);
           } else {
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
 // item the accumulator is flushed as in k_grid.  Gridding u as soon as it is updated is
 // valid because Phi^dagger is applied to u itself (c scales the image later), so no global
 // reduction separates the two passes.
-template <int J, bool FO, class Epi>
+template <int J, int TM, class Epi>
 __global__ void __launch_bounds__(kThreads, 2)
     k_degrid_grid(VisGeom geo, const float2* __restrict__ spec, float2* __restrict__ grid, Epi epi) {
   static_assert(sizeof(typename Epi::real) == 4, "FP32 path only");
@@ -247,6 +249,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   extern __shared__ float4 smem_dgg[];
   constexpr int P = kTile + J - 1;
   constexpr int W = kThreads / 32;
+  static_assert(TM == kTapTable || TM == kTapFO, "table kernels (polynomial taps: k_degrid_grid_fast)");
   R* sw = reinterpret_cast<R*>(smem_dgg);
   const int S = 1 << geo.log2S;
   const int lane = threadIdx.x & 31;
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int k = 0; k < kRun; ++k)
           if (k0 + k < sr.y) {
             m[k] = geo.meta[sr.x + k0 + k];
-            if constexpr (FO) fr[k] = geo.frac[sr.x + k0 + k];
+            if constexpr (TM == kTapFO) fr[k] = geo.frac[sr.x + k0 + k];
             pre[k] = epi.pre_from(streams, sr.x + k0 + k);
           }
         if (k0 == 0) {  // the run's cell: its J x J block of the window
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int k = 0; k < kRun; ++k) {
           if (k0 + k >= sr.y) break;
           R wx[J], wy[J];
-          if constexpr (FO) {
+          if constexpr (TM == kTapFO) {
             load_taps_fo<J>(sw, (m[k].x & 0xffff) & (S - 1), fr[k] & 0xff, S, wx);
             load_taps_fo<J>(sw, (m[k].x >> 16) & (S - 1), fr[k] >> 8, S, wy);
           } else {
@@ -366,23 +369,26 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 inline size_t degrid_grid_smem(const gbri_plan* p) {
-  return (size_t)table_elems(p->S, p->J) * sizeof(float) +
+  return (size_t)smem_table_elems(p->tap_mode, p->S, p->J) * sizeof(float) +
          (size_t)(kThreads / 32) * (kTile + p->J - 1) * (kWinPitch + kAccPitch2) * sizeof(float2);
 }
 
 template <class Epi>
 int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s) {
   using R = typename Epi::real;
+  if constexpr (sizeof(R) == 4)
+    if (p->tap_mode == kTapPoly) return launch_degrid_fast(p, epi, s);
   launch_begin(GBRI_K_DEGRID, s);
   const cplx<R>* g = p->as<cplx<R>>(p->spec);
   const size_t sm = degrid_smem(p);
   const VisGeom geo = vis_geom(p);
-  if (p->frac) {
-    if (p->J == 4) k_degrid<4, true, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
-    else k_degrid<6, true, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
+  const int tm = p->tap_mode;
+  if (tm == kTapFO) {
+    if (p->J == 4) k_degrid<4, kTapFO, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
+    else k_degrid<6, kTapFO, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
   } else {
-    if (p->J == 4) k_degrid<4, false, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
-    else k_degrid<6, false, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
+    if (p->J == 4) k_degrid<4, kTapTable, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
+    else k_degrid<6, kTapTable, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi);
   }
   return launch_end(GBRI_K_DEGRID, s);
 }
@@ -393,17 +399,23 @@ int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s, bool zeroed) {
   cplx<R>* g = p->as<cplx<R>>(p->grid);
   if (!zeroed) GBRI_CHECK_CUDA(cudaMemsetAsync(g, 0, sizeof(cplx<R>) * (size_t)p->K * p->K, s));
   if (p->n_gtiles == 0) return GBRI_OK;
+  if constexpr (sizeof(R) == 4)
+    if (p->tap_mode == kTapPoly) return launch_grid_fast(p, src, s);
   launch_begin(GBRI_K_GRID, s);
   const VisGeom geo = vis_geom(p);
-  if (p->frac) {
-    if (p->J == 4) k_grid<4, true, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
-    else k_grid<6, true, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
+  const int tm = p->tap_mode;
+  if (tm == kTapFO) {
+    if (p->J == 4) k_grid<4, kTapFO, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
+    else k_grid<6, kTapFO, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
   } else {
-    if (p->J == 4) k_grid<4, false, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
-    else k_grid<6, false, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
+    if (p->J == 4) k_grid<4, kTapTable, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
+    else k_grid<6, kTapTable, Src><<<p->grid_blocks, kThreads, grid_smem(p), s>>>(geo, g, src);
   }
   return launch_end(GBRI_K_GRID, s);
 }
+
+// Shared-memory attributes of the FP32 polynomial-tap kernels (defined with them).
+cudaError_t prepare_fast_kernels();
 
 // Dynamic shared memory above 48 KB needs a per-kernel attribute; it is set once
 // for every instantiation of one precision before any launch (so never inside a
@@ -416,8 +428,8 @@ int32_t prepare_visibility_kernels() {
     const int lim = 220 * 1024;
     cudaError_t e = cudaSuccess;
 #define GBRI_ATTR(kern) if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-#define GBRI_ATTR4(K, T) GBRI_ATTR((K<4, false, T<R>>)); GBRI_ATTR((K<6, false, T<R>>)); \
-                         GBRI_ATTR((K<4, true, T<R>>)); GBRI_ATTR((K<6, true, T<R>>))
+#define GBRI_ATTR4(K, T) GBRI_ATTR((K<4, kTapTable, T<R>>)); GBRI_ATTR((K<6, kTapTable, T<R>>)); \
+                         GBRI_ATTR((K<4, kTapFO, T<R>>)); GBRI_ATTR((K<6, kTapFO, T<R>>))
     GBRI_ATTR4(k_degrid, EpiStorePlan); GBRI_ATTR4(k_degrid, EpiStoreRaw); GBRI_ATTR4(k_degrid, EpiPD1);
     GBRI_ATTR4(k_degrid, EpiADMM1); GBRI_ATTR4(k_degrid, EpiResid); GBRI_ATTR4(k_degrid, EpiPD1L);
     GBRI_ATTR4(k_degrid, EpiADMM1L);
@@ -425,12 +437,14 @@ int32_t prepare_visibility_kernels() {
     GBRI_ATTR4(k_grid, SrcRaw); GBRI_ATTR4(k_grid, SrcADMM2);
 #undef GBRI_ATTR4
     if constexpr (sizeof(R) == 4) {
-      GBRI_ATTR((k_degrid_grid<4, false, EpiPD1<float>>));
-      GBRI_ATTR((k_degrid_grid<4, false, EpiResid<float>>));
-      GBRI_ATTR((k_degrid_grid<4, true, EpiPD1<float>>));
-      GBRI_ATTR((k_degrid_grid<4, true, EpiResid<float>>));
+      GBRI_ATTR((k_degrid_grid<4, kTapTable, EpiPD1<float>>));
+      GBRI_ATTR((k_degrid_grid<4, kTapTable, EpiResid<float>>));
+      GBRI_ATTR((k_degrid_grid<4, kTapFO, EpiPD1<float>>));
+      GBRI_ATTR((k_degrid_grid<4, kTapFO, EpiResid<float>>));
     }
 #undef GBRI_ATTR
+    if constexpr (sizeof(R) == 4)
+      if (e == cudaSuccess) e = prepare_fast_kernels();
     status = (e == cudaSuccess) ? GBRI_OK : cuda_error(e, "cudaFuncSetAttribute");
   });
   return status;

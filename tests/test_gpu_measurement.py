@@ -45,11 +45,18 @@ CASES = [  # (n_side, M, J): several tiles, ragged chunk tails
 ]
 
 
+@pytest.mark.parametrize("taps", ["poly", "table"])
 @pytest.mark.parametrize("n,M,J", CASES)
-def test_phi_and_adjoint_match_oracle(g, n, M, J):
+def test_phi_and_adjoint_match_oracle(g, monkeypatch, n, M, J, taps):
+    """Both ways of getting the tap weights of an FP32 plan: the polynomial fit (the default)
+    and the shared-memory table (GBRI_TAP_TABLE=1)."""
     x, uvw = make(n, M, J, seed=n + M)
     geo = me.Geometry(uvw, n, 2, J, 4096)
+    if taps == "table":
+        monkeypatch.setenv("GBRI_TAP_TABLE", "1")
     plan = g.Plan(torch.from_numpy(uvw).cuda(), n, J=J, S=4096)
+    monkeypatch.delenv("GBRI_TAP_TABLE", raising=False)
+    assert plan.tap_mode() == (2 if taps == "poly" else 0)
     y = g.phi(plan, torch.from_numpy(x).cuda()).cpu().numpy()
     y_ref = me.phi(x.astype(np.float64), geo)
     assert rel(y, y_ref) <= TOL
