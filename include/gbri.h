@@ -80,7 +80,17 @@ typedef struct {
                                 sample; 1: first order, k is quantised 256 S steps per cell and each
                                 tap interpolates linearly between its two table samples (8 bits of
                                 fraction per axis kept beside the metadata: 2 more bytes per visibility) */
-  int32_t reserved;          /* must be 0 */
+  int32_t deterministic;     /* 1: gridding results are bitwise reproducible from run to run (and the
+                                same alone or inside a batch): work items are taken in a fixed order,
+                                every gridding work item writes its whole window to a slot of its own,
+                                and a second pass sums, for every grid cell, the windows covering it in
+                                a fixed order, instead of float atomics on the cells tiles share; the
+                                slots take 8 (T + J - 1)^2 bytes per work item (FP32; 16 for FP64);
+                                plan creation orders each cell's visibilities by caller index, and
+                                autotune is ignored (timed choices would change the layout); local
+                                l2 balls (n_balls > 1) still sum their block norms with shared-memory
+                                atomics and are not covered;
+                                0: atomics (faster, last-bit differences between runs) */
 } gbri_plan_desc;
 
 /* Build a plan: quantises every (u, v) once in FP64 to the fixed-point grid

@@ -120,6 +120,13 @@ struct gbri_plan {
   // work counters of the kTapPoly kernels, a pair {next item, finished blocks} per kernel
   // (degridding, gridding, fused); zero between launches
   unsigned int* work = nullptr;
+  // deterministic gridding: every gridding work item writes its (T + J - 1)^2 window to
+  // slots[item] (plan precision, complex), and k_grid_reduce sums, for every grid cell, the
+  // windows covering it in a fixed order (tiles by position, a tile's items by index)
+  int det = 0;
+  void* slots = nullptr;             // C [n_gtiles][P][P]
+  int32_t* tile_items_off = nullptr;  // [nT^2 + 1] CSR offsets: items of each tile
+  int32_t* tile_items = nullptr;      // [n_gtiles] item indices, ascending per tile
   int autotune = 0;
   template <class T> T* as(void* q) const { return static_cast<T*>(q); }
 };
@@ -187,6 +194,7 @@ struct VisGeom {
   const int4* __restrict__ gtiles;
   const void* __restrict__ wtab;
   const uint16_t* __restrict__ frac;  // first-order fractions (null: zeroth order)
+  void* slots;                         // deterministic gridding: per-item windows (null: atomics)
   int n_chunks, n_gtiles, K, log2S, nT;
   PolyTaps poly;                       // kTapPoly coefficients (kernel parameter space)
 };
@@ -214,6 +222,7 @@ inline VisGeom vis_geom(const gbri_plan* p) {
   g.gtiles = p->gtiles;
   g.wtab = p->wtab;
   g.frac = p->frac;
+  g.slots = p->det ? p->slots : nullptr;
   g.n_chunks = (int)p->n_chunks;
   g.n_gtiles = (int)p->n_gtiles;
   g.K = p->K;

@@ -233,6 +233,29 @@ __global__ void k_scatter(const int32_t* __restrict__ key, const uint32_t* __res
   }
 }
 
+// Deterministic plans: the atomic scatter above leaves a cell's visibilities in a
+// run-dependent order; sort every cell's segment by caller index (insertion sort, one thread
+// per cell: segments are short, and this runs once per plan), so that the plan order, and
+// with it every sum the kernels form, is the same in every run.
+__global__ void k_sort_cells(const int32_t* __restrict__ off, int64_t cells, uint2* __restrict__ meta,
+                             int32_t* __restrict__ perm) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += (int64_t)gridDim.x * blockDim.x) {
+    const int lo = off[c], hi = off[c + 1];
+    for (int i = lo + 1; i < hi; ++i) {
+      const int32_t pk = perm[i];
+      const uint2 mk = meta[i];
+      int j = i - 1;
+      while (j >= lo && perm[j] > pk) {
+        perm[j + 1] = perm[j];
+        meta[j + 1] = meta[j];
+        --j;
+      }
+      perm[j + 1] = pk;
+      meta[j + 1] = mk;
+    }
+  }
+}
+
 // out[pos] = in[perm[pos]]
 __global__ void k_gather_u16(const uint16_t* __restrict__ in, const int32_t* __restrict__ perm,
                              uint16_t* __restrict__ out, int64_t M) {
@@ -341,6 +364,9 @@ void destroy_plan(gbri_plan* p) {
   cudaFree(p->partials);
   cudaFree(p->scalars);
   cudaFree(p->work);
+  cudaFree(p->slots);
+  cudaFree(p->tile_items_off);
+  cudaFree(p->tile_items);
   if (p->fft_ok) cufftDestroy(p->fft);
   if (p->fft_r2c_ok) cufftDestroy(p->fft_r2c);
   delete p;
@@ -365,6 +391,8 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
   constexpr int NC = kTile * kTile;
   cudaFree(p->meta); cudaFree(p->perm); cudaFree(p->subruns); cudaFree(p->chunks); cudaFree(p->gtiles);
   p->meta = nullptr; p->perm = nullptr; p->subruns = nullptr; p->chunks = nullptr; p->gtiles = nullptr;
+  cudaFree(p->slots); cudaFree(p->tile_items_off); cudaFree(p->tile_items);
+  p->slots = nullptr; p->tile_items_off = nullptr; p->tile_items = nullptr;
   std::vector<int2> sub;
   sub.reserve((size_t)(M / std::max(R, 4) + order.size() * 64 + 16));
   std::vector<int4> ch, gt;
@@ -486,8 +514,29 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
     GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   if (!gt.empty())
     GBRI_CHECK_CUDA(cudaMemcpyAsync(p->gtiles, gt.data(), gt.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-  GBRI_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   p->layout_bytes = (int64_t)(sub.size() * sizeof(int2) + (ch.size() + gt.size()) * sizeof(int4));
+  std::vector<int32_t> toff, titems;
+  if (p->det) {  // per-tile item lists (CSR over every tile, items ascending) and the window slots
+    const int64_t ntiles = (int64_t)p->nT * p->nT;
+    toff.assign((size_t)ntiles + 1, 0);
+    for (const int4& g : gt) ++toff[(size_t)g.x + 1];
+    for (int64_t t = 0; t < ntiles; ++t) toff[t + 1] += toff[t];
+    titems.resize(gt.size());
+    std::vector<int32_t> cur(toff.begin(), toff.end() - 1);
+    for (size_t i = 0; i < gt.size(); ++i) titems[cur[gt[i].x]++] = (int32_t)i;
+    const int P = kTile + p->J - 1;
+    const size_t slot_bytes = (size_t)gt.size() * P * P * 2 * real_bytes(p->prec);
+    if ((st = bmalloc(&p->slots, slot_bytes, nullptr)) || (st = dmalloc(&p->tile_items_off, toff.size(), nullptr)) ||
+        (st = dmalloc(&p->tile_items, titems.size(), nullptr)))
+      return st;
+    GBRI_CHECK_CUDA(cudaMemcpyAsync(p->tile_items_off, toff.data(), toff.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+    if (!titems.empty())
+      GBRI_CHECK_CUDA(cudaMemcpyAsync(p->tile_items, titems.data(), titems.size() * sizeof(int32_t),
+                                      cudaMemcpyHostToDevice, s));
+    p->layout_bytes += (int64_t)(slot_bytes + (toff.size() + titems.size()) * sizeof(int32_t));
+  }
+  GBRI_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   return GBRI_OK;
 }
 
@@ -620,6 +669,12 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
       launch_begin(GBRI_K_OTHER, s);
       k_scatter<<<vb, 256, 0, s>>>(key, packed, wt, M, counts, p->meta, p->perm);
       st = launch_end(GBRI_K_OTHER, s);
+      if (st == GBRI_OK && p->det) {
+        launch_begin(GBRI_K_OTHER, s);
+        k_sort_cells<<<(unsigned)std::min<int64_t>(ceil_div(cells, 256), (int64_t)num_sms() * 16), 256, 0, s>>>(
+            offsets, cells, p->meta, p->perm);
+        st = launch_end(GBRI_K_OTHER, s);
+      }
     }
   }
   std::vector<int32_t> hst(n_tiles + 1);
@@ -788,7 +843,7 @@ extern "C" {
 int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* d_uvw, void* stream) {
   GBRI_CHECK(out && d, GBRI_EINVAL, "null argument");
   *out = nullptr;
-  GBRI_CHECK(d->reserved == 0, GBRI_EINVAL, "reserved must be 0");
+  GBRI_CHECK(d->deterministic == 0 || d->deterministic == 1, GBRI_EINVAL, "deterministic must be 0 or 1");
   GBRI_CHECK(d->precision == GBRI_F32 || d->precision == GBRI_F64, GBRI_EINVAL, "precision must be GBRI_F32 or GBRI_F64");
   GBRI_CHECK(d->n_side >= 16 && d->n_side % 2 == 0, GBRI_EINVAL, "n_side must be even and >= 16");
   GBRI_CHECK(d->oversample >= 2 && d->oversample <= 4, GBRI_EINVAL, "oversample must be in [2, 4]");
@@ -818,7 +873,8 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* 
   p->prec = d->precision;
   p->run_len = d->vis_per_run ? d->vis_per_run : kDefaultRun;
   p->interp = d->interp_order;
-  p->autotune = d->autotune;
+  p->det = d->deterministic;
+  p->autotune = d->deterministic ? 0 : d->autotune;  // timed choices would make the layout vary
   const int32_t st = build_plan(p, d_uvw, (cudaStream_t)stream);
   if (st != GBRI_OK) {
     destroy_plan(p);

@@ -57,7 +57,8 @@ cudaError_t prepare_fast_kernels() {
 template <class Epi>
 int32_t degrid_grid(gbri_plan* p, Epi epi, cudaStream_t s, bool zeroed) {
   float2* g = p->as<float2>(p->grid);
-  if (!zeroed) GBRI_CHECK_CUDA(cudaMemsetAsync(g, 0, sizeof(float2) * (size_t)p->K * p->K, s));
+  // deterministic plans: the item windows go to slots and the fixed-order pass writes every cell
+  if (!zeroed && !p->det) GBRI_CHECK_CUDA(cudaMemsetAsync(g, 0, sizeof(float2) * (size_t)p->K * p->K, s));
   // two blocks per SM (a window and an accumulator per warp); each block writes one
   // partial of the epilogue's sum of squares
   const int blocks = (int)std::max<int64_t>(
@@ -70,7 +71,8 @@ int32_t degrid_grid(gbri_plan* p, Epi epi, cudaStream_t s, bool zeroed) {
     k_degrid_grid_fast<4, Epi><<<blocks, kThreads, sm, s>>>(geo, spec, g, epi, p->work + 4);
   else if (p->tap_mode == kTapFO) k_degrid_grid<4, kTapFO, Epi><<<blocks, kThreads, sm, s>>>(geo, spec, g, epi);
   else k_degrid_grid<4, kTapTable, Epi><<<blocks, kThreads, sm, s>>>(geo, spec, g, epi);
-  return launch_end(GBRI_K_DEGRID_GRID, s);
+  GBRI_TRY(launch_end(GBRI_K_DEGRID_GRID, s));
+  return p->det ? launch_grid_reduce<float>(p, s) : GBRI_OK;
 }
 
 int32_t launch_degrid_grid(gbri_plan* p, EpiPD1<float> epi, cudaStream_t s, bool zeroed) {

@@ -50,6 +50,16 @@ __device__ __forceinline__ int take_item(unsigned int* ctr) {
   return (int)__shfl_sync(0xffffffffu, v, 0);
 }
 
+// The first / next work item of a warp: from the device counter, or, for deterministic
+// plans, in a fixed order (warp w of the launch takes items w, w + warps, ...), so that every
+// block's partial sums cover the same items in every run.
+__device__ __forceinline__ int first_item(unsigned int* ctr, bool fixed) {
+  return fixed ? (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) : take_item(ctr);
+}
+__device__ __forceinline__ int next_item(unsigned int* ctr, bool fixed, int cur) {
+  return fixed ? cur + (int)(gridDim.x * (blockDim.x >> 5)) : take_item(ctr);
+}
+
 // Called by every thread of a block once its warps have taken their last item: the last
 // block of the launch to get here resets the counter pair {next item, finished blocks} for
 // the next launch (stream order makes the reset visible to it).
@@ -125,9 +135,9 @@ __global__ void __launch_bounds__(kThreads, 3)
   const E* streams[2] = {Epi::kStreams > 0 ? epi.stream(0) : nullptr, Epi::kStreams > 1 ? epi.stream(1) : nullptr};
   epi.init();  // block barrier
   int cur_tile = -1;
-  int c = take_item(ctr);
+  int c = first_item(ctr, geo.slots != nullptr);
   while (c < geo.n_chunks) {
-    const int c_next = take_item(ctr);
+    const int c_next = next_item(ctr, geo.slots != nullptr, c);
     const int4 ch = geo.chunks[c];
     const int lo = ch.y, cnt = ch.z;
     epi.begin_chunk(lo);  // warp-uniform
@@ -200,9 +210,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   const float two_over_S = 2.f / (float)S;
   const int K = geo.K;
   constexpr int lo_x = J - 1, hi_x = kTile;
-  int it = take_item(ctr);
+  int it = first_item(ctr, geo.slots != nullptr);
   while (it < geo.n_gtiles) {
-    const int it_next = take_item(ctr);
+    const int it_next = next_item(ctr, geo.slots != nullptr, it);
     const int4 gt = geo.gtiles[it];
     const typename Src::Ctx sctx = src.ctx(geo.subruns[gt.y].x);  // a tile's first run is never padding
     int2 sr = geo.subruns[gt.y + lane];  // gt.z is a multiple of 32
@@ -258,6 +268,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       float2* q = acc + r * kAccPitch2 + cc;
       const float2 a = *q;
       *q = make_float2(0.f, 0.f);
+      if (geo.slots) {  // deterministic: the whole window to the item's slot
+        static_cast<float2*>(geo.slots)[(size_t)it * (P * P) + i] = a;
+        continue;
+      }
       float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
       if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) *dst = a;
       else if (a.x != 0.f || a.y != 0.f) atomicAdd(dst, a);
@@ -295,9 +309,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   const E* streams[2] = {Epi::kStreams > 0 ? epi.stream(0) : nullptr, Epi::kStreams > 1 ? epi.stream(1) : nullptr};
   epi.init();  // block barrier: zeroed accumulators in place
   constexpr int lo_x = J - 1, hi_x = kTile;
-  int it = take_item(ctr);
+  int it = first_item(ctr, geo.slots != nullptr);
   while (it < geo.n_gtiles) {
-    const int it_next = take_item(ctr);
+    const int it_next = next_item(ctr, geo.slots != nullptr, it);
     const int4 gt = geo.gtiles[it];
     int2 sr = geo.subruns[gt.y + lane];  // gt.z is a multiple of 32
     load_window_f32<J>(win, spec, gt.x, geo.nT, K, lane);
@@ -371,6 +385,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       float2* q = acc + r * kAccPitch2 + cc;
       const float2 a = *q;
       *q = make_float2(0.f, 0.f);
+      if (geo.slots) {  // deterministic: the whole window to the item's slot
+        static_cast<float2*>(geo.slots)[(size_t)it * (P * P) + i] = a;
+        continue;
+      }
       float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
       if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) *dst = a;
       else if (a.x != 0.f || a.y != 0.f) atomicAdd(dst, a);

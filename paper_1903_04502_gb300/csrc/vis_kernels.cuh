@@ -213,6 +213,10 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
       C* q = acc + r * kAccPitch2 + cc;
       const C a = *q;
       *q = mkc<R>(0, 0);
+      if (geo.slots) {  // deterministic: the whole window to the item's slot
+        static_cast<C*>(geo.slots)[(size_t)it * (P * P) + i] = a;
+        continue;
+      }
       C* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
       if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) {
         *dst = a;
@@ -359,6 +363,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       C* q = acc + r * kAccPitch2 + cc;
       const C a = *q;
       *q = mkc<R>(0, 0);
+      if (geo.slots) {  // deterministic: the whole window to the item's slot
+        static_cast<C*>(geo.slots)[(size_t)it * (P * P) + i] = a;
+        continue;
+      }
       C* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
       if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) *dst = a;
       else if (a.x != 0 || a.y != 0) atomicAdd(dst, a);
@@ -371,6 +379,55 @@ __global__ void __launch_bounds__(kThreads, 2)
 inline size_t degrid_grid_smem(const gbri_plan* p) {
   return (size_t)smem_table_elems(p->tap_mode, p->S, p->J) * sizeof(float) +
          (size_t)(kThreads / 32) * (kTile + p->J - 1) * (kWinPitch + kAccPitch2) * sizeof(float2);
+}
+
+// Deterministic gridding, second pass: every grid cell is the sum of the item windows that
+// cover it, in a fixed order (the tile above / left before the tile itself along each axis,
+// a tile's items in index order); cells no window covers are zero.  The window of tile t
+// starts at cell t T - (J/2 - 1) and spans T + J - 1 cells (periodic), so along one axis a
+// cell lies in the window of tile t_a = floor((k + J/2 - 1) / T) at offset k + J/2 - 1 - t_a T,
+// and also in tile t_a - 1's at that offset + T when the offset is below J - 1.
+template <class R>
+__global__ void k_grid_reduce(const cplx<R>* __restrict__ slots, const int32_t* __restrict__ toff,
+                              const int32_t* __restrict__ titems, cplx<R>* __restrict__ grid, int K, int nT, int J) {
+  const int P = kTile + J - 1, hb = J / 2 - 1;
+  const int64_t cells = (int64_t)K * K;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cells; q += (int64_t)gridDim.x * blockDim.x) {
+    const int ky = (int)(q / K), kx = (int)(q - (int64_t)ky * K);
+    int ty[2], oy[2], ny = 0, tx[2], ox[2], nx = 0;
+    {
+      const int ta = (ky + hb) / kTile, ra = ky + hb - ta * kTile;
+      if (ra < J - 1) { ty[ny] = (ta - 1 + nT) % nT; oy[ny++] = ra + kTile; }
+      ty[ny] = ta % nT; oy[ny++] = ra;
+    }
+    {
+      const int ta = (kx + hb) / kTile, ra = kx + hb - ta * kTile;
+      if (ra < J - 1) { tx[nx] = (ta - 1 + nT) % nT; ox[nx++] = ra + kTile; }
+      tx[nx] = ta % nT; ox[nx++] = ra;
+    }
+    R sr = 0, si = 0;
+    for (int a = 0; a < ny; ++a)
+      for (int b = 0; b < nx; ++b) {
+        const int t = ty[a] * nT + tx[b];
+        const int w = oy[a] * P + ox[b];
+        for (int j = toff[t]; j < toff[t + 1]; ++j) {
+          const cplx<R> v = slots[(size_t)titems[j] * (P * P) + w];
+          sr += v.x;
+          si += v.y;
+        }
+      }
+    grid[q] = mkc<R>(sr, si);
+  }
+}
+
+template <class R>
+int32_t launch_grid_reduce(gbri_plan* p, cudaStream_t s) {
+  launch_begin(GBRI_K_GRID, s);
+  const int64_t cells = (int64_t)p->K * p->K;
+  const int blocks = (int)std::min<int64_t>(ceil_div(cells, 256), (int64_t)num_sms() * 16);
+  k_grid_reduce<R><<<blocks, 256, 0, s>>>(p->as<const cplx<R>>(p->slots), p->tile_items_off, p->tile_items,
+                                          p->as<cplx<R>>(p->grid), p->K, p->nT, p->J);
+  return launch_end(GBRI_K_GRID, s);
 }
 
 template <class Epi>
@@ -394,13 +451,34 @@ int32_t launch_degrid(gbri_plan* p, Epi epi, cudaStream_t s) {
 }
 
 template <class Src>
+int32_t launch_grid_generic(gbri_plan* p, Src src, cudaStream_t s);
+
+template <class Src>
 int32_t launch_grid(gbri_plan* p, Src src, cudaStream_t s, bool zeroed) {
   using R = typename Src::real;
   cplx<R>* g = p->as<cplx<R>>(p->grid);
+  if (p->det) {  // the item windows go to slots; the fixed-order pass writes every cell
+    if (p->n_gtiles > 0) {
+      if constexpr (sizeof(R) == 4) {
+        if (p->tap_mode == kTapPoly) GBRI_TRY(launch_grid_fast(p, src, s));
+        else GBRI_TRY(launch_grid_generic(p, src, s));
+      } else {
+        GBRI_TRY(launch_grid_generic(p, src, s));
+      }
+    }
+    return launch_grid_reduce<R>(p, s);
+  }
   if (!zeroed) GBRI_CHECK_CUDA(cudaMemsetAsync(g, 0, sizeof(cplx<R>) * (size_t)p->K * p->K, s));
   if (p->n_gtiles == 0) return GBRI_OK;
   if constexpr (sizeof(R) == 4)
     if (p->tap_mode == kTapPoly) return launch_grid_fast(p, src, s);
+  return launch_grid_generic(p, src, s);
+}
+
+template <class Src>
+int32_t launch_grid_generic(gbri_plan* p, Src src, cudaStream_t s) {
+  using R = typename Src::real;
+  cplx<R>* g = p->as<cplx<R>>(p->grid);
   launch_begin(GBRI_K_GRID, s);
   const VisGeom geo = vis_geom(p);
   const int tm = p->tap_mode;
