@@ -267,41 +267,59 @@ __device__ __forceinline__ void idwt_block(SynSmem<R>& sm, const R* __restrict__
     }
   }
   __syncthreads();
-  // column synthesis, two output rows (2p, 2p + 1) per item: both read the same L/2
-  // coefficient rows kq = p + L/2 - 1 - s of the a and d halves.  A warp takes one row
-  // pair p, its lanes consecutive columns (no row straddles a warp).
+  // column synthesis, register-blocked: an item is one coefficient column sc and two output
+  // row pairs (2 pr, 2 pr + 1), pr = 2 pg, 2 pg + 1, which read the L/2 + 1 coefficient rows
+  // kq = pr .. pr + L/2 of the a and d halves they share once
+  for (int sc = tx; sc < 2 * KB; sc += 32) {
+    const int pr0 = 2 * ty;  // pg = ty: 8 warps cover the kSB / 4 = 8 pair groups
+    R a[L / 2 + 1], d[L / 2 + 1];
 #pragma unroll
-  for (int pr = ty; pr < kSB / 2; pr += 8) {
+    for (int j = 0; j <= L / 2; ++j) {
+      a[j] = sm.tc[pr0 + j][sc];
+      d[j] = sm.tc[KB + pr0 + j][sc];
+    }
 #pragma unroll
-    for (int sc = tx; sc < 2 * KB; sc += 32) {
+    for (int p = 0; p < 2; ++p) {
       R ve = 0, vo = 0;
 #pragma unroll
       for (int q = 0; q < L / 2; ++q) {
-        const int kq = pr + L / 2 - 1 - q;
-        const R a = sm.tc[kq][sc], d = sm.tc[KB + kq][sc];
-        ve = fma_r(h[2 * q], a, fma_r(g[2 * q], d, ve));
-        vo = fma_r(h[2 * q + 1], a, fma_r(g[2 * q + 1], d, vo));
+        const int j = p + L / 2 - 1 - q;
+        ve = fma_r(h[2 * q], a[j], fma_r(g[2 * q], d[j], ve));
+        vo = fma_r(h[2 * q + 1], a[j], fma_r(g[2 * q + 1], d[j], vo));
       }
-      sm.tm[2 * pr][sc] = ve;
-      sm.tm[2 * pr + 1][sc] = vo;
+      sm.tm[2 * (pr0 + p)][sc] = ve;
+      sm.tm[2 * (pr0 + p) + 1][sc] = vo;
     }
   }
   __syncthreads();
-  // row synthesis, two output columns per item
-  for (int idx = threadIdx.x; idx < kSB * (kSB / 2); idx += blockDim.x) {
-    const int r = idx / (kSB / 2), pc = idx - r * (kSB / 2);
-    R ve = 0, vo = 0;
+  // row synthesis, register-blocked: an item is one output row r and two output column
+  // pairs (four consecutive samples), reading the L/2 + 1 a and d values they share once
+  {
+    const int r = threadIdx.x >> 3, pc0 = 2 * (threadIdx.x & 7);  // kSB * kSB / 4 = 256 items
+    R a[L / 2 + 1], d[L / 2 + 1];
 #pragma unroll
-    for (int q = 0; q < L / 2; ++q) {
-      const int kq = pc + L / 2 - 1 - q;
-      const R a = sm.tm[r][kq], d = sm.tm[r][KB + kq];
-      ve = fma_r(h[2 * q], a, fma_r(g[2 * q], d, ve));
-      vo = fma_r(h[2 * q + 1], a, fma_r(g[2 * q + 1], d, vo));
+    for (int j = 0; j <= L / 2; ++j) {
+      a[j] = sm.tm[r][pc0 + j];
+      d[j] = sm.tm[r][KB + pc0 + j];
     }
-    const int Rr = r0 + r, Cc = c0 + 2 * pc;
+    R o[4];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      R ve = 0, vo = 0;
+#pragma unroll
+      for (int q = 0; q < L / 2; ++q) {
+        const int j = p + L / 2 - 1 - q;
+        ve = fma_r(h[2 * q], a[j], fma_r(g[2 * q], d[j], ve));
+        vo = fma_r(h[2 * q + 1], a[j], fma_r(g[2 * q + 1], d[j], vo));
+      }
+      o[2 * p] = ve;
+      o[2 * p + 1] = vo;
+    }
+    const int Rr = r0 + r, Cc = c0 + 2 * pc0;
     if (Rr < m) {
-      if (Cc < m) dst[(size_t)Rr * n + Cc] = ve;
-      if (Cc + 1 < m) dst[(size_t)Rr * n + Cc + 1] = vo;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (Cc + i < m) dst[(size_t)Rr * n + Cc + i] = o[i];
     }
   }
 }
