@@ -274,6 +274,13 @@ int32_t gbri_solver_destroy(gbri_solver* s);
  * the call returns with every iteration enqueued behind `stream`'s earlier work and ahead
  * of its later work.  A solver is stepped by one host thread at a time. */
 int32_t gbri_solver_step(gbri_solver* s, int32_t n_iter, void* stream);
+/* Capture the solver's iteration as a CUDA graph now (stream capture on a stream of the
+ * solver's own, thread-local capture mode); otherwise the first graph step or the first batch
+ * step that holds the solver does it.  A program that sets solvers up on one thread while
+ * another thread synchronises or frees device memory should capture on the set-up thread, so
+ * that no capture runs while those calls do.  Idempotent.  Errors: EINVAL (null solver, or kernel
+ * timing on), ECUDA. */
+int32_t gbri_solver_capture(gbri_solver* s);
 /* Reweighted l1 (SARA's reweighting, Sec. 3.1; the weights' formula follows the SARA
  * paper the text cites): sets per-coefficient weights w_i = delta / (delta + |(Psi^dagger x)_i|)
  * from the current iterate x; from then on the l1 prior is gamma sum_i w_i |(Psi^dagger x)_i|
@@ -333,6 +340,11 @@ int32_t gbri_batch_step(gbri_batch* b, int32_t n_iter, void* stream);
 int32_t gbri_profile_enable(int32_t capacity);
 /* Sum of recorded durations (ms) and number of launches of one kind. Synchronises the device. */
 int32_t gbri_profile_read(int32_t kind, double* total_ms, int64_t* launches);
+/* Test hook for allocation-failure handling (the paper has no counterpart): the after_n-th
+ * device allocation the library makes from now on (plan, solver state) fails as if the device
+ * were out of memory, and the call that made it returns GBRI_ENOMEM after releasing what it had
+ * allocated; 0 disarms.  No GPU fault is involved.  Errors: EINVAL (after_n < 0). */
+int32_t gbri_debug_inject_alloc_failure(int32_t after_n);
 /* Total number of library kernel launches since the last gbri_profile_enable / reset. */
 int64_t gbri_launch_count(void);
 void gbri_launch_count_reset(void);

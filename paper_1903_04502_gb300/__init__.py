@@ -309,6 +309,10 @@ class Solver:
     def step(self, n_iter=1, stream=None):
         _lib.check(_lib.load().gbri_solver_step(self._h, int(n_iter), _stream(stream)))
 
+    def capture(self):
+        """Capture the iteration graph now, on this thread (gbri_solver_capture)."""
+        _lib.check(_lib.load().gbri_solver_capture(self._h))
+
     def reweight(self, delta, stream=None):
         """Reweighted l1: w_i = delta / (delta + |(Psi^dagger x)_i|) from the current iterate
         (gbri_solver_reweight)."""
@@ -402,6 +406,12 @@ def profile_read(kind):
     t, n = C.c_double(), C.c_int64()
     _lib.check(_lib.load().gbri_profile_read(int(kind), C.byref(t), C.byref(n)))
     return t.value, n.value
+
+
+def inject_alloc_failure(after_n):
+    """Make the after_n-th device allocation of the library from now on fail with GBRI_ENOMEM
+    (test hook for out-of-memory handling; 0 disarms)."""
+    _lib.check(_lib.load().gbri_debug_inject_alloc_failure(int(after_n)))
 
 
 def launch_count():

@@ -43,6 +43,9 @@ void launch_begin(int kind, cudaStream_t s, bool own = true);
 int32_t launch_end(int kind, cudaStream_t s);  // checks cudaGetLastError
 
 int num_sms();
+// Test hook (gbri_debug_inject_alloc_failure): true for the one device allocation the caller
+// asked to fail; the library's allocation helpers then report GBRI_ENOMEM as for a real failure.
+bool alloc_fault_injected();
 // True while per-kernel event timing is on (graph replay is then avoided so that
 // every kernel launch gets its own event pair).
 bool profiling_enabled();

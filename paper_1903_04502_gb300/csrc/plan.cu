@@ -288,7 +288,7 @@ __global__ void k_tile_starts(const int32_t* __restrict__ offsets, int n_tiles, 
 template <class T>
 int32_t dmalloc(T** p, size_t n, int64_t* acct) {
   if (n == 0) n = 1;
-  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  cudaError_t e = alloc_fault_injected() ? cudaErrorMemoryAllocation : cudaMalloc((void**)p, n * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
     return set_error(GBRI_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -299,7 +299,7 @@ int32_t dmalloc(T** p, size_t n, int64_t* acct) {
 
 int32_t bmalloc(void** p, size_t bytes, int64_t* acct) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = alloc_fault_injected() ? cudaErrorMemoryAllocation : cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
     return set_error(GBRI_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));

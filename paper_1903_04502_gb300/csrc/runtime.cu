@@ -82,6 +82,18 @@ int64_t launch_counter() {
   return g_launches;
 }
 
+namespace {
+std::atomic<int64_t> g_alloc_countdown{0};
+}
+
+bool alloc_fault_injected() {
+  int64_t v = g_alloc_countdown.load(std::memory_order_relaxed);
+  while (v > 0) {
+    if (g_alloc_countdown.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return v == 1;
+  }
+  return false;
+}
+
 int num_sms() {
   // cached per device ordinal: a host may hold GPUs with different SM counts
   constexpr int kMaxDev = 64;
@@ -148,6 +160,12 @@ int32_t gbri_profile_read(int32_t kind, double* total_ms, int64_t* launches) {
   }
   if (total_ms) *total_ms = tot;
   if (launches) *launches = k.used;
+  return GBRI_OK;
+}
+
+int32_t gbri_debug_inject_alloc_failure(int32_t after_n) {
+  if (after_n < 0) return set_error(GBRI_EINVAL, "after_n < 0");
+  g_alloc_countdown.store(after_n, std::memory_order_relaxed);
   return GBRI_OK;
 }
 

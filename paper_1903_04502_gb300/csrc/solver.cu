@@ -626,7 +626,7 @@ int32_t capture_iteration(gbri_solver* S) {
 template <class T>
 int32_t zalloc(T** p, size_t n, cudaStream_t s) {
   if (n == 0) n = 1;
-  if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) {
+  if (alloc_fault_injected() || cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) {
     *p = nullptr;
     return set_error(GBRI_ENOMEM, "cudaMalloc solver state");
   }
@@ -637,7 +637,7 @@ int32_t zalloc(T** p, size_t n, cudaStream_t s) {
 // zeroed device buffer of `bytes` bytes
 int32_t zalloc_bytes(void** p, size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
-  if (cudaMalloc(p, bytes) != cudaSuccess) {
+  if (alloc_fault_injected() || cudaMalloc(p, bytes) != cudaSuccess) {
     *p = nullptr;
     return set_error(GBRI_ENOMEM, "cudaMalloc solver state");
   }
@@ -775,6 +775,11 @@ void solver_add_iterations(gbri_solver* s, int n) { s->iters += n; }
 }  // namespace gbri
 
 extern "C" {
+
+int32_t gbri_solver_capture(gbri_solver* s) {
+  GBRI_CHECK(s, GBRI_EINVAL, "null solver");
+  return solver_iteration_graph(s);
+}
 
 int32_t gbri_solver_create(gbri_solver** out, gbri_plan* plan, gbri_wavelet* wav, const void* d_y,
                            const gbri_solve_params* params, uint32_t flags, void* stream) {

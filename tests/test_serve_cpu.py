@@ -127,3 +127,51 @@ def test_latency_from_arrival_to_result():
         assert j.latency > 0 and j.done_at >= j.admitted_at >= j.arrival
     st = srv.stats()
     assert st["p50_ms"] <= st["p99_ms"]
+
+
+class AsyncFakeEngine(FakeEngine):
+    """Prepares a job over `delay` loop turns (as the GPU engine does on its worker thread);
+    preparation of sizes in `fail_prepare` fails when the job is activated."""
+
+    def __init__(self, clock, delay=3, fail_prepare=()):
+        super().__init__(clock)
+        self.delay = delay
+        self.fail_prepare = set(fail_prepare)
+        self.countdown = {}
+        self.jobs = {}
+
+    def start(self, job):
+        self.countdown[job.job_id] = self.delay
+        self.jobs[job.job_id] = job
+
+    def poll_ready(self):
+        ready = []
+        for jid in list(self.countdown):
+            self.countdown[jid] -= 1
+            if self.countdown[jid] <= 0:
+                ready.append(jid)
+        return ready
+
+    def activate(self, job):
+        self.countdown.pop(job.job_id)
+        if job.n_side in self.fail_prepare:
+            raise MemoryError("gbri error -2: cudaMalloc: out of memory")
+        super().start(job)
+
+
+def test_asynchronous_preparation_and_failed_setup():
+    clk = FakeClock()
+    fp = device_footprint(64, 1000, 4, 9)
+    eng = AsyncFakeEngine(clk, delay=3, fail_prepare={48})
+    srv = Server(eng, hbm_budget=3 * fp, check_every=5, clock=clk)
+    a = srv.submit(job(max_iter=20))
+    bad = srv.submit(job(n=48, max_iter=20))
+    b = srv.submit(job(max_iter=20))
+    assert srv.tick() == -1                 # admitted, still being prepared: nothing to step
+    assert len(srv.preparing) == 3 and not srv.active
+    while srv.queue or srv.preparing or srv.active:
+        srv.tick()
+        assert srv.used <= srv.budget
+    assert bad in srv.failed and "out of memory" in bad.error
+    assert a in srv.done and b in srv.done and srv.used == 0
+    assert all(j.admitted_at > 0 for j in (a, b))
