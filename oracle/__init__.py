@@ -22,6 +22,9 @@ Modules (each function cites the passage of the paper it follows):
 * ``solvers``     -- power iteration for ||Phi||^2, the primal-dual solver
                      (Appendix A.4, Algorithm 7) and Dual Forward-Backward ADMM
                      (Sec. 5, Algorithm 1).
+* ``wstack``      -- the non-coplanar measurement equation (brute force) and its
+                     w-stacking operator (the wide-field method Sec. 7.1 names;
+                     reading R14).
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test to
 something other than itself (closed forms, a brute-force DFT, quadrature,
@@ -29,4 +32,4 @@ orthonormality, a special case with a closed-form solution).  No function is
 "parity unpinned".
 """
 
-from . import kb, measurement, wavelets, prox, solvers  # noqa: F401
+from . import kb, measurement, wavelets, prox, solvers, wstack  # noqa: F401

@@ -79,6 +79,19 @@ def uv_coverage(M, seed=0, outlier_frac=0.0, weights="ones", sigma=np.pi / 3.0):
     return out[perm]
 
 
+def uvw_noncoplanar(M, seed=0, delta=0.01, w_frac=0.5, outlier_frac=0.2, weights="uniform"):
+    """``uv_coverage`` rows with a w column for a non-coplanar array, in wavelengths: with
+    u, v in radians per pixel the baseline length in wavelengths is |(u, v)| / (2 pi delta)
+    (delta the pixel size in direction cosines), and w = w_frac |(u, v)| / (2 pi delta) s, s
+    uniform in [-1, 1]: longer baselines reach larger |w|, and |w| stays below w_frac times
+    the baseline length (an array tilted by up to asin(w_frac) from the plane), float32."""
+    out = uv_coverage(M, seed=seed, outlier_frac=outlier_frac, weights=weights)
+    rng = _rng(seed, _AUX + 1)
+    r = np.sqrt(out[:, 0].astype(np.float64) ** 2 + out[:, 1].astype(np.float64) ** 2) / (2.0 * np.pi * delta)
+    out[:, 2] = (w_frac * r * rng.uniform(-1.0, 1.0, size=M)).astype(np.float32)
+    return out
+
+
 def complex_normal(M, seed=0, stream=_NOISE):
     """Standard complex normal draws CN(0, 1), complex128."""
     rng = _rng(seed, stream)
