@@ -62,6 +62,8 @@ def parse():
                     help="timed iterations per solver of the algorithms leg (0: skip)")
     ap.add_argument("--interp-steps", type=int, default=200,
                     help="timed iterations of the first-order interpolation leg (0: skip)")
+    ap.add_argument("--wstack-planes", default="8,32",
+                    help="comma-separated w-plane counts of the w-stacking leg (empty: skip)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: short power method, no end-to-end, operator or CPU legs")
     return ap.parse_args()
@@ -333,6 +335,43 @@ def serving_leg(args, dev, seed=1000, rate=None, budget_gb=None):
             "jobs_mix": "n in {256,512,1024,2048}, M log-uniform [1e5, 5e7], J in {4,6}, inputs on the device",
             "note": "served vis/s over the span from the first arrival to the last result (includes waiting "
                     "for arrivals and the set-up of each job); one at a time includes each job's set-up"}
+
+
+def wstack_leg(args, dev, cfg, seed=9000, reps=10):
+    """Non-coplanar operator by w-stacking on the FP32 workload's coverage size: 1024^2 image,
+    M = 1e7, J = 4, w tied to baseline length (``synth.uvw_noncoplanar``, w_frac 0.5, pixel
+    size 0.5 / n_side: a 0.5 rad field), for each plane count: ms per application of Phi and
+    Phi^dagger (caller order) and visibilities per second; CUDA events on the launching stream."""
+    import torch
+    import paper_1903_04502_gb300 as g
+    n, M = cfg["n_side"], cfg["M"]
+    delta = 0.5 / n
+    uvw = torch.from_numpy(synth.uvw_noncoplanar(M, seed=seed, delta=delta, w_frac=0.5)).to(dev)
+    x = torch.from_numpy(synth.sky(n, 10, 4, seed=seed).astype(np.float32)).to(dev)
+    stream = torch.cuda.current_stream()
+    out = []
+    for planes in [int(p) for p in args.wstack_planes.split(",") if p]:
+        w = g.WStack(uvw, n, planes, delta, J=cfg["J"], S=cfg["S"])
+        y = w.phi(x)
+        xa = w.phi_adjoint(y)
+        torch.cuda.synchronize()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        for _ in range(reps):
+            w.phi(x, y)
+        b.record(stream)
+        for _ in range(reps):
+            w.phi_adjoint(y, xa)
+        c.record(stream)
+        torch.cuda.synchronize()
+        t_phi, t_adj = a.elapsed_time(b) / reps, b.elapsed_time(c) / reps
+        counts, _ = w.info()
+        out.append({"planes": planes, "non_empty_planes": int((counts > 0).sum()), "phi_ms": t_phi,
+                    "phi_adjoint_ms": t_adj, "phi_vis_per_s": M / (t_phi * 1e-3),
+                    "phi_adjoint_vis_per_s": M / (t_adj * 1e-3)})
+        w.close()
+    return {"n_side": n, "M": M, "pixel_size": delta, "w_frac": 0.5, "runs": out,
+            "note": "two coplanar applications per plane (the screened image's real and imaginary parts)"}
 
 
 def sweep_leg(dev, seed=7000, M=5_000_000, reps=20):
@@ -812,6 +851,9 @@ def run_gbri(args):
     algorithms = None
     if args.algo_steps > 0:
         algorithms = algorithms_leg(args, g, plan, wav, y, eps, opn, gamma, stream, len(cfg["db_orders"]))
+    wstacking = None
+    if args.wstack_planes and ws == 1:
+        wstacking = wstack_leg(args, dev, cfg)
     interpolation = None
     if args.interp_steps > 0:
         interpolation = interp_leg(args, g, cfg, torch.from_numpy(uvw).to(dev), y, eps, opn, gamma, ms_per, stream)
@@ -849,7 +891,7 @@ def run_gbri(args):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "profiled_region": {"steps": k_prof, "ms_per_step": ms_prof, "launch": "kernel by kernel with events"},
         "clocks": clk, "kernels": kern, "operators": ops, "operator_sweep": sweep, "precision": precision,
-        "interpolation": interpolation, "algorithms": algorithms,
+        "interpolation": interpolation, "algorithms": algorithms, "wstacking": wstacking,
         "batching": batching,
         "serving": serving,
         "impl": "gbri",

@@ -60,6 +60,7 @@ extern "C" {
 typedef struct gbri_plan gbri_plan;
 typedef struct gbri_wavelet gbri_wavelet;
 typedef struct gbri_solver gbri_solver;
+typedef struct gbri_wstack gbri_wstack;
 
 /* ---- measurement operator plan (Sec. 2, Eq. 2; Sec. 8.1) ------------------ */
 typedef struct {
@@ -124,6 +125,29 @@ int32_t gbri_plan_tap_mode(const gbri_plan* plan, int32_t* mode);
 /* Plan facts: K, M, number of non-empty 16 x 16 grid tiles, device bytes held. Any pointer may be NULL. */
 int32_t gbri_plan_info(const gbri_plan* plan, int64_t* K, int64_t* M, int64_t* n_tiles,
                        int64_t* device_bytes);
+
+/* ---- non-coplanar measurement operator by w-stacking (Sec. 7.1 names w-stacking as the
+ * software's wide-field method and defers its definition to the wide-field paper; reading R14) --
+ * y_i = w_i sum_{q,p} x[q,p] exp(-i (u_i p' + v_i q')) exp(-2 pi i w_i (n - 1)), n = sqrt(1 - l^2 - m^2),
+ * l = p' pixel_size, m = q' pixel_size: u, v in radians per pixel as for the coplanar plan, w (the
+ * third column of d_uvw_weight) in wavelengths.  The w range is cut into n_planes equal bins;
+ * each visibility's w is replaced by its bin centre w_k, and plane k applies a coplanar plan
+ * (desc, with M the plane's count) to the image times C_k = exp(-2 pi i w_k (n - 1)); the adjoint
+ * sums Re(conj(C_k) (plane k's adjoint)).  The phase error of the binning is at most
+ * 2 pi (dw / 2) max|n - 1| per visibility.  Creation copies the coordinates to the host, bins
+ * them in FP64 and builds one plan per non-empty plane (synchronises `stream`); every plan owns
+ * its grids (about 60 bytes per grid cell in FP32).  Errors: EINVAL (n_planes outside [1, 4096],
+ * pixel_size <= 0, a field of view reaching the horizon, the plan errors), ENONFINITE, ENOMEM, ECUDA. */
+int32_t gbri_wstack_create(gbri_wstack** out, const gbri_plan_desc* desc, const float* d_uvw_weight,
+                           int32_t n_planes, double pixel_size, void* stream);
+int32_t gbri_wstack_destroy(gbri_wstack* w);
+/* Planes, and (host arrays of n_planes entries, may be NULL) visibilities per plane and plane centres w_k. */
+int32_t gbri_wstack_info(const gbri_wstack* w, int32_t* n_planes, int64_t* counts, double* centres);
+/* y = Phi x (caller order): x real [n_side][n_side], y complex [M], desc's precision.  Two coplanar
+ * applications per non-empty plane (the screened image's real and imaginary parts). */
+int32_t gbri_wstack_phi(gbri_wstack* w, const void* d_x, void* d_y, void* stream);
+/* x = Phi^dagger y (x overwritten).  Two coplanar adjoints per non-empty plane. */
+int32_t gbri_wstack_phi_adjoint(gbri_wstack* w, const void* d_y, void* d_x, void* stream);
 
 /* Copy the plan's permutation (plan position -> caller's visibility index) to d_perm [M] int32. */
 int32_t gbri_plan_permutation(const gbri_plan* plan, int32_t* d_perm, void* stream);

@@ -166,6 +166,64 @@ def op_norm(plan, max_iter=200, tol=1e-8, seed=0, stream=None):
     return v.value, it.value
 
 
+class WStack:
+    """Non-coplanar measurement operator by w-stacking (gbri_wstack_create): uvw [M, 4] float32
+    CUDA tensor with w in wavelengths (third column), pixel_size in direction cosines, n_planes
+    equal w bins, each a coplanar plan with the given options."""
+
+    def __init__(self, uvw, n_side, n_planes, pixel_size, oversample=2, J=4, S=4096, beta=0.0,
+                 precision=F32, stream=None):
+        _need(uvw, torch.float32, name="uvw")
+        if uvw.dim() != 2 or uvw.shape[1] != 4:
+            raise ValueError("uvw must be [M, 4]")
+        self.n_side, self.M = int(n_side), int(uvw.shape[0])
+        self.precision = _precision(precision)
+        self.real_dtype, self.complex_dtype = _REAL[self.precision], _CPLX[self.precision]
+        d = _lib.PlanDesc(self.n_side, int(oversample), int(J), int(S), float(beta), self.M, self.precision, 0, 0, 0, 0)
+        h = C.c_void_p()
+        _lib.check(_lib.load().gbri_wstack_create(C.byref(h), C.byref(d), _ptr(uvw), int(n_planes), float(pixel_size),
+                                                  _stream(stream)))
+        self._h = h
+        self.n_planes = int(n_planes)
+
+    def info(self):
+        """(visibilities per plane, plane centres w_k) as numpy arrays."""
+        import numpy as np
+        n = C.c_int32()
+        counts = np.zeros(self.n_planes, dtype=np.int64)
+        centres = np.zeros(self.n_planes, dtype=np.float64)
+        _lib.check(_lib.load().gbri_wstack_info(self._h, C.byref(n), C.c_void_p(counts.ctypes.data),
+                                                C.c_void_p(centres.ctypes.data)))
+        return counts, centres
+
+    def phi(self, x, y=None, stream=None):
+        _need(x, self.real_dtype, (self.n_side, self.n_side), "x")
+        if y is None:
+            y = torch.empty(self.M, dtype=self.complex_dtype, device=x.device)
+        _need(y, self.complex_dtype, (self.M,), "y")
+        _lib.check(_lib.load().gbri_wstack_phi(self._h, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def phi_adjoint(self, y, x=None, stream=None):
+        _need(y, self.complex_dtype, (self.M,), "y")
+        if x is None:
+            x = torch.empty((self.n_side, self.n_side), dtype=self.real_dtype, device=y.device)
+        _need(x, self.real_dtype, (self.n_side, self.n_side), "x")
+        _lib.check(_lib.load().gbri_wstack_phi_adjoint(self._h, _ptr(y), _ptr(x), _stream(stream)))
+        return x
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().gbri_wstack_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Wavelet:
     """SARA dictionary (gbri_wavelet_create): db_orders with 0 = Dirac, N = dbN; precision F32 or F64."""
 

@@ -54,6 +54,11 @@ SIGNATURES = {
     "gbri_plan_launch_config": (I32, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
     "gbri_plan_tap_mode": (I32, [P, C.POINTER(I32)]),
     "gbri_solver_capture": (I32, [P]),
+    "gbri_wstack_create": (I32, [P, P, P, I32, D, P]),
+    "gbri_wstack_destroy": (I32, [P]),
+    "gbri_wstack_info": (I32, [P, C.POINTER(I32), P, P]),
+    "gbri_wstack_phi": (I32, [P, P, P, P]),
+    "gbri_wstack_phi_adjoint": (I32, [P, P, P, P]),
     "gbri_debug_inject_alloc_failure": (I32, [I32]),
     "gbri_plan_permutation": (I32, [P, P, P]),
     "gbri_vis_reorder": (I32, [P, P, P, I32, P]),
