@@ -113,6 +113,17 @@ int32_t gbri_plan_destroy(gbri_plan* plan);
 int32_t gbri_plan_launch_config(const gbri_plan* plan, int32_t* vis_per_run, int32_t* degrid_blocks,
                                 int32_t* grid_blocks);
 
+/* Bounds-check report of a library built with GBRI_DEBUG (paper_1903_04502_gb300/build.py,
+ * debug=True: libgbri_debug.so; the paper has no counterpart).  In that build every visibility
+ * kernel checks its window, accumulator, grid, half-spectrum, slot and visibility indices; an
+ * index that would leave its buffer sets a bit in the plan's device error word (1 window,
+ * 2 accumulator, 4 grid, 8 visibility position, 16 half spectrum, 32 deterministic slot),
+ * records the first such index, and the access is skipped (no trap).  Copies the bits and that
+ * index (may be NULL) to the host and clears the word when reset != 0; synchronises `stream`.
+ * Errors: EINVAL (null arguments, or a library built without the checks). */
+int32_t gbri_plan_debug_word(const gbri_plan* plan, uint32_t* bits, int64_t* first_index, int32_t reset,
+                             void* stream);
+
 /* How the plan's visibility kernels get the Kaiser-Bessel tap weights (Sec. 8.1):
  * 0 = the zeroth-order pre-sampled table in shared memory; 1 = first-order interpolation
  * between table samples (interp_order = 1); 2 = FP32 zeroth-order plans: a polynomial fit of

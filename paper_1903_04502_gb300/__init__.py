@@ -105,6 +105,13 @@ class Plan:
         _lib.check(_lib.load().gbri_plan_launch_config(self._h, C.byref(r), C.byref(d), C.byref(g_)))
         return r.value, d.value, g_.value
 
+    def debug_word(self, reset=True, stream=None):
+        """(error bits, first bad index) of a GBRI_DEBUG library build (gbri_plan_debug_word)."""
+        b, i = C.c_uint32(), C.c_int64()
+        _lib.check(_lib.load().gbri_plan_debug_word(self._h, C.byref(b), C.byref(i), 1 if reset else 0,
+                                                    _stream(stream)))
+        return b.value, i.value
+
     def tap_mode(self):
         """0: shared-memory table, 1: first-order table, 2: polynomial taps (gbri_plan_tap_mode)."""
         m = C.c_int32()

@@ -9,7 +9,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgbri.so")
+# GBRI_DEBUG_LIB=1 selects the bounds-checked build libgbri_debug.so (build(debug=True))
+LIB_PATH = os.path.join(HERE, "libgbri_debug.so" if os.environ.get("GBRI_DEBUG_LIB") == "1" else "libgbri.so")
 
 OK = 0
 EINVAL, ENOMEM, ECUDA, ECUFFT, ETIMEOUT, ENONFINITE = -1, -2, -3, -4, -5, -6
@@ -54,6 +55,7 @@ SIGNATURES = {
     "gbri_plan_launch_config": (I32, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
     "gbri_plan_tap_mode": (I32, [P, C.POINTER(I32)]),
     "gbri_solver_capture": (I32, [P]),
+    "gbri_plan_debug_word": (I32, [P, C.POINTER(U32), C.POINTER(I64), I32, P]),
     "gbri_wstack_create": (I32, [P, P, P, I32, D, P]),
     "gbri_wstack_destroy": (I32, [P]),
     "gbri_wstack_info": (I32, [P, C.POINTER(I32), P, P]),
@@ -110,7 +112,7 @@ def load():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libgbri.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        raise ImportError("%s is not built; run __graft_entry__.build()" % LIB_PATH)
     lib = C.CDLL(LIB_PATH)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)

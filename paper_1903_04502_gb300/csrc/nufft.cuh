@@ -52,6 +52,27 @@ constexpr int kWinPitch = 22;
 constexpr int kLog2FracSteps = 8;
 constexpr int kFracSteps = 1 << kLog2FracSteps;
 
+// Bounds checks of the GBRI_DEBUG build: an index that would leave its buffer sets a bit in
+// the plan's device error word (and the first such index beside it) and the access is
+// skipped; nothing traps.  In the default build every check is the constant true.
+enum DebugBit : unsigned {
+  kDbgWindow = 1u,       // degridding window / shared spectrum block
+  kDbgAccum = 2u,        // gridding accumulator
+  kDbgGrid = 4u,         // grid cell of the flush
+  kDbgVis = 8u,          // visibility position (metadata, streams)
+  kDbgSpec = 16u,        // half-spectrum cell
+  kDbgSlot = 32u,        // deterministic window slot
+};
+__device__ __forceinline__ bool debug_fail(unsigned int* word, unsigned int bit, long long idx) {
+  if (word && atomicOr(word, bit) == 0u) *reinterpret_cast<long long*>(word + 2) = idx;
+  return false;
+}
+#ifdef GBRI_DEBUG
+#define GBRI_DCHECK(word, cond, bit, idx) ((cond) || ::gbri::debug_fail((word), (bit), (long long)(idx)))
+#else
+#define GBRI_DCHECK(word, cond, bit, idx) true
+#endif
+
 // How a visibility kernel gets its tap weights:
 //   kTapTable: zeroth-order pre-sampled table in shared memory (Sec. 8.1);
 //   kTapFO:    first-order interpolation between two table rows (Sec. 8.1, reading R13);
@@ -120,6 +141,7 @@ struct gbri_plan {
   // work counters of the kTapPoly kernels, a pair {next item, finished blocks} per kernel
   // (degridding, gridding, fused); zero between launches
   unsigned int* work = nullptr;
+  unsigned int* dbg = nullptr;  // GBRI_DEBUG builds: {error bits, 0, first bad index (int64)}
   // deterministic gridding: every gridding work item writes its (T + J - 1)^2 window to
   // slots[item] (plan precision, complex), and k_grid_reduce sums, for every grid cell, the
   // windows covering it in a fixed order (tiles by position, a tile's items by index)
@@ -195,6 +217,8 @@ struct VisGeom {
   const void* __restrict__ wtab;
   const uint16_t* __restrict__ frac;  // first-order fractions (null: zeroth order)
   void* slots;                         // deterministic gridding: per-item windows (null: atomics)
+  unsigned int* dbg;                   // GBRI_DEBUG builds: the plan's error word (else null)
+  int64_t M;                           // visibilities (bounds checks)
   int n_chunks, n_gtiles, K, log2S, nT;
   PolyTaps poly;                       // kTapPoly coefficients (kernel parameter space)
 };
@@ -223,6 +247,8 @@ inline VisGeom vis_geom(const gbri_plan* p) {
   g.wtab = p->wtab;
   g.frac = p->frac;
   g.slots = p->det ? p->slots : nullptr;
+  g.dbg = p->dbg;
+  g.M = p->M;
   g.n_chunks = (int)p->n_chunks;
   g.n_gtiles = (int)p->n_gtiles;
   g.K = p->K;

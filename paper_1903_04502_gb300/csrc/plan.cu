@@ -11,6 +11,7 @@
 #include <array>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
@@ -364,6 +365,7 @@ void destroy_plan(gbri_plan* p) {
   cudaFree(p->partials);
   cudaFree(p->scalars);
   cudaFree(p->work);
+  cudaFree(p->dbg);
   cudaFree(p->slots);
   cudaFree(p->tile_items_off);
   cudaFree(p->tile_items);
@@ -726,6 +728,10 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   GBRI_CHECK_CUDA(cudaMemsetAsync(p->scalars, 0, 64 * sizeof(double), s));
   GBRI_TRY(dmalloc(&p->work, 16, &p->device_bytes));
   GBRI_CHECK_CUDA(cudaMemsetAsync(p->work, 0, 16 * sizeof(unsigned int), s));
+#ifdef GBRI_DEBUG
+  GBRI_TRY(dmalloc(&p->dbg, 4, &p->device_bytes));
+  GBRI_CHECK_CUDA(cudaMemsetAsync(p->dbg, 0, 4 * sizeof(unsigned int), s));
+#endif
   if (cufftPlan2d(&p->fft, K, K, p->prec == GBRI_F64 ? CUFFT_Z2Z : CUFFT_C2C) != CUFFT_SUCCESS) {
     cudaFree(meta_cell); cudaFree(perm_cell);
     return set_error(GBRI_ECUFFT, "cufftPlan2d failed");
@@ -895,6 +901,24 @@ int32_t gbri_plan_launch_config(const gbri_plan* p, int32_t* run, int32_t* dg, i
   if (run) *run = p->run_len;
   if (dg) *dg = p->degrid_blocks;
   if (gr) *gr = p->grid_blocks;
+  return GBRI_OK;
+}
+
+int32_t gbri_plan_debug_word(const gbri_plan* p, uint32_t* bits, int64_t* first_index, int32_t reset,
+                             void* stream) {
+  GBRI_CHECK(p && bits, GBRI_EINVAL, "null argument");
+  GBRI_CHECK(p->dbg, GBRI_EINVAL, "the library was built without GBRI_DEBUG bounds checks");
+  uint32_t h[4] = {0, 0, 0, 0};
+  cudaStream_t s = (cudaStream_t)stream;
+  GBRI_CHECK_CUDA(cudaMemcpyAsync(h, p->dbg, sizeof(h), cudaMemcpyDeviceToHost, s));
+  if (reset) GBRI_CHECK_CUDA(cudaMemsetAsync(p->dbg, 0, sizeof(h), s));
+  GBRI_CHECK_CUDA(cudaStreamSynchronize(s));
+  *bits = h[0];
+  if (first_index) {
+    int64_t v = 0;
+    std::memcpy(&v, &h[2], sizeof(v));
+    *first_index = v;
+  }
   return GBRI_OK;
 }
 

@@ -80,7 +80,7 @@ __device__ __forceinline__ void release_items(unsigned int* ctr) {
 // with one lane per column.  Others (the window crosses column 0 or K/2) go cell by cell.
 template <int J>
 __device__ __forceinline__ void load_window_f32(float2* win, const float2* __restrict__ spec, int tile, int nT, int K,
-                                                int lane) {
+                                                int lane, unsigned int* dbg = nullptr) {
   constexpr int P = kTile + J - 1;
   const int H = (K >> 1) + 1;
   const int ty = tile / nT, tx = tile - ty * nT;
@@ -89,7 +89,10 @@ __device__ __forceinline__ void load_window_f32(float2* win, const float2* __res
     if (lane < P) {
       const float2* src = spec + ox + lane;
 #pragma unroll 5
-      for (int r = 0; r < P; ++r) win[r * kWinPitch + lane] = __ldg(src + (size_t)wrapK(oy + r, K) * H);
+      for (int r = 0; r < P; ++r) {
+        const size_t q = (size_t)wrapK(oy + r, K) * H + ox + lane;
+        if (GBRI_DCHECK(dbg, q < (size_t)K * H, kDbgSpec, q)) win[r * kWinPitch + lane] = __ldg(spec + q);
+      }
     }
   } else if (ox > (K >> 1) && ox + P - 1 < K) {
     if (lane < P) {
@@ -97,7 +100,9 @@ __device__ __forceinline__ void load_window_f32(float2* win, const float2* __res
 #pragma unroll 5
       for (int r = 0; r < P; ++r) {
         const int ky = wrapK(oy + r, K);
-        float2 v = __ldg(src + (size_t)(ky == 0 ? 0 : K - ky) * H);
+        const size_t q = (size_t)(ky == 0 ? 0 : K - ky) * H + (K - ox - lane);
+        if (!GBRI_DCHECK(dbg, q < (size_t)K * H, kDbgSpec, q)) continue;
+        float2 v = __ldg(spec + q);
         v.y = -v.y;
         win[r * kWinPitch + lane] = v;
       }
@@ -108,7 +113,9 @@ __device__ __forceinline__ void load_window_f32(float2* win, const float2* __res
       const int ky = wrapK(oy + r, K), kx = wrapK(ox + cc, K);
       const bool mirror = kx > (K >> 1);
       const int sy = mirror ? (ky == 0 ? 0 : K - ky) : ky, sx = mirror ? K - kx : kx;
-      float2 v = __ldg(spec + (size_t)sy * H + sx);
+      const size_t q = (size_t)sy * H + sx;
+      if (!GBRI_DCHECK(dbg, q < (size_t)K * H, kDbgSpec, q)) continue;
+      float2 v = __ldg(spec + q);
       if (mirror) v.y = -v.y;
       win[r * kWinPitch + cc] = v;
     }
@@ -147,14 +154,14 @@ __global__ void __launch_bounds__(kThreads, 3)
 #pragma unroll
       for (int k = 0; k < kRun; ++k) {
         const int i = b0 + lane + 32 * k;
-        if (i < cnt) {
+        if (i < cnt && GBRI_DCHECK(geo.dbg, lo + i < geo.M, kDbgVis, lo + i)) {
           m[k] = geo.meta[lo + i];
           pre[k] = epi.pre_from(streams, lo + i);
         }
       }
       if (ch.x != cur_tile) {  // warp-uniform
         __syncwarp();
-        load_window_f32<J>(win, spec, ch.x, geo.nT, K, lane);
+        load_window_f32<J>(win, spec, ch.x, geo.nT, K, lane, geo.dbg);
         cur_tile = ch.x;
         __syncwarp();
       }
@@ -164,7 +171,9 @@ __global__ void __launch_bounds__(kThreads, 3)
         if (i >= cnt) break;
         float2 w[J];
         taps_xy<J>(geo.poly, m[k].x, S, two_over_S, w);
-        const float2* base = win + ((int)(m[k].x >> 16) >> geo.log2S) * kWinPitch + ((int)(m[k].x & 0xffff) >> geo.log2S);
+        const int cy = (int)(m[k].x >> 16) >> geo.log2S, cx = (int)(m[k].x & 0xffff) >> geo.log2S;
+        const bool in_win = GBRI_DCHECK(geo.dbg, cy < kTile && cx < kTile, kDbgWindow, lo + i);
+        const float2* base = win + (in_win ? cy * kWinPitch + cx : 0);
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int tp = 0; tp < J; ++tp) {
@@ -224,16 +233,21 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
       int a0 = 0;
+      bool in_acc = true;
       for (int k0 = 0; k0 < sr.y; k0 += kRun) {
         uint2 m[kRun];
         float2 v[kRun];
 #pragma unroll
         for (int k = 0; k < kRun; ++k)
-          if (k0 + k < sr.y) {
+          if (k0 + k < sr.y && GBRI_DCHECK(geo.dbg, sr.x + k0 + k < geo.M, kDbgVis, sr.x + k0 + k)) {
             m[k] = geo.meta[sr.x + k0 + k];
             v[k] = src(sr.x + k0 + k, sctx);
           }
-        if (k0 == 0) a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S);
+        if (k0 == 0) {
+          const int cy = (int)(m[0].x >> 16) >> geo.log2S, cx = (int)(m[0].x & 0xffff) >> geo.log2S;
+          in_acc = GBRI_DCHECK(geo.dbg, cy < kTile && cx < kTile, kDbgAccum, sr.x);
+          a0 = in_acc ? cy * kAccPitch2 + cx : 0;
+        }
 #pragma unroll
         for (int k = 0; k < kRun; ++k) {
           if (k0 + k >= sr.y) break;
@@ -248,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
         }
       }
-      const bool active = sr.y > 0;
+      const bool active = sr.y > 0 && in_acc;
 #pragma unroll
       for (int tp = 0; tp < J; ++tp)
 #pragma unroll
@@ -269,10 +283,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       const float2 a = *q;
       *q = make_float2(0.f, 0.f);
       if (geo.slots) {  // deterministic: the whole window to the item's slot
-        static_cast<float2*>(geo.slots)[(size_t)it * (P * P) + i] = a;
+        if (GBRI_DCHECK(geo.dbg, it < geo.n_gtiles, kDbgSlot, it))
+          static_cast<float2*>(geo.slots)[(size_t)it * (P * P) + i] = a;
         continue;
       }
-      float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      const size_t gq = (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      if (!GBRI_DCHECK(geo.dbg, gq < (size_t)K * K, kDbgGrid, gq)) continue;
+      float2* dst = grid + gq;
       if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) *dst = a;
       else if (a.x != 0.f || a.y != 0.f) atomicAdd(dst, a);
     }
@@ -287,7 +304,11 @@ __global__ void __launch_bounds__(kThreads, 2)
 // warp per gridding work item and one lane per run; the lane holds its cell's J x J window
 // block in registers, and per visibility one tap evaluation serves both directions.  Two
 // visibilities per lane in flight (the window block and the patch take 64 registers; four
-// in flight spilled and ran 15 % slower).
+// in flight spilled and ran 15 % slower).  Items are taken in a fixed order (warp w: items
+// w, w + warps, ...), not from the counter: the kernel then releases SMs one by one as its
+// warps finish, and the primal-dual iteration's wavelet branch, which runs beside it, fills
+// them (0.389 against 0.403 ms per iteration, although the kernel alone takes 215 us instead
+// of 194 with the counter).
 constexpr int kFusedRun = 2;
 template <int J, class Epi>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -309,12 +330,12 @@ __global__ void __launch_bounds__(kThreads, 2)
   const E* streams[2] = {Epi::kStreams > 0 ? epi.stream(0) : nullptr, Epi::kStreams > 1 ? epi.stream(1) : nullptr};
   epi.init();  // block barrier: zeroed accumulators in place
   constexpr int lo_x = J - 1, hi_x = kTile;
-  int it = first_item(ctr, geo.slots != nullptr);
+  int it = first_item(ctr, true);
   while (it < geo.n_gtiles) {
-    const int it_next = next_item(ctr, geo.slots != nullptr, it);
+    const int it_next = next_item(ctr, true, it);
     const int4 gt = geo.gtiles[it];
     int2 sr = geo.subruns[gt.y + lane];  // gt.z is a multiple of 32
-    load_window_f32<J>(win, spec, gt.x, geo.nT, K, lane);
+    load_window_f32<J>(win, spec, gt.x, geo.nT, K, lane, geo.dbg);
     __syncwarp();
     for (int b0 = 0; b0 < gt.z; b0 += 32) {
       const int2 sr_next = (b0 + 32 < gt.z) ? geo.subruns[gt.y + b0 + 32 + lane] : make_int2(0, 0);
@@ -325,17 +346,20 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
       int a0 = 0;
+      bool in_win = true;
       for (int k0 = 0; k0 < sr.y; k0 += kFusedRun) {
         uint2 m[kFusedRun];
         typename Epi::Pre pre[kFusedRun];
 #pragma unroll
         for (int k = 0; k < kFusedRun; ++k)
-          if (k0 + k < sr.y) {
+          if (k0 + k < sr.y && GBRI_DCHECK(geo.dbg, sr.x + k0 + k < geo.M, kDbgVis, sr.x + k0 + k)) {
             m[k] = geo.meta[sr.x + k0 + k];
             pre[k] = epi.pre_from(streams, sr.x + k0 + k);
           }
         if (k0 == 0) {  // the run's cell: its J x J block of the window
-          a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kWinPitch + ((int)(m[0].x & 0xffff) >> geo.log2S);
+          const int cy = (int)(m[0].x >> 16) >> geo.log2S, cx = (int)(m[0].x & 0xffff) >> geo.log2S;
+          in_win = GBRI_DCHECK(geo.dbg, cy < kTile && cx < kTile, kDbgWindow, sr.x);
+          a0 = in_win ? cy * kWinPitch + cx : 0;
 #pragma unroll
           for (int tp = 0; tp < J; ++tp)
 #pragma unroll
@@ -365,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
         }
       }
-      const bool active = sr.y > 0;
+      const bool active = sr.y > 0 && in_win;
 #pragma unroll
       for (int tp = 0; tp < J; ++tp)
 #pragma unroll
@@ -386,10 +410,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       const float2 a = *q;
       *q = make_float2(0.f, 0.f);
       if (geo.slots) {  // deterministic: the whole window to the item's slot
-        static_cast<float2*>(geo.slots)[(size_t)it * (P * P) + i] = a;
+        if (GBRI_DCHECK(geo.dbg, it < geo.n_gtiles, kDbgSlot, it))
+          static_cast<float2*>(geo.slots)[(size_t)it * (P * P) + i] = a;
         continue;
       }
-      float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      const size_t gq = (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      if (!GBRI_DCHECK(geo.dbg, gq < (size_t)K * K, kDbgGrid, gq)) continue;
+      float2* dst = grid + gq;
       if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) *dst = a;
       else if (a.x != 0.f || a.y != 0.f) atomicAdd(dst, a);
     }

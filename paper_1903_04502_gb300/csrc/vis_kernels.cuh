@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
 #pragma unroll
       for (int k = 0; k < kRun; ++k) {
         const int i = b0 + lane + 32 * k;
-        if (i < cnt) {
+        if (i < cnt && GBRI_DCHECK(geo.dbg, lo + i < geo.M, kDbgVis, lo + i)) {
           m[k] = geo.meta[lo + i];
           if constexpr (TM == kTapFO) fr[k] = geo.frac[lo + i];
           pre[k] = epi.pre_from(streams, lo + i);
@@ -67,7 +67,9 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
           const int ky = wrapK(oy + r, K), kx = wrapK(ox + cc, K);
           const bool mirror = kx > (K >> 1);
           const int sy = mirror ? (ky == 0 ? 0 : K - ky) : ky, sx = mirror ? K - kx : kx;
-          C v = __ldg(spec + (size_t)sy * H + sx);
+          const size_t q = (size_t)sy * H + sx;
+          if (!GBRI_DCHECK(geo.dbg, q < (size_t)K * H, kDbgSpec, q)) continue;
+          C v = __ldg(spec + q);
           if (mirror) v.y = -v.y;
           win[r * kWinPitch + cc] = v;
         }
@@ -87,7 +89,9 @@ __global__ void __launch_bounds__(kThreads, degrid_occupancy(sizeof(typename Epi
           load_taps<J>(sw, lx & (S - 1), S, wx);
           load_taps<J>(sw, ly & (S - 1), S, wy);
         }
-        const C* base = win + (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S);
+        const bool in_win = GBRI_DCHECK(geo.dbg, (ly >> geo.log2S) < kTile && (lx >> geo.log2S) < kTile, kDbgWindow,
+                                         lo + i);
+        const C* base = win + (in_win ? (ly >> geo.log2S) * kWinPitch + (lx >> geo.log2S) : 0);
         R ar = 0, ai = 0;
 #pragma unroll
         for (int tp = 0; tp < J; ++tp) {
@@ -155,18 +159,23 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
 #pragma unroll
         for (int t = 0; t < J; ++t) pt[tp][t] = mkc<R>(0, 0);
       int a0 = 0;
+      bool in_acc = true;
       for (int k0 = 0; k0 < sr.y; k0 += kRun) {
         uint2 m[kRun];
         uint32_t fr[kRun];
         C v[kRun];
 #pragma unroll
         for (int k = 0; k < kRun; ++k)
-          if (k0 + k < sr.y) {
+          if (k0 + k < sr.y && GBRI_DCHECK(geo.dbg, sr.x + k0 + k < geo.M, kDbgVis, sr.x + k0 + k)) {
             m[k] = geo.meta[sr.x + k0 + k];
             if constexpr (TM == kTapFO) fr[k] = geo.frac[sr.x + k0 + k];
             v[k] = src(sr.x + k0 + k, sctx);
           }
-        if (k0 == 0) a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kAccPitch2 + ((int)(m[0].x & 0xffff) >> geo.log2S);
+        if (k0 == 0) {
+          const int cy = (int)(m[0].x >> 16) >> geo.log2S, cx = (int)(m[0].x & 0xffff) >> geo.log2S;
+          in_acc = GBRI_DCHECK(geo.dbg, cy < kTile && cx < kTile, kDbgAccum, sr.x);
+          a0 = in_acc ? cy * kAccPitch2 + cx : 0;
+        }
 #pragma unroll
         for (int k = 0; k < kRun; ++k) {
           if (k0 + k >= sr.y) break;
@@ -198,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
       for (int tp = 0; tp < J; ++tp)
 #pragma unroll
         for (int t = 0; t < J; ++t) {
-          if (active) {
+          if (active && in_acc) {
             C* q = acc + a0 + tp * kAccPitch2 + t;
             const C o = *q;
             *q = mkc<R>(o.x + pt[tp][t].x, o.y + pt[tp][t].y);
@@ -214,10 +223,12 @@ __global__ void __launch_bounds__(kThreads, grid_occupancy(sizeof(typename Src::
       const C a = *q;
       *q = mkc<R>(0, 0);
       if (geo.slots) {  // deterministic: the whole window to the item's slot
-        static_cast<C*>(geo.slots)[(size_t)it * (P * P) + i] = a;
+        if (GBRI_DCHECK(geo.dbg, it < geo.n_gtiles, kDbgSlot, it)) static_cast<C*>(geo.slots)[(size_t)it * (P * P) + i] = a;
         continue;
       }
-      C* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      const size_t gq = (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      if (!GBRI_DCHECK(geo.dbg, gq < (size_t)K * K, kDbgGrid, gq)) continue;
+      C* dst = grid + gq;
       if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) {
         *dst = a;
       } else if (a.x != 0 || a.y != 0) {
@@ -275,7 +286,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int ky = wrapK(oy + r, K), kx = wrapK(ox + cc, K);
       const bool mirror = kx > (K >> 1);
       const int sy = mirror ? (ky == 0 ? 0 : K - ky) : ky, sx = mirror ? K - kx : kx;
-      C v = __ldg(spec + (size_t)sy * H + sx);
+      const size_t q = (size_t)sy * H + sx;
+      if (!GBRI_DCHECK(geo.dbg, q < (size_t)K * H, kDbgSpec, q)) continue;
+      C v = __ldg(spec + q);
       if (mirror) v.y = -v.y;
       win[r * kWinPitch + cc] = v;
     }
@@ -290,19 +303,22 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int t = 0; t < J; ++t) pt[tp][t] = mkc<R>(0, 0);
       int a0 = 0;
+      bool in_acc = true;
       for (int k0 = 0; k0 < sr.y; k0 += kRun) {
         uint2 m[kRun];
         uint32_t fr[kRun];
         typename Epi::Pre pre[kRun];
 #pragma unroll
         for (int k = 0; k < kRun; ++k)
-          if (k0 + k < sr.y) {
+          if (k0 + k < sr.y && GBRI_DCHECK(geo.dbg, sr.x + k0 + k < geo.M, kDbgVis, sr.x + k0 + k)) {
             m[k] = geo.meta[sr.x + k0 + k];
             if constexpr (TM == kTapFO) fr[k] = geo.frac[sr.x + k0 + k];
             pre[k] = epi.pre_from(streams, sr.x + k0 + k);
           }
         if (k0 == 0) {  // the run's cell: its J x J block of the window
-          a0 = ((int)(m[0].x >> 16) >> geo.log2S) * kWinPitch + ((int)(m[0].x & 0xffff) >> geo.log2S);
+          const int cy = (int)(m[0].x >> 16) >> geo.log2S, cx = (int)(m[0].x & 0xffff) >> geo.log2S;
+          in_acc = GBRI_DCHECK(geo.dbg, cy < kTile && cx < kTile, kDbgWindow, sr.x);
+          a0 = in_acc ? cy * kWinPitch + cx : 0;
 #pragma unroll
           for (int tp = 0; tp < J; ++tp)
 #pragma unroll
@@ -350,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int tp = 0; tp < J; ++tp)
 #pragma unroll
         for (int t = 0; t < J; ++t) {
-          if (active) {
+          if (active && in_acc) {
             C* q = acc + a0 + tp * kAccPitch2 + t;
             const C o = *q;
             *q = mkc<R>(o.x + pt[tp][t].x, o.y + pt[tp][t].y);
@@ -364,10 +380,12 @@ __global__ void __launch_bounds__(kThreads, 2)
       const C a = *q;
       *q = mkc<R>(0, 0);
       if (geo.slots) {  // deterministic: the whole window to the item's slot
-        static_cast<C*>(geo.slots)[(size_t)it * (P * P) + i] = a;
+        if (GBRI_DCHECK(geo.dbg, it < geo.n_gtiles, kDbgSlot, it)) static_cast<C*>(geo.slots)[(size_t)it * (P * P) + i] = a;
         continue;
       }
-      C* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      const size_t gq = (size_t)wrapK(oy + r, K) * K + wrapK(ox + cc, K);
+      if (!GBRI_DCHECK(geo.dbg, gq < (size_t)K * K, kDbgGrid, gq)) continue;
+      C* dst = grid + gq;
       if (gt.w == 0 && r >= lo_x && r < hi_x && cc >= lo_x && cc < hi_x) *dst = a;
       else if (a.x != 0 || a.y != 0) atomicAdd(dst, a);
     }
