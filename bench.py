@@ -564,11 +564,12 @@ def interp_leg(args, g, cfg, uvw_dev, y, eps, opn, gamma, ms_zeroth, stream):
             "note": "same data, ||Phi||^2, gamma and eps; FP32 path; CUDA-graph replays"}
 
 
-def algorithms_leg(args, g, plan, wav, y, eps, opn, gamma, stream, nw):
+def algorithms_leg(args, g, plan, wav, y, eps, opn, gamma, stream, nw, uvw_dev=None, cfg=None):
     """The other solvers and options on the same plan and data (graph replays, CUDA events):
     ms per iteration of Dual-FB ADMM, FISTA (default gamma), primal-dual with 8 local l2
-    balls and primal-dual after one reweighting; and the proximal operators on the
-    workload's vectors (the coefficient stack and the visibilities), us per call."""
+    balls, primal-dual after one reweighting and primal-dual on a deterministic plan (its
+    cost: bitwise-reproducible gridding); and the proximal operators on the workload's
+    vectors (the coefficient stack and the visibilities), us per call."""
     import torch
     n, M = plan.n_side, plan.M
     steps = args.algo_steps
@@ -592,6 +593,12 @@ def algorithms_leg(args, g, plan, wav, y, eps, opn, gamma, stream, nw):
             s.reweight(1e-3)
         out[name + "_ms_per_iter"] = per_iter(s)
         s.close()
+    if uvw_dev is not None:
+        pdet = g.Plan(uvw_dev, n, oversample=cfg["oversample"], J=cfg["J"], S=cfg["S"], deterministic=True)
+        s = g.Solver(pdet, wav, y, eps=eps, op_norm_sq=opn, gamma=gamma)
+        out["pd_deterministic_ms_per_iter"] = per_iter(s)
+        s.close()
+        pdet.close()
 
     def per_call(fn, reps=200):
         for _ in range(5):
@@ -850,7 +857,8 @@ def run_gbri(args):
         precision = precision_leg(args, g, cfg, torch.from_numpy(uvw).to(dev), y, eps, opn, gamma, ms_per, stream)
     algorithms = None
     if args.algo_steps > 0:
-        algorithms = algorithms_leg(args, g, plan, wav, y, eps, opn, gamma, stream, len(cfg["db_orders"]))
+        algorithms = algorithms_leg(args, g, plan, wav, y, eps, opn, gamma, stream, len(cfg["db_orders"]),
+                                    torch.from_numpy(uvw).to(dev), cfg)
     wstacking = None
     if args.wstack_planes and ws == 1:
         wstacking = wstack_leg(args, dev, cfg)

@@ -304,11 +304,13 @@ __global__ void __launch_bounds__(kThreads, 2)
 // warp per gridding work item and one lane per run; the lane holds its cell's J x J window
 // block in registers, and per visibility one tap evaluation serves both directions.  Two
 // visibilities per lane in flight (the window block and the patch take 64 registers; four
-// in flight spilled and ran 15 % slower).  Items are taken in a fixed order (warp w: items
-// w, w + warps, ...), not from the counter: the kernel then releases SMs one by one as its
-// warps finish, and the primal-dual iteration's wavelet branch, which runs beside it, fills
-// them (0.389 against 0.403 ms per iteration, although the kernel alone takes 215 us instead
-// of 194 with the counter).
+// in flight spilled and ran 15 % slower).  Items come from the counter ctr (dynamic,
+// heaviest first), so that blocks which start late -- the iteration's wavelet branch holds
+// SMs when the kernel is launched -- take fewer items instead of stretching the kernel: with
+// items in a fixed order the iteration took either 0.390 or 0.406 ms depending on how the two
+// branches met, with the counter 0.386-0.388 ms, and the kernel alone 178 us against 207.
+// Deterministic plans keep the fixed order (each block's partial of the ball norm then covers
+// the same items in every run).
 constexpr int kFusedRun = 2;
 template <int J, class Epi>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -330,9 +332,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   const E* streams[2] = {Epi::kStreams > 0 ? epi.stream(0) : nullptr, Epi::kStreams > 1 ? epi.stream(1) : nullptr};
   epi.init();  // block barrier: zeroed accumulators in place
   constexpr int lo_x = J - 1, hi_x = kTile;
-  int it = first_item(ctr, true);
+  const bool fixed = geo.slots != nullptr;  // deterministic plans: the same block partials every run
+  int it = first_item(ctr, fixed);
   while (it < geo.n_gtiles) {
-    const int it_next = next_item(ctr, true, it);
+    const int it_next = next_item(ctr, fixed, it);
     const int4 gt = geo.gtiles[it];
     int2 sr = geo.subruns[gt.y + lane];  // gt.z is a multiple of 32
     load_window_f32<J>(win, spec, gt.x, geo.nT, K, lane, geo.dbg);

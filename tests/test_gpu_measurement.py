@@ -168,11 +168,11 @@ def test_plan_order_and_permutation(g):
     assert rel(b, a) <= 1e-6
 
 
-def expected_plan_order(tile, cell, K, T, R, load=4):
+def expected_plan_order(tile, cell, K, T, R, load=2):
     """(tile, cell) of every plan position under the plan's layout rule: non-empty 16 x 16
     tiles heaviest first (ties by tile index); inside a tile the runs (up to R consecutive
     visibilities of one cell) round by round (every cell's first run, then every second
-    one, ...); inside a round in bands of equal load rounds ceil(length / 4), most first;
+    one, ...); inside a round in bands ceil(length / 2), most first;
     inside a band round robin over the 16 shared-memory bank slots (row * 22 + col) mod 16
     of the cell, in cell order within a slot."""
     counts = np.bincount(tile, minlength=(K // T) ** 2)
