@@ -102,6 +102,19 @@ __device__ __forceinline__ void emit(R* __restrict__ out, size_t q, R v, const E
   }
 }
 
+// emit() with the output's current value (and weight) read ahead of the filtering, so that
+// the load's latency overlaps the block's work; the same arithmetic as emit().
+template <class R>
+__device__ __forceinline__ void emit_pre(R* __restrict__ out, size_t q, R v, const EpiR<R>& e, R prev, R wq) {
+  if (e.mode == 0) {
+    out[q] = v;
+  } else {
+    const R u = fma_r(e.ca, prev, e.cb * v);
+    const R lim = e.w ? e.lim * wq : e.lim;
+    out[q] = min_r(max_r(u, -lim), lim) * e.ce;
+  }
+}
+
 constexpr int kAB = 16;                         // analysis: output coefficients per block side (per quadrant)
 constexpr int kATile = 2 * kAB + kMaxTaps - 2;  // input rows / cols a block reads
 constexpr int kSB = 32;                         // synthesis: output samples per block side
@@ -122,71 +135,122 @@ struct SynSmem {
 };
 
 // One analysis level of one basis with an L-tap filter pair (unrolled), block
-// (blockIdx.x, blockIdx.y) = 16 x 16 output coefficients of each quadrant.
+// (blockIdx.x, blockIdx.y) = 16 x 16 output coefficients of each quadrant.  Written for
+// latency: every element of the input window and the epilogue's current outputs are
+// loaded into registers before the first use, so that the block waits for one round of
+// L2 / HBM latency instead of one per loop trip; the row and column filters are
+// register-blocked (a thread filters two neighbouring outputs from one sliding window of
+// L + 2 samples).  Each output's sum runs over the taps in the same order as a plain
+// loop, so the coefficients are those of the one-output-per-thread form.
 template <int L, class R>
 __device__ __forceinline__ void dwt_block(AnaSmem<R>& sm, const R* __restrict__ src, R* __restrict__ carry,
                                           R* __restrict__ dst, int m, int n, bool last, R scale,
                                           const R* __restrict__ hf, const R* __restrict__ gf, const EpiR<R>& e) {
   constexpr int T = 2 * kAB + L - 2;
+  constexpr int NL = (T * T + 255) / 256;  // window elements per thread
+  static_assert(kAB == 16 && T <= kATile, "block shape");
   const int half = m >> 1;
   const int k0 = blockIdx.y * kAB, l0 = blockIdx.x * kAB;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const bool interior = 2 * k0 + T <= m && 2 * l0 + T <= m;  // no periodic wrap
+  R v[NL];
+#pragma unroll
+  for (int k = 0; k < NL; ++k) {
+    const int idx = threadIdx.x + 256 * k;
+    if (idx < T * T) {
+      const int rr = idx / T, cc = idx - rr * T;
+      int gr = 2 * k0 + rr, gc = 2 * l0 + cc;
+      if (!interior) {
+        gr = gr < m ? gr : gr % m;
+        gc = gc < m ? gc : gc % m;
+      }
+      v[k] = src[(size_t)gr * n + gc];
+    }
+  }
+  // this thread's outputs: column c of the [a | d] halves, rows kA and kA + 1 of the block
+  const int c = tx;
+  const int kA = 2 * ty;
+  const int ll_ = l0 + (c & (kAB - 1));
+  const int col = (c < kAB) ? ll_ : half + ll_;
+  const bool lo_final = !(c < kAB && !last);  // else the LL value is carried to the next level
+  R pv[4] = {0, 0, 0, 0}, pw[4] = {0, 0, 0, 0};
+  if (e.mode != 0) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int kk = k0 + kA + i;
+      if (kk < half && ll_ < half) {
+        const size_t qlo = (size_t)kk * n + col, qhi = (size_t)(half + kk) * n + col;
+        if (lo_final) pv[2 * i] = dst[qlo];
+        pv[2 * i + 1] = dst[qhi];
+        if (e.w) {
+          if (lo_final) pw[2 * i] = e.w[qlo];
+          pw[2 * i + 1] = e.w[qhi];
+        }
+      }
+    }
+  }
   R h[L], g[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) {
     h[i] = hf[i];
     g[i] = gf[i];
   }
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  if (2 * k0 + T <= m && 2 * l0 + T <= m) {  // interior window: no periodic wrap
-    const R* base = src + (size_t)(2 * k0) * n + 2 * l0;
-    for (int rr = ty; rr < T; rr += 8) {
-      const R* row = base + (size_t)rr * n;
-      for (int cc = tx; cc < T; cc += 32) sm.tin[rr][cc] = row[cc];
-    }
-  } else {
-    for (int rr = ty; rr < T; rr += 8) {
-      int gr = 2 * k0 + rr;
-      gr = gr < m ? gr : gr % m;
-      const R* row = src + (size_t)gr * n;
-      for (int cc = tx; cc < T; cc += 32) {
-        int gc = 2 * l0 + cc;
-        gc = gc < m ? gc : gc % m;
-        sm.tin[rr][cc] = row[gc];
-      }
-    }
-  }
-  __syncthreads();
-  {
-    const int l = threadIdx.x & (kAB - 1);
-    for (int rr = threadIdx.x >> 4; rr < T; rr += 256 / kAB) {
-      R a = 0, d = 0;
 #pragma unroll
-      for (int i = 0; i < L; ++i) {
-        const R v = sm.tin[rr][2 * l + i];
-        a = fma_r(h[i], v, a);
-        d = fma_r(g[i], v, d);
-      }
-      sm.trow[rr][l] = a;
-      sm.trow[rr][kAB + l] = d;
+  for (int k = 0; k < NL; ++k) {
+    const int idx = threadIdx.x + 256 * k;
+    if (idx < T * T) {
+      const int rr = idx / T;
+      sm.tin[rr][idx - rr * T] = v[k];
     }
   }
   __syncthreads();
-  const int c = tx;  // c < 16: low-pass columns, else high-pass
-  const int ll_ = l0 + (c & (kAB - 1));
-  for (int k = ty; k < kAB; k += 8) {
-    const int kk = k0 + k;
+  {  // rows: thread (row rr, pair p) -> a and d of outputs 2p, 2p + 1 from samples 4p .. 4p + L + 1
+    const int p = threadIdx.x & 7;
+    for (int rr = threadIdx.x >> 3; rr < T; rr += 32) {
+      const R* row = &sm.tin[rr][4 * p];
+      R a0 = 0, a1 = 0, d0 = 0, d1 = 0;
+#pragma unroll
+      for (int i = 0; i < L + 2; ++i) {
+        const R x = row[i];
+        if (i < L) {
+          a0 = fma_r(h[i], x, a0);
+          d0 = fma_r(g[i], x, d0);
+        }
+        if (i >= 2) {
+          a1 = fma_r(h[i - 2], x, a1);
+          d1 = fma_r(g[i - 2], x, d1);
+        }
+      }
+      sm.trow[rr][2 * p] = a0;
+      sm.trow[rr][2 * p + 1] = a1;
+      sm.trow[rr][kAB + 2 * p] = d0;
+      sm.trow[rr][kAB + 2 * p + 1] = d1;
+    }
+  }
+  __syncthreads();
+  // columns: rows 2 kA .. 2 kA + L + 1 of column c give outputs kA and kA + 1
+  R lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+#pragma unroll
+  for (int i = 0; i < L + 2; ++i) {
+    const R x = sm.trow[2 * kA + i][c];
+    if (i < L) {
+      lo0 = fma_r(h[i], x, lo0);
+      hi0 = fma_r(g[i], x, hi0);
+    }
+    if (i >= 2) {
+      lo1 = fma_r(h[i - 2], x, lo1);
+      hi1 = fma_r(g[i - 2], x, hi1);
+    }
+  }
+  const R lo[2] = {lo0, lo1}, hi[2] = {hi0, hi1};
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int kk = k0 + kA + i;
     if (kk >= half || ll_ >= half) continue;
-    R lo = 0, hi = 0;
-#pragma unroll
-    for (int i = 0; i < L; ++i) {
-      const R v = sm.trow[2 * k + i][c];
-      lo = fma_r(h[i], v, lo);
-      hi = fma_r(g[i], v, hi);
-    }
-    const int col = (c < kAB) ? ll_ : half + ll_;
-    if (c < kAB && !last) carry[(size_t)kk * n + col] = lo;
-    else emit(dst, (size_t)kk * n + col, scale * lo, e);
-    emit(dst, (size_t)(half + kk) * n + col, scale * hi, e);
+    const size_t qlo = (size_t)kk * n + col;
+    if (!lo_final) carry[qlo] = lo[i];
+    else emit_pre(dst, qlo, scale * lo[i], e, pv[2 * i], pw[2 * i]);
+    emit_pre(dst, (size_t)(half + kk) * n + col, scale * hi[i], e, pv[2 * i + 1], pw[2 * i + 1]);
   }
 }
 
@@ -218,7 +282,9 @@ __global__ void __launch_bounds__(256) k_dwt_level(const R* __restrict__ in, siz
 
 // One synthesis level of one basis with an L-tap filter pair (the transpose of the
 // analysis): reconstructs a 32 x 32 window of the m x m block from the
-// 2 x (16 + L/2 - 1) coefficient rows and columns it touches (periodic).
+// 2 x (16 + L/2 - 1) coefficient rows and columns it touches (periodic).  Every
+// coefficient of the window is loaded into registers before the first shared-memory store
+// (one round of load latency per block).
 template <int L, class R>
 __device__ __forceinline__ void idwt_block(SynSmem<R>& sm, const R* __restrict__ coef, const R* __restrict__ llsrc,
                                            R* __restrict__ dst, int m, int n, const R* __restrict__ hf,
@@ -237,33 +303,37 @@ __device__ __forceinline__ void idwt_block(SynSmem<R>& sm, const R* __restrict__
   // coefficient indexes stay within [-half, 2 half) once half >= 16 and half >= L: one
   // conditional wrap instead of an integer modulo per element
   const bool small = half < 16 || half < L;
-  if (kr_lo >= 0 && kr_lo + KB <= half && kc_lo >= 0 && kc_lo + KB <= half) {
-    // interior: each quadrant's KB x KB coefficients are one rectangle, no wrap
+  const bool interior = kr_lo >= 0 && kr_lo + KB <= half && kc_lo >= 0 && kc_lo + KB <= half;
+  constexpr int NW = 4 * KB * KB;         // the window: [a | d rows] x [a | d cols]
+  constexpr int NL = (NW + 255) / 256;    // elements per thread
+  R v[NL];
 #pragma unroll
-    for (int qd = 0; qd < 4; ++qd) {
-      const int pr = qd >> 1, pc = qd & 1;
-      const R* base = ((pr == 0 && pc == 0) ? llsrc : coef) + (size_t)(pr * half + kr_lo) * n + pc * half + kc_lo;
-      for (int sr = ty; sr < KB; sr += 8) {
-        const R* row = base + (size_t)sr * n;
-        for (int sc = tx; sc < KB; sc += 32) sm.tc[pr * KB + sr][pc * KB + sc] = row[sc];
+  for (int k = 0; k < NL; ++k) {
+    const int idx = threadIdx.x + 256 * k;
+    if (idx < NW) {
+      const int sr = idx / (2 * KB), sc = idx - sr * (2 * KB);
+      const int pr = sr >= KB ? 1 : 0, pc = sc >= KB ? 1 : 0;
+      int kr = kr_lo + sr - pr * KB, kc = kc_lo + sc - pc * KB;
+      if (!interior) {
+        if (small) {
+          kr %= half;
+          kc %= half;
+        }
+        if (kr < 0) kr += half;
+        if (kr >= half) kr -= half;
+        if (kc < 0) kc += half;
+        if (kc >= half) kc -= half;
       }
-    }
-  } else
-  for (int sr = ty; sr < 2 * KB; sr += 8) {
-    const int pr = sr >= KB ? 1 : 0;
-    int kr = kr_lo + sr - pr * KB;
-    if (small) kr %= half;
-    if (kr < 0) kr += half;
-    if (kr >= half) kr -= half;
-    const size_t rowoff = (size_t)(pr * half + kr) * n;
-    for (int sc = tx; sc < 2 * KB; sc += 32) {
-      const int pc = sc >= KB ? 1 : 0;
-      int kc = kc_lo + sc - pc * KB;
-      if (small) kc %= half;
-      if (kc < 0) kc += half;
-      if (kc >= half) kc -= half;
       const R* srcp = (pr == 0 && pc == 0) ? llsrc : coef;
-      sm.tc[sr][sc] = srcp[rowoff + pc * half + kc];
+      v[k] = srcp[(size_t)(pr * half + kr) * n + pc * half + kc];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NL; ++k) {
+    const int idx = threadIdx.x + 256 * k;
+    if (idx < NW) {
+      const int sr = idx / (2 * KB);
+      sm.tc[sr][idx - sr * (2 * KB)] = v[k];
     }
   }
   __syncthreads();
