@@ -92,44 +92,60 @@ __global__ void k_pd_update(const cplx<R>* __restrict__ grid, const R* __restric
   const R c = (R)*cp;
   acc_t<R> dd, xx;
   const int groups = n * n / V;
-  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < groups; gi += gridDim.x * blockDim.x) {
-    const int i = gi * V;
-    const int q = i / n, p = i - q * n;
-    int r = q - n / 2; if (r < 0) r += K;
-    int cc = p - n / 2; if (cc < 0) cc += K;
-    R gr[V], cr[V], ps[V], xo[V];
-    if constexpr (V == 4) {
-      const float4 g01 = *reinterpret_cast<const float4*>(grid + (size_t)r * K + cc);
-      const float4 g23 = *reinterpret_cast<const float4*>(grid + (size_t)r * K + cc + 2);
-      gr[0] = g01.x; gr[1] = g01.z; gr[2] = g23.x; gr[3] = g23.z;
-      const float4 c4 = *reinterpret_cast<const float4*>(corr + p);
-      cr[0] = c4.x; cr[1] = c4.y; cr[2] = c4.z; cr[3] = c4.w;
-      const float4 p4 = *reinterpret_cast<const float4*>(psiz + i);
-      ps[0] = p4.x; ps[1] = p4.y; ps[2] = p4.z; ps[3] = p4.w;
-      const float4 x4 = *reinterpret_cast<const float4*>(x + i);
-      xo[0] = x4.x; xo[1] = x4.y; xo[2] = x4.z; xo[3] = x4.w;
-    } else {
-      gr[0] = grid[(size_t)r * K + cc].x;
-      cr[0] = corr[p];
-      ps[0] = psiz[i];
-      xo[0] = x[i];
-    }
-    const R cq = corr[q];
-    R xn[V], xh[V];
+  const int stride = gridDim.x * blockDim.x;
+  // U grid-stride steps per pass with all their loads issued first (one round of load
+  // latency per pass); the steps are applied in grid-stride order, so the per-thread sums
+  // take their terms in the same order as a one-step loop
+  constexpr int U = 4;
+  for (int g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < groups; g0 += U * stride) {
+    R gr[U][V], cr[U][V], ps[U][V], xo[U][V], cq[U];
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-      const R phit = c * cr[j] * cq * gr[j];
-      xn[j] = max_r(xo[j] - tau * (ps[j] + phit), (R)0);
-      xh[j] = fma_r(theta, xn[j] - xo[j], xn[j]);
-      dd.add((xn[j] - xo[j]) * (xn[j] - xo[j]));
-      xx.add(xn[j] * xn[j]);
+    for (int u = 0; u < U; ++u) {
+      const int gi = g0 + u * stride;
+      if (gi >= groups) break;
+      const int i = gi * V;
+      const int q = i / n, p = i - q * n;
+      int r = q - n / 2; if (r < 0) r += K;
+      int cc = p - n / 2; if (cc < 0) cc += K;
+      if constexpr (V == 4) {
+        const float4 g01 = *reinterpret_cast<const float4*>(grid + (size_t)r * K + cc);
+        const float4 g23 = *reinterpret_cast<const float4*>(grid + (size_t)r * K + cc + 2);
+        gr[u][0] = g01.x; gr[u][1] = g01.z; gr[u][2] = g23.x; gr[u][3] = g23.z;
+        const float4 c4 = *reinterpret_cast<const float4*>(corr + p);
+        cr[u][0] = c4.x; cr[u][1] = c4.y; cr[u][2] = c4.z; cr[u][3] = c4.w;
+        const float4 p4 = *reinterpret_cast<const float4*>(psiz + i);
+        ps[u][0] = p4.x; ps[u][1] = p4.y; ps[u][2] = p4.z; ps[u][3] = p4.w;
+        const float4 x4 = *reinterpret_cast<const float4*>(x + i);
+        xo[u][0] = x4.x; xo[u][1] = x4.y; xo[u][2] = x4.z; xo[u][3] = x4.w;
+      } else {
+        gr[u][0] = grid[(size_t)r * K + cc].x;
+        cr[u][0] = corr[p];
+        ps[u][0] = psiz[i];
+        xo[u][0] = x[i];
+      }
+      cq[u] = corr[q];
     }
-    if constexpr (V == 4) {
-      *reinterpret_cast<float4*>(xhat + i) = make_float4(xh[0], xh[1], xh[2], xh[3]);
-      *reinterpret_cast<float4*>(x + i) = make_float4(xn[0], xn[1], xn[2], xn[3]);
-    } else {
-      xhat[i] = xh[0];
-      x[i] = xn[0];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int gi = g0 + u * stride;
+      if (gi >= groups) break;
+      const int i = gi * V;
+      R xn[V], xh[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const R phit = c * cr[u][j] * cq[u] * gr[u][j];
+        xn[j] = max_r(xo[u][j] - tau * (ps[u][j] + phit), (R)0);
+        xh[j] = fma_r(theta, xn[j] - xo[u][j], xn[j]);
+        dd.add((xn[j] - xo[u][j]) * (xn[j] - xo[u][j]));
+        xx.add(xn[j] * xn[j]);
+      }
+      if constexpr (V == 4) {
+        *reinterpret_cast<float4*>(xhat + i) = make_float4(xh[0], xh[1], xh[2], xh[3]);
+        *reinterpret_cast<float4*>(x + i) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+      } else {
+        xhat[i] = xh[0];
+        x[i] = xn[0];
+      }
     }
   }
   const double a = block_sum(dd.value(), sh);

@@ -102,17 +102,19 @@ __device__ __forceinline__ void emit(R* __restrict__ out, size_t q, R v, const E
   }
 }
 
-// emit() with the output's current value (and weight) read ahead of the filtering, so that
+// The epilogue's value for v given the output's current value prev and weight wq (mode 0:
+// v itself); emit_pre() stores it.  The current value is read ahead of the filtering, so that
 // the load's latency overlaps the block's work; the same arithmetic as emit().
 template <class R>
+__device__ __forceinline__ R epi_value(R v, const EpiR<R>& e, R prev, R wq) {
+  if (e.mode == 0) return v;
+  const R u = fma_r(e.ca, prev, e.cb * v);
+  const R lim = e.w ? e.lim * wq : e.lim;
+  return min_r(max_r(u, -lim), lim) * e.ce;
+}
+template <class R>
 __device__ __forceinline__ void emit_pre(R* __restrict__ out, size_t q, R v, const EpiR<R>& e, R prev, R wq) {
-  if (e.mode == 0) {
-    out[q] = v;
-  } else {
-    const R u = fma_r(e.ca, prev, e.cb * v);
-    const R lim = e.w ? e.lim * wq : e.lim;
-    out[q] = min_r(max_r(u, -lim), lim) * e.ce;
-  }
+  out[q] = epi_value(v, e, prev, wq);
 }
 
 constexpr int kAB = 16;                         // analysis: output coefficients per block side (per quadrant)
@@ -416,22 +418,53 @@ __global__ void __launch_bounds__(256) k_idwt_level(const R* __restrict__ alpha,
 #undef GBRI_IDWT_CASE
 }
 
-// x[q] = scale * (sum_j rec[j][q] + dirac[q])
-template <class R>
+// x[q] = scale * (sum_j rec[j][q] + dirac[q]), summed in that order; V = 4 consecutive
+// samples per thread (float4) on the FP32 path when N % 4 == 0 and the pointers are 16-byte
+// aligned, else V = 1.
+template <class R, int V>
 __global__ void k_psi_sum(const R* __restrict__ rec, int nb, const R* __restrict__ dirac, R* __restrict__ x,
                           int64_t N, R scale) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-    R v = dirac ? dirac[q] : (R)0;
-    for (int j = 0; j < nb; ++j) v += rec[(size_t)N * j + q];
-    x[q] = scale * v;
+  static_assert(V == 1 || (V == 4 && sizeof(R) == 4), "vector path is FP32 only");
+  const int64_t G = N / V;
+  for (int64_t gq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gq < G; gq += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (V == 4) {
+      float4 v = dirac ? *reinterpret_cast<const float4*>(dirac + 4 * gq) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+      for (int j = 0; j < nb; ++j) {
+        const float4 r = *reinterpret_cast<const float4*>(rec + (size_t)N * j + 4 * gq);
+        v.x += r.x;
+        v.y += r.y;
+        v.z += r.z;
+        v.w += r.w;
+      }
+      *reinterpret_cast<float4*>(x + 4 * gq) = make_float4(scale * v.x, scale * v.y, scale * v.z, scale * v.w);
+    } else {
+      R v = dirac ? dirac[gq] : (R)0;
+#pragma unroll 8
+      for (int j = 0; j < nb; ++j) v += rec[(size_t)N * j + gq];
+      x[gq] = scale * v;
+    }
   }
 }
 
-// Dirac basis of the analysis: out[q] = epi(scale * x[q]).
-template <class R>
+// Dirac basis of the analysis: out[q] = epi(scale * x[q]); V as in k_psi_sum.
+template <class R, int V>
 __global__ void k_dirac(const R* __restrict__ x, R* __restrict__ out, int64_t N, R scale, const EpiR<R> e) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
-    emit(out, (size_t)q, scale * x[q], e);
+  static_assert(V == 1 || (V == 4 && sizeof(R) == 4), "vector path is FP32 only");
+  const int64_t G = N / V;
+  for (int64_t gq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gq < G; gq += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (V == 4) {
+      const float4 xv = *reinterpret_cast<const float4*>(x + 4 * gq);
+      float4 pv = make_float4(0.f, 0.f, 0.f, 0.f), wv = pv;
+      if (e.mode != 0) pv = *reinterpret_cast<const float4*>(out + 4 * gq);
+      if (e.w) wv = *reinterpret_cast<const float4*>(e.w + 4 * gq);
+      *reinterpret_cast<float4*>(out + 4 * gq) =
+          make_float4(epi_value(scale * xv.x, e, pv.x, wv.x), epi_value(scale * xv.y, e, pv.y, wv.y),
+                      epi_value(scale * xv.z, e, pv.z, wv.z), epi_value(scale * xv.w, e, pv.w, wv.w));
+    } else {
+      emit(out, (size_t)gq, scale * x[gq], e);
+    }
+  }
 }
 
 // x[q] = scale * dirac[q] (a dictionary that holds only the Dirac basis)
@@ -439,6 +472,14 @@ template <class R>
 __global__ void k_scale_copy(const R* __restrict__ a, R* __restrict__ x, int64_t N, R scale) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
     x[q] = scale * a[q];
+}
+
+// float4 access: FP32, a length that is a multiple of 4 and 16-byte aligned pointers
+// (null pointers are not accessed)
+template <class R>
+bool vec4_ok(int64_t N, const void* a, const void* b, const void* c) {
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  return sizeof(R) == 4 && N % 4 == 0 && al(a) && al(b) && al(c);
 }
 
 int blocks_for(int64_t work) {
@@ -460,7 +501,11 @@ int32_t psi_adjoint_apply(gbri_wavelet* w, const R* x, R* out, DualEpi epi, cuda
     launch_begin(GBRI_K_PSI_ADJ, s);
     EpiR<R> ed(epi);
     if (ed.w) ed.w += (size_t)N * w->dirac_idx;
-    k_dirac<R><<<blocks_for(N), 256, 0, s>>>(x, out + (size_t)N * w->dirac_idx, N, scale, ed);
+    R* od = out + (size_t)N * w->dirac_idx;
+    if (vec4_ok<R>(N, x, od, ed.w))
+      k_dirac<R, (sizeof(R) == 4 ? 4 : 1)><<<blocks_for(N / 4), 256, 0, s>>>(x, od, N, scale, ed);
+    else
+      k_dirac<R, 1><<<blocks_for(N), 256, 0, s>>>(x, od, N, scale, ed);
     GBRI_TRY(launch_end(GBRI_K_PSI_ADJ, s));
   }
   if (w->nb == 0) return GBRI_OK;
@@ -504,7 +549,10 @@ int32_t psi_apply(gbri_wavelet* w, const R* alpha, R* x, cudaStream_t s) {
     cur ^= 1;
   }
   launch_begin(GBRI_K_PSI, s);
-  k_psi_sum<R><<<blocks_for(N), 256, 0, s>>>(bufs[cur ^ 1], w->nb, dirac, x, N, scale);
+  if (vec4_ok<R>(N, bufs[cur ^ 1], x, dirac))
+    k_psi_sum<R, (sizeof(R) == 4 ? 4 : 1)><<<blocks_for(N / 4), 256, 0, s>>>(bufs[cur ^ 1], w->nb, dirac, x, N, scale);
+  else
+    k_psi_sum<R, 1><<<blocks_for(N), 256, 0, s>>>(bufs[cur ^ 1], w->nb, dirac, x, N, scale);
   return launch_end(GBRI_K_PSI, s);
 }
 
