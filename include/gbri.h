@@ -92,6 +92,14 @@ typedef struct {
                                 l2 balls (n_balls > 1) still sum their block norms with shared-memory
                                 atomics and are not covered;
                                 0: atomics (faster, last-bit differences between runs) */
+  int32_t layout;            /* order of the visibilities inside a grid tile: 0 = automatic, the step
+                                layout for FP32 plans whose taps come from the kernel's polynomial fit
+                                with J = 4 (each 32-run group stored step-major: the k-th visibility of
+                                every run side by side; the layout of the fused degridding + gridding
+                                pass of the primal-dual iteration and FISTA) and the run layout
+                                otherwise; 1 = the run layout (each run of one cell's visibilities
+                                consecutive; faster for Phi and Phi^dagger applied alone, ADMM and
+                                local l2 balls) */
 } gbri_plan_desc;
 
 /* Build a plan: quantises every (u, v) once in FP64 to the fixed-point grid

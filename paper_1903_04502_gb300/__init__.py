@@ -72,10 +72,12 @@ class Plan:
     linearly between the two samples around it with coordinates quantised 256 times finer.
     deterministic: gridding bitwise reproducible from run to run (fixed-order sums of the cells
     that tiles share instead of float atomics; costs a second pass and a slot buffer).
+    layout: 0 automatic (the step layout of the fused primal-dual pass for FP32 polynomial-tap
+    plans with J = 4, else the run layout), 1 the run layout (faster Phi / Phi^dagger alone).
     """
 
     def __init__(self, uvw, n_side, oversample=2, J=4, S=4096, beta=0.0, vis_per_run=0, autotune=False,
-                 precision=F32, interp_order=0, deterministic=False, stream=None):
+                 precision=F32, interp_order=0, deterministic=False, layout=0, stream=None):
         lib = _lib.load()
         _need(uvw, torch.float32, name="uvw")
         if uvw.dim() != 2 or uvw.shape[1] != 4:
@@ -87,7 +89,8 @@ class Plan:
         self.real_dtype, self.complex_dtype = _REAL[self.precision], _CPLX[self.precision]
         self.interp_order = int(interp_order)
         d = _lib.PlanDesc(self.n_side, int(oversample), self.J, self.S, float(beta), self.M, self.precision,
-                          int(vis_per_run), 1 if autotune else 0, self.interp_order, 1 if deterministic else 0)
+                          int(vis_per_run), 1 if autotune else 0, self.interp_order, 1 if deterministic else 0,
+                          int(layout))
         h = C.c_void_p()
         _lib.check(lib.gbri_plan_create(C.byref(h), C.byref(d), _ptr(uvw), _stream(stream)))
         self._h = h

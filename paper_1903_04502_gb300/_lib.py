@@ -27,7 +27,8 @@ class PlanDesc(C.Structure):
     _fields_ = [("n_side", C.c_int32), ("oversample", C.c_int32), ("J", C.c_int32),
                 ("samples_per_unit", C.c_int32), ("kb_beta", C.c_double), ("M", C.c_int64),
                 ("precision", C.c_int32), ("vis_per_run", C.c_int32), ("autotune", C.c_int32),
-                ("interp_order", C.c_int32), ("deterministic", C.c_int32)]
+                ("interp_order", C.c_int32), ("deterministic", C.c_int32),
+                ("layout", C.c_int32)]
 
 
 class SolveParams(C.Structure):

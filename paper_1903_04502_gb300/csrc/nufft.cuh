@@ -13,10 +13,15 @@
 //   gtiles [G] int4    gridding work items: {tile, first run, runs, split}; one per non-empty
 //                      tile, or several (split = 1) for a tile heavier than twice a warp's
 //                      share of the visibilities.
+//   steps  [N] int2    step-layout plans only (FP32, polynomial taps, J = 4): the runs of
+//                      every 32-run group are stored step-major (step k: the k-th visibility
+//                      of each run longer than k, in lane order); steps[s] = {plan position
+//                      of the step's first visibility | group start << 31, mask of the lanes
+//                      holding one}; gtiles then list {tile, first step, steps, split}.
 //   chunks [C] int4    degridding work items: {tile, first plan position, visibilities
-//                      (<= kChunk), 0}: consecutive visibilities of one tile.
+//                      (<= kChunk), 0}: consecutive visibilities of one tile (any layout).
 //   Visibilities are stored in run order: a tile's visibilities are contiguous, and so
-//   are a run's.
+//   are a run's (step-layout plans: a tile's and a group's are contiguous).
 //   wtab   [S/2+1][J] R  tap weights by fractional offset f = k~ mod S: entry t is
 //                      table[|f + (J/2 - 1 - t) S|] (Sec. 8.1 zeroth-order table,
 //                      re-indexed so one visibility reads one row per axis).
@@ -150,6 +155,13 @@ struct gbri_plan {
   int32_t* tile_items_off = nullptr;  // [nT^2 + 1] CSR offsets: items of each tile
   int32_t* tile_items = nullptr;      // [n_gtiles] item indices, ascending per tile
   int autotune = 0;
+  // step layout (FP32 polynomial-tap plans with J = 4): visibilities of every 32-run group
+  // stored step-major, steps[s] = {first plan position | group start << 31, lanes holding a
+  // visibility}; gtiles are then {tile, first step, steps, split}
+  int step_layout = 0;
+  int layout_req = 0;  // gbri_plan_desc.layout: 0 automatic, 1 the run layout
+  int2* steps = nullptr;
+  int64_t n_steps = 0;
   template <class T> T* as(void* q) const { return static_cast<T*>(q); }
 };
 
@@ -214,6 +226,7 @@ struct VisGeom {
   const int4* __restrict__ chunks;
   const int2* __restrict__ subruns;
   const int4* __restrict__ gtiles;
+  const int2* __restrict__ steps;      // step layout: step descriptors (else null)
   const void* __restrict__ wtab;
   const uint16_t* __restrict__ frac;  // first-order fractions (null: zeroth order)
   void* slots;                         // deterministic gridding: per-item windows (null: atomics)
@@ -244,6 +257,7 @@ inline VisGeom vis_geom(const gbri_plan* p) {
   g.chunks = p->chunks;
   g.subruns = p->subruns;
   g.gtiles = p->gtiles;
+  g.steps = p->steps;
   g.wtab = p->wtab;
   g.frac = p->frac;
   g.slots = p->det ? p->slots : nullptr;

@@ -280,6 +280,28 @@ __global__ void k_relayout(const int2* __restrict__ old_sub, const int32_t* __re
   }
 }
 
+// Step layout: move every run from its cell-sorted place to its step-major places.  Run i
+// is lane i mod 32 of group i / 32, whose steps start at group_step[i / 32]; its k-th
+// visibility goes to step k's first position plus the number of lanes below it holding a
+// visibility at that step.  One thread per run.
+__global__ void k_relayout_steps(const int2* __restrict__ old_sub, const int32_t* __restrict__ group_step,
+                                 const int2* __restrict__ steps, int64_t n_sub, const uint2* __restrict__ meta_in,
+                                 const int32_t* __restrict__ perm_in, uint2* __restrict__ meta_out,
+                                 int32_t* __restrict__ perm_out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sub; i += stride) {
+    const int2 o = old_sub[i];
+    const int32_t g0 = group_step[i >> 5];
+    const unsigned below = (1u << (unsigned)(i & 31)) - 1u;
+    for (int k = 0; k < o.y; ++k) {
+      const int2 d = steps[g0 + k];
+      const int dst = (d.x & 0x7fffffff) + __popc((unsigned)d.y & below);
+      meta_out[dst] = meta_in[o.x + k];
+      perm_out[dst] = perm_in[o.x + k];
+    }
+  }
+}
+
 __global__ void k_tile_starts(const int32_t* __restrict__ offsets, int n_tiles, int cells_per_tile,
                               int32_t* __restrict__ starts) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -355,6 +377,7 @@ void destroy_plan(gbri_plan* p) {
   cudaFree(p->frac_in);
   cudaFree(p->chunks);
   cudaFree(p->subruns);
+  cudaFree(p->steps);
   cudaFree(p->gtiles);
   cudaFree(p->wtab);
   cudaFree(p->corr);
@@ -403,6 +426,15 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
   p->meta = nullptr; p->perm = nullptr; p->subruns = nullptr; p->chunks = nullptr; p->gtiles = nullptr;
   cudaFree(p->slots); cudaFree(p->tile_items_off); cudaFree(p->tile_items);
   p->slots = nullptr; p->tile_items_off = nullptr; p->tile_items = nullptr;
+  cudaFree(p->steps);
+  p->steps = nullptr;
+  p->n_steps = 0;
+  // FP32 polynomial-tap plans with J = 4 store every 32-run group step-major (the step
+  // kernels); the others keep each run's visibilities consecutive
+  const bool steps = p->step_layout != 0;
+  std::vector<int2> stp;         // step descriptors {first position | start << 31, lanes}
+  std::vector<int32_t> gstep;    // first step of every 32-entry group of sub
+  int64_t next_pos = 0;          // plan position of the next step's first visibility
   std::vector<int2> sub;
   sub.reserve((size_t)(M / std::max(R, 4) + order.size() * 64 + 16));
   std::vector<int4> ch, gt;
@@ -470,21 +502,45 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
     }
     const int64_t nt = (int64_t)sub.size() - first;
     const int64_t nv_tile = hst[t + 1] - hst[t];
+    if (steps) {  // the tile's groups step-major: step k holds the k-th visibility of each run
+      for (int64_t g = first; g < first + nt; g += 32) {
+        gstep.push_back((int32_t)stp.size());
+        int maxlen = 0;
+        for (int j = 0; j < 32; ++j) maxlen = std::max(maxlen, sub[g + j].y);
+        for (int k = 0; k < maxlen; ++k) {
+          unsigned mask = 0u;
+          for (int j = 0; j < 32; ++j)
+            if (sub[g + j].y > k) mask |= 1u << j;
+          stp.push_back(make_int2((int)next_pos | (k == 0 ? (int)0x80000000u : 0), (int)mask));
+          next_pos += __builtin_popcount(mask);
+        }
+      }
+    }
+    // an item's runs [a, b) of sub, as runs or (step layout) as steps
+    auto item = [&](int64_t a, int64_t b, int split) {
+      if (!steps) {
+        gt.push_back(make_int4(t, (int)a, (int)(b - a), split));
+        return;
+      }
+      const int64_t ga = a / 32, gb = b / 32;  // groups, relative to every group so far
+      const int64_t sa = gstep[ga], sb = gb < (int64_t)gstep.size() ? gstep[gb] : (int64_t)stp.size();
+      gt.push_back(make_int4(t, (int)sa, (int)(sb - sa), split));
+    };
     if (nv_tile <= item_cap) {
-      gt.push_back(make_int4(t, (int)first, (int)nt, 0));
+      item(first, first + nt, 0);
     } else {
       int64_t g0 = first, w = 0;
       for (int64_t g = first; g < first + nt; g += 32) {
         int64_t wg = 0;
         for (int i = 0; i < 32; ++i) wg += sub[g + i].y;
         if (w > 0 && w + wg > item_cap) {
-          gt.push_back(make_int4(t, (int)g0, (int)(g - g0), 1));
+          item(g0, g, 1);
           g0 = g;
           w = 0;
         }
         w += wg;
       }
-      gt.push_back(make_int4(t, (int)g0, (int)(first + nt - g0), 1));
+      item(g0, first + nt, 1);
     }
     const int64_t nv = hst[t + 1] - hst[t];
     const int64_t nch = (nv + kChunk - 1) / kChunk;
@@ -505,10 +561,38 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
   p->n_gtiles = (int64_t)gt.size();
   int32_t st = GBRI_OK;
   if ((st = dmalloc(&p->meta, (size_t)M, nullptr)) || (st = dmalloc(&p->perm, (size_t)M, nullptr)) ||
-      (st = dmalloc(&p->chunks, ch.size(), nullptr)) || (st = dmalloc(&p->subruns, sub.size(), nullptr)) ||
-      (st = dmalloc(&p->gtiles, gt.size(), nullptr)))
+      (st = dmalloc(&p->chunks, ch.size(), nullptr)) ||
+      (st = dmalloc(&p->subruns, steps ? 1 : sub.size(), nullptr)) || (st = dmalloc(&p->gtiles, gt.size(), nullptr)))
     return st;
-  if (!sub.empty()) {
+  if (steps && !sub.empty()) {
+    GBRI_CHECK(next_pos == M, GBRI_EINVAL, "step layout does not cover every visibility");
+    p->n_steps = (int64_t)stp.size();
+    if ((st = dmalloc(&p->steps, stp.size(), nullptr))) return st;
+    int2* dold = nullptr;
+    int32_t* dgs = nullptr;
+    if ((st = dmalloc(&dold, sub.size(), nullptr)) || (st = dmalloc(&dgs, gstep.size(), nullptr))) {
+      cudaFree(dold);
+      return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(p->steps, stp.data(), stp.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dold, sub.data(), sub.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dgs, gstep.data(), gstep.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      st = cuda_error(e, "cudaMemcpyAsync (step layout)");
+    } else {
+      launch_begin(GBRI_K_OTHER, s);
+      k_relayout_steps<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)sub.size(), 256), (int64_t)num_sms() * 16),
+                         256, 0, s>>>(dold, dgs, p->steps, (int64_t)sub.size(), meta_cell, perm_cell, p->meta,
+                                      p->perm);
+      st = launch_end(GBRI_K_OTHER, s);
+    }
+    e = cudaStreamSynchronize(s);  // the host vectors are read by the copies
+    if (st == GBRI_OK && e != cudaSuccess) st = cuda_error(e, "cudaStreamSynchronize (step layout)");
+    cudaFree(dold);
+    cudaFree(dgs);
+    if (st != GBRI_OK) return st;
+  } else if (!sub.empty()) {
     int2* dold = nullptr;
     int32_t* dnew = nullptr;
     if ((st = dmalloc(&dold, sub.size(), nullptr)) || (st = dmalloc(&dnew, sub.size(), nullptr))) {
@@ -539,7 +623,7 @@ int32_t layout(gbri_plan* p, const std::vector<int32_t>& hoff, const std::vector
     GBRI_CHECK_CUDA(cudaMemcpyAsync(p->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   if (!gt.empty())
     GBRI_CHECK_CUDA(cudaMemcpyAsync(p->gtiles, gt.data(), gt.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-  p->layout_bytes = (int64_t)(sub.size() * sizeof(int2) + (ch.size() + gt.size()) * sizeof(int4));
+  p->layout_bytes = (int64_t)((steps ? stp.size() : sub.size()) * sizeof(int2) + (ch.size() + gt.size()) * sizeof(int4));
   std::vector<int32_t> toff, titems;
   if (p->det) {  // per-tile item lists (CSR over every tile, items ascending) and the window slots
     const int64_t ntiles = (int64_t)p->nT * p->nT;
@@ -630,6 +714,9 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     const char* force_table = std::getenv("GBRI_TAP_TABLE");
     const bool table_only = force_table && force_table[0] == '1';
     p->tap_mode = p->interp ? kTapFO : (!table_only && fit_poly_taps(p)) ? kTapPoly : kTapTable;
+    // FP32 polynomial-tap plans with J = 4 take the step layout and its kernels unless the
+    // caller asks for the run layout (each run's visibilities consecutive; the run kernels)
+    p->step_layout = p->tap_mode == kTapPoly && p->J == 4 && p->layout_req == 0;
   }
 
   GBRI_TRY(dmalloc(&p->meta, (size_t)M, &p->device_bytes));
@@ -873,6 +960,7 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* 
   GBRI_CHECK(out && d, GBRI_EINVAL, "null argument");
   *out = nullptr;
   GBRI_CHECK(d->deterministic == 0 || d->deterministic == 1, GBRI_EINVAL, "deterministic must be 0 or 1");
+  GBRI_CHECK(d->layout == 0 || d->layout == 1, GBRI_EINVAL, "layout must be 0 or 1");
   GBRI_CHECK(d->precision == GBRI_F32 || d->precision == GBRI_F64, GBRI_EINVAL, "precision must be GBRI_F32 or GBRI_F64");
   GBRI_CHECK(d->n_side >= 16 && d->n_side % 2 == 0, GBRI_EINVAL, "n_side must be even and >= 16");
   GBRI_CHECK(d->oversample >= 2 && d->oversample <= 4, GBRI_EINVAL, "oversample must be in [2, 4]");
@@ -903,6 +991,7 @@ int32_t gbri_plan_create(gbri_plan** out, const gbri_plan_desc* d, const float* 
   p->run_len = d->vis_per_run ? d->vis_per_run : kDefaultRun;
   p->interp = d->interp_order;
   p->det = d->deterministic;
+  p->layout_req = d->layout;
   p->autotune = d->deterministic ? 0 : d->autotune;  // timed choices would make the layout vary
   const int32_t st = build_plan(p, d_uvw, (cudaStream_t)stream);
   if (st != GBRI_OK) {

@@ -2,6 +2,7 @@
 // the polynomial-tap kernels of vis_fast.cuh.
 #include "vis_fast.cuh"
 #include "vis_kernels.cuh"
+#include "vis_steps.cuh"
 
 GBRI_INSTANTIATE_VIS(float)
 
@@ -10,9 +11,9 @@ namespace gbri {
 template <class Epi>
 int32_t launch_degrid_fast(gbri_plan* p, Epi epi, cudaStream_t s) {
   launch_begin(GBRI_K_DEGRID, s);
-  const size_t sm = degrid_smem(p);
   const VisGeom geo = vis_geom(p);
   const float2* g = p->as<const float2>(p->spec);
+  const size_t sm = degrid_smem(p);
   if (p->J == 4) k_degrid_fast<4, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi, p->work);
   else k_degrid_fast<6, Epi><<<p->degrid_blocks, kThreads, sm, s>>>(geo, g, epi, p->work);
   return launch_end(GBRI_K_DEGRID, s);
@@ -24,7 +25,10 @@ int32_t launch_grid_fast(gbri_plan* p, Src src, cudaStream_t s) {
   const size_t sm = grid_smem(p);
   const VisGeom geo = vis_geom(p);
   float2* g = p->as<float2>(p->grid);
-  if (p->J == 4) k_grid_fast<4, Src><<<p->grid_blocks, kThreads, sm, s>>>(geo, g, src, p->work + 2);
+  if (p->step_layout)
+    k_steps<kStepGrid, Src><<<p->grid_blocks, kThreads, step_smem<kStepGrid, Src>(), s>>>(geo, nullptr, g, src,
+                                                                                         p->work + 2);
+  else if (p->J == 4) k_grid_fast<4, Src><<<p->grid_blocks, kThreads, sm, s>>>(geo, g, src, p->work + 2);
   else k_grid_fast<6, Src><<<p->grid_blocks, kThreads, sm, s>>>(geo, g, src, p->work + 2);
   return launch_end(GBRI_K_GRID, s);
 }
@@ -48,6 +52,10 @@ cudaError_t prepare_fast_kernels() {
   GBRI_ATTR_GR(SrcScaledL); GBRI_ATTR_GR(SrcADMM2L); GBRI_ATTR_GR(SrcPlan); GBRI_ATTR_GR(SrcRaw); GBRI_ATTR_GR(SrcADMM2);
   GBRI_ATTR((k_degrid_grid_fast<4, EpiPD1<float>>));
   GBRI_ATTR((k_degrid_grid_fast<4, EpiResid<float>>));
+  GBRI_ATTR((k_steps<kStepGrid, SrcScaledL<float>>)); GBRI_ATTR((k_steps<kStepGrid, SrcADMM2L<float>>));
+  GBRI_ATTR((k_steps<kStepGrid, SrcPlan<float>>)); GBRI_ATTR((k_steps<kStepGrid, SrcRaw<float>>));
+  GBRI_ATTR((k_steps<kStepGrid, SrcADMM2<float>>));
+  GBRI_ATTR((k_steps<kStepFused, EpiPD1<float>>)); GBRI_ATTR((k_steps<kStepFused, EpiResid<float>>));
 #undef GBRI_ATTR_DG
 #undef GBRI_ATTR_GR
 #undef GBRI_ATTR
@@ -67,7 +75,9 @@ int32_t degrid_grid(gbri_plan* p, Epi epi, cudaStream_t s, bool zeroed) {
   const size_t sm = degrid_grid_smem(p);
   const VisGeom geo = vis_geom(p);
   const float2* spec = p->as<const float2>(p->spec);
-  if (p->tap_mode == kTapPoly)
+  if (p->step_layout)
+    k_steps<kStepFused, Epi><<<blocks, kThreads, step_smem<kStepFused, Epi>(), s>>>(geo, spec, g, epi, p->work + 4);
+  else if (p->tap_mode == kTapPoly)
     k_degrid_grid_fast<4, Epi><<<blocks, kThreads, sm, s>>>(geo, spec, g, epi, p->work + 4);
   else if (p->tap_mode == kTapFO) k_degrid_grid<4, kTapFO, Epi><<<blocks, kThreads, sm, s>>>(geo, spec, g, epi);
   else k_degrid_grid<4, kTapTable, Epi><<<blocks, kThreads, sm, s>>>(geo, spec, g, epi);

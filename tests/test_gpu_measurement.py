@@ -45,18 +45,19 @@ CASES = [  # (n_side, M, J): several tiles, ragged chunk tails
 ]
 
 
-@pytest.mark.parametrize("taps", ["poly", "table"])
+@pytest.mark.parametrize("taps", ["poly", "table", "poly-runs"])
 @pytest.mark.parametrize("n,M,J", CASES)
 def test_phi_and_adjoint_match_oracle(g, monkeypatch, n, M, J, taps):
-    """Both ways of getting the tap weights of an FP32 plan: the polynomial fit (the default)
-    and the shared-memory table (GBRI_TAP_TABLE=1)."""
+    """Both ways of getting the tap weights of an FP32 plan: the polynomial fit (the default;
+    at J = 4 on the step layout, or on the run layout with layout=1) and the
+    shared-memory table (GBRI_TAP_TABLE=1)."""
     x, uvw = make(n, M, J, seed=n + M)
     geo = me.Geometry(uvw, n, 2, J, 4096)
     if taps == "table":
         monkeypatch.setenv("GBRI_TAP_TABLE", "1")
-    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, J=J, S=4096)
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, J=J, S=4096, layout=1 if taps == "poly-runs" else 0)
     monkeypatch.delenv("GBRI_TAP_TABLE", raising=False)
-    assert plan.tap_mode() == (2 if taps == "poly" else 0)
+    assert plan.tap_mode() == (0 if taps == "table" else 2)
     y = g.phi(plan, torch.from_numpy(x).cuda()).cpu().numpy()
     y_ref = me.phi(x.astype(np.float64), geo)
     assert rel(y, y_ref) <= TOL
@@ -168,13 +169,16 @@ def test_plan_order_and_permutation(g):
     assert rel(b, a) <= 1e-6
 
 
-def expected_plan_order(tile, cell, K, T, R, load=2):
+def expected_plan_order(tile, cell, K, T, R, load=2, steps=True):
     """(tile, cell) of every plan position under the plan's layout rule: non-empty 16 x 16
     tiles heaviest first (ties by tile index); inside a tile the runs (up to R consecutive
     visibilities of one cell) round by round (every cell's first run, then every second
-    one, ...); inside a round in bands ceil(length / 2), most first;
-    inside a band round robin over the 16 shared-memory bank slots (row * 22 + col) mod 16
-    of the cell, in cell order within a slot."""
+    one, ...); inside a round in bands ceil(length / 2), most first; inside a band round
+    robin over the 16 shared-memory bank slots (row * 22 + col) mod 16 of the cell, in cell
+    order within a slot; each round padded with empty runs to a multiple of 32.  Run layout
+    (steps=False): each run's visibilities consecutive.  Step layout (FP32 polynomial-tap
+    plans with J = 4): every group of 32 runs step-major, step k holding the k-th visibility
+    of each run longer than k in run order."""
     counts = np.bincount(tile, minlength=(K // T) ** 2)
     tiles = np.nonzero(counts)[0]
     order = tiles[np.argsort(-counts[tiles], kind="stable")]
@@ -184,27 +188,46 @@ def expected_plan_order(tile, cell, K, T, R, load=2):
         for r in range(int(-(-cc.max() // R))):
             ln = {c: min(R, cc[c] - r * R) for c in range(T * T) if cc[c] > r * R}
             bands = {c: -(-ln[c] // load) for c in ln}
+            runs = []
             for b in range(max(bands.values()), 0, -1):
                 buckets = [[c for c in sorted(ln) if bands[c] == b and ((c // T) * 22 + c % T) % 16 == q]
                            for q in range(16)]
                 while any(buckets):
                     for q in range(16):
                         if buckets[q]:
-                            c = buckets[q].pop(0)
-                            exp_t += [t] * ln[c]
-                            exp_c += [c] * ln[c]
+                            runs.append(buckets[q].pop(0))
+            runs += [None] * (-len(runs) % 32)
+            for g0 in range(0, len(runs), 32):
+                grp = runs[g0:g0 + 32]
+                lens = [ln[c] if c is not None else 0 for c in grp]
+                if steps:
+                    for k in range(max(lens)):
+                        for j, c in enumerate(grp):
+                            if lens[j] > k:
+                                exp_t.append(t)
+                                exp_c.append(c)
+                else:
+                    for j, c in enumerate(grp):
+                        exp_t += [t] * lens[j]
+                        exp_c += [c] * lens[j]
     return np.array(exp_t), np.array(exp_c), len(tiles)
 
 
-@pytest.mark.parametrize("run", [0, 2])
-def test_sort_is_bit_exact_tile_major(g, run):
+@pytest.mark.parametrize("run,layout", [(0, "steps"), (2, "steps"), (0, "runs"), (2, "runs"), (0, "runs-poly")])
+def test_sort_is_bit_exact_tile_major(g, monkeypatch, run, layout):
     """The plan's visibility order follows the oracle's FP64 quantisation exactly (integer
     work, compared exactly) under the layout rule of expected_plan_order; run 0 is the
-    default run length 64, run 2 splits cells into several rounds."""
+    default run length 64, run 2 splits cells into several rounds.  The default FP32 J = 4
+    plan takes the step layout; the table-tap plan (GBRI_TAP_TABLE=1) and a polynomial-tap plan
+    asking for layout=1 the run layout."""
     n, M, K, S, T = 128, 30_000, 256, 4096, 16
     R = run or 64
     _, uvw = make(n, M)
-    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, S=S, vis_per_run=run)
+    if layout == "runs":
+        monkeypatch.setenv("GBRI_TAP_TABLE", "1")
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, S=S, vis_per_run=run, layout=1 if layout == "runs-poly" else 0)
+    monkeypatch.delenv("GBRI_TAP_TABLE", raising=False)
+    assert plan.tap_mode() == (0 if layout == "runs" else 2)
     assert plan.launch_config()[0] == R
     perm = plan.permutation().cpu().numpy()
     assert np.array_equal(np.sort(perm), np.arange(M))
@@ -214,7 +237,7 @@ def test_sort_is_bit_exact_tile_major(g, run):
     cy = np.mod(np.floor_divide(ky, S), K)
     tile = (cy // T) * (K // T) + cx // T
     cell = (cy % T) * T + (cx % T)
-    exp_t, exp_c, n_tiles = expected_plan_order(tile, cell, K, T, R)
+    exp_t, exp_c, n_tiles = expected_plan_order(tile, cell, K, T, R, steps=(layout == "steps"))
     assert np.array_equal(tile[perm], exp_t)
     assert np.array_equal(cell[perm], exp_c)
     assert plan.n_tiles == n_tiles
@@ -266,6 +289,8 @@ def test_invalid_inputs_rejected(g):
         g.Plan(torch.from_numpy(far).cuda(), n)
     with pytest.raises(g.GbriError):
         g.Plan(torch.zeros((4, 4), device="cuda"), n, J=5)
+    with pytest.raises(g.GbriError):
+        g.Plan(torch.zeros((4, 4), device="cuda"), n, layout=2)
 
 
 def test_full_size_sampled_parity(g):
