@@ -342,11 +342,39 @@ __device__ __forceinline__ void idwt_block(SynSmem<R>& sm, const R* __restrict__
   const bool interior = kr_lo >= 0 && kr_lo + KB <= half && kc_lo >= 0 && kc_lo + KB <= half;
   constexpr int NW = 4 * KB * KB;         // the window: [a | d rows] x [a | d cols]
   constexpr int NL = (NW + 255) / 256;    // elements per thread
+  // interior blocks of an FP32 level read each window row's two column segments (KB
+  // coefficients of the a and of the d half) as float4 from the 16-byte boundary at or below
+  // the segment's start, when the last float4 ends inside the row: a quarter of the load and
+  // index instructions
+  constexpr int S4 = (KB + 6) / 4;             // float4 per segment (start up to 3 below)
+  constexpr int NV4 = 2 * KB * 2 * S4;
+  constexpr int NL4 = (NV4 + 255) / 256;
+  const int dlt = kc_lo & 3;
+  bool vec = false;
+  if constexpr (sizeof(R) == 4)
+    vec = interior && (n & 3) == 0 && (half & 3) == 0 && kc_lo - dlt + 4 * S4 <= half &&
+          ((reinterpret_cast<uintptr_t>(coef) | reinterpret_cast<uintptr_t>(llsrc)) & 15) == 0;
+  float4 v4[NL4];
+  if (vec) {
+#pragma unroll
+    for (int k = 0; k < NL4; ++k) {
+      const int idx = threadIdx.x + 256 * k;
+      if (idx < NV4) {
+        const int sr = idx / (2 * S4), rem = idx - sr * (2 * S4);
+        const int pc = rem >= S4 ? 1 : 0, c4 = rem - pc * S4;
+        const int pr = sr >= KB ? 1 : 0;
+        const int kr = kr_lo + sr - pr * KB;
+        const R* srcp = (pr == 0 && pc == 0) ? llsrc : coef;
+        v4[k] = *reinterpret_cast<const float4*>(srcp + (size_t)(pr * half + kr) * n + pc * half + kc_lo - dlt +
+                                                 4 * c4);
+      }
+    }
+  }
   R v[NL];
 #pragma unroll
   for (int k = 0; k < NL; ++k) {
     const int idx = threadIdx.x + 256 * k;
-    if (idx < NW) {
+    if (!vec && idx < NW) {
       const int sr = idx / (2 * KB), sc = idx - sr * (2 * KB);
       const int pr = sr >= KB ? 1 : 0, pc = sc >= KB ? 1 : 0;
       int kr = kr_lo + sr - pr * KB, kc = kc_lo + sc - pc * KB;
@@ -364,12 +392,29 @@ __device__ __forceinline__ void idwt_block(SynSmem<R>& sm, const R* __restrict__
       v[k] = srcp[(size_t)(pr * half + kr) * n + pc * half + kc];
     }
   }
+  if (vec) {
 #pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    const int idx = threadIdx.x + 256 * k;
-    if (idx < NW) {
-      const int sr = idx / (2 * KB);
-      sm.tc[sr][idx - sr * (2 * KB)] = v[k];
+    for (int k = 0; k < NL4; ++k) {
+      const int idx = threadIdx.x + 256 * k;
+      if (idx < NV4) {
+        const int sr = idx / (2 * S4), rem = idx - sr * (2 * S4);
+        const int pc = rem >= S4 ? 1 : 0, c4 = rem - pc * S4;
+        const float e4[4] = {v4[k].x, v4[k].y, v4[k].z, v4[k].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int e = 4 * c4 + j - dlt;
+          if (e >= 0 && e < KB) sm.tc[sr][pc * KB + e] = (R)e4[j];
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int idx = threadIdx.x + 256 * k;
+      if (idx < NW) {
+        const int sr = idx / (2 * KB);
+        sm.tc[sr][idx - sr * (2 * KB)] = v[k];
+      }
     }
   }
   __syncthreads();
