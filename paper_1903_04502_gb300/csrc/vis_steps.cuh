@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       // refill slot q with step i + D (its descriptor is in this batch or the next)
       const int i2 = i + D;
-      const int2 d2 = ((i2 >> 5) == (i >> 5)) ? shfl_int2(dcur, i2 & 31) : shfl_int2(dnxt, i2 & 31);
+      const int2 d2 = shfl_int2(((i2 >> 5) == (i >> 5)) ? dcur : dnxt, i2 & 31);
       if (i2 < ns) issue(q, d2);
       cp_async_commit();
     }
