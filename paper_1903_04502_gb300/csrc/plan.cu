@@ -828,10 +828,12 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   const int sms = num_sms();
   const int lim_dg =
       std::min(std::max(1, (int)((227 * 1024) / (degrid_smem(p) + 1024))), degrid_occupancy((int)rb, p->J));
-  // the pipelined FP32 polynomial-tap gridding kernel is compiled for two blocks per SM
+  // the pipelined FP32 polynomial-tap gridding kernel of the run layout is compiled for two
+  // blocks per SM, the step layout's for three (80 registers; at M = 1e7: 126.9 us at two
+  // blocks, 123.4 at three, 118.7 at three with the step loop unrolled by two)
   const int lim_gr = std::min(std::min(std::max(1, (int)((227 * 1024) / (grid_smem(p) + 1024))),
                                        grid_occupancy((int)rb, p->J)),
-                              p->tap_mode == kTapPoly ? 2 : 1 << 20);
+                              p->tap_mode == kTapPoly ? (p->step_layout ? 3 : 2) : 1 << 20);
   p->n_partials = std::max(sms * 8, 1024);
   GBRI_TRY(dmalloc(&p->partials, (size_t)p->n_partials * 4, &p->device_bytes));
   GBRI_TRY(dmalloc(&p->scalars, 64, &p->device_bytes));

@@ -114,7 +114,7 @@ constexpr size_t step_smem() {
 }
 
 template <int Mode, class Op>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, Mode == kStepGrid ? 3 : 2)
     k_steps(VisGeom geo, const float2* __restrict__ spec, float2* __restrict__ grid, Op op, unsigned int* ctr) {
   constexpr int J = 4;
   constexpr int P = kTile + J - 1;
@@ -196,6 +196,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
     int a0 = 0;
     bool has = false;  // this lane holds a run in the current group (and its cell is in the tile)
+    // two steps per trip give the scheduler independent work from both (fused pass 172 -> 168 us,
+    // gridding 123 -> 119 us; no spills)
+#pragma unroll 2
     for (int i = 0; i < ns; ++i) {
       if (i > 0 && (i & 31) == 0) {  // next batch of descriptors (warp-uniform)
         dcur = dnxt;
