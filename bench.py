@@ -33,7 +33,7 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernels at the 1024^2 / M = 1e7 workload; set to None
 # whenever a kernel changes after its capture.
-KERNEL_TRAFFIC = {"degrid": None, "grid": 196.98e6, "degrid_grid": 360.87e6}
+KERNEL_TRAFFIC = {"degrid": None, "grid": 195.45e6, "degrid_grid": 361.91e6}
 
 
 def parse():
