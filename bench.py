@@ -410,9 +410,11 @@ def sweep_leg(dev, seed=7000, M=5_000_000, reps=20):
 def batch_leg(args, dev, seed=5000):
     """Many independent problems at once: image side uniform in {256, 512, 1024, 2048}, M
     log-uniform in [1e5, 5e7], J in {4, 6}, SARA Dirac + db1..db8 over 4 levels, FP32 with
-    FP64 norms, autotuned plans.  Times the batch (one CUDA-graph launch per iteration whose
-    branches are every problem's iteration) against the same problems stepped one after the
-    other (one graph launch per problem and iteration)."""
+    FP64 norms, autotuned plans.  Times the batch (one CUDA-graph launch per iteration: the
+    primal-dual members on J = 4 step-layout plans share one fused degridding + gridding
+    launch, the others are branches holding their own iterations), the batch without the
+    shared pass, and the same problems stepped one after the other (one graph launch per
+    problem and iteration)."""
     import torch
     import paper_1903_04502_gb300 as g
     rng = np.random.default_rng(seed)
@@ -444,17 +446,27 @@ def batch_leg(args, dev, seed=5000):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     stream = torch.cuda.current_stream()
-    batch = g.Batch()
-    for _, _, s in objs:
-        batch.add(s)
-    batch.step(3)
-    torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    batch.step(args.batch_steps)
-    b.record(stream)
-    torch.cuda.synchronize()
-    t_batch = a.elapsed_time(b) * 1e-3
+
+    def time_batch(shared):
+        batch = g.Batch()
+        batch.set_shared_pass(shared)
+        for _, _, s in objs:
+            batch.add(s)
+        batch.step(3)
+        torch.cuda.synchronize()
+        a.record(stream)
+        batch.step(args.batch_steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        n_shared = batch.shared_members()
+        batch.close()
+        return a.elapsed_time(b) * 1e-3, n_shared
+
+    # the primal-dual members on FP32 step-layout plans share one fused pass per iteration
+    # (gbri_batch_set_shared_pass), and without it every member keeps its own launches
+    t_batch, n_shared = time_batch(True)
+    t_sep, _ = time_batch(False)
     for _, _, s in objs:
         s.step(3)
     torch.cuda.synchronize()
@@ -464,7 +476,6 @@ def batch_leg(args, dev, seed=5000):
     b.record(stream)
     torch.cuda.synchronize()
     t_seq = a.elapsed_time(b) * 1e-3
-    batch.close()
     for plan, wav, s in objs:
         s.close()
         wav.close()
@@ -474,7 +485,8 @@ def batch_leg(args, dev, seed=5000):
     return {"problems": len(Ms), "total_visibilities": int(sum(Ms)), "steps": args.batch_steps,
             "batch_vis_per_s": vis / t_batch, "batch_iterations_per_s": its / t_batch,
             "one_by_one_vis_per_s": vis / t_seq, "one_by_one_iterations_per_s": its / t_seq,
-            "speedup": t_seq / t_batch, "setup_s": t_setup,
+            "speedup": t_seq / t_batch, "setup_s": t_setup, "shared_pass_members": n_shared,
+            "batch_without_shared_pass_vis_per_s": vis / t_sep,
             "autotune": {k: v for k, v in sorted(tune.items())},
             "mix": "n in {256,512,1024,2048}, M log-uniform [1e5, 5e7], J in {4,6}, uv drawn on the device"}
 

@@ -364,6 +364,17 @@ int32_t gbri_batch_remove(gbri_batch* b, gbri_solver* s);
 int32_t gbri_batch_size(const gbri_batch* b);
 /* No host synchronisation.  EINVAL while kernel timing (gbri_profile_enable) is on. */
 int32_t gbri_batch_step(gbri_batch* b, int32_t n_iter, void* stream);
+/* Shared pass (on by default): members that are primal-dual solvers with a global l2 ball on
+ * FP32 plans of the step layout (gbri_plan_desc.layout) with the same kernel, not
+ * deterministic, share one launch of the fused degridding + gridding pass per iteration: a
+ * work list over all of their gridding items, taken from one counter (up to 256 members,
+ * heaviest first; at least two).  Each such member's iteration runs in two phases around it
+ * (up to its forward FFT; from its inverse FFT on); the other members keep their own
+ * captured iterations.  Results equal the members stepped alone up to the summation order of
+ * the l2-ball norm.  enable: 0 or 1 (EINVAL otherwise); takes effect at the next step. */
+int32_t gbri_batch_set_shared_pass(gbri_batch* b, int32_t enable);
+/* Members in the shared pass at the last step (0 when none). */
+int32_t gbri_batch_shared_members(const gbri_batch* b);
 
 /* ---- diagnostics ------------------------------------------------------------ */
 /* Kernel timing with CUDA events recorded around each library kernel launch on its

@@ -442,6 +442,15 @@ class Batch:
     def step(self, n_iter=1, stream=None):
         _lib.check(_lib.load().gbri_batch_step(self._h, int(n_iter), _stream(stream)))
 
+    def set_shared_pass(self, enable):
+        """Primal-dual members on FP32 step-layout plans share one fused degridding + gridding
+        launch per iteration (default on; gbri_batch_set_shared_pass)."""
+        _lib.check(_lib.load().gbri_batch_set_shared_pass(self._h, 1 if enable else 0))
+
+    def shared_members(self):
+        """Members in the shared pass at the last step (gbri_batch_shared_members)."""
+        return int(_lib.load().gbri_batch_shared_members(self._h))
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.load().gbri_batch_destroy(self._h)

@@ -90,6 +90,8 @@ SIGNATURES = {
     "gbri_batch_remove": (I32, [P, P]),
     "gbri_batch_size": (I32, [P]),
     "gbri_batch_step": (I32, [P, I32, P]),
+    "gbri_batch_set_shared_pass": (I32, [P, I32]),
+    "gbri_batch_shared_members": (I32, [P]),
     "gbri_profile_enable": (I32, [I32]),
     "gbri_profile_read": (I32, [I32, C.POINTER(D), C.POINTER(I64)]),
     "gbri_launch_count": (I64, []),

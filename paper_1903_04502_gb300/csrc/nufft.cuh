@@ -639,6 +639,30 @@ inline bool fused_pd_applies(const gbri_plan* p) {
 // Bytes of p->grid.
 inline size_t grid_bytes(const gbri_plan* p) { return (size_t)p->K * p->K * 2 * real_bytes(p->prec); }
 
+// One member of the batch executor's fused pass over several problems (k_steps_multi):
+// a primal-dual solver with a global l2 ball on an FP32 step-layout plan.
+struct FusedMember {
+  const uint2* meta;
+  const int2* steps;
+  const int4* gtiles;
+  const float2* spec;  // the member's half spectrum (the forward FFT of its x-hat)
+  float2* grid;        // its gridding target, zeroed before the pass
+  float2* u;           // l2-ball dual (plan order), updated in place
+  const float2* y;     // data (plan order)
+  double* c;           // ball scalar: read by every item, written by the last block
+  double* dist;        // ||u|| / sigma2 after the pass
+  double eps, sigma2d;
+  float sigma2;
+  int K, nT, log2S;
+  int item0;           // first item of this member in the launch's numbering
+};
+constexpr int kMaxFusedMembers = 256;  // members of one shared pass
+// Runs the fused degridding + gridding pass of n_mem members in one launch (device table
+// d_mem, items numbered member after member, n_items in all; d_sums[n_mem] zero on entry and
+// on exit; d_ctr a zeroed counter pair).
+int32_t launch_fused_multi(const FusedMember* d_mem, int n_mem, int n_items, double* d_sums, const PolyTaps& poly,
+                           unsigned int* d_ctr, cudaStream_t s);
+
 // Sets the shared-memory attributes of every visibility kernel of one precision
 // (once per process).
 template <class R>

@@ -378,8 +378,11 @@ void free_solver(gbri_solver* s) {
 template <class R> R* vec(void* p) { return static_cast<R*>(p); }
 template <class R> cplx<R>* cvec(void* p) { return static_cast<cplx<R>*>(p); }
 
+// phase 0: the whole iteration; 1: up to the forward FFT (the stream then also waits for the
+// zeroed grid); 2: from the inverse FFT on.  Phases 1 and 2 leave the fused degridding +
+// gridding pass between them to the batch executor's pass over several problems.
 template <class R>
-int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
+int32_t pd_iteration(gbri_solver* S, cudaStream_t st, int phase = 0) {
   gbri_plan* P = S->plan;
   gbri_wavelet* W = S->wav;
   const auto& p = S->p;
@@ -394,6 +397,7 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   // around each kernel time that kernel alone.
   const bool fork = !profiling_enabled();
   cudaStream_t sw = fork ? S->aux_stream : st;
+  if (phase == 2) goto after_pass;
   if (fork) {
     GBRI_CHECK_CUDA(cudaEventRecord(S->ev_fork, st));
     GBRI_CHECK_CUDA(cudaStreamWaitEvent(sw, S->ev_fork, 0));
@@ -411,6 +415,10 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
   // u <- c u + sigma2 (Phi xhat - y), ||u||^2
   GBRI_TRY(launch_pad<R>(P, vec<R>(S->xhat), nullptr, st));
   GBRI_TRY(fft_forward(P, st));
+  if (phase == 1) {
+    if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_zero, 0));
+    return GBRI_OK;
+  }
   if (S->nb == 0) {
     // (the degridding's last block also stores the ball scalar c of this iteration)
     EpiPD1<R> e1{cvec<R>(S->u), cvec<R>(S->yp), S->sc + SC_C, S->partials, (R)p.sigma2, acc_t<R>{}, (R)0,
@@ -439,6 +447,7 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st) {
     if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_zero, 0));
     GBRI_TRY(launch_grid(P, SrcScaledL<R>{cvec<R>(S->u), S->bsc, S->bstart, S->nb}, st, fork));
   }
+after_pass:
   GBRI_TRY(fft_inverse(P, st));
   if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_join, 0));
   const bool v4 = sizeof(R) == 4 && n % 8 == 0;
@@ -787,6 +796,43 @@ int64_t solver_launches_per_iteration(gbri_solver* s) { return s->launches_per_i
 const gbri_plan* solver_plan(const gbri_solver* s) { return s->plan; }
 const gbri_wavelet* solver_wavelet(const gbri_solver* s) { return s->wav; }
 void solver_add_iterations(gbri_solver* s, int n) { s->iters += n; }
+
+bool solver_fused_eligible(const gbri_solver* s) {
+  const gbri_plan* P = s->plan;
+  return s->prec == GBRI_F32 && s->p.algo == GBRI_ALGO_PD && s->nb == 0 && P->step_layout && !P->det &&
+         fused_pd_applies(P) && !profiling_enabled();
+}
+
+int32_t solver_phase(gbri_solver* s, int phase, cudaStream_t st) {
+  GBRI_CHECK(solver_fused_eligible(s), GBRI_EINVAL, "solver cannot split its iteration around a shared pass");
+  return pd_iteration<float>(s, st, phase);
+}
+
+cudaStream_t solver_stream(gbri_solver* s) {
+  if (!s->cap_stream && cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return nullptr;
+  return s->cap_stream;
+}
+
+void solver_fused_member(const gbri_solver* s, FusedMember* m) {
+  const gbri_plan* P = s->plan;
+  m->meta = P->meta;
+  m->steps = P->steps;
+  m->gtiles = P->gtiles;
+  m->spec = P->as<const float2>(P->spec);
+  m->grid = P->as<float2>(P->grid);
+  m->u = static_cast<float2*>(s->u);
+  m->y = static_cast<const float2*>(s->yp);
+  m->c = s->sc + SC_C;
+  m->dist = s->sc + SC_DIST;
+  m->eps = s->p.eps;
+  m->sigma2d = s->p.sigma2;
+  m->sigma2 = (float)s->p.sigma2;
+  m->K = P->K;
+  m->nT = P->nT;
+  m->log2S = P->log2S;
+  m->item0 = 0;
+}
 
 }  // namespace gbri
 

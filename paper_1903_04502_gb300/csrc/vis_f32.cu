@@ -56,10 +56,22 @@ cudaError_t prepare_fast_kernels() {
   GBRI_ATTR((k_steps<kStepGrid, SrcPlan<float>>)); GBRI_ATTR((k_steps<kStepGrid, SrcRaw<float>>));
   GBRI_ATTR((k_steps<kStepGrid, SrcADMM2<float>>));
   GBRI_ATTR((k_steps<kStepFused, EpiPD1<float>>)); GBRI_ATTR((k_steps<kStepFused, EpiResid<float>>));
+  GBRI_ATTR(k_steps_multi);
 #undef GBRI_ATTR_DG
 #undef GBRI_ATTR_GR
 #undef GBRI_ATTR
   return e;
+}
+
+int32_t launch_fused_multi(const FusedMember* d_mem, int n_mem, int n_items, double* d_sums, const PolyTaps& poly,
+                           unsigned int* d_ctr, cudaStream_t s) {
+  GBRI_CHECK(n_mem >= 1 && n_mem <= kMaxFusedMembers, GBRI_EINVAL, "fused pass: 1 to 256 members");
+  if (n_items == 0) return GBRI_OK;
+  // two blocks per SM, as the single-problem pass
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_items, kThreads / 32), num_sms() * 2));
+  launch_begin(GBRI_K_DEGRID_GRID, s);
+  k_steps_multi<<<blocks, kThreads, steps_multi_smem(), s>>>(d_mem, n_mem, n_items, d_sums, poly, d_ctr);
+  return launch_end(GBRI_K_DEGRID_GRID, s);
 }
 
 template <class Epi>

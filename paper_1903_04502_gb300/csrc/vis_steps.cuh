@@ -318,3 +318,228 @@ __global__ void __launch_bounds__(kThreads, Mode == kStepGrid ? 3 : 2)
 }
 
 }  // namespace gbri
+
+namespace gbri {
+
+// ---- the fused pass over several problems in one launch (batch executor) ----------------
+// Every member is a primal-dual solver with a global l2 ball on an FP32 step-layout plan with
+// the same kernel polynomial; its gridding work items are numbered after the previous
+// members' (item0), and the warps take items of all members from one counter, heaviest
+// members first.  Per visibility the arithmetic is the single-problem pass's (EpiPD1): u <- c u
+// + sigma2 (Phi xhat - y), stored and gridded; each member's sum of |u|^2 is accumulated in
+// FP64 per item and added to its slot of `sums`, and the launch's last block turns every
+// slot into the member's ball scalar c = 1 - min(1, eps / dist), dist = sqrt(sum) / sigma2,
+// and clears the slot.
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_steps_multi(const FusedMember* __restrict__ mem, int n_mem, int n_items, double* __restrict__ sums,
+                  PolyTaps poly, unsigned int* ctr) {
+  constexpr int J = 4;
+  constexpr int P = kTile + J - 1;
+  constexpr int W = kThreads / 32;
+  constexpr int D = kStageDepth;
+  constexpr int NA = 3;  // metadata, u, y
+  extern __shared__ float4 smem_multi[];
+  __shared__ int s_item0[kMaxFusedMembers + 1];
+  __shared__ const void* s_ptr[W][3];  // the current item's member: meta, u, y
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* base = reinterpret_cast<float2*>(smem_multi);
+  float2* win = base + warp * (P * kWinPitch);
+  float2* accs = base + W * P * kWinPitch;
+  float2* acc = accs + warp * (P * kAccPitch2);
+  uint2* stg = reinterpret_cast<uint2*>(accs + W * P * kAccPitch2) + warp * (D * NA * 32);
+  for (int i = threadIdx.x; i < W * P * kAccPitch2; i += blockDim.x) accs[i] = make_float2(0.f, 0.f);
+  for (int m = threadIdx.x; m < n_mem; m += blockDim.x) s_item0[m] = mem[m].item0;
+  if (threadIdx.x == 0) s_item0[n_mem] = n_items;
+  __syncthreads();
+  constexpr int lo_x = J - 1, hi_x = kTile;
+  const unsigned lanes_below = (1u << lane) - 1u;
+
+  auto issue = [&](int q, int2 d) {
+    if ((((unsigned)d.y) >> lane) & 1u) {
+      const int pos = (d.x & 0x7fffffff) + __popc((unsigned)d.y & lanes_below);
+      uint2* col = stg + (q * NA) * 32 + lane;
+      cp_async8(col, static_cast<const uint2*>(s_ptr[warp][0]) + pos);
+      cp_async8(col + 32, static_cast<const float2*>(s_ptr[warp][1]) + pos);
+      cp_async8(col + 64, static_cast<const float2*>(s_ptr[warp][2]) + pos);
+    }
+  };
+
+  int it = take_item(ctr);
+  while (it < n_items) {
+    const int it_next = take_item(ctr);
+    int mi = 0;  // the member: the last whose first item is at most it
+    {
+      int hi = n_mem - 1;
+      while (mi < hi) {
+        const int mid = (mi + hi + 1) >> 1;
+        if (s_item0[mid] <= it) mi = mid;
+        else hi = mid - 1;
+      }
+    }
+    const FusedMember& F = mem[mi];
+    if (lane == 0) {
+      s_ptr[warp][0] = F.meta;
+      s_ptr[warp][1] = F.u;
+      s_ptr[warp][2] = F.y;
+    }
+    __syncwarp();
+    const int4 gt = F.gtiles[it - s_item0[mi]];  // {tile, first step, steps, split}
+    const int2* steps = F.steps;
+    const int K = F.K, nT = F.nT, log2S = F.log2S;
+    const int S = 1 << log2S;
+    const float two_over_S = 2.f / (float)S;
+    const float cc = (float)*F.c;
+    const float sigma2 = F.sigma2;
+    float2* u = F.u;
+    const int s0 = gt.y, ns = gt.z;
+    int2 dcur = lane < ns ? steps[s0 + lane] : make_int2(0, 0);
+    int2 dnxt = 32 + lane < ns ? steps[s0 + 32 + lane] : make_int2(0, 0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      const int2 d = shfl_int2(dcur, q);
+      if (q < ns) issue(q, d);
+      cp_async_commit();
+    }
+    load_window_f32<J>(win, F.spec, gt.x, nT, K, lane, nullptr);
+    __syncwarp();
+    KahanF sum;
+    float2 pt[J][J];
+    float2 blk[J][J];
+#pragma unroll
+    for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+      for (int t = 0; t < J; ++t) pt[tp][t] = make_float2(0.f, 0.f);
+    int a0 = 0;
+    bool has = false;
+    for (int i = 0; i < ns; ++i) {
+      if (i > 0 && (i & 31) == 0) {
+        dcur = dnxt;
+        dnxt = i + 32 + lane < ns ? steps[s0 + i + 32 + lane] : make_int2(0, 0);
+      }
+      const int2 d = shfl_int2(dcur, i & 31);
+      const bool start = d.x < 0;
+      if (start && i > 0) {  // the previous group's patches into the accumulator
+#pragma unroll
+        for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+          for (int t = 0; t < J; ++t) {
+            if (has) {
+              float2* q = acc + a0 + tp * kAccPitch2 + t;
+              *q = add2(*q, pt[tp][t]);
+            }
+            pt[tp][t] = make_float2(0.f, 0.f);
+            __syncwarp();
+          }
+      }
+      cp_async_wait<D - 1>();
+      const int q = i & (D - 1);
+      const bool act = ((((unsigned)d.y) >> lane) & 1u) != 0u;
+      const uint2* col = stg + (q * NA) * 32 + lane;
+      if (act) {
+        const int pos = (d.x & 0x7fffffff) + __popc((unsigned)d.y & lanes_below);
+        const uint2 m = col[0];
+        if (start) {
+          const int cy = (int)(m.x >> 16) >> log2S, cx = (int)(m.x & 0xffff) >> log2S;
+          has = true;
+          a0 = cy * kWinPitch + cx;
+#pragma unroll
+          for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+            for (int t = 0; t < J; ++t) blk[tp][t] = win[a0 + tp * kWinPitch + t];
+        }
+        float2 w[J];
+        taps_xy<J>(poly, m.x, S, two_over_S, w);
+        const float2 wt = f2(__uint_as_float(m.y));
+        float2 dg = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int tp = 0; tp < J; ++tp) {
+          float2 row = mul2(f2(w[0].x), blk[tp][0]);
+#pragma unroll
+          for (int t = 1; t < J; ++t) row = fma2(f2(w[t].x), blk[tp][t], row);
+          dg = fma2(f2(w[tp].y), row, dg);
+        }
+        // u <- c u + sigma2 (w phi - y), as EpiPD1::update
+        const float2 uo = *reinterpret_cast<const float2*>(col + 32);
+        const float2 yo = *reinterpret_cast<const float2*>(col + 64);
+        const float2 phi = mul2(wt, dg);
+        const float2 un = make_float2(fmaf(cc, uo.x, sigma2 * (phi.x - yo.x)), fmaf(cc, uo.y, sigma2 * (phi.y - yo.y)));
+        u[pos] = un;
+        sum.add(fmaf(un.x, un.x, un.y * un.y));
+        const float2 wv = mul2(wt, un);
+#pragma unroll
+        for (int tp = 0; tp < J; ++tp) {
+          const float2 b = mul2(f2(w[tp].y), wv);
+#pragma unroll
+          for (int t = 0; t < J; ++t) pt[tp][t] = fma2(f2(w[t].x), b, pt[tp][t]);
+        }
+      } else if (start) {
+        has = false;
+      }
+      const int i2 = i + D;
+      const int2 d2 = shfl_int2(((i2 >> 5) == (i >> 5)) ? dcur : dnxt, i2 & 31);
+      if (i2 < ns) issue(q, d2);
+      cp_async_commit();
+    }
+#pragma unroll
+    for (int tp = 0; tp < J; ++tp)
+#pragma unroll
+      for (int t = 0; t < J; ++t) {
+        if (has && ns > 0) {
+          float2* q = acc + a0 + tp * kAccPitch2 + t;
+          *q = add2(*q, pt[tp][t]);
+        }
+        __syncwarp();
+      }
+    // the member's sum of |u|^2 over this item
+    const double v = warp_sum(sum.value());
+    if (lane == 0) atomicAdd(sums + mi, v);
+    const int ty = gt.x / nT, tx = gt.x - ty * nT;
+    const int oy = ty * kTile - (J / 2 - 1), ox = tx * kTile - (J / 2 - 1);
+    float2* grid = F.grid;
+    for (int e = lane; e < P * P; e += 32) {
+      const int r = e / P, c2 = e - r * P;
+      float2* qa = acc + r * kAccPitch2 + c2;
+      const float2 a = *qa;
+      *qa = make_float2(0.f, 0.f);
+      float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + c2, K);
+      if (gt.w == 0 && r >= lo_x && r < hi_x && c2 >= lo_x && c2 < hi_x) *dst = a;
+      else if (a.x != 0.f || a.y != 0.f) atomicAdd(dst, a);
+    }
+    __syncwarp();
+    it = it_next;
+  }
+  cp_async_wait<0>();
+  // the last block to finish turns every member's sum into its ball scalar and resets the
+  // counters and sums for the next launch (stream order makes that visible to it)
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ctr + 1, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int m = threadIdx.x; m < n_mem; m += blockDim.x) {
+    const double s = __ldcg(sums + m);
+    const FusedMember& F = mem[m];
+    const double dist = sqrt(s) / F.sigma2d;
+    const double rho = dist > F.eps ? F.eps / dist : 1.0;
+    *F.c = 1.0 - rho;
+    *F.dist = dist;
+    sums[m] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    atomicExch(ctr, 0u);
+    atomicExch(ctr + 1, 0u);
+  }
+}
+
+// Shared memory of k_steps_multi (window, accumulator and a three-stream ring per warp).
+constexpr size_t steps_multi_smem() {
+  constexpr int P = kTile + 4 - 1;
+  return (size_t)(kThreads / 32) * (P * kWinPitch + P * kAccPitch2) * 8 + (size_t)(kThreads / 32) * kStageDepth * 3 * 32 * 8;
+}
+
+}  // namespace gbri

@@ -97,9 +97,11 @@ class GpuEngine:
         self.power_iters, self.power_tol = int(power_iters), float(power_tol)
         self._streams = threading.local()
         # plan creation and teardown free and synchronise device memory; a graph capture on
-        # another thread must not overlap them, so the three take turns (the power method and
+        # another thread (a job's iteration, or the batch's shared pass) must not overlap
+        # them, so they take turns (the power method and
         # the solver state run concurrently on the workers' own streams)
         self._sync_lock = threading.Lock()
+        self._rebuild = False  # the batch's membership changed since its last step
         self.worker = concurrent.futures.ThreadPoolExecutor(max_workers=max(1, int(workers)))
 
     def _stream(self):
@@ -150,9 +152,17 @@ class GpuEngine:
         plan, wav, s = self.pending.pop(job.job_id).result()
         self.state[job.job_id] = (plan, wav, s)
         self.batch.add(s)
+        self._rebuild = True
 
     def step(self, n_iter):
-        self.batch.step(n_iter)
+        # after a change of membership the batch rebuilds its graph on this step, capturing the
+        # shared pass's members: that capture takes its turn with plan creation and teardown
+        if self._rebuild:
+            with self._sync_lock:
+                self.batch.step(n_iter)
+            self._rebuild = False
+        else:
+            self.batch.step(n_iter)
 
     def status(self, job):
         return self.state[job.job_id][2].status()
@@ -166,6 +176,7 @@ class GpuEngine:
         plan, wav, s = self.state.pop(job.job_id)
         x = s.x().cpu().numpy()
         self.batch.remove(s)
+        self._rebuild = True
         self.worker.submit(self._teardown, (s, wav, plan))
         return x
 
@@ -183,6 +194,7 @@ class GpuEngine:
         plan, wav, s = st
         try:
             self.batch.remove(s)
+            self._rebuild = True
         except Exception:
             pass
         self.worker.submit(self._teardown, (s, wav, plan))
