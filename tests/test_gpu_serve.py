@@ -32,13 +32,17 @@ def make_job(serve, n, M, J, seed, arrival, max_iter=60, rel_tol=2e-3):
                      arrival=arrival)
 
 
-def test_served_jobs_match_alone(g):
+@pytest.mark.parametrize("shared_pass", [False, True])
+def test_served_jobs_match_alone(g, shared_pass):
+    """Every served job equals the same job run alone; with the batch's shared fused pass on,
+    the primal-dual J = 4 jobs resident together share its launch (rebuilt as jobs come and
+    go, under the engine's set-up lock)."""
     from paper_1903_04502_gb300 import serve
     specs = [(64, 6000, 4), (32, 2000, 6), (96, 12000, 4), (64, 4000, 6), (32, 3000, 4), (128, 20000, 4)]
     jobs = [make_job(serve, n, M, J, seed=i + 1, arrival=0.0 if i < 3 else 0.005 * i, max_iter=300, rel_tol=1e-4)
             for i, (n, M, J) in enumerate(specs)]
     budget = 3 * max(serve.device_footprint(n, M, J, 4) for n, M, J in specs)
-    srv = serve.Server(serve.GpuEngine(), hbm_budget=budget, check_every=5)
+    srv = serve.Server(serve.GpuEngine(shared_pass=shared_pass), hbm_budget=budget, check_every=5)
     done = srv.run(jobs)
     assert len(done) == len(jobs) and not srv.failed
     assert srv.max_resident >= 2                      # jobs overlapped on the device
