@@ -655,6 +655,8 @@ struct FusedMember {
   float sigma2;
   int K, nT, log2S;
   int item0;           // first item of this member in the launch's numbering
+  long long M;         // visibilities (bounds checks)
+  unsigned int* dbg;   // GBRI_DEBUG builds: the plan's error word (else null)
 };
 constexpr int kMaxFusedMembers = 256;  // members of one shared pass
 // Runs the fused degridding + gridding pass of n_mem members in one launch (device table

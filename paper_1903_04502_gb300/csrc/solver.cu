@@ -832,6 +832,8 @@ void solver_fused_member(const gbri_solver* s, FusedMember* m) {
   m->nT = P->nT;
   m->log2S = P->log2S;
   m->item0 = 0;
+  m->M = P->M;
+  m->dbg = P->dbg;
 }
 
 }  // namespace gbri

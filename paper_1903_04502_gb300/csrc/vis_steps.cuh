@@ -355,9 +355,12 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int lo_x = J - 1, hi_x = kTile;
   const unsigned lanes_below = (1u << lane) - 1u;
 
+  unsigned int* dbg = nullptr;  // the current member's error word (GBRI_DEBUG builds)
+  long long M = 0;
   auto issue = [&](int q, int2 d) {
     if ((((unsigned)d.y) >> lane) & 1u) {
       const int pos = (d.x & 0x7fffffff) + __popc((unsigned)d.y & lanes_below);
+      if (!GBRI_DCHECK(dbg, pos < M, kDbgVis, pos)) return;
       uint2* col = stg + (q * NA) * 32 + lane;
       cp_async8(col, static_cast<const uint2*>(s_ptr[warp][0]) + pos);
       cp_async8(col + 32, static_cast<const float2*>(s_ptr[warp][1]) + pos);
@@ -384,6 +387,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       s_ptr[warp][2] = F.y;
     }
     __syncwarp();
+    dbg = F.dbg;
+    M = F.M;
     const int4 gt = F.gtiles[it - s_item0[mi]];  // {tile, first step, steps, split}
     const int2* steps = F.steps;
     const int K = F.K, nT = F.nT, log2S = F.log2S;
@@ -401,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (q < ns) issue(q, d);
       cp_async_commit();
     }
-    load_window_f32<J>(win, F.spec, gt.x, nT, K, lane, nullptr);
+    load_window_f32<J>(win, F.spec, gt.x, nT, K, lane, dbg);
     __syncwarp();
     KahanF sum;
     float2 pt[J][J];
@@ -441,8 +446,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint2 m = col[0];
         if (start) {
           const int cy = (int)(m.x >> 16) >> log2S, cx = (int)(m.x & 0xffff) >> log2S;
-          has = true;
-          a0 = cy * kWinPitch + cx;
+          has = GBRI_DCHECK(dbg, cy < kTile && cx < kTile, kDbgWindow, pos);
+          a0 = has ? cy * kWinPitch + cx : 0;
 #pragma unroll
           for (int tp = 0; tp < J; ++tp)
 #pragma unroll
@@ -502,7 +507,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       float2* qa = acc + r * kAccPitch2 + c2;
       const float2 a = *qa;
       *qa = make_float2(0.f, 0.f);
-      float2* dst = grid + (size_t)wrapK(oy + r, K) * K + wrapK(ox + c2, K);
+      const size_t gq = (size_t)wrapK(oy + r, K) * K + wrapK(ox + c2, K);
+      if (!GBRI_DCHECK(dbg, gq < (size_t)K * K, kDbgGrid, gq)) continue;
+      float2* dst = grid + gq;
       if (gt.w == 0 && r >= lo_x && r < hi_x && c2 >= lo_x && c2 < hi_x) *dst = a;
       else if (a.x != 0.f || a.y != 0.f) atomicAdd(dst, a);
     }

@@ -1,7 +1,7 @@
 """The bounds-checked build (libgbri_debug.so, -DGBRI_DEBUG): on the parity cases of every
 visibility-kernel variant (FP32 polynomial and table taps, first-order table, FP64,
 deterministic gridding, J = 4 and 6, Nyquist points and a pile-up in one cell, the fused
-primal-dual pass, FISTA's residual pass) no window, accumulator, grid, half-spectrum, slot or
+primal-dual pass, FISTA's residual pass, a batch's shared pass over two problems) no window, accumulator, grid, half-spectrum, slot or
 visibility index leaves its buffer (the plan's error word stays zero), and the results still
 match the oracle.  Runs in a child process, since one process loads one library build."""
 
@@ -69,6 +69,23 @@ for (n, M, J, kw, env, prec) in [
         check(plan, ("solver", algo, n, M, J, kw, env, prec))
         s.close()
     n_cases += 1
+# the batch's shared fused pass (k_steps_multi) over two primal-dual members
+b, keep = g.Batch(), []
+for k, (n, M) in enumerate([(64, 6_000), (96, 9_000)]):
+    uvw = synth.uv_coverage(M, seed=50 + k, outlier_frac=0.2, weights="uniform")
+    plan = g.Plan(torch.from_numpy(uvw).cuda(), n, J=4)
+    wav = g.Wavelet(n, 2, (0, 1, 2))
+    yin = synth.complex_normal(M, seed=60 + k).astype(np.complex64)
+    s = g.Solver(plan, wav, torch.from_numpy(yin).cuda(), eps=1.0, op_norm_sq=float(M), gamma=1e-3)
+    b.add(s)
+    keep.append((plan, wav, s))
+b.step(5)
+torch.cuda.synchronize()
+assert b.shared_members() == 2
+for plan, _, _ in keep:
+    check(plan, "shared pass")
+b.close()
+n_cases += 1
 print("DEBUG_BUILD_OK", n_cases)
 '''
 
@@ -83,7 +100,7 @@ def test_bounds_checked_build_reports_no_violation():
     env = dict(os.environ, GBRI_DEBUG_LIB="1")
     r = subprocess.run([sys.executable, "-c", CHILD % {"root": ROOT}], env=env, capture_output=True, text=True,
                        timeout=600)
-    assert r.returncode == 0 and "DEBUG_BUILD_OK 7" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
+    assert r.returncode == 0 and "DEBUG_BUILD_OK 8" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
 
 
 def test_default_build_has_no_checks():
