@@ -33,6 +33,7 @@ def rel(a, b):
     (96, 2, (3, 0, 1)),          # side not a multiple of 32, Dirac in the middle of the stack
     (40, 3, (0, 4)),
     (64, 2, (0,)),               # Dirac only
+    (64, 2, tuple(range(11))),   # ten wavelet bases, db1 to db10 (20 taps, the longest filter)
 ])
 def test_psi_adjoint_and_psi_match_oracle(g, n, levels, orders):
     x = synth.normal(n * n, seed=n).reshape(n, n).astype(np.float32)
