@@ -106,23 +106,23 @@ def per_kernel_roofline(kern, cfg, K, M, peak):
     over the kernel's device time per iteration (launch-averaged CUDA events on the launching
     stream, times its launches per iteration).
       pad: x read, the n x n block of the padded image written (8 B per pixel);
-      fft_fwd: real K x K in, half spectrum K (K/2 + 1) complex out; fft_inv: K x K complex in
-      place (read and written);
+      fft_fwd: real K x K in, half spectrum K (K/2 + 1) complex out; fft_inv: the K x K complex
+      grid read, its real inverse transform (K x K real) written;
       degrid_grid: 32 B per visibility (metadata, u, y read, u written), half spectrum read and
       grid written once;
       psi_adjoint: x read once, the dual z1 of every basis read and written (8 B per
       coefficient), the LL carries of levels 1 .. L-1 written and read back;
       psi: z1 of every basis read, x written;
-      update: the grid value (complex) at every pixel, psi z1 and x read, x and xhat written."""
+      update: the real inverse transform at every pixel, psi z1 and x read, x and xhat written."""
     n = cfg["n_side"]
     N = n * n
     nw = len(cfg["db_orders"])
     nb = nw - (1 if 0 in cfg["db_orders"] else 0)
     L = cfg["levels"]
     carry = sum(4.0 ** -l for l in range(1, L))
-    alg = {"pad": 8 * N, "fft_fwd": 4 * K * K + 8 * K * (K // 2 + 1), "fft_inv": 16 * K * K,
+    alg = {"pad": 8 * N, "fft_fwd": 4 * K * K + 8 * K * (K // 2 + 1), "fft_inv": 12 * K * K,
            "degrid_grid": 32 * M + 8 * K * (K // 2 + 1) + 8 * K * K,
-           "psi_adjoint": 4 * N + 8 * nw * N + 8 * N * nb * carry, "psi": 4 * nw * N + 4 * N, "update": 24 * N}
+           "psi_adjoint": 4 * N + 8 * nw * N + 8 * N * nb * carry, "psi": 4 * nw * N + 4 * N, "update": 20 * N}
     launches = {"pad": 1, "fft_fwd": 1, "fft_inv": 1, "degrid_grid": 1, "update": 1,
                 "psi_adjoint": (1 if 0 in cfg["db_orders"] else 0) + (L if nb else 0),
                 "psi": (L + 1) if nb else 1}

@@ -39,6 +39,26 @@ __global__ void k_pad(const R* __restrict__ x, const R* __restrict__ corr, R* __
 }
 
 // S^T Z^T and the real part: x[q][p] = corr[p] corr[q] Re(grid[(q - n/2) mod K][(p - n/2) mod K])
+// The Hermitian part of the grid on the half plane kx = 0 .. K/2 (the layout of a
+// real-to-complex transform): spec[ky][kx] = (grid[ky][kx] + conj(grid[-ky][-kx])) / 2,
+// indices mod K.  Its complex-to-real inverse is the real part of the grid's inverse
+// transform: the transform of conj(G(-k)) is the conjugate of that of G(k).  One thread per
+// half-plane element, rows after rows.
+template <class R>
+__global__ void k_herm_fold(const cplx<R>* __restrict__ grid, cplx<R>* __restrict__ spec, int K) {
+  const int H = K / 2 + 1;
+  const int64_t total = (int64_t)K * H;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int ky = (int)(e / H), kx = (int)(e - (int64_t)ky * H);
+    const int my = ky == 0 ? 0 : K - ky, mx = kx == 0 ? 0 : K - kx;
+    const cplx<R> a = grid[(size_t)ky * K + kx], b = grid[(size_t)my * K + mx];
+    cplx<R> h;
+    h.x = (R)0.5 * (a.x + b.x);
+    h.y = (R)0.5 * (a.y - b.y);
+    spec[e] = h;
+  }
+}
+
 template <class R>
 __global__ void k_crop(const cplx<R>* __restrict__ grid, const R* __restrict__ corr, R* __restrict__ x, int n,
                        int K) {
@@ -152,6 +172,25 @@ int32_t fft_inverse(gbri_plan* p, cudaStream_t s) {
           : cufftExecC2C(p->fft, p->as<cufftComplex>(p->grid), p->as<cufftComplex>(p->grid), CUFFT_INVERSE);
   const int32_t st = launch_end(GBRI_K_FFT_INV, s);
   if (r != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cuFFT inverse");
+  return st;
+}
+
+int32_t fft_inverse_real(gbri_plan* p, cudaStream_t s) {
+  if (cufftSetStream(p->fft_c2r, s) != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cufftSetStream");
+  const int64_t total = (int64_t)p->K * (p->K / 2 + 1);
+  const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), (int64_t)num_sms() * 16);
+  launch_begin(GBRI_K_FFT_INV, s);
+  cufftResult r;
+  if (p->prec == GBRI_F64) {
+    k_herm_fold<double><<<blocks, 256, 0, s>>>(p->as<const cplx<double>>(p->grid), p->as<cplx<double>>(p->spec),
+                                                p->K);
+    r = cufftExecZ2D(p->fft_c2r, p->as<cufftDoubleComplex>(p->spec), p->as<cufftDoubleReal>(p->grid));
+  } else {
+    k_herm_fold<float><<<blocks, 256, 0, s>>>(p->as<const cplx<float>>(p->grid), p->as<cplx<float>>(p->spec), p->K);
+    r = cufftExecC2R(p->fft_c2r, p->as<cufftComplex>(p->spec), p->as<cufftReal>(p->grid));
+  }
+  const int32_t st = launch_end(GBRI_K_FFT_INV, s);
+  if (r != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cuFFT complex-to-real inverse");
   return st;
 }
 

@@ -131,7 +131,8 @@ struct gbri_plan {
   int n_partials = 0;
   cufftHandle fft = 0;      // C2C / Z2Z, inverse (in place on grid)
   cufftHandle fft_r2c = 0;  // R2C / D2Z, forward (padded -> spec)
-  bool fft_ok = false, fft_r2c_ok = false;
+  cufftHandle fft_c2r = 0;  // C2R / Z2D, inverse of a Hermitian half spectrum (spec -> grid as R [K][K])
+  bool fft_ok = false, fft_r2c_ok = false, fft_c2r_ok = false;
   int64_t device_bytes = 0;
   int64_t layout_bytes = 0;
   int degrid_blocks = 0, grid_blocks = 0;
@@ -675,6 +676,9 @@ int32_t launch_pad(gbri_plan* p, const R* x, const double* d_norm, cudaStream_t 
 // F: padded -> grid (forward, unnormalised); F^H: grid in place (inverse, unnormalised).
 int32_t fft_forward(gbri_plan* p, cudaStream_t s);
 int32_t fft_inverse(gbri_plan* p, cudaStream_t s);
+// Re(F^H grid) alone, as R [K][K] at the start of p->grid (unnormalised): the Hermitian part
+// of the grid folded into p->spec, then the complex-to-real inverse (spec is overwritten).
+int32_t fft_inverse_real(gbri_plan* p, cudaStream_t s);
 // S^T Z^T Re(grid) into x.
 template <class R>
 int32_t launch_crop(gbri_plan* p, R* x, cudaStream_t s);

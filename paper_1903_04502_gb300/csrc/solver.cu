@@ -73,8 +73,9 @@ __global__ void k_ball_scalar_local(const double* __restrict__ partials, int n, 
   }
 }
 
-// PD primal update fused with S^T Z^T Re(.) of the gridded dual (scaled by *cp, the
-// l2-ball scalar c; 1 with local balls, whose scalars the gridding source applied) and the
+// PD primal update fused with S^T Z^T of img = Re(F^H grid) of the gridded dual (real
+// [K][K], from the complex-to-real inverse; scaled by *cp, the l2-ball scalar c; 1 with local
+// balls, whose scalars the gridding source applied) and the
 // relative-change reduction: each block writes its FP64 sums of (x+ - x)^2 and x+^2; the
 // last block to finish (device-wide counter, reset by that block) reduces them in block
 // order into sc[SC_REL] = ||x+ - x|| / ||x+|| and sc[SC_XN] = ||x+||.
@@ -82,7 +83,7 @@ __global__ void k_ball_scalar_local(const double* __restrict__ partials, int n, 
 // (a group never straddles the periodic wrap at column n/2, and every vector access is
 // 16-byte aligned), else V = 1.
 template <class R, int V>
-__global__ void k_pd_update(const cplx<R>* __restrict__ grid, const R* __restrict__ corr, const R* __restrict__ psiz,
+__global__ void k_pd_update(const R* __restrict__ img, const R* __restrict__ corr, const R* __restrict__ psiz,
                             R* __restrict__ x, R* __restrict__ xhat, int n, int K, R tau, R theta,
                             const double* __restrict__ cp, double* __restrict__ sc, double* __restrict__ partials,
                             unsigned int* __restrict__ done) {
@@ -108,9 +109,8 @@ __global__ void k_pd_update(const cplx<R>* __restrict__ grid, const R* __restric
       int r = q - n / 2; if (r < 0) r += K;
       int cc = p - n / 2; if (cc < 0) cc += K;
       if constexpr (V == 4) {
-        const float4 g01 = *reinterpret_cast<const float4*>(grid + (size_t)r * K + cc);
-        const float4 g23 = *reinterpret_cast<const float4*>(grid + (size_t)r * K + cc + 2);
-        gr[u][0] = g01.x; gr[u][1] = g01.z; gr[u][2] = g23.x; gr[u][3] = g23.z;
+        const float4 g4 = *reinterpret_cast<const float4*>(img + (size_t)r * K + cc);
+        gr[u][0] = g4.x; gr[u][1] = g4.y; gr[u][2] = g4.z; gr[u][3] = g4.w;
         const float4 c4 = *reinterpret_cast<const float4*>(corr + p);
         cr[u][0] = c4.x; cr[u][1] = c4.y; cr[u][2] = c4.z; cr[u][3] = c4.w;
         const float4 p4 = *reinterpret_cast<const float4*>(psiz + i);
@@ -118,7 +118,7 @@ __global__ void k_pd_update(const cplx<R>* __restrict__ grid, const R* __restric
         const float4 x4 = *reinterpret_cast<const float4*>(x + i);
         xo[u][0] = x4.x; xo[u][1] = x4.y; xo[u][2] = x4.z; xo[u][3] = x4.w;
       } else {
-        gr[u][0] = grid[(size_t)r * K + cc].x;
+        gr[u][0] = img[(size_t)r * K + cc];
         cr[u][0] = corr[p];
         ps[u][0] = psiz[i];
         xo[u][0] = x[i];
@@ -448,7 +448,8 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st, int phase = 0) {
     GBRI_TRY(launch_grid(P, SrcScaledL<R>{cvec<R>(S->u), S->bsc, S->bstart, S->nb}, st, fork));
   }
 after_pass:
-  GBRI_TRY(fft_inverse(P, st));
+  // the update reads only Re(F^H grid): the complex-to-real inverse of the grid's Hermitian part
+  GBRI_TRY(fft_inverse_real(P, st));
   if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_join, 0));
   const bool v4 = sizeof(R) == 4 && n % 8 == 0;
   // two blocks per SM looping over the image: fewer block reductions and counter atomics
@@ -458,10 +459,10 @@ after_pass:
   launch_begin(GBRI_K_UPDATE, st);
   if (v4)
     k_pd_update<R, (sizeof(R) == 4 ? 4 : 1)><<<ib, 256, 0, st>>>(
-        P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz), vec<R>(S->x), vec<R>(S->xhat), n,
+        P->as<const R>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz), vec<R>(S->x), vec<R>(S->xhat), n,
         P->K, (R)p.tau, (R)p.theta, cp, S->sc, S->partials + S->n_partials, S->done + 1);
   else
-    k_pd_update<R, 1><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz),
+    k_pd_update<R, 1><<<ib, 256, 0, st>>>(P->as<const R>(P->grid), P->as<const R>(P->corr), vec<R>(S->psiz),
                                           vec<R>(S->x), vec<R>(S->xhat), n, P->K, (R)p.tau, (R)p.theta, cp, S->sc,
                                           S->partials + S->n_partials, S->done + 1);
   return launch_end(GBRI_K_UPDATE, st);
