@@ -59,15 +59,16 @@ __global__ void k_herm_fold(const cplx<R>* __restrict__ grid, cplx<R>* __restric
   }
 }
 
+// S^T Z^T of img = Re(F^H grid) (real [K][K], from the complex-to-real inverse) with the
+// correction: x[q][p] = corr[p] corr[q] img[(q - n/2) mod K][(p - n/2) mod K].
 template <class R>
-__global__ void k_crop(const cplx<R>* __restrict__ grid, const R* __restrict__ corr, R* __restrict__ x, int n,
-                       int K) {
+__global__ void k_crop(const R* __restrict__ img, const R* __restrict__ corr, R* __restrict__ x, int n, int K) {
   const int total = n * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int q = i / n, p = i - q * n;
     int r = q - n / 2; if (r < 0) r += K;
     int c = p - n / 2; if (c < 0) c += K;
-    x[i] = corr[p] * corr[q] * grid[(size_t)r * K + c].x;
+    x[i] = corr[p] * corr[q] * img[(size_t)r * K + c];
   }
 }
 
@@ -139,7 +140,7 @@ template <class R>
 int32_t launch_crop(gbri_plan* p, R* x, cudaStream_t s) {
   launch_begin(GBRI_K_CROP, s);
   k_crop<R><<<grid_blocks_for((int64_t)p->n_side * p->n_side), 256, 0, s>>>(
-      p->as<const cplx<R>>(p->grid), p->as<const R>(p->corr), x, p->n_side, p->K);
+      p->as<const R>(p->grid), p->as<const R>(p->corr), x, p->n_side, p->K);
   return launch_end(GBRI_K_CROP, s);
 }
 
@@ -159,19 +160,6 @@ int32_t fft_forward(gbri_plan* p, cudaStream_t s) {
           : cufftExecR2C(p->fft_r2c, p->as<cufftReal>(p->padded), p->as<cufftComplex>(p->spec));
   const int32_t st = launch_end(GBRI_K_FFT_FWD, s);
   if (r != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cuFFT forward");
-  return st;
-}
-
-int32_t fft_inverse(gbri_plan* p, cudaStream_t s) {
-  if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cufftSetStream");
-  launch_begin(GBRI_K_FFT_INV, s, false);
-  const cufftResult r =
-      p->prec == GBRI_F64
-          ? cufftExecZ2Z(p->fft, p->as<cufftDoubleComplex>(p->grid), p->as<cufftDoubleComplex>(p->grid),
-                         CUFFT_INVERSE)
-          : cufftExecC2C(p->fft, p->as<cufftComplex>(p->grid), p->as<cufftComplex>(p->grid), CUFFT_INVERSE);
-  const int32_t st = launch_end(GBRI_K_FFT_INV, s);
-  if (r != CUFFT_SUCCESS) return set_error(GBRI_ECUFFT, "cuFFT inverse");
   return st;
 }
 
@@ -203,7 +191,7 @@ int32_t normal_op(gbri_plan* p, const R* b, const double* d_norm, R* out, cudaSt
   GBRI_TRY(fft_forward(p, s));
   GBRI_TRY(launch_degrid(p, EpiStorePlan<R>{p->as<cplx<R>>(p->vis_tmp)}, s));
   GBRI_TRY(launch_grid(p, SrcPlan<R>{p->as<const cplx<R>>(p->vis_tmp)}, s));
-  GBRI_TRY(fft_inverse(p, s));
+  GBRI_TRY(fft_inverse_real(p, s));
   return launch_crop<R>(p, out, s);
 }
 
@@ -249,7 +237,7 @@ int32_t phi_adjoint(gbri_plan* p, const void* d_y, void* d_x, uint32_t flags, cu
     GBRI_TRY(launch_grid(p, SrcPlan<R>{y}, s));
   else
     GBRI_TRY(launch_grid(p, SrcRaw<R>{y, p->perm}, s));
-  GBRI_TRY(fft_inverse(p, s));
+  GBRI_TRY(fft_inverse_real(p, s));
   return launch_crop<R>(p, static_cast<R*>(d_x), s);
 }
 

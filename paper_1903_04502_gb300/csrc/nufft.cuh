@@ -30,7 +30,8 @@
 //   corr   [n] R       1 / ghat(p'/K) (the S factor along one axis).
 //   padded [K][K] R    real FFT input; zero outside the n x n image block (kept zero).
 //   spec   [K][K/2+1] C  its real-to-complex FFT (half spectrum), read by degridding.
-//   grid   [K][K] C    gridding accumulator, inverse FFT in place.
+//   grid   [K][K] C    gridding accumulator; after the inverse its first half holds
+//                       Re(F^H grid) as R [K][K].
 // R is the plan's real type (float for GBRI_F32, double for GBRI_F64) and C the
 // interleaved complex of R; the visibility order and metadata do not depend on it.
 #pragma once
@@ -124,15 +125,14 @@ struct gbri_plan {
   void* corr = nullptr;     // R
   void* padded = nullptr;   // R [K][K]: Z S x (zero outside the image)
   void* spec = nullptr;     // C [K][K/2 + 1]: its real-to-complex FFT (half spectrum; Phi)
-  void* grid = nullptr;     // C [K][K]: the gridded visibilities and their inverse FFT (Phi^dagger)
+  void* grid = nullptr;     // C [K][K]: the gridded visibilities; then Re of their inverse FFT, R [K][K]
   void* vis_tmp = nullptr;  // C [M] plan-order scratch
   double* partials = nullptr;  // reduction partials
   double* scalars = nullptr;   // small device scalars
   int n_partials = 0;
-  cufftHandle fft = 0;      // C2C / Z2Z, inverse (in place on grid)
   cufftHandle fft_r2c = 0;  // R2C / D2Z, forward (padded -> spec)
   cufftHandle fft_c2r = 0;  // C2R / Z2D, inverse of a Hermitian half spectrum (spec -> grid as R [K][K])
-  bool fft_ok = false, fft_r2c_ok = false, fft_c2r_ok = false;
+  bool fft_r2c_ok = false, fft_c2r_ok = false;
   int64_t device_bytes = 0;
   int64_t layout_bytes = 0;
   int degrid_blocks = 0, grid_blocks = 0;
@@ -673,13 +673,12 @@ int32_t prepare_visibility_kernels();
 // Z S x into p->padded; optional extra scaling by 1 / *d_norm (device, may be null).
 template <class R>
 int32_t launch_pad(gbri_plan* p, const R* x, const double* d_norm, cudaStream_t s);
-// F: padded -> grid (forward, unnormalised); F^H: grid in place (inverse, unnormalised).
+// F: padded -> spec (forward, unnormalised, real-to-complex).
 int32_t fft_forward(gbri_plan* p, cudaStream_t s);
-int32_t fft_inverse(gbri_plan* p, cudaStream_t s);
 // Re(F^H grid) alone, as R [K][K] at the start of p->grid (unnormalised): the Hermitian part
 // of the grid folded into p->spec, then the complex-to-real inverse (spec is overwritten).
 int32_t fft_inverse_real(gbri_plan* p, cudaStream_t s);
-// S^T Z^T Re(grid) into x.
+// S^T Z^T Re(F^H grid) into x (after fft_inverse_real).
 template <class R>
 int32_t launch_crop(gbri_plan* p, R* x, cudaStream_t s);
 

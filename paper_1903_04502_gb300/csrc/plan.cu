@@ -392,7 +392,6 @@ void destroy_plan(gbri_plan* p) {
   cudaFree(p->slots);
   cudaFree(p->tile_items_off);
   cudaFree(p->tile_items);
-  if (p->fft_ok) cufftDestroy(p->fft);
   if (p->fft_r2c_ok) cufftDestroy(p->fft_r2c);
   if (p->fft_c2r_ok) cufftDestroy(p->fft_c2r);
   delete p;
@@ -845,11 +844,6 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
   GBRI_TRY(dmalloc(&p->dbg, 4, &p->device_bytes));
   GBRI_CHECK_CUDA(cudaMemsetAsync(p->dbg, 0, 4 * sizeof(unsigned int), s));
 #endif
-  if (cufftPlan2d(&p->fft, K, K, p->prec == GBRI_F64 ? CUFFT_Z2Z : CUFFT_C2C) != CUFFT_SUCCESS) {
-    cudaFree(meta_cell); cudaFree(perm_cell);
-    return set_error(GBRI_ECUFFT, "cufftPlan2d failed");
-  }
-  p->fft_ok = true;
   // the padded image is real: the forward transform is real-to-complex (half the work of
   // C2C); degridding reads the other half through G[-k] = conj(G[k])
   if (cufftPlan2d(&p->fft_r2c, K, K, p->prec == GBRI_F64 ? CUFFT_D2Z : CUFFT_R2C) != CUFFT_SUCCESS) {
@@ -857,18 +851,18 @@ int32_t build_plan(gbri_plan* p, const float* d_uvw, cudaStream_t s) {
     return set_error(GBRI_ECUFFT, "cufftPlan2d (real-to-complex) failed");
   }
   p->fft_r2c_ok = true;
-  // the primal-dual update reads only the real part of the adjoint's inverse transform: the
-  // complex-to-real inverse of the grid's Hermitian part gives it with about half the work
+  // every reader of the adjoint's inverse transform (crop, the solvers' updates) takes only
+  // its real part: the complex-to-real inverse of the grid's Hermitian part gives it with
+  // about half the work of the complex inverse
   if (cufftPlan2d(&p->fft_c2r, K, K, p->prec == GBRI_F64 ? CUFFT_Z2D : CUFFT_C2R) != CUFFT_SUCCESS) {
     cudaFree(meta_cell); cudaFree(perm_cell);
     return set_error(GBRI_ECUFFT, "cufftPlan2d (complex-to-real) failed");
   }
   p->fft_c2r_ok = true;
   {
-    size_t ws1 = 0, ws2 = 0, ws3 = 0;
-    if (cufftGetSize(p->fft, &ws1) == CUFFT_SUCCESS && cufftGetSize(p->fft_r2c, &ws2) == CUFFT_SUCCESS &&
-        cufftGetSize(p->fft_c2r, &ws3) == CUFFT_SUCCESS)
-      p->device_bytes += (int64_t)(ws1 + ws2 + ws3);
+    size_t ws1 = 0, ws2 = 0;
+    if (cufftGetSize(p->fft_r2c, &ws1) == CUFFT_SUCCESS && cufftGetSize(p->fft_c2r, &ws2) == CUFFT_SUCCESS)
+      p->device_bytes += (int64_t)(ws1 + ws2);
   }
 
   auto set_blocks = [&](int bpm_dg, int bpm_gr) {

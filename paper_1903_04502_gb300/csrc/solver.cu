@@ -190,16 +190,16 @@ __global__ void k_rel_change(const double* __restrict__ partials, int n, double*
   }
 }
 
-// ADMM: xt = x - rho * S^T Z^T Re(grid); zbar = max(xt, 0)
+// ADMM: xt = x - rho * S^T Z^T img, img = Re(F^H grid) (real [K][K]); zbar = max(xt, 0)
 template <class R>
-__global__ void k_admm_xt(const cplx<R>* __restrict__ grid, const R* __restrict__ corr, const R* __restrict__ x,
+__global__ void k_admm_xt(const R* __restrict__ img, const R* __restrict__ corr, const R* __restrict__ x,
                           R* __restrict__ xt, R* __restrict__ zbar, int n, int K, R rho) {
   const int total = n * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int q = i / n, p = i - q * n;
     int r = q - n / 2; if (r < 0) r += K;
     int cc = p - n / 2; if (cc < 0) cc += K;
-    const R v = x[i] - rho * corr[p] * corr[q] * grid[(size_t)r * K + cc].x;
+    const R v = x[i] - rho * corr[p] * corr[q] * img[(size_t)r * K + cc];
     xt[i] = v;
     zbar[i] = max_r(v, (R)0);
   }
@@ -448,7 +448,6 @@ int32_t pd_iteration(gbri_solver* S, cudaStream_t st, int phase = 0) {
     GBRI_TRY(launch_grid(P, SrcScaledL<R>{cvec<R>(S->u), S->bsc, S->bstart, S->nb}, st, fork));
   }
 after_pass:
-  // the update reads only Re(F^H grid): the complex-to-real inverse of the grid's Hermitian part
   GBRI_TRY(fft_inverse_real(P, st));
   if (fork) GBRI_CHECK_CUDA(cudaStreamWaitEvent(st, S->ev_join, 0));
   const bool v4 = sizeof(R) == 4 && n % 8 == 0;
@@ -493,10 +492,10 @@ int32_t admm_iteration(gbri_solver* S, cudaStream_t st) {
     GBRI_TRY(launch_grid(P, SrcADMM2L<R>{cvec<R>(S->w), cvec<R>(S->u), S->bsc, S->bstart, S->nb, (R)p.varrho},
                          st));
   }
-  GBRI_TRY(fft_inverse(P, st));
+  GBRI_TRY(fft_inverse_real(P, st));
   const int ib = std::min(img_blocks(N), S->n_partials / 2);
   launch_begin(GBRI_K_UPDATE, st);
-  k_admm_xt<R><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->x),
+  k_admm_xt<R><<<ib, 256, 0, st>>>(P->as<const R>(P->grid), P->as<const R>(P->corr), vec<R>(S->x),
                                    vec<R>(S->xt), vec<R>(S->xhat) /* zbar */, n, P->K, (R)p.rho);
   GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
   for (int k = 0; k < p.dualfb_iters; ++k) {
@@ -537,10 +536,10 @@ int32_t fista_iteration(gbri_solver* S, cudaStream_t st) {
     // z = xhat - lambda Re Phi^dagger r (into xt); zbar = P_C(z) (into zb)
     GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->u)}, st));
   }
-  GBRI_TRY(fft_inverse(P, st));
+  GBRI_TRY(fft_inverse_real(P, st));
   const int ib = std::min(img_blocks(N), S->n_partials / 2);
   launch_begin(GBRI_K_UPDATE, st);
-  k_admm_xt<R><<<ib, 256, 0, st>>>(P->as<const cplx<R>>(P->grid), P->as<const R>(P->corr), vec<R>(S->xhat),
+  k_admm_xt<R><<<ib, 256, 0, st>>>(P->as<const R>(P->grid), P->as<const R>(P->corr), vec<R>(S->xhat),
                                    vec<R>(S->xt), vec<R>(S->zb), n, P->K, (R)p.rho);
   GBRI_TRY(launch_end(GBRI_K_UPDATE, st));
   launch_begin(GBRI_K_OTHER, st);
@@ -598,7 +597,7 @@ int32_t default_gamma(gbri_solver* S, cudaStream_t st, double* out) {
   gbri_plan* P = S->plan;
   const int64_t N = (int64_t)P->n_side * P->n_side;
   GBRI_TRY(launch_grid(P, SrcPlan<R>{cvec<R>(S->yp)}, st));
-  GBRI_TRY(fft_inverse(P, st));
+  GBRI_TRY(fft_inverse_real(P, st));
   GBRI_TRY(launch_crop<R>(P, vec<R>(S->psiz), st));
   GBRI_TRY(psi_adjoint_apply<R>(S->wav, vec<R>(S->psiz), vec<R>(S->z1), DualEpi{0, 0.0, 0.0, 0.0, 0.0}, st));
   const int64_t tot = N * S->wav->nw;
